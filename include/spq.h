@@ -1,0 +1,196 @@
+/*
+ * spq.h — shortest-path distance queries on a partitioned undirected graph, on one GPU.
+ *
+ * The data structure is the one of Chapuis & Djidjev, "Shortest-Path Queries in Planar
+ * Graphs on GPU-Accelerated Architectures" (arXiv 1503.07192):
+ *   - Algorithm 1, line 3: for every component C of a given k-partition, the table
+ *     APSP(C) of distances dist_C inside the subgraph induced by C (Sec. 2 defines
+ *     dist_H for a subgraph H);
+ *   - Algorithm 1, lines 4-6: the boundary graph BG on all boundary vertices (Sec. 2:
+ *     vertices with a neighbour in another component), with G's edges between boundary
+ *     vertices plus one edge per pair of boundary vertices of a component, weighted
+ *     dist_C;
+ *   - Algorithm 1, lines 7-9: all-pairs distances in BG (Lemma 1: they equal the
+ *     distances in G), held as one |BG| x |BG| matrix, rows and columns grouped by
+ *     component (Sec. 4, Fig. 1);
+ *   - Algorithm 2 (correct by Lemma 3): dist(v1, v2) = min over b1 in B(C1), b2 in B(C2)
+ *     of dist_C1(v1, b1) + dist_BG(b1, b2) + dist_C2(b2, v2), and, if C1 = C2, also
+ *     dist_C1(v1, v2).
+ * Every step runs in CUDA kernels on the device of the stream passed in.
+ *
+ * Conventions for every call:
+ *   - Pointer arguments may point to host memory or to device memory of the current
+ *     device; the library tells them apart with cudaPointerGetAttributes.  Inputs are
+ *     borrowed for the duration of the call only; outputs are owned by the caller.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is queued on
+ *     it.  spq_build returns after its work has completed.  spq_query with host output
+ *     returns after the results are in host memory; with device output it returns once
+ *     the work is queued (read the result after synchronising the stream, and call
+ *     spq_query_status for range errors).
+ *   - Nothing aborts or prints: every failure is a returned spq_status.
+ */
+#ifndef SPQ_H
+#define SPQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spq_handle spq_handle; /* opaque; owns all device tables of one graph */
+
+typedef enum {
+    SPQ_OK = 0,
+    SPQ_EINVAL = 1,       /* malformed input: see spq_build / spq_query */
+    SPQ_ENOMEM = 2,       /* the tables do not fit in free device memory, or host malloc failed */
+    SPQ_ECUDA = 3,        /* a CUDA runtime call failed (the CUDA error is kept: spq_last_cuda_error) */
+    SPQ_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    SPQ_EUNSUPPORTED = 5, /* a valid request this build does not handle (e.g. dtype) */
+} spq_status;
+
+typedef enum {
+    SPQ_I32 = 0, /* int32 edge weights and distances; results are exact */
+    SPQ_F32 = 1, /* float32 edge weights and distances (IEEE single-precision sums) */
+} spq_dtype;
+
+/* Distance reported for an unreachable pair in SPQ_I32 mode (2^29).  Every finite
+ * distance must be below it; the sum of three table entries then stays below 2^31.
+ * In SPQ_F32 mode an unreachable pair reports +infinity. */
+#define SPQ_INF_I32 0x20000000
+
+/* How the min-plus arithmetic of the Floyd-Warshall steps is carried out for SPQ_I32
+ * graphs.  Both give bit-identical results; see spq_build. */
+typedef enum {
+    SPQ_ARITH_AUTO = 0, /* float32 when exact (see below), else int32 */
+    SPQ_ARITH_I32 = 1,  /* int32 add and min */
+    SPQ_ARITH_F32 = 2,  /* float32 add and min over exact integers, falling back to int32 */
+} spq_arith;
+
+/* Order of the components along the boundary-graph matrix (its rows and columns stay
+ * grouped by component, as in the paper's Fig. 1). */
+typedef enum {
+    SPQ_ORDER_AUTO = 0,      /* nested dissection when it pays, else by component id */
+    SPQ_ORDER_ID = 1,        /* components in id order */
+    SPQ_ORDER_DISSECTION = 2 /* nested-dissection order of the component adjacency graph */
+} spq_order;
+
+typedef struct spq_opts {
+    int32_t struct_size; /* sizeof(spq_opts); lets later versions grow the struct */
+    int32_t arith;       /* spq_arith */
+    int32_t order;       /* spq_order */
+    int32_t skip_inf_tiles; /* 1 (default when opts is NULL): the boundary-graph
+                               Floyd-Warshall skips tile updates whose pivot row or
+                               column panel is entirely infinite (they cannot change
+                               anything); 0: update every tile every round */
+} spq_opts;
+
+/* Fill *opts with the defaults (also what opts == NULL means). */
+void spq_opts_default(spq_opts* opts);
+
+/*
+ * Build the query structure for the undirected graph G and the k-partition `part`.
+ *
+ *   n        number of vertices, >= 1
+ *   row_ptr  int64[n + 1], CSR row offsets; row_ptr[0] = 0, nondecreasing; m = row_ptr[n]
+ *   col      int32[m], neighbour ids in [0, n)
+ *   w        int32[m] (SPQ_I32) or float[m] (SPQ_F32): weight of the CSR slot
+ *   wt       element type of w
+ *   part     int32[n], part[v] in [0, k): the component of v (Sec. 2's k-partition;
+ *            components may be disconnected or have no boundary vertex)
+ *   k        number of components, >= 1 (empty components are allowed)
+ *   opts     NULL for the defaults
+ *   stream   cudaStream_t to queue the work on
+ *   out      receives the handle (NULL on failure)
+ *
+ * G must be symmetric: for every slot u -> v (u != v) there is a slot v -> u, and the
+ * smallest weight over the parallel slots u -> v equals that over v -> u.  Parallel
+ * slots are allowed (the smallest weight is the edge's weight, as a path takes the
+ * lightest) and self-loops are ignored.  Weights must be >= 0 (and finite for SPQ_F32).
+ * For SPQ_I32 every finite distance must be < SPQ_INF_I32.
+ *
+ * Arithmetic: with SPQ_ARITH_AUTO or _F32 the Floyd-Warshall updates of an SPQ_I32
+ * graph run in float32 and the library then checks that every finite table entry is
+ * below 2^24; below that bound each stored value is an exact integer (a float32 sum of
+ * two exact integers whose result is below 2^24 is exact, and a sum at or above 2^24
+ * never rounds below 2^24), so the tables equal the int32 ones.  If the check fails the
+ * build is redone with int32 arithmetic.
+ *
+ * Errors: SPQ_EINVAL for n < 1, k < 1, a bad row_ptr, col or part entry, a negative or
+ * non-finite weight, or an asymmetric graph; SPQ_ENOMEM if the tables (about
+ * 4 * (sum over C of |C|^2 + |BG|^2) bytes, rows padded to 4 entries) exceed free device
+ * memory; SPQ_ECUDA on a CUDA failure.  On error nothing is leaked and *out is NULL.
+ */
+spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
+                     const int32_t* part, int32_t k, const spq_opts* opts, void* stream, spq_handle** out);
+
+/*
+ * Answer q distance queries (Algorithm 2 for each pair).
+ *
+ *   pairs     int32[q][2]: (v1, v2) vertex ids of the original numbering
+ *   q         number of pairs, >= 0 (0 is a no-op)
+ *   dist_out  int32[q] (SPQ_I32 graphs) or float[q] (SPQ_F32) : dist(v1, v2);
+ *             SPQ_INF_I32 / +inf if v2 is unreachable from v1; 0 if v1 == v2
+ *   pairs and dist_out must both be host memory or both device memory.
+ *
+ * A pair with an id outside [0, n) yields -1 (SPQ_I32) or NaN (SPQ_F32) in its slot and
+ * marks the handle: with host buffers the call then returns SPQ_EINVAL; with device
+ * buffers, spq_query_status reports it.
+ */
+spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream);
+
+/* Synchronise `stream`, return SPQ_EINVAL if any spq_query on h since the last call
+ * met an out-of-range pair (and clear the mark), else SPQ_OK (or SPQ_ECUDA). */
+spq_status spq_query_status(spq_handle* h, void* stream);
+
+/* Release every device table of h.  NULL-safe.  Synchronises the device. */
+void spq_free(spq_handle* h);
+
+/* Static English text for a status code. */
+const char* spq_strerror(spq_status s);
+
+/* The CUDA error code (cudaError_t) behind the most recent SPQ_ECUDA of this thread. */
+int spq_last_cuda_error(void);
+
+/* Device bytes owned by h (tables and per-vertex/per-component arrays). */
+size_t spq_footprint_bytes(const spq_handle* h);
+
+/* Build statistics of h, for reporting.  Any pointer may be NULL.
+ *   n_bg          |BG|, the number of boundary vertices
+ *   comp_updates  min-plus updates issued by the component Floyd-Warshall (sum of
+ *                 padded |C|^3)
+ *   bg_updates    min-plus updates issued by the boundary-graph Floyd-Warshall
+ *                 (|BG|^3 minus the skipped tiles' share)
+ *   arith         the spq_arith actually used (SPQ_ARITH_I32 or SPQ_ARITH_F32) */
+void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double* bg_updates, int32_t* arith);
+
+/* Device time (ms, CUDA events on the build stream) of the build's stages, in order:
+ *   [0] validation and boundary detection, [1] table sizing and vertex reordering,
+ *   [2] component tables (init + batched Floyd-Warshall), [3] boundary-graph assembly,
+ *   [4] boundary-graph Floyd-Warshall, [5] exactness check (float32 arithmetic only).
+ * Writes min(count, 6) values; returns how many it wrote (0 if h is NULL).  With the
+ * float32 arithmetic falling back to int32, stages 2-5 hold the int32 run's times. */
+int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count);
+
+/* Copy out the tables (device or host destination, same rules as spq_query), for
+ * inspection and tests.  Layouts:
+ *   comp[n], local[n]     component of each vertex and its index inside the component
+ *                         (boundary vertices first, each class in ascending vertex id)
+ *   csize[k], nb[k]       |C| and |B(C)|
+ *   bg_off[k]             BG index of the first boundary vertex of C (its boundary
+ *                         vertex with local index i has BG index bg_off[c] + i)
+ * spq_get_meta copies these (any pointer may be NULL).  spq_get_apsp copies APSP(C) of
+ * component c as a dense |C| x |C| int32/float matrix in local-index order.
+ * spq_get_bg copies the |BG| x |BG| distance matrix of BG in BG-index order
+ * (|BG|^2 elements: large graphs need a large buffer). */
+spq_status spq_get_meta(const spq_handle* h, int32_t* comp, int32_t* local, int32_t* csize, int32_t* nb,
+                        int32_t* bg_off, void* stream);
+spq_status spq_get_apsp(const spq_handle* h, int32_t c, void* out, void* stream);
+spq_status spq_get_bg(const spq_handle* h, void* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPQ_H */

@@ -1,0 +1,28 @@
+/*
+ * spq_bench.h — measurement helper of the distance-query library (not part of the
+ * query API).  The paper has no counterpart: it only reports wall times.
+ */
+#ifndef SPQ_BENCH_H
+#define SPQ_BENCH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Issue-rate micro-benchmark of the min-plus update c = min(c, a + b) with all operands
+ * in registers, on the current device, over SMs * blocks_per_sm CTAs of 256 threads.
+ *   mode 0: float32 add + two-input min          (one update per add)
+ *   mode 1: float32 add + three-input min         (two updates per min)
+ *   mode 2: packed float32x2 add + three-input min
+ *   mode 3: int32 add + min
+ *   mode 4: int32 fused add-min (__viaddmin_s32)
+ *   mode 5: int32 add, add, min, min               (two updates)
+ * Writes the achieved updates per second and the timed launch's milliseconds (the
+ * second of two identical launches).  Returns 0 or a cudaError_t code. */
+int spq_peak_minplus(int mode, int iters, int blocks_per_sm, double* updates_per_s, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPQ_BENCH_H */

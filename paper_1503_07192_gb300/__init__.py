@@ -1,0 +1,196 @@
+"""Shortest-path distance queries on partitioned planar graphs, on one GB300 GPU.
+
+Thin Python binding of the C ABI in include/spq.h: the functions below have the C
+names and only marshal arguments (numpy arrays or torch tensors, host or device) into
+pointers.  Every step of the build (Algorithm 1 of Chapuis & Djidjev, arXiv 1503.07192)
+and of the queries (Algorithm 2) runs in the library's CUDA kernels; there is no
+Python or CPU fallback, and a missing library raises.
+
+    h = spq_build(n, row_ptr, col, w, part, k)     # -> SpqHandle
+    d = spq_query(h, pairs)                        # int32[q] (or float32[q])
+    spq_free(h)
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    SPQ_ECUDA,
+    SPQ_EINVAL,
+    SPQ_ENOMEM,
+    SPQ_OK,
+    SPQ_ARITH_AUTO,
+    SPQ_ARITH_F32,
+    SPQ_ARITH_I32,
+    SPQ_F32,
+    SPQ_I32,
+    SPQ_INF_I32,
+    SPQ_ORDER_AUTO,
+    SPQ_ORDER_DISSECTION,
+    SPQ_ORDER_ID,
+    SpqError,
+    SpqOpts,
+)
+
+try:  # torch is optional for host-only callers
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+def _is_torch(x) -> bool:
+    return torch is not None and isinstance(x, torch.Tensor)
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive, is_device) for a numpy array or torch tensor of dtype."""
+    if _is_torch(x):
+        tdt = {np.int32: torch.int32, np.int64: torch.int64, np.float32: torch.float32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        return ctypes.c_void_p(x.data_ptr()), x, x.is_cuda
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a, False
+
+
+def _stream(stream, device: bool):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if device and torch is not None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def spq_opts_default() -> SpqOpts:
+    o = SpqOpts()
+    _lib.load().spq_opts_default(ctypes.byref(o))
+    return o
+
+
+class SpqHandle:
+    """Owner of one built query structure (the device tables of one graph)."""
+
+    def __init__(self, ptr: ctypes.c_void_p, n: int, k: int, wt: int):
+        self._h = ptr
+        self.n, self.k, self.wt = n, k, wt
+
+    @property
+    def ptr(self):
+        if not self._h:
+            raise ValueError("handle already freed")
+        return self._h
+
+    def stats(self) -> dict:
+        nbg, cu, bu, ar = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        _lib.load().spq_stats(self.ptr, ctypes.byref(nbg), ctypes.byref(cu), ctypes.byref(bu), ctypes.byref(ar))
+        return {"n_bg": nbg.value, "comp_updates": cu.value, "bg_updates": bu.value, "arith": ar.value,
+                "footprint_bytes": int(_lib.load().spq_footprint_bytes(self.ptr))}
+
+    def profile(self) -> dict:
+        """Device milliseconds of the build stages (CUDA events)."""
+        ms = (ctypes.c_double * 6)()
+        cnt = _lib.load().spq_build_profile(self.ptr, ms, 6)
+        names = ["validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check"]
+        return {names[i]: ms[i] for i in range(cnt)}
+
+    def meta(self) -> dict:
+        comp = np.empty(self.n, np.int32)
+        local = np.empty(self.n, np.int32)
+        csize = np.empty(self.k, np.int32)
+        nb = np.empty(self.k, np.int32)
+        bg_off = np.empty(self.k, np.int32)
+        st = _lib.load().spq_get_meta(self.ptr, *(ctypes.c_void_p(a.ctypes.data) for a in
+                                                  (comp, local, csize, nb, bg_off)), ctypes.c_void_p(0))
+        if st:
+            raise SpqError(st, "spq_get_meta")
+        return {"comp": comp, "local": local, "csize": csize, "nb": nb, "bg_off": bg_off}
+
+    def apsp(self, c: int) -> np.ndarray:
+        sz = int(self.meta()["csize"][c])
+        out = np.empty((sz, sz), np.float32 if self.wt == SPQ_F32 else np.int32)
+        st = _lib.load().spq_get_apsp(self.ptr, int(c), ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(0))
+        if st:
+            raise SpqError(st, "spq_get_apsp")
+        return out
+
+    def bg(self) -> np.ndarray:
+        nbg = self.stats()["n_bg"]
+        out = np.empty((nbg, nbg), np.float32 if self.wt == SPQ_F32 else np.int32)
+        if nbg:
+            st = _lib.load().spq_get_bg(self.ptr, ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(0))
+            if st:
+                raise SpqError(st, "spq_get_bg")
+        return out
+
+    def free(self):
+        if self._h:
+            _lib.load().spq_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def spq_build(n: int, row_ptr, col, w, part, k: int, opts: SpqOpts | None = None, stream=None) -> SpqHandle:
+    """Build the query structure (Algorithm 1) for the symmetric CSR graph and partition."""
+    lib = _lib.load()
+    wt = SPQ_F32 if (getattr(w, "dtype", None) in (np.float32, np.float64) or
+                     (_is_torch(w) and w.is_floating_point())) else SPQ_I32
+    rp_p, rp_k, rp_d = _ptr(row_ptr, np.int64)
+    col_p, col_k, _ = _ptr(col, np.int32)
+    w_p, w_k, _ = _ptr(w, np.float32 if wt == SPQ_F32 else np.int32)
+    pt_p, pt_k, _ = _ptr(part, np.int32)
+    out = ctypes.c_void_p()
+    st = lib.spq_build(int(n), rp_p, col_p, w_p, wt, pt_p, int(k), ctypes.byref(opts) if opts is not None else None,
+                       _stream(stream, rp_d), ctypes.byref(out))
+    del rp_k, col_k, w_k, pt_k
+    if st:
+        raise SpqError(st, "spq_build")
+    return SpqHandle(out, int(n), int(k), wt)
+
+
+def spq_query(h: SpqHandle, pairs, out=None, stream=None):
+    """dist(v1, v2) for each row of pairs (int32[q, 2]); returns int32[q] (float32 for
+    float-weight graphs) in the same memory space as pairs."""
+    lib = _lib.load()
+    p_p, p_k, p_dev = _ptr(pairs, np.int32)
+    q = int(p_k.shape[0]) if p_k.ndim > 1 else int(p_k.shape[0]) // 2
+    odt = np.float32 if h.wt == SPQ_F32 else np.int32
+    if out is None:
+        if p_dev:
+            out = torch.empty(q, dtype=torch.float32 if h.wt == SPQ_F32 else torch.int32, device=p_k.device)
+        else:
+            out = np.empty(q, odt)
+    o_p, o_k, _ = _ptr(out, odt)
+    st = lib.spq_query(h.ptr, p_p, q, o_p, _stream(stream, p_dev))
+    if st:
+        raise SpqError(st, "spq_query")
+    return o_k
+
+
+def spq_query_status(h: SpqHandle, stream=None):
+    st = _lib.load().spq_query_status(h.ptr, _stream(stream, True))
+    if st:
+        raise SpqError(st, "spq_query_status")
+
+
+def spq_free(h: SpqHandle):
+    h.free()
+
+
+def spq_strerror(status: int) -> str:
+    return _lib.load().spq_strerror(status).decode()
+
+
+def build(force: bool = False) -> str:
+    """Compile libspq.so (nvcc, sm_103a) in-tree."""
+    from .build_ext import build as _b
+
+    return _b(force=force)

@@ -1,0 +1,551 @@
+// C-ABI entry points and host orchestration of the build (Algorithm 1) and of queries
+// (Algorithm 2).  The host only sizes and allocates the tables, orders the components
+// and launches kernels; every per-vertex, per-edge and per-cell step runs on the GPU.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "order.h"
+
+using namespace spq;
+
+struct spq_handle {
+    int device = 0;
+    int32_t n = 0, k = 0;
+    spq_dtype wt = SPQ_I32;
+    bool f32store = false;  // tables hold float32 values
+    int32_t arith = SPQ_ARITH_I32;
+    int32_t* comp = nullptr;
+    int32_t* local = nullptr;
+    MatDesc* descs = nullptr;
+    int32_t* nb = nullptr;
+    int32_t* bg_off = nullptr;
+    int32_t* csize = nullptr;
+    void* apsp = nullptr;
+    void* D = nullptr;
+    uint32_t* err = nullptr;
+    int64_t N = 0, nbg = 0;
+    int64_t apsp_elems = 0;
+    size_t bytes = 0;
+    double comp_updates = 0.0, bg_updates = 0.0;
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<int32_t> h_csize, h_nb, h_bgoff;
+    std::vector<MatDesc> h_descs;
+};
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+spq_status cuda_fail(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return SPQ_ECUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered temporaries released together (on scope exit).
+struct Temps {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit Temps(cudaStream_t s) : st(s) {}
+    ~Temps() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), st);
+        if (e == cudaSuccess) ptrs.push_back((void*)*p);
+        return e;
+    }
+};
+
+void free_handle_memory(spq_handle* h) {
+    void* ps[] = {h->comp, h->local, h->descs, h->nb, h->bg_off, h->csize, h->apsp, h->D, h->err};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count, size_t* total) {
+    if (count == 0) count = 1;
+    *total += count * sizeof(T);
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+int bits_for(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+// CUDA events bracketing the build stages (see spq_build_profile).
+struct StageEvents {
+    cudaEvent_t ev[7] = {};
+    bool ok = true;
+    StageEvents() {
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    }
+    ~StageEvents() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    void mark(int i, cudaStream_t st) {
+        if (ok) cudaEventRecord(ev[i], st);
+    }
+    void collect(double* ms) {
+        for (int i = 0; i < 6; ++i) {
+            float t = 0.f;
+            ms[i] = (ok && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ? (double)t : 0.0;
+        }
+        cudaGetLastError();
+    }
+};
+
+struct BuildInputs {
+    int32_t n;
+    int64_t m;
+    const int64_t* rp;
+    const int32_t* col;
+    const void* w;
+    const int32_t* part;
+    bool f32w;
+};
+
+// Tables of Algorithm 1 in element type T: component blocks, their Floyd-Warshall,
+// boundary-graph assembly and its Floyd-Warshall.  Sets *inexact if a float32 table
+// holds a finite entry >= 2^24.
+template <typename T>
+cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact, bool skip_inf, uint32_t* d_flag,
+                         uint32_t* fw_scratch, int32_t max_n, bool* inexact, StageEvents& evs, cudaStream_t st) {
+    *inexact = false;
+    evs.mark(2, st);
+    T* apsp = (T*)h->apsp;
+    T* D = (T*)h->D;
+    cudaError_t e;
+    if ((e = launch_fill_blocks<T>(apsp, h->descs, h->k, st)) != cudaSuccess) return e;
+    if ((e = launch_scatter_intra<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->descs, apsp, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = fw_batched<T>(apsp, h->descs, h->k, max_n, st)) != cudaSuccess) return e;
+    evs.mark(3, st);
+    if (h->N > 0) {
+        if ((e = launch_bg_fill<T>(D, h->N, st)) != cudaSuccess) return e;
+        if ((e = launch_bg_clique<T>(apsp, h->descs, h->nb, h->bg_off, h->k, D, h->N, st)) != cudaSuccess) return e;
+        if ((e = launch_bg_inter<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->bg_off, D, h->N, st)) !=
+            cudaSuccess)
+            return e;
+    }
+    evs.mark(4, st);
+    if (h->N > 0) {
+        if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, &h->bg_updates, st)) != cudaSuccess) return e;
+    }
+    evs.mark(5, st);
+    if (check_exact) {
+        if ((e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        if ((e = launch_check_exact((const float*)h->apsp, h->apsp_elems, d_flag, st)) != cudaSuccess) return e;
+        if (h->N > 0 && (e = launch_check_exact((const float*)h->D, h->N * h->N, d_flag, st)) != cudaSuccess) return e;
+        uint32_t f = 0;
+        if ((e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        *inexact = (f & kErrExact) != 0;
+    }
+    evs.mark(6, st);
+    return cudaSuccess;
+}
+
+spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
+                      const int32_t* part, int32_t k, const spq_opts& opts, cudaStream_t st, spq_handle* h) {
+    Temps tmp(st);
+    StageEvents evs;
+    // ---- inputs on the device ----
+    const bool rp_dev = is_device_ptr(row_ptr);
+    int64_t rp_ends[2] = {0, 0};
+    if (rp_dev) {
+        CK(cudaMemcpyAsync(&rp_ends[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&rp_ends[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        rp_ends[0] = row_ptr[0];
+        rp_ends[1] = row_ptr[n];
+    }
+    const int64_t m = rp_ends[1];
+    if (rp_ends[0] != 0 || m < 0 || m > INT32_MAX) return SPQ_EINVAL;
+    if (m > 0 && (!col || !w)) return SPQ_EINVAL;
+    const size_t wsz = 4;
+    const int64_t* d_rp = row_ptr;
+    const int32_t* d_col = col;
+    const void* d_w = w;
+    const int32_t* d_part = part;
+    if (!rp_dev) {
+        int64_t* p;
+        CK(tmp.alloc(&p, (size_t)n + 1));
+        CK(cudaMemcpyAsync(p, row_ptr, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        d_rp = p;
+    }
+    if (m > 0 && !is_device_ptr(col)) {
+        int32_t* p;
+        CK(tmp.alloc(&p, (size_t)m));
+        CK(cudaMemcpyAsync(p, col, (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        d_col = p;
+    }
+    if (m > 0 && !is_device_ptr(w)) {
+        uint32_t* p;
+        CK(tmp.alloc(&p, (size_t)m));
+        CK(cudaMemcpyAsync(p, w, (size_t)m * wsz, cudaMemcpyHostToDevice, st));
+        d_w = p;
+    }
+    if (!is_device_ptr(part)) {
+        int32_t* p;
+        CK(tmp.alloc(&p, (size_t)n));
+        CK(cudaMemcpyAsync(p, part, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        d_part = p;
+    }
+    const bool f32w = wt == SPQ_F32;
+    evs.mark(0, st);
+
+    // ---- validation, boundary flags, per-component counts (GPU) ----
+    uint8_t* d_bflag;
+    int32_t* d_cnt;
+    uint32_t* d_flag;
+    CK(tmp.alloc(&d_bflag, (size_t)n));
+    CK(tmp.alloc(&d_cnt, 2 * (size_t)k));
+    CK(tmp.alloc(&d_flag, 1));
+    CK(cudaMemsetAsync(d_cnt, 0, 2 * (size_t)k * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st));
+    CK(launch_validate(f32w, n, m, d_rp, d_col, d_w, d_part, k, d_bflag, d_cnt, d_cnt + k, d_flag, st));
+    evs.mark(1, st);
+    std::vector<int32_t> cnt(2 * (size_t)k);
+    uint32_t flag = 0;
+    CK(cudaMemcpyAsync(cnt.data(), d_cnt, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&flag, d_flag, sizeof(flag), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag != 0) return SPQ_EINVAL;
+
+    // ---- sizes and offsets of the tables (host, O(k)) ----
+    h->h_csize.assign(cnt.begin(), cnt.begin() + k);
+    h->h_nb.assign(cnt.begin() + k, cnt.end());
+    std::vector<int32_t> vstart(k);
+    h->h_descs.resize(k);
+    int64_t acc = 0, vs = 0;
+    int32_t max_n = 0;
+    for (int32_t c = 0; c < k; ++c) {
+        vstart[c] = (int32_t)vs;
+        vs += h->h_csize[c];
+        int32_t ld = (int32_t)round_up(h->h_csize[c], 4);
+        h->h_descs[c] = MatDesc{acc, ld, 0};
+        acc += (int64_t)ld * ld;
+        max_n = std::max(max_n, ld);
+    }
+    h->apsp_elems = acc;
+    // component order along the boundary-graph matrix
+    std::vector<int32_t> corder;
+    {
+        spq_order ord = (spq_order)opts.order;
+        if (ord == SPQ_ORDER_ID) {
+            corder.resize(k);
+            for (int32_t c = 0; c < k; ++c) corder[c] = c;
+        } else {
+            // adjacency of components (pairs joined by an inter-component edge), from the GPU
+            spq_status s = component_order(n, m, d_rp, d_col, d_part, k, h->h_nb, ord, st, &corder);
+            if (s != SPQ_OK) return s;
+        }
+    }
+    h->h_bgoff.assign(k, 0);
+    int64_t bo = 0;
+    for (int32_t i = 0; i < k; ++i) {
+        int32_t c = corder[i];
+        h->h_bgoff[c] = (int32_t)bo;
+        bo += h->h_nb[c];
+    }
+    h->nbg = bo;
+    h->N = round_up(bo, 4);
+    if (h->N > 0 && h->N * h->N > (int64_t)1 << 40) return SPQ_ENOMEM;
+
+    // ---- memory check, then allocation ----
+    const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
+    const int64_t hist_words = radix_hist_words(n);
+    size_t need = 4 * (size_t)h->apsp_elems + 4 * (size_t)h->N * (size_t)h->N + 8 * (size_t)n +
+                  (size_t)k * (sizeof(MatDesc) + 12) + 16 * (size_t)n + 4 * (size_t)(fw_words + hist_words) + (64u << 20);
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    if (need > free_b) return SPQ_ENOMEM;
+    size_t bytes = 0;
+    CK(dev_alloc(&h->comp, (size_t)n, &bytes));
+    CK(dev_alloc(&h->local, (size_t)n, &bytes));
+    CK(dev_alloc(&h->descs, (size_t)k, &bytes));
+    CK(dev_alloc(&h->nb, (size_t)k, &bytes));
+    CK(dev_alloc(&h->bg_off, (size_t)k, &bytes));
+    CK(dev_alloc(&h->csize, (size_t)k, &bytes));
+    CK(dev_alloc(&h->err, 4, &bytes));
+    CK(dev_alloc((uint32_t**)&h->apsp, (size_t)h->apsp_elems, &bytes));
+    if (h->N > 0) CK(dev_alloc((uint32_t**)&h->D, (size_t)(h->N * h->N), &bytes));
+    h->bytes = bytes;
+    CK(cudaMemsetAsync(h->err, 0, 4 * sizeof(uint32_t), st));
+    CK(cudaMemcpyAsync(h->descs, h->h_descs.data(), (size_t)k * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->nb, h->h_nb.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->bg_off, h->h_bgoff.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->csize, h->h_csize.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    int32_t* d_vstart;
+    CK(tmp.alloc(&d_vstart, (size_t)k));
+    CK(cudaMemcpyAsync(d_vstart, vstart.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+
+    // ---- vertex reordering (Sec. 4, Fig. 1): stable sort by (component, interior) ----
+    {
+        uint32_t *k0, *v0, *k1, *v1, *hist;
+        CK(tmp.alloc(&k0, (size_t)n));
+        CK(tmp.alloc(&v0, (size_t)n));
+        CK(tmp.alloc(&k1, (size_t)n));
+        CK(tmp.alloc(&v1, (size_t)n));
+        CK(tmp.alloc(&hist, (size_t)hist_words));
+        CK(launch_make_keys(n, d_part, d_bflag, k0, v0, st));
+        bool in_k1 = false;
+        int key_bits = bits_for(2 * (uint64_t)k - 1);
+        CK(radix_sort_pairs(k0, v0, k1, v1, hist, n, key_bits, &in_k1, st));
+        CK(launch_assign_local(n, in_k1 ? v1 : v0, d_part, d_vstart, h->local, h->comp, st));
+    }
+
+    // ---- tables: component APSP, boundary graph, boundary-graph APSP ----
+    uint32_t* fw_scratch;
+    CK(tmp.alloc(&fw_scratch, (size_t)fw_words));
+    BuildInputs in{n, m, d_rp, d_col, d_w, d_part, f32w};
+    const bool skip = opts.skip_inf_tiles != 0;
+    if (f32w) {
+        h->f32store = true;
+        h->arith = SPQ_ARITH_F32;
+        bool inexact = false;
+        CK(build_tables<float>(h, in, false, skip, d_flag, fw_scratch, max_n, &inexact, evs, st));
+    } else {
+        bool try_f32 = opts.arith != SPQ_ARITH_I32;
+        bool inexact = false;
+        if (try_f32) {
+            h->f32store = true;
+            h->arith = SPQ_ARITH_F32;
+            CK(build_tables<float>(h, in, true, skip, d_flag, fw_scratch, max_n, &inexact, evs, st));
+        }
+        if (!try_f32 || inexact) {
+            h->f32store = false;
+            h->arith = SPQ_ARITH_I32;
+            CK(build_tables<int32_t>(h, in, false, skip, d_flag, fw_scratch, max_n, &inexact, evs, st));
+        }
+    }
+    double cu = 0.0;
+    for (int32_t c = 0; c < k; ++c) {
+        double R = (double)((h->h_descs[c].n + kTile - 1) / kTile);
+        cu += R * R * R * (double)kTile * kTile * kTile;
+    }
+    h->comp_updates = cu;
+    CK(cudaStreamSynchronize(st));
+    evs.collect(h->prof_ms);
+    return SPQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void spq_opts_default(spq_opts* o) {
+    if (!o) return;
+    o->struct_size = (int32_t)sizeof(spq_opts);
+    o->arith = SPQ_ARITH_AUTO;
+    o->order = SPQ_ORDER_AUTO;
+    o->skip_inf_tiles = 1;
+}
+
+spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
+                     const int32_t* part, int32_t k, const spq_opts* opts, void* stream, spq_handle** out) {
+    if (!out) return SPQ_EINVAL;
+    *out = nullptr;
+    if (n < 1 || k < 1 || !row_ptr || !part) return SPQ_EINVAL;
+    if (wt != SPQ_I32 && wt != SPQ_F32) return SPQ_EINVAL;
+    spq_opts o;
+    spq_opts_default(&o);
+    if (opts) {
+        if (opts->struct_size < (int32_t)sizeof(spq_opts)) return SPQ_EINVAL;
+        o = *opts;
+        if (o.arith < SPQ_ARITH_AUTO || o.arith > SPQ_ARITH_F32) return SPQ_EINVAL;
+        if (o.order < SPQ_ORDER_AUTO || o.order > SPQ_ORDER_DISSECTION) return SPQ_EINVAL;
+    }
+    spq_handle* h = new (std::nothrow) spq_handle();
+    if (!h) return SPQ_ENOMEM;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e);
+    }
+    h->n = n;
+    h->k = k;
+    h->wt = wt;
+    spq_status s = build_impl(n, row_ptr, col, w, wt, part, k, o, (cudaStream_t)stream, h);
+    if (s != SPQ_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        free_handle_memory(h);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return SPQ_OK;
+}
+
+spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream) {
+    if (!h || q < 0) return SPQ_EINVAL;
+    if (q == 0) return SPQ_OK;
+    if (!pairs || !dist_out) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool pd = is_device_ptr(pairs), od = is_device_ptr(dist_out);
+    if (pd != od) return SPQ_EINVAL;
+    const bool out_f32 = h->wt == SPQ_F32;
+    auto launch = [&](const int32_t* p, void* o) -> cudaError_t {
+        if (h->f32store) {
+            QueryCtx<float> c{h->n, h->comp, h->local, h->descs, h->nb, h->bg_off, (const float*)h->apsp,
+                              (const float*)h->D, h->N, h->err};
+            return launch_query<float>(c, p, q, o, out_f32, st);
+        }
+        QueryCtx<int32_t> c{h->n, h->comp, h->local, h->descs, h->nb, h->bg_off, (const int32_t*)h->apsp,
+                            (const int32_t*)h->D, h->N, h->err};
+        return launch_query<int32_t>(c, p, q, o, out_f32, st);
+    };
+    if (pd) {
+        if (((uintptr_t)pairs & 7u) || ((uintptr_t)dist_out & 3u)) return SPQ_EINVAL;
+        CK(launch(pairs, dist_out));
+        return SPQ_OK;
+    }
+    Temps tmp(st);
+    int32_t* dp;
+    int32_t* dout;
+    CK(tmp.alloc(&dp, 2 * (size_t)q));
+    CK(tmp.alloc(&dout, (size_t)q));
+    CK(cudaMemcpyAsync(dp, pairs, 2 * (size_t)q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(launch(dp, dout));
+    CK(cudaMemcpyAsync(dist_out, dout, (size_t)q * 4, cudaMemcpyDeviceToHost, st));
+    uint32_t f = 0;
+    CK(cudaMemcpyAsync(&f, h->err, sizeof(f), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (f & kErrPair) {
+        CK(cudaMemsetAsync(h->err, 0, sizeof(uint32_t), st));
+        CK(cudaStreamSynchronize(st));
+        return SPQ_EINVAL;
+    }
+    return SPQ_OK;
+}
+
+spq_status spq_query_status(spq_handle* h, void* stream) {
+    if (!h) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t f = 0;
+    CK(cudaMemcpyAsync(&f, h->err, sizeof(f), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (f & kErrPair) {
+        CK(cudaMemsetAsync(h->err, 0, sizeof(uint32_t), st));
+        CK(cudaStreamSynchronize(st));
+        return SPQ_EINVAL;
+    }
+    return SPQ_OK;
+}
+
+void spq_free(spq_handle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_handle_memory(h);
+    delete h;
+}
+
+const char* spq_strerror(spq_status s) {
+    switch (s) {
+        case SPQ_OK: return "success";
+        case SPQ_EINVAL: return "invalid argument or malformed graph, partition or query pair";
+        case SPQ_ENOMEM: return "not enough device (or host) memory for the tables";
+        case SPQ_ECUDA: return "CUDA runtime error";
+        case SPQ_ETIMEOUT: return "bounded device-side wait ran out";
+        case SPQ_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+int spq_last_cuda_error(void) { return g_last_cuda; }
+
+size_t spq_footprint_bytes(const spq_handle* h) { return h ? h->bytes : 0; }
+
+void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double* bg_updates, int32_t* arith) {
+    if (!h) return;
+    if (n_bg) *n_bg = h->nbg;
+    if (comp_updates) *comp_updates = h->comp_updates;
+    if (bg_updates) *bg_updates = h->bg_updates;
+    if (arith) *arith = h->arith;
+}
+
+int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
+    if (!h || !ms || count <= 0) return 0;
+    int32_t c = count < 6 ? count : 6;
+    for (int32_t i = 0; i < c; ++i) ms[i] = h->prof_ms[i];
+    return c;
+}
+
+spq_status spq_get_meta(const spq_handle* h, int32_t* comp, int32_t* local, int32_t* csize, int32_t* nb,
+                        int32_t* bg_off, void* stream) {
+    if (!h) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Item {
+        int32_t* dst;
+        const void* src;
+        size_t bytes;
+        bool src_dev;
+    } items[] = {{comp, h->comp, (size_t)h->n * 4, true},
+                 {local, h->local, (size_t)h->n * 4, true},
+                 {csize, h->h_csize.data(), (size_t)h->k * 4, false},
+                 {nb, h->h_nb.data(), (size_t)h->k * 4, false},
+                 {bg_off, h->h_bgoff.data(), (size_t)h->k * 4, false}};
+    for (auto& it : items) {
+        if (!it.dst) continue;
+        CK(cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyDefault, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return SPQ_OK;
+}
+
+spq_status spq_get_apsp(const spq_handle* h, int32_t c, void* out, void* stream) {
+    if (!h || c < 0 || c >= h->k || !out) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t sz = h->h_csize[c];
+    if (sz == 0) return SPQ_OK;
+    const MatDesc d = h->h_descs[c];
+    const void* src = (const char*)h->apsp + d.off * 4;
+    return copy_table_out(h->f32store && h->wt == SPQ_I32, src, sz, sz, d.n, out, st) == cudaSuccess
+               ? SPQ_OK
+               : cuda_fail(cudaGetLastError());
+}
+
+spq_status spq_get_bg(const spq_handle* h, void* out, void* stream) {
+    if (!h || !out) return SPQ_EINVAL;
+    if (h->nbg == 0) return SPQ_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return copy_table_out(h->f32store && h->wt == SPQ_I32, h->D, h->nbg, h->nbg, h->N, out, st) == cudaSuccess
+               ? SPQ_OK
+               : cuda_fail(cudaGetLastError());
+}
+
+}  // extern "C"

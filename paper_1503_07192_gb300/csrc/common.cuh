@@ -1,0 +1,105 @@
+// Shared definitions of the distance-query library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spq.h"
+
+namespace spq {
+
+// Bits of the device-side status word.
+enum : uint32_t {
+    kErrCsr = 1u,     // row_ptr / col out of range
+    kErrPart = 2u,    // part[v] outside [0, k)
+    kErrWeight = 4u,  // negative or non-finite weight
+    kErrAsym = 8u,    // slot u->v without a matching v->u of the same smallest weight
+    kErrPair = 16u,   // query pair id outside [0, n)
+    kErrExact = 32u,  // float32 tables hold a finite entry >= 2^24 (not provably exact)
+};
+
+constexpr int kTile = 128;  // Floyd-Warshall tile edge (rows = columns = pivot block)
+
+// +infinity / the int32 sentinel, per table element type.
+template <typename T>
+struct Inf;
+template <>
+struct Inf<int32_t> {
+    __host__ __device__ static constexpr int32_t value() { return SPQ_INF_I32; }
+};
+template <>
+struct Inf<float> {
+    __host__ __device__ static float value() { return __builtin_inff(); }
+};
+
+// One square matrix of a batched Floyd-Warshall: element offset from the batch base,
+// and its size n (= its row stride; a multiple of 4 so rows stay 16-byte aligned).
+struct MatDesc {
+    int64_t off;
+    int32_t n;
+    int32_t pad_;
+};
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---- prep.cu: input validation, boundary detection, stable radix sort ----
+cudaError_t launch_validate(bool f32, int32_t n, int64_t m, const int64_t* rp, const int32_t* col, const void* w,
+                            const int32_t* part, int32_t k, uint8_t* bflag, int32_t* cnt_c, int32_t* cnt_b,
+                            uint32_t* err, cudaStream_t st);
+// Stable LSD radix sort of (key, val) by the low key_bits bits.  Buffers: k0/v0 hold
+// the input, k1/v1 are scratch of the same size; hist needs radix_hist_words(n) words.
+// Returns (via *in_k1) whether the sorted result ended in k1/v1.
+int64_t radix_hist_words(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist, int64_t n,
+                             int key_bits, bool* in_k1, cudaStream_t st);
+cudaError_t launch_make_keys(int32_t n, const int32_t* part, const uint8_t* bflag, uint32_t* keys, uint32_t* vals,
+                             cudaStream_t st);
+cudaError_t launch_assign_local(int32_t n, const uint32_t* sorted_vals, const int32_t* part, const int32_t* vstart,
+                                int32_t* local, int32_t* comp, cudaStream_t st);
+
+// ---- assemble.cu: table initialisation and boundary-graph assembly ----
+template <typename T>
+cudaError_t launch_fill_blocks(T* apsp, const MatDesc* descs, int32_t nmat, cudaStream_t st);
+template <typename T>
+cudaError_t launch_scatter_intra(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
+                                 const int32_t* part, const int32_t* local, const MatDesc* descs, T* apsp,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_bg_fill(T* D, int64_t N, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bg_clique(const T* apsp, const MatDesc* descs, const int32_t* nb, const int32_t* bg_off, int32_t k,
+                             T* D, int64_t N, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bg_inter(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
+                            const int32_t* part, const int32_t* local, const int32_t* bg_off, T* D, int64_t N,
+                            cudaStream_t st);
+cudaError_t launch_check_exact(const float* a, int64_t count, uint32_t* err, cudaStream_t st);
+
+// ---- fw.cu: blocked Floyd-Warshall (Venkataraman, Sahni & Mukhopadhyaya 2003) ----
+template <typename T>
+cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, cudaStream_t st);
+// One matrix of size N, optionally skipping tiles whose pivot panel is all infinite.
+// *updates receives the number of min-plus updates issued (host-side count).
+template <typename T>
+cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, double* updates, cudaStream_t st);
+int64_t fw_single_scratch_words(int64_t N);
+
+// ---- query.cu ----
+template <typename T>
+struct QueryCtx {
+    int32_t n;
+    const int32_t* comp;
+    const int32_t* local;
+    const MatDesc* descs;
+    const int32_t* nb;
+    const int32_t* bg_off;
+    const T* apsp;
+    const T* D;
+    int64_t N;
+    uint32_t* err;
+};
+template <typename T>
+cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
+                         cudaStream_t st);
+
+}  // namespace spq

@@ -1,0 +1,494 @@
+// Blocked Floyd-Warshall in the (min, +) semiring, for the component tables APSP(C)
+// (Algorithm 1, line 3) and for the boundary graph (Algorithm 1, lines 7-9).
+//
+// The paper computes APSP(C) with the GPU algorithm of its reference [ipdps-apsp] and
+// the boundary-graph rows with Dijkstra's algorithm; both are exact all-pairs distance
+// computations, and here both are the three-phase blocked Floyd-Warshall of
+// Venkataraman, Sahni and Mukhopadhyaya (J. Exp. Algorithmics 8, 2003).  For pivot block r:
+//   phase 1: close the diagonal tile (r, r) with plain Floyd-Warshall, in shared memory;
+//   phase 2: row tiles (r, J) <- D*(r, r) (x) D(r, J)   [(x) = min-plus product]
+//   phase 3: tiles (I, J), I, J != r <- min(D(I, J), D(I, r) (x) D(r, J)).
+// Every matrix here is symmetric (undirected graphs; a + b = b + a and min is
+// order-free, so float sums keep the symmetry exactly), so phase 2 writes each row tile
+// also transposed into the column tile (J, r), and phase 3 reads the column panel
+// D(I, r) as the transpose of the row tile D(r, I).  Both panels of phase 3 are then
+// row-major rows of the pivot block, staged into shared memory with cp.async.
+//
+// Arithmetic: int32 (add, min) or float32 (add, three-input min over two k steps).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace spq {
+
+namespace {
+
+constexpr int T_ = kTile;  // 128
+constexpr int KC = 32;     // k rows per staged panel chunk
+constexpr int NTH = 256;   // threads per CTA; each owns an 8 x 8 block of the tile
+constexpr int NCHUNK = T_ / KC;
+
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+template <typename T>
+struct MP;
+template <>
+struct MP<float> {
+    // min(c, a0 + b0, a1 + b1)
+    static __device__ __forceinline__ float upd2(float c, float a0, float b0, float a1, float b1) {
+        return fmin3(c, a0 + b0, a1 + b1);
+    }
+    static __device__ __forceinline__ float upd1(float c, float a, float b) { return fminf(c, a + b); }
+};
+template <>
+struct MP<int32_t> {
+    static __device__ __forceinline__ int32_t upd2(int32_t c, int32_t a0, int32_t b0, int32_t a1, int32_t b1) {
+        return __viaddmin_s32(a0, b0, __viaddmin_s32(a1, b1, c));
+    }
+    static __device__ __forceinline__ int32_t upd1(int32_t c, int32_t a, int32_t b) { return __viaddmin_s32(a, b, c); }
+};
+
+template <typename T>
+__device__ __forceinline__ int4 inf4() {
+    T v = Inf<T>::value();
+    int x = *reinterpret_cast<int*>(&v);
+    return make_int4(x, x, x, x);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename T>
+struct alignas(16) PanelSmem {
+    T a[2][KC][T_];
+    T b[2][KC][T_];
+};
+
+// Thread-owned rows / columns inside a tile: {q*4 .. q*4+3} and {64 + q*4 .. 64+q*4+3}.
+__device__ __forceinline__ int own(int q, int i) { return (i < 4) ? q * 4 + i : 64 + q * 4 + (i - 4); }
+
+// Stage rows [row0, row0+KC) x cols [col0, col0+128) of M (n x n) into P; cells outside
+// the matrix read as infinity.
+template <typename T>
+__device__ __forceinline__ void stage_chunk(T (*P)[T_], const T* __restrict__ M, int64_t n, int64_t row0,
+                                            int64_t col0, int tid) {
+#pragma unroll
+    for (int it = 0; it < (KC * T_ / 4) / NTH; ++it) {
+        int idx = it * NTH + tid;
+        int kk = idx >> 5, c4 = idx & 31;
+        int64_t r = row0 + kk, c = col0 + c4 * 4;
+        T* dst = &P[kk][c4 * 4];
+        if (r < n && c < n)
+            cp_async16(dst, M + r * n + c);
+        else
+            *reinterpret_cast<int4*>(dst) = inf4<T>();
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_c(T (&acc)[8][8], const T* __restrict__ M, int64_t n, int64_t r0, int64_t c0,
+                                       int tx, int ty) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int64_t r = r0 + own(ty, i);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int64_t c = c0 + own(tx, h * 4);
+            int4 v = (r < n && c < n) ? *reinterpret_cast<const int4*>(M + r * n + c) : inf4<T>();
+            acc[i][h * 4 + 0] = *reinterpret_cast<T*>(&v.x);
+            acc[i][h * 4 + 1] = *reinterpret_cast<T*>(&v.y);
+            acc[i][h * 4 + 2] = *reinterpret_cast<T*>(&v.z);
+            acc[i][h * 4 + 3] = *reinterpret_cast<T*>(&v.w);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_c(const T (&acc)[8][8], T* __restrict__ M, int64_t n, int64_t r0, int64_t c0,
+                                        int tx, int ty) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int64_t r = r0 + own(ty, i);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int64_t c = c0 + own(tx, h * 4);
+            if (r < n && c < n) {
+                int4 v;
+                v.x = *reinterpret_cast<const int*>(&acc[i][h * 4 + 0]);
+                v.y = *reinterpret_cast<const int*>(&acc[i][h * 4 + 1]);
+                v.z = *reinterpret_cast<const int*>(&acc[i][h * 4 + 2]);
+                v.w = *reinterpret_cast<const int*>(&acc[i][h * 4 + 3]);
+                *reinterpret_cast<int4*>(M + r * n + c) = v;
+            }
+        }
+    }
+}
+
+// Transposed store: acc[i][j] -> M[c0 + col(j)][r0 + row(i)].  Each thread writes
+// 4 consecutive transposed columns (its rows q*4..q*4+3) as one 16-byte vector.
+template <typename T>
+__device__ __forceinline__ void store_c_transposed(const T (&acc)[8][8], T* __restrict__ M, int64_t n, int64_t r0,
+                                                   int64_t c0, int tx, int ty) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int64_t tr = c0 + own(tx, j);  // transposed row
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int64_t tc = r0 + own(ty, h * 4);  // transposed column (multiple of 4)
+            if (tr < n && tc < n) {
+                int4 v;
+                v.x = *reinterpret_cast<const int*>(&acc[h * 4 + 0][j]);
+                v.y = *reinterpret_cast<const int*>(&acc[h * 4 + 1][j]);
+                v.z = *reinterpret_cast<const int*>(&acc[h * 4 + 2][j]);
+                v.w = *reinterpret_cast<const int*>(&acc[h * 4 + 3][j]);
+                *reinterpret_cast<int4*>(M + tr * n + tc) = v;
+            }
+        }
+    }
+}
+
+// acc = min(acc, A (x) B) over the KC-row chunk held in stage s:
+// A[i][k] = a[s][k][i] (the panel is stored k-major), B[k][j] = b[s][k][j].
+template <typename T>
+__device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>& sm, int s, int tx, int ty) {
+#pragma unroll 1
+    for (int kk = 0; kk < KC; kk += 2) {
+        T a0[8], a1[8], b0[8], b1[8];
+        {
+            const int4 x0 = *reinterpret_cast<const int4*>(&sm.a[s][kk][ty * 4]);
+            const int4 x1 = *reinterpret_cast<const int4*>(&sm.a[s][kk][64 + ty * 4]);
+            const int4 y0 = *reinterpret_cast<const int4*>(&sm.a[s][kk + 1][ty * 4]);
+            const int4 y1 = *reinterpret_cast<const int4*>(&sm.a[s][kk + 1][64 + ty * 4]);
+            const int4 z0 = *reinterpret_cast<const int4*>(&sm.b[s][kk][tx * 4]);
+            const int4 z1 = *reinterpret_cast<const int4*>(&sm.b[s][kk][64 + tx * 4]);
+            const int4 w0 = *reinterpret_cast<const int4*>(&sm.b[s][kk + 1][tx * 4]);
+            const int4 w1 = *reinterpret_cast<const int4*>(&sm.b[s][kk + 1][64 + tx * 4]);
+            const int xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const int ya[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+            const int zb[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            const int wb[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                a0[i] = *reinterpret_cast<const T*>(&xa[i]);
+                a1[i] = *reinterpret_cast<const T*>(&ya[i]);
+                b0[i] = *reinterpret_cast<const T*>(&zb[i]);
+                b1[i] = *reinterpret_cast<const T*>(&wb[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = MP<T>::upd2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
+    }
+}
+
+// acc = min(acc, A (x) B) with A[i][k] = M[arow0 + k][acol0 + i] and
+// B[k][j] = M[arow0 + k][bcol0 + j], k over the pivot block [arow0, arow0 + 128).
+template <typename T>
+__device__ __forceinline__ void minplus_panels(T (&acc)[8][8], const T* __restrict__ M, int64_t n, int64_t prow0,
+                                               int64_t acol0, int64_t bcol0, PanelSmem<T>& sm, int tid, int tx,
+                                               int ty) {
+    stage_chunk<T>(sm.a[0], M, n, prow0, acol0, tid);
+    stage_chunk<T>(sm.b[0], M, n, prow0, bcol0, tid);
+    cp_async_commit();
+#pragma unroll 1
+    for (int ch = 0; ch < NCHUNK; ++ch) {
+        if (ch + 1 < NCHUNK) {
+            const int s = (ch + 1) & 1;
+            stage_chunk<T>(sm.a[s], M, n, prow0 + (ch + 1) * KC, acol0, tid);
+            stage_chunk<T>(sm.b[s], M, n, prow0 + (ch + 1) * KC, bcol0, tid);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        compute_chunk<T>(acc, sm, ch & 1, tx, ty);
+        __syncthreads();
+    }
+}
+
+// ---------------- phase 1: closure of the diagonal tile ----------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatDesc* __restrict__ descs,
+                                                int32_t nmat, int32_t r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T(*S)[T_] = reinterpret_cast<T(*)[T_]>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int32_t mi = blockIdx.y; mi < nmat; mi += gridDim.y) {
+        const MatDesc d = descs[mi];
+        const int64_t n = d.n;
+        const int32_t R = (int32_t)((n + T_ - 1) / T_);
+        if (r >= R) continue;
+        T* M = base + d.off;
+        const int64_t o = (int64_t)r * T_;
+        for (int idx = tid; idx < T_ * T_ / 4; idx += NTH) {
+            int i = idx >> 5, c4 = idx & 31;
+            int64_t gr = o + i, gc = o + c4 * 4;
+            int4 v = (gr < n && gc < n) ? *reinterpret_cast<const int4*>(M + gr * n + gc) : inf4<T>();
+            *reinterpret_cast<int4*>(&S[i][c4 * 4]) = v;
+        }
+        __syncthreads();
+        T acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = S[own(ty, i)][own(tx, j)];
+        const int K = (int)((n - o) < T_ ? (n - o) : T_);
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            // row k of S is current: by symmetry it is also column k
+            T a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                a[i] = S[k][own(ty, i)];
+                b[i] = S[k][own(tx, i)];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = MP<T>::upd1(acc[i][j], a[i], b[j]);
+            const int kn = k + 1;
+            if (kn < K) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (own(ty, i) == kn) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) S[kn][own(tx, j)] = acc[i][j];
+                    }
+            }
+            __syncthreads();
+        }
+        store_c<T>(acc, M, n, o, o, tx, ty);
+        __syncthreads();
+    }
+}
+
+// ---------------- phase 2: pivot row tiles (and their transposes) ----------------
+template <typename T>
+__global__ void __launch_bounds__(NTH, 2) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
+                                                   int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int32_t mi = blockIdx.y; mi < nmat; mi += gridDim.y) {
+        const MatDesc d = descs[mi];
+        const int64_t n = d.n;
+        const int32_t R = (int32_t)((n + T_ - 1) / T_);
+        if (r >= R || (int32_t)blockIdx.x >= R - 1) continue;
+        const int32_t J = (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
+        T* M = base + d.off;
+        const int64_t o = (int64_t)r * T_, cj = (int64_t)J * T_;
+        T acc[8][8];
+        load_c<T>(acc, M, n, o, cj, tx, ty);
+        minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        store_c<T>(acc, M, n, o, cj, tx, ty);
+        store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
+        if (row_finite) {
+            bool fin = false;
+            const T inf = Inf<T>::value();
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
+            if (__syncthreads_or(fin) && tid == 0) row_finite[J] = 1u;
+        }
+    }
+}
+
+// ---------------- phase 3, batched form: every tile (I, J), I, J != r ----------------
+template <typename T>
+__global__ void __launch_bounds__(NTH, 2) k_phase3_batched(T* __restrict__ base, const MatDesc* __restrict__ descs,
+                                                           int32_t nmat, int32_t r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int32_t mi = blockIdx.y; mi < nmat; mi += gridDim.y) {
+        const MatDesc d = descs[mi];
+        const int64_t n = d.n;
+        const int32_t R = (int32_t)((n + T_ - 1) / T_);
+        const int32_t Rm = R - 1;
+        if (r >= R || (int64_t)blockIdx.x >= (int64_t)Rm * Rm) continue;
+        int32_t I = (int32_t)blockIdx.x / Rm, J = (int32_t)blockIdx.x % Rm;
+        I += (I >= r);
+        J += (J >= r);
+        T* M = base + d.off;
+        const int64_t o = (int64_t)r * T_, ci = (int64_t)I * T_, cj = (int64_t)J * T_;
+        T acc[8][8];
+        load_c<T>(acc, M, n, ci, cj, tx, ty);
+        minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+        store_c<T>(acc, M, n, ci, cj, tx, ty);
+    }
+}
+
+// ---------------- phase 3, single large matrix: persistent over a tile list ----------------
+// list[0] = count c, list[1..c] = tile indices J != r whose row tile (r, J) holds a
+// finite entry; every (I, J) in list x list is updated.
+template <typename T>
+__global__ void __launch_bounds__(NTH, 2) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
+                                                        const uint32_t* __restrict__ list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t c = list[0];
+    const int64_t o = (int64_t)r * T_;
+    for (int64_t t = blockIdx.x; t < c * c; t += gridDim.x) {
+        const int64_t I = list[1 + t / c], J = list[1 + t % c];
+        const int64_t ci = I * T_, cj = J * T_;
+        T acc[8][8];
+        load_c<T>(acc, M, n, ci, cj, tx, ty);
+        minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+        store_c<T>(acc, M, n, ci, cj, tx, ty);
+    }
+}
+
+// Build the tile list of round r from the flags phase 2 set (and clear the flags).
+// Also accumulates the number of phase-3 tiles into *tiles.
+__global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, uint32_t* __restrict__ list,
+                          unsigned long long* __restrict__ tiles) {
+    __shared__ uint32_t cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int32_t base = 0; base < R; base += blockDim.x) {
+        int32_t J = base + threadIdx.x;
+        bool take = J < R && J != r && flags[J] != 0u;
+        unsigned ballot = __ballot_sync(0xffffffffu, take);
+        // ordered compaction: warp prefix, then warps in order
+        __shared__ uint32_t wsum[32];
+        int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) wsum[warp] = __popc(ballot);
+        __syncthreads();
+        uint32_t off = cnt;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (take) list[1 + off + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)J;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+            cnt += tot;
+        }
+        __syncthreads();
+    }
+    for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
+    if (threadIdx.x == 0) {
+        list[0] = cnt;
+        *tiles += (unsigned long long)cnt * cnt;
+    }
+}
+
+int g_sms = 0;
+int sms() {
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
+template <typename T>
+cudaError_t set_smem_attrs() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_phase1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_ * T_ * (int)sizeof(T));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase3_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase3_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
+    done = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, cudaStream_t st) {
+    if (nmat <= 0 || max_n <= 0) return cudaSuccess;
+    cudaError_t e = set_smem_attrs<T>();
+    if (e != cudaSuccess) return e;
+    const int32_t R = (max_n + T_ - 1) / T_;
+    const unsigned gy = (unsigned)(nmat < 65535 ? nmat : 65535);
+    const size_t psm = sizeof(PanelSmem<T>);
+    for (int32_t r = 0; r < R; ++r) {
+        k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r);
+        if (R > 1) {
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, nullptr);
+            k_phase3_batched<T><<<dim3((R - 1) * (R - 1), gy), NTH, psm, st>>>(base, d_descs, nmat, r);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int64_t fw_single_scratch_words(int64_t N) {
+    int64_t R = (N + T_ - 1) / T_;
+    return 2 * R + 2 + 2;  // flags[R], list[1 + R], tile counter (u64)
+}
+
+template <typename T>
+cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double* updates, cudaStream_t st) {
+    if (updates) *updates = 0.0;
+    if (N <= 0) return cudaSuccess;
+    cudaError_t e = set_smem_attrs<T>();
+    if (e != cudaSuccess) return e;
+    const int32_t R = (int32_t)((N + T_ - 1) / T_);
+    uint32_t* flags = scratch;
+    uint32_t* list = scratch + R;
+    unsigned long long* tiles = reinterpret_cast<unsigned long long*>(scratch + 2 * R + 2);
+    e = cudaMemsetAsync(scratch, 0, fw_single_scratch_words(N) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    MatDesc h{0, (int32_t)N, 0};
+    MatDesc* dd = nullptr;
+    e = cudaMallocAsync(&dd, sizeof(MatDesc), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dd, &h, sizeof(MatDesc), cudaMemcpyHostToDevice, st);
+    const size_t psm = sizeof(PanelSmem<T>);
+    const int p3_grid = sms() * 2;
+    for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
+        k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r);
+        if (R > 1) {
+            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags);
+            if (!skip_inf) {
+                // mark every tile: the compaction then lists all J != r
+                cudaMemsetAsync(flags, 0xff, R * sizeof(uint32_t), st);
+            }
+            k_compact<<<1, 1024, 0, st>>>(flags, R, r, list, tiles);
+            k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
+        }
+        e = cudaGetLastError();
+    }
+    unsigned long long ht = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ht, tiles, sizeof(ht), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(dd, st);
+    if (updates) {
+        double t3 = (double)T_ * T_ * T_;
+        *updates = ((double)ht + (double)R * R) * t3;  // phase-3 tiles + R phase-1 and R(R-1) phase-2 tiles
+    }
+    return e;
+}
+
+template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, cudaStream_t);
+template cudaError_t fw_batched<float>(float*, const MatDesc*, int32_t, int32_t, cudaStream_t);
+template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, double*, cudaStream_t);
+template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, double*, cudaStream_t);
+
+}  // namespace spq

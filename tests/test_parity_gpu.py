@@ -1,0 +1,250 @@
+"""CUDA path vs the oracle, through the C ABI (needs a GPU).
+
+Integer-weight results must be bit-identical to the oracle's dist(v, w) (the paper's
+Lemma 3 says the method is exact).  Besides the final distances, the intermediate
+tables are checked against the definitions they stand for:
+  - APSP(C) = dist_C, Dijkstra restricted to the subgraph induced by C (Sec. 2);
+  - the boundary-graph matrix = dist_G between boundary vertices (Lemma 1).
+Sizes span several 128-wide tiles with ragged tails; edge cases: one component (no
+boundary), every vertex its own component, empty and disconnected components,
+unreachable pairs, v == w, parallel edges, self-loops, zero weights.
+"""
+
+import numpy as np
+import pytest
+
+from _util import (all_pairs, assert_pairs_exact, build, graph_from_edges, oracle_i32, query, random_graph,
+                   spq)
+
+import gen
+import oracle
+from make_golden import FIXTURES, load
+
+pytestmark = pytest.mark.gpu
+
+ARITHS = [1, 2]  # SPQ_ARITH_I32, SPQ_ARITH_F32
+ORDERS = [1, 2]  # SPQ_ORDER_ID, SPQ_ORDER_DISSECTION
+
+
+@pytest.mark.parametrize("name", sorted(FIXTURES))
+@pytest.mark.parametrize("arith", ARITHS)
+def test_golden_fixtures(name, arith):
+    n, k, part, edges, dist = load(name)
+    g = graph_from_edges(n, edges)
+    h = build(g, np.array(part, np.int32), k, arith=arith)
+    got = query(h, all_pairs(n)).reshape(n, n).astype(np.int64)
+    exp = np.array(dist, dtype=np.int64)
+    exp[exp < 0] = spq().SPQ_INF_I32
+    assert np.array_equal(got, exp)
+    h.free()
+
+
+def _check_tables(h, g, part, k):
+    """APSP(C) against dist_C, the boundary-graph matrix against Lemma 1."""
+    meta = h.meta()
+    comp, local, nb, bg_off = meta["comp"], meta["local"], meta["nb"], meta["bg_off"]
+    assert np.array_equal(comp, part)
+    for c in range(k):
+        ids = np.nonzero(part == c)[0]
+        # local order: boundary vertices first, each class by ascending id (Sec. 4, Fig. 1)
+        order = ids[np.argsort(local[ids])]
+        nbc = nb[c]
+        assert np.all(np.diff(order[:nbc]) > 0) and np.all(np.diff(order[nbc:]) > 0)
+        A = h.apsp(c)
+        for li, v in enumerate(order):
+            ref = oracle_i32(oracle.subgraph_sssp(g.row_ptr, g.col, g.w, part, c, int(v)))
+            assert np.array_equal(A[li].astype(np.int64), ref[order]), (c, v)
+    B = h.bg()
+    nbg = B.shape[0]
+    bvert = np.empty(nbg, np.int64)
+    for c in range(k):
+        ids = np.nonzero((part == c) & (local < nb[c]))[0]
+        bvert[bg_off[c] + local[ids]] = ids
+    rows = oracle_i32(oracle.multi_sssp(g.row_ptr, g.col, g.w, bvert))
+    assert np.array_equal(B.astype(np.int64), rows[:, bvert])
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("order", ORDERS)
+def test_grid64_all_queries_and_tables(arith, order):
+    w = gen.configs.grid64()
+    h = build(w.graph, w.part, w.k, arith=arith, order=order)
+    st = h.stats()
+    assert st["n_bg"] == 732
+    assert_pairs_exact(h, w.graph, w.pairs)
+    _check_tables(h, w.graph, w.part, w.k)
+    h.free()
+
+
+def test_modes_agree_on_delaunay():
+    w = gen.configs.delaunay_rcb(6000, 3, 3000, seed=31)
+    outs = []
+    for arith in ARITHS:
+        for order in ORDERS:
+            for skip in (0, 1):
+                h = build(w.graph, w.part, w.k, arith=arith, order=order, skip=skip)
+                outs.append(query(h, w.pairs))
+                h.free()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    h = build(w.graph, w.part, w.k)
+    assert_pairs_exact(h, w.graph, w.pairs)
+    h.free()
+
+
+@pytest.mark.parametrize("n", [5, 128, 300, 517])
+def test_single_component_is_plain_apsp(n):
+    """k = 1: no boundary vertex, the query is APSP(G) (= plain Floyd-Warshall)."""
+    g = random_graph(n, 3 * n, seed=n, wmax=40)
+    part = np.zeros(n, np.int32)
+    h = build(g, part, 1)
+    assert h.stats()["n_bg"] == 0
+    got = query(h, all_pairs(n)).reshape(n, n).astype(np.int64)
+    fw = oracle.floyd_warshall(oracle.dense_from_csr(n, g.row_ptr, g.col, g.w))
+    assert np.array_equal(got, oracle_i32(fw))
+    h.free()
+
+
+@pytest.mark.parametrize("n", [1, 2, 60, 200])
+def test_every_vertex_its_own_component(n):
+    """k = n: every vertex with an edge is a boundary vertex and BG is G itself."""
+    g = random_graph(n, 2 * n, seed=100 + n, wmax=30)
+    part = np.arange(n, dtype=np.int32)
+    h = build(g, part, n)
+    got = query(h, all_pairs(n)).reshape(n, n).astype(np.int64)
+    fw = oracle.floyd_warshall(oracle.dense_from_csr(n, g.row_ptr, g.col, g.w))
+    assert np.array_equal(got, oracle_i32(fw))
+    h.free()
+
+
+def test_uneven_empty_and_disconnected_components():
+    g = gen.delaunay(4000, seed=41)
+    rng = np.random.default_rng(41)
+    part, k = gen.kdtree(g.xy, 300)  # leaves of 150..300 vertices
+    # merge two far-apart leaves into one (disconnected) component, leave an id empty,
+    # and split one leaf into a tiny piece of 3 vertices
+    part = part.copy()
+    part[part == k - 1] = 0
+    tiny = np.nonzero(part == 5)[0][:3]
+    part[tiny] = k  # new id k; id k-1 is now empty
+    k += 1
+    h = build(g, part, k)
+    pairs = rng.integers(0, g.n, size=(20000, 2)).astype(np.int32)
+    pairs[:50, 1] = pairs[:50, 0]  # v == w
+    assert_pairs_exact(h, g, pairs)
+    _check_tables(h, g, part, k)
+    h.free()
+
+
+def test_ragged_uneven_random_graph_tables():
+    """Random sparse graph, components of 1..700 vertices: several tiles and ragged
+    tails in both the component blocks and the boundary-graph matrix."""
+    n = 1900
+    g = random_graph(n, 4 * n, seed=7, wmax=1000, wmin=0)  # zero weights allowed
+    rng = np.random.default_rng(7)
+    cuts = np.sort(rng.choice(np.arange(1, n), size=6, replace=False))
+    part = np.searchsorted(cuts, np.arange(n), side="right").astype(np.int32)
+    part = rng.permutation(7)[part].astype(np.int32)
+    h = build(g, part, 7)
+    assert_pairs_exact(h, g, rng.integers(0, n, size=(30000, 2)).astype(np.int32))
+    _check_tables(h, g, part, 7)
+    h.free()
+
+
+def test_unreachable_pairs_report_inf():
+    a = gen.grid4(20, 20, wmax=9, seed=1)
+    # two copies side by side, no edge between them
+    u, v, w = gen.edges_from_csr(a)
+    u2 = np.concatenate([u, u + a.n])
+    v2 = np.concatenate([v, v + a.n])
+    w2 = np.concatenate([w, w])
+    rp, col, ww = gen.csr_from_edges(2 * a.n, u2, v2, w2)
+    g = gen.Graph(2 * a.n, rp, col, ww.astype(np.int32))
+    part = (np.arange(g.n) // 100).astype(np.int32)
+    h = build(g, part, 8)
+    pairs = np.array([[0, a.n], [5, 799], [399, 400], [3, 3]], np.int32)
+    got = query(h, pairs)
+    inf = spq().SPQ_INF_I32
+    assert got[0] == inf and got[1] == inf and got[2] == inf and got[3] == 0
+    assert_pairs_exact(h, g, np.random.default_rng(2).integers(0, g.n, (5000, 2)).astype(np.int32))
+    h.free()
+
+
+def test_host_buffers_match_device_buffers():
+    w = gen.configs.grid_blocks_workload(40, 30, 10, 10, 100, 4000, seed=13)
+    hd = build(w.graph, w.part, w.k, on_device=True)
+    hh = build(w.graph, w.part, w.k, on_device=False)
+    a = query(hd, w.pairs, on_device=True)
+    b = query(hh, w.pairs, on_device=False)
+    c = query(hd, w.pairs, on_device=False)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert query(hd, np.zeros((0, 2), np.int32), on_device=False).shape == (0,)
+    hd.free()
+    hh.free()
+
+
+def test_invalid_inputs_are_rejected():
+    m = spq()
+    g = gen.grid4(8, 8, wmax=5, seed=3)
+    part = (np.arange(64) // 16).astype(np.int32)
+    # asymmetric weight
+    bad = g.w.copy()
+    bad[0] += 1
+    with pytest.raises(m.SpqError) as e:
+        build(gen.Graph(g.n, g.row_ptr, g.col, bad), part, 4)
+    assert e.value.status == m.SPQ_EINVAL
+    # negative weight (both directions, so the graph stays symmetric)
+    neg = g.w.copy()
+    neg[:] = -1
+    with pytest.raises(m.SpqError):
+        build(gen.Graph(g.n, g.row_ptr, g.col, neg), part, 4)
+    # part out of range
+    with pytest.raises(m.SpqError):
+        build(g, np.full(64, 4, np.int32), 4)
+    # column id out of range
+    col = g.col.copy()
+    col[3] = 64
+    with pytest.raises(m.SpqError):
+        build(gen.Graph(g.n, g.row_ptr, col, g.w), part, 4)
+    # a missing reverse slot
+    one_way = gen.Graph(3, np.array([0, 1, 1, 1], np.int64), np.array([1], np.int32), np.array([1], np.int32))
+    with pytest.raises(m.SpqError):
+        build(one_way, np.zeros(3, np.int32), 1)
+    h = build(g, part, 4)
+    # out-of-range pair: host path returns EINVAL, device path marks the handle
+    with pytest.raises(m.SpqError):
+        query(h, np.array([[0, 64]], np.int32), on_device=False)
+    with pytest.raises(m.SpqError):
+        query(h, np.array([[-1, 3]], np.int32), on_device=True)
+    # the handle stays usable
+    assert query(h, np.array([[0, 63]], np.int32))[0] == oracle.pairs_dist(
+        g.row_ptr, g.col, g.w, np.array([[0, 63]], np.int32))[0]
+    h.free()
+
+
+def test_f32_weights_within_rounding():
+    """SPQ_F32 graphs: float32 sums; compared with the FP64 oracle.  A distance is a
+    sum of at most H edge weights, each addition rounding by at most 2^-24 relative,
+    so |gpu - exact| <= H * 2^-24 * exact; H < 200 hops here, so rtol = 2e-5."""
+    g = gen.delaunay(5000, seed=51, weight="f32_lognormal", scale=100.0)
+    part, k = gen.rcb(g.xy, 3)
+    rng = np.random.default_rng(51)
+    pairs = rng.integers(0, g.n, size=(20000, 2)).astype(np.int32)
+    h = build(g, part, k)
+    got = query(h, pairs).astype(np.float64)
+    ref = oracle.pairs_dist_f64(g.row_ptr, g.col, g.w.astype(np.float64), pairs)
+    np.testing.assert_allclose(got, ref, rtol=2e-5, atol=0)
+    h.free()
+
+
+def test_delaunay16k_sampled_and_full_rows():
+    w = gen.configs.delaunay_rcb(1 << 14, 4, 20000, seed=61)
+    h = build(w.graph, w.part, w.k)
+    assert_pairs_exact(h, w.graph, w.pairs)
+    g = w.graph
+    srcs = np.array([0, 4097, 16383])
+    rows = oracle_i32(oracle.multi_sssp(g.row_ptr, g.col, g.w, srcs))
+    for i, s in enumerate(srcs):
+        pairs = np.stack([np.full(g.n, s), np.arange(g.n)], 1).astype(np.int32)
+        assert np.array_equal(query(h, pairs).astype(np.int64), rows[i])
+    h.free()
