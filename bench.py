@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the distance-query hot path on one or more GB300s.
+
+One step = the whole path on one synthetic batch: spq_build on the workload's graph and
+partition (validation, reordering, batched component Floyd-Warshall, boundary-graph
+assembly, boundary-graph blocked Floyd-Warshall) followed by spq_query on the
+workload's query pairs, then spq_free.
+
+Default workload (the configuration the headline metric is quoted on): Delaunay
+triangulation of 2^20 uniform points, w = round(1e6 * length), recursive coordinate
+bisection into 1,024 components of 1,024 vertices, 10,000,000 uniform query pairs.
+Inputs are synthetic (gen/), seeded, built on the host before timing and resident in
+HBM when the timed region starts.  The boundary-graph matrix (about 71 GB) is larger
+than L2 and rewritten every step, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (Dijkstra per
+pair, OpenMP over the host cores) on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "queries/s + build min-plus Gop/s (1M-vertex planar), vs INT32/HBM roofline, 1xGB300"
+UNIT = "queries/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="delaunay1m", choices=["delaunay1m", "grid64", "delaunay65k"])
+    p.add_argument("--queries", type=int, default=None, help="override the workload's query count")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    p.add_argument("--e2e-steps", type=int, default=1)
+    return p.parse_args()
+
+
+def make_workload(name, q):
+    import gen
+
+    if name == "delaunay1m":
+        w = gen.configs.delaunay1m(q=q or 10_000_000)
+        desc = {"workload": "delaunay1m", "vertices": w.graph.n, "edges": w.graph.m // 2,
+                "components": w.k, "partition": "recursive coordinate bisection, 10 levels",
+                "weights": "int32 round(1e6 * Euclidean length)", "queries_per_step": int(w.pairs.shape[0])}
+    elif name == "delaunay65k":
+        w = gen.configs.delaunay_rcb(1 << 16, 6, q or 1_000_000, seed=1240)
+        desc = {"workload": "delaunay65k", "vertices": w.graph.n, "components": w.k,
+                "queries_per_step": int(w.pairs.shape[0])}
+    else:
+        w = gen.configs.grid64(q=q or 10_000)
+        desc = {"workload": "grid64", "vertices": w.graph.n, "components": w.k,
+                "queries_per_step": int(w.pairs.shape[0])}
+    return w, desc
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
+    """Time the oracle (Dijkstra per pair, all host cores) on a bounded sample of the
+    workload's pairs; returns (queries/s, sample size, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    g = w.graph
+    rng = np.random.default_rng(seed)
+    probe = w.pairs[rng.integers(0, w.pairs.shape[0], size=4 * cores)]
+    t0 = time.perf_counter()
+    oracle.pairs_dist(g.row_ptr, g.col, g.w, probe, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(max(probe.shape[0] * budget_s / dt, probe.shape[0]), w.pairs.shape[0], 200_000))
+    sample = w.pairs[rng.integers(0, w.pairs.shape[0], size=n)]
+    t0 = time.perf_counter()
+    oracle.pairs_dist(g.row_ptr, g.col, g.w, sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, cores
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    w, desc = make_workload(args.workload, args.queries)
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    g = w.graph
+    rng = np.random.default_rng(7)
+    # size each step for a few seconds of oracle time
+    probe = w.pairs[rng.integers(0, w.pairs.shape[0], size=4 * cores)]
+    t0 = time.perf_counter()
+    oracle.pairs_dist(g.row_ptr, g.col, g.w, probe, nthreads=cores)
+    per_q = max(time.perf_counter() - t0, 1e-6) / probe.shape[0]
+    step_q = int(min(max(8.0 / per_q, 4 * cores), w.pairs.shape[0]))
+    times = []
+    for s in range(args.warmup + args.steps):
+        sample = w.pairs[rng.integers(0, w.pairs.shape[0], size=step_q)]
+        t0 = time.perf_counter()
+        oracle.pairs_dist(g.row_ptr, g.col, g.w, sample, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = step_q * len(times) / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "impl": "reference", "config": desc,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{step_q} uniformly drawn pairs of the workload per step, "
+                                       f"binary-heap Dijkstra with early exit, OpenMP over pairs"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_1503_07192_gb300 as spq
+    from paper_1503_07192_gb300 import _lib
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    spq.build()
+    lib = _lib.load()
+
+    t0 = time.time()
+    w, desc = make_workload(args.workload, args.queries)
+    g = w.graph
+    q = int(w.pairs.shape[0])
+    log(f"[rank {rank}] workload {desc['workload']}: n={g.n} m={g.m} k={w.k} q={q} ({time.time() - t0:.1f}s)")
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    d_rp, d_col, d_w, d_part, d_pairs = T(g.row_ptr), T(g.col), T(g.w), T(w.part), T(w.pairs)
+    d_out = torch.empty(q, dtype=torch.int32, device=dev)
+    opts = spq.spq_opts_default()
+    opts.profile_kernels = 1
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        """One pass of the whole path; returns (build stats, profile, query ms)."""
+        h = spq.spq_build(g.n, d_rp, d_col, d_w, d_part, w.k, opts=opts)
+        eq0 = torch.cuda.Event(enable_timing=True)
+        eq1 = torch.cuda.Event(enable_timing=True)
+        eq0.record(stream)
+        spq.spq_query(h, d_pairs, out=d_out)
+        eq1.record(stream)
+        st, pf = h.stats(), h.profile()
+        h.free()  # synchronises the device
+        return st, pf, eq0.elapsed_time(eq1)
+
+    for i in range(args.warmup):
+        st, pf, qms = step()
+        log(f"[rank {rank}] warmup {i}: build stages {[round(pf[k], 1) for k in list(pf)[:6]]} ms, query {qms:.1f} ms")
+
+    # correctness spot check outside the timed region (CUDA path vs the last step's output)
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = spq.spq_kernel_launches()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    e0.record(stream)
+    per = []
+    for _ in range(args.steps):
+        per.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = spq.spq_kernel_launches() - launches0
+    elapsed_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    K = args.steps
+    build_ms = [sum(pf[k] for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check"))
+                for _, pf, _ in per]
+    query_ms = [qm for _, _, qm in per]
+    st0 = per[0][0]
+    total_updates = st0["comp_updates"] + st0["bg_updates"]
+    p3_ms = sum(pf["p3_ms"] for _, pf, _ in per)
+    p3_launches = sum(pf["p3_launches"] for _, pf, _ in per)
+    p3_updates = sum(pf["p3_updates"] for _, pf, _ in per)
+    achieved_gops = p3_updates / (p3_ms * 1e-3) / 1e9 if p3_ms > 0 else None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_gops = sms * 128 * 2070e6 / 2 / 1e9  # 128 lanes/SM, 2 lane-ops per update, max SM clock
+
+    # measured issue peak of the update (same process, after the timed region)
+    ups, pms = ctypes.c_double(), ctypes.c_double()
+    micro = {}
+    for mode in (1, 2, 3):
+        if lib.spq_peak_minplus(mode, 20000, 8, ctypes.byref(ups), ctypes.byref(pms)) == 0:
+            micro[str(mode)] = round(ups.value / 1e9, 1)
+
+    line = {
+        "metric": METRIC,
+        "value": world * K * q / (elapsed_ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if st0["arith"] == spq.SPQ_ARITH_F32 else "int32",
+        "data": "synthetic",
+        "config": dict(desc, l2="inputs larger than L2 (the 71 GB boundary-graph matrix is rebuilt every step)",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "build_ms": statistics.mean(build_ms),
+        "build_gops": total_updates / (statistics.mean(build_ms) * 1e-3) / 1e9,
+        "build_updates": total_updates,
+        "n_bg": st0["n_bg"],
+        "query_ms": statistics.mean(query_ms),
+        "query_qps": q / (statistics.mean(query_ms) * 1e-3),
+        "build_stage_ms": {k: round(statistics.mean(pf[k] for _, pf, _ in per), 2)
+                           for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check")},
+        "roofline": {
+            "kernel": "k_phase3_list (boundary-graph Floyd-Warshall, phase 3)",
+            "bound": "alu",
+            "achieved": achieved_gops,
+            "peak": peak_gops,
+            "unit": "Gop/s",
+            "frac": (achieved_gops / peak_gops) if achieved_gops else None,
+            "traffic": None,
+            "launches": int(p3_launches),
+            "avg_launch_ms": p3_ms / max(p3_launches, 1),
+            "peak_basis": f"{sms} SMs x 128 lanes x 2070 MHz / 2 lane-ops per min-plus update (derived)",
+            "microbench_gops": micro,
+        },
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+
+    # end to end through the public API with host buffers (pinned), H2D/D2H inside
+    if args.e2e_steps > 0:
+        h_rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr)).pin_memory()
+        h_col = torch.from_numpy(np.ascontiguousarray(g.col)).pin_memory()
+        h_w = torch.from_numpy(np.ascontiguousarray(g.w)).pin_memory()
+        h_part = torch.from_numpy(np.ascontiguousarray(w.part)).pin_memory()
+        h_pairs = torch.from_numpy(np.ascontiguousarray(w.pairs)).pin_memory()
+        h_out = torch.empty(q, dtype=torch.int32).pin_memory()
+        del d_rp, d_col, d_w, d_part, d_pairs, d_out
+        torch.cuda.empty_cache()
+        h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_col, h_w, h_part, h_pairs))
+        d2h = h_out.numel() * h_out.element_size()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h = spq.spq_build(g.n, h_rp, h_col, h_w, h_part, w.k)
+            spq.spq_query(h, h_pairs, out=h_out)
+            h.free()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        line["e2e"] = {"value": world * args.e2e_steps * q / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+
+    if rank == 0 and world == 1:
+        qps, n, dt, cores = cpu_oracle_sample(w, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n} uniformly drawn pairs of the workload ({dt:.1f} s), binary-heap "
+                                          f"Dijkstra with early exit per pair, OpenMP over pairs, no preprocessing"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

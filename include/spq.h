@@ -84,6 +84,9 @@ typedef struct spq_opts {
                                Floyd-Warshall skips tile updates whose pivot row or
                                column panel is entirely infinite (they cannot change
                                anything); 0: update every tile every round */
+    int32_t profile_kernels; /* 1: time every launch of the boundary-graph
+                               Floyd-Warshall's phase-3 kernel with CUDA events (see
+                               spq_build_profile); 0 (default): no per-launch events */
 } spq_opts;
 
 /* Fill *opts with the defaults (also what opts == NULL means). */
@@ -168,8 +171,13 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
 /* Device time (ms, CUDA events on the build stream) of the build's stages, in order:
  *   [0] validation and boundary detection, [1] table sizing and vertex reordering,
  *   [2] component tables (init + batched Floyd-Warshall), [3] boundary-graph assembly,
- *   [4] boundary-graph Floyd-Warshall, [5] exactness check (float32 arithmetic only).
- * Writes min(count, 6) values; returns how many it wrote (0 if h is NULL).  With the
+ *   [4] boundary-graph Floyd-Warshall, [5] exactness check and float32 -> int32
+ *   conversion (float32 arithmetic only);
+ * and, when the build ran with opts.profile_kernels = 1:
+ *   [6] summed device ms of the phase-3 kernel launches of the boundary-graph
+ *   Floyd-Warshall, [7] their number, [8] the min-plus updates they issued (128^3 per
+ *   updated tile).
+ * Writes min(count, 9) values; returns how many it wrote (0 if h is NULL).  With the
  * float32 arithmetic falling back to int32, stages 2-5 hold the int32 run's times. */
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count);
 

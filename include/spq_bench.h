@@ -21,6 +21,10 @@ extern "C" {
  * second of two identical launches).  Returns 0 or a cudaError_t code. */
 int spq_peak_minplus(int mode, int iters, int blocks_per_sm, double* updates_per_s, double* ms);
 
+/* Number of kernels this library has launched in this process so far (all entry
+ * points, all devices; the micro-benchmark above excluded). */
+unsigned long long spq_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

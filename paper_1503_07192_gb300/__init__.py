@@ -91,10 +91,12 @@ class SpqHandle:
                 "footprint_bytes": int(_lib.load().spq_footprint_bytes(self.ptr))}
 
     def profile(self) -> dict:
-        """Device milliseconds of the build stages (CUDA events)."""
-        ms = (ctypes.c_double * 6)()
-        cnt = _lib.load().spq_build_profile(self.ptr, ms, 6)
-        names = ["validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check"]
+        """Device milliseconds of the build stages (CUDA events), and the phase-3 kernel
+        timing of the boundary-graph Floyd-Warshall when built with profile_kernels."""
+        ms = (ctypes.c_double * 9)()
+        cnt = _lib.load().spq_build_profile(self.ptr, ms, 9)
+        names = ["validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check", "p3_ms", "p3_launches",
+                 "p3_updates"]
         return {names[i]: ms[i] for i in range(cnt)}
 
     def meta(self) -> dict:
@@ -183,6 +185,10 @@ def spq_query_status(h: SpqHandle, stream=None):
 
 def spq_free(h: SpqHandle):
     h.free()
+
+
+def spq_kernel_launches() -> int:
+    return int(_lib.load().spq_kernel_launches())
 
 
 def spq_strerror(status: int) -> str:

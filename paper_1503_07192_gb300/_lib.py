@@ -20,7 +20,8 @@ i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 
 
 class SpqOpts(ctypes.Structure):
-    _fields_ = [("struct_size", i32), ("arith", i32), ("order", i32), ("skip_inf_tiles", i32)]
+    _fields_ = [("struct_size", i32), ("arith", i32), ("order", i32), ("skip_inf_tiles", i32),
+                ("profile_kernels", i32)]
 
 
 SIGNATURES = {
@@ -37,6 +38,7 @@ SIGNATURES = {
     "spq_build_profile": (i32, [P, ctypes.POINTER(f64), i32]),
     "spq_peak_minplus": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(f64),
                                         ctypes.POINTER(f64)]),
+    "spq_kernel_launches": (ctypes.c_ulonglong, []),
     "spq_get_meta": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "spq_get_apsp": (ctypes.c_int, [P, i32, P, P]),
     "spq_get_bg": (ctypes.c_int, [P, P, P]),

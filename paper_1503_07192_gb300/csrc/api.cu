@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -14,6 +15,12 @@
 #include "order.h"
 
 using namespace spq;
+
+namespace spq {
+extern std::atomic<unsigned long long> g_kernel_launches;
+std::atomic<unsigned long long> g_kernel_launches{0};
+void count_launches(int n) { g_kernel_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace spq
 
 struct spq_handle {
     int device = 0;
@@ -35,6 +42,7 @@ struct spq_handle {
     size_t bytes = 0;
     double comp_updates = 0.0, bg_updates = 0.0;
     double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    FwProfile fwprof;
     std::vector<int32_t> h_csize, h_nb, h_bgoff;
     std::vector<MatDesc> h_descs;
 };
@@ -140,7 +148,8 @@ struct BuildInputs {
 // boundary-graph assembly and its Floyd-Warshall.  Sets *inexact if a float32 table
 // holds a finite entry >= 2^24.
 template <typename T>
-cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact, bool skip_inf, uint32_t* d_flag,
+cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact, bool skip_inf, bool profile,
+                         uint32_t* d_flag,
                          uint32_t* fw_scratch, int32_t max_n, bool* inexact, StageEvents& evs, cudaStream_t st) {
     *inexact = false;
     evs.mark(2, st);
@@ -162,13 +171,16 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
     }
     evs.mark(4, st);
     if (h->N > 0) {
-        if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, &h->bg_updates, st)) != cudaSuccess) return e;
+        if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, &h->bg_updates, profile ? &h->fwprof : nullptr, st)) !=
+            cudaSuccess)
+            return e;
     }
     evs.mark(5, st);
     if (check_exact) {
+        // the float32 tables become int32 ones (every entry below 2^24 is an exact integer)
         if ((e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-        if ((e = launch_check_exact((const float*)h->apsp, h->apsp_elems, d_flag, st)) != cudaSuccess) return e;
-        if (h->N > 0 && (e = launch_check_exact((const float*)h->D, h->N * h->N, d_flag, st)) != cudaSuccess) return e;
+        if ((e = launch_check_convert((float*)h->apsp, h->apsp_elems, d_flag, st)) != cudaSuccess) return e;
+        if (h->N > 0 && (e = launch_check_convert((float*)h->D, h->N * h->N, d_flag, st)) != cudaSuccess) return e;
         uint32_t f = 0;
         if ((e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
@@ -334,23 +346,24 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     CK(tmp.alloc(&fw_scratch, (size_t)fw_words));
     BuildInputs in{n, m, d_rp, d_col, d_w, d_part, f32w};
     const bool skip = opts.skip_inf_tiles != 0;
+    const bool prof = opts.profile_kernels != 0;
     if (f32w) {
         h->f32store = true;
         h->arith = SPQ_ARITH_F32;
         bool inexact = false;
-        CK(build_tables<float>(h, in, false, skip, d_flag, fw_scratch, max_n, &inexact, evs, st));
+        CK(build_tables<float>(h, in, false, skip, prof, d_flag, fw_scratch, max_n, &inexact, evs, st));
     } else {
         bool try_f32 = opts.arith != SPQ_ARITH_I32;
         bool inexact = false;
         if (try_f32) {
             h->f32store = true;
             h->arith = SPQ_ARITH_F32;
-            CK(build_tables<float>(h, in, true, skip, d_flag, fw_scratch, max_n, &inexact, evs, st));
+            CK(build_tables<float>(h, in, true, skip, prof, d_flag, fw_scratch, max_n, &inexact, evs, st));
         }
+        h->f32store = false;  // converted to int32 by the exactness check
         if (!try_f32 || inexact) {
-            h->f32store = false;
             h->arith = SPQ_ARITH_I32;
-            CK(build_tables<int32_t>(h, in, false, skip, d_flag, fw_scratch, max_n, &inexact, evs, st));
+            CK(build_tables<int32_t>(h, in, false, skip, prof, d_flag, fw_scratch, max_n, &inexact, evs, st));
         }
     }
     double cu = 0.0;
@@ -374,6 +387,7 @@ void spq_opts_default(spq_opts* o) {
     o->arith = SPQ_ARITH_AUTO;
     o->order = SPQ_ORDER_AUTO;
     o->skip_inf_tiles = 1;
+    o->profile_kernels = 0;
 }
 
 spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
@@ -500,10 +514,17 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
 
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     if (!h || !ms || count <= 0) return 0;
-    int32_t c = count < 6 ? count : 6;
-    for (int32_t i = 0; i < c; ++i) ms[i] = h->prof_ms[i];
+    double v[9];
+    for (int i = 0; i < 6; ++i) v[i] = h->prof_ms[i];
+    v[6] = h->fwprof.p3_ms;
+    v[7] = (double)h->fwprof.p3_launches;
+    v[8] = h->fwprof.p3_updates;
+    int32_t c = count < 9 ? count : 9;
+    for (int32_t i = 0; i < c; ++i) ms[i] = v[i];
     return c;
 }
+
+unsigned long long spq_kernel_launches(void) { return spq::g_kernel_launches.load(); }
 
 spq_status spq_get_meta(const spq_handle* h, int32_t* comp, int32_t* local, int32_t* csize, int32_t* nb,
                         int32_t* bg_off, void* stream) {

@@ -136,14 +136,18 @@ __global__ void k_bg_inter(int32_t n, const int64_t* __restrict__ rp, const int3
     }
 }
 
-// Flag any finite entry >= 2^24 (float32 values below 2^24 are provably exact integers).
-__global__ void k_check_exact(const float4* __restrict__ a, int64_t count4, uint32_t* __restrict__ err) {
+// Float32 -> int32 in place, flagging any finite entry >= 2^24 (float32 values below
+// 2^24 reached by the Floyd-Warshall updates are provably exact integers).
+__device__ __forceinline__ int32_t to_i32(float x, bool& bad) {
+    bad |= (x >= 16777216.0f) && !isinf(x);
+    return isinf(x) ? SPQ_INF_I32 : (int32_t)x;
+}
+__global__ void k_check_convert(float4* __restrict__ a, int64_t count4, uint32_t* __restrict__ err) {
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
         float4 x = a[i];
-        const float lim = 16777216.0f;
-        bad |= (x.x >= lim && !isinf(x.x)) | (x.y >= lim && !isinf(x.y)) | (x.z >= lim && !isinf(x.z)) |
-               (x.w >= lim && !isinf(x.w));
+        int4 y = make_int4(to_i32(x.x, bad), to_i32(x.y, bad), to_i32(x.z, bad), to_i32(x.w, bad));
+        reinterpret_cast<int4*>(a)[i] = y;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrExact);
 }
@@ -166,6 +170,7 @@ cudaError_t launch_fill_blocks(T* apsp, const MatDesc* descs, int32_t nmat, cuda
     if (nmat <= 0) return cudaSuccess;
     int blocks = nmat < 65535 ? nmat : 65535;
     k_fill_blocks<T><<<blocks, 256, 0, st>>>(apsp, descs, nmat);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -174,6 +179,7 @@ cudaError_t launch_scatter_intra(bool f32w, int32_t n, const int64_t* rp, const 
                                  const int32_t* part, const int32_t* local, const MatDesc* descs, T* apsp,
                                  cudaStream_t st) {
     k_scatter_intra<T><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, w, f32w, part, local, descs, apsp);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -182,6 +188,7 @@ cudaError_t launch_bg_fill(T* D, int64_t N, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     int64_t blocks = N < (int64_t)sm_count() * 16 ? N : (int64_t)sm_count() * 16;
     k_bg_fill<T><<<(unsigned)blocks, 256, 0, st>>>(D, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -191,6 +198,7 @@ cudaError_t launch_bg_clique(const T* apsp, const MatDesc* descs, const int32_t*
     if (k <= 0 || N <= 0) return cudaSuccess;
     int blocks = k < 65535 ? k : 65535;
     k_bg_clique<T><<<blocks, dim3(32, 8), 0, st>>>(apsp, descs, nb, bg_off, k, D, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -200,16 +208,18 @@ cudaError_t launch_bg_inter(bool f32w, int32_t n, const int64_t* rp, const int32
                             cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     k_bg_inter<T><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, w, f32w, part, local, bg_off, D, N);
+    count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_check_exact(const float* a, int64_t count, uint32_t* err, cudaStream_t st) {
+cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     int64_t c4 = count / 4;  // every table's element count is a multiple of 4
     int64_t blocks = (c4 + 255) / 256;
     int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
-    k_check_exact<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(a), c4, err);
+    k_check_convert<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4*>(a), c4, err);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,17 @@ struct MatDesc {
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Process-wide count of this library's kernel launches (read by spq_kernel_launches).
+void count_launches(int n);
+
+// Per-launch timing of the boundary-graph Floyd-Warshall's phase-3 kernel (filled only
+// when requested: CUDA events around each launch).
+struct FwProfile {
+    double p3_ms = 0.0;
+    int64_t p3_launches = 0;
+    double p3_updates = 0.0;
+};
+
 // ---- prep.cu: input validation, boundary detection, stable radix sort ----
 cudaError_t launch_validate(bool f32, int32_t n, int64_t m, const int64_t* rp, const int32_t* col, const void* w,
                             const int32_t* part, int32_t k, uint8_t* bflag, int32_t* cnt_c, int32_t* cnt_b,
@@ -73,7 +84,9 @@ template <typename T>
 cudaError_t launch_bg_inter(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
                             const int32_t* part, const int32_t* local, const int32_t* bg_off, T* D, int64_t N,
                             cudaStream_t st);
-cudaError_t launch_check_exact(const float* a, int64_t count, uint32_t* err, cudaStream_t st);
+// In place: float32 table -> int32 (+inf -> SPQ_INF_I32), flagging kErrExact if a
+// finite entry is >= 2^24 (then the converted values are not used).
+cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStream_t st);
 
 // ---- fw.cu: blocked Floyd-Warshall (Venkataraman, Sahni & Mukhopadhyaya 2003) ----
 template <typename T>
@@ -81,7 +94,8 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t ma
 // One matrix of size N, optionally skipping tiles whose pivot panel is all infinite.
 // *updates receives the number of min-plus updates issued (host-side count).
 template <typename T>
-cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, double* updates, cudaStream_t st);
+cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, double* updates, FwProfile* prof,
+                      cudaStream_t st);
 int64_t fw_single_scratch_words(int64_t N);
 
 // ---- query.cu ----

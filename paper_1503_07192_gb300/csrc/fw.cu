@@ -17,6 +17,8 @@
 // Arithmetic: int32 (add, min) or float32 (add, three-input min over two k steps).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace spq {
@@ -428,9 +430,11 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t ma
     const size_t psm = sizeof(PanelSmem<T>);
     for (int32_t r = 0; r < R; ++r) {
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r);
+        count_launches(1);
         if (R > 1) {
             k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, nullptr);
             k_phase3_batched<T><<<dim3((R - 1) * (R - 1), gy), NTH, psm, st>>>(base, d_descs, nmat, r);
+            count_launches(2);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -444,7 +448,8 @@ int64_t fw_single_scratch_words(int64_t N) {
 }
 
 template <typename T>
-cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double* updates, cudaStream_t st) {
+cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double* updates, FwProfile* prof,
+                      cudaStream_t st) {
     if (updates) *updates = 0.0;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
@@ -462,8 +467,16 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
     e = cudaMemcpyAsync(dd, &h, sizeof(MatDesc), cudaMemcpyHostToDevice, st);
     const size_t psm = sizeof(PanelSmem<T>);
     const int p3_grid = sms() * 2;
+    // optional per-launch timing of phase 3 (one event pair per round)
+    std::vector<cudaEvent_t> evs;
+    if (prof && R > 1) {
+        evs.resize(2 * (size_t)R, nullptr);
+        for (auto& ev : evs)
+            if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    }
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
         k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r);
+        count_launches(1);
         if (R > 1) {
             k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags);
             if (!skip_inf) {
@@ -471,7 +484,10 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
                 cudaMemsetAsync(flags, 0xff, R * sizeof(uint32_t), st);
             }
             k_compact<<<1, 1024, 0, st>>>(flags, R, r, list, tiles);
+            if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
             k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
+            if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
+            count_launches(3);
         }
         e = cudaGetLastError();
     }
@@ -479,6 +495,20 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ht, tiles, sizeof(ht), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(dd, st);
+    if (prof) {
+        prof->p3_ms = 0.0;
+        prof->p3_launches = 0;
+        for (size_t r = 0; e == cudaSuccess && 2 * r + 1 < evs.size(); ++r) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, evs[2 * r], evs[2 * r + 1]) == cudaSuccess) {
+                prof->p3_ms += t;
+                prof->p3_launches += 1;
+            }
+        }
+        prof->p3_updates = (double)ht * (double)T_ * T_ * T_;
+    }
+    for (auto& ev : evs)
+        if (ev) cudaEventDestroy(ev);
     if (updates) {
         double t3 = (double)T_ * T_ * T_;
         *updates = ((double)ht + (double)R * R) * t3;  // phase-3 tiles + R phase-1 and R(R-1) phase-2 tiles
@@ -488,7 +518,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
 
 template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_batched<float>(float*, const MatDesc*, int32_t, int32_t, cudaStream_t);
-template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, double*, cudaStream_t);
-template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, double*, cudaStream_t);
+template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, double*, FwProfile*, cudaStream_t);
+template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, double*, FwProfile*, cudaStream_t);
 
 }  // namespace spq

@@ -215,6 +215,7 @@ spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int3
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
     if (e == cudaSuccess) {
         k_emit_comp_pairs<<<(n + 255) / 256, 256, 0, st>>>(n, d_rp, d_col, d_part, (uint32_t)k, keys, vals, cnt);
+        count_launches(1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st);
@@ -259,6 +260,7 @@ cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t c
         k_copy_out<true><<<(unsigned)blocks, 256, 0, st>>>((const uint32_t*)src, rows, cols, ld, dst);
     else
         k_copy_out<false><<<(unsigned)blocks, 256, 0, st>>>((const uint32_t*)src, rows, cols, ld, dst);
+    count_launches(1);
     e = cudaGetLastError();
     if (!od) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(out, dst, (size_t)(rows * cols) * 4, cudaMemcpyDeviceToHost, st);

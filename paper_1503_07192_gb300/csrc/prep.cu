@@ -203,18 +203,21 @@ cudaError_t launch_validate(bool f32, int32_t n, int64_t m, const int64_t* rp, c
     else
         k_validate<int32_t>
             <<<blocks, 256, 0, st>>>(n, m, rp, col, (const int32_t*)w, part, k, bflag, cnt_c, cnt_b, err);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_make_keys(int32_t n, const int32_t* part, const uint8_t* bflag, uint32_t* keys, uint32_t* vals,
                              cudaStream_t st) {
     k_make_keys<<<(n + 255) / 256, 256, 0, st>>>(n, part, bflag, keys, vals);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign_local(int32_t n, const uint32_t* sorted_vals, const int32_t* part, const int32_t* vstart,
                                 int32_t* local, int32_t* comp, cudaStream_t st) {
     k_assign_local<<<(n + 255) / 256, 256, 0, st>>>(n, sorted_vals, part, vstart, local, comp);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -237,6 +240,7 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
         k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, st>>>(ki, n, shift, hist, ntiles);
         k_scan_excl<<<1, 1024, 0, st>>>(hist, 256 * ntiles);
         k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
+        count_launches(3);
         flip = !flip;
     }
     *in_k1 = flip;

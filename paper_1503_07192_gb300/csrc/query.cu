@@ -183,6 +183,7 @@ cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q
     } else {
         k_query<T, kOutF32><<<(unsigned)blocks, QTH, 0, st>>>(ctx, p2, q, out);
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 
