@@ -21,6 +21,16 @@ extern "C" {
  * second of two identical launches).  Returns 0 or a cudaError_t code. */
 int spq_peak_minplus(int mode, int iters, int blocks_per_sm, double* updates_per_s, double* ms);
 
+/* Host-only: the component order the build uses along the boundary-graph matrix, for
+ * a component adjacency graph given as CSR (adj_ptr[k+1], adj) with weights (boundary
+ * sizes).  method 0 = id order, 1 = level-structure nested dissection, 2 = id-range
+ * nested dissection, 3 = the least costly of the three.  Writes the order (k ids) and
+ * the three symbolic costs (Floyd-Warshall work with infinite-panel skipping, in
+ * weight^3 units) when cost_out != NULL.  Returns the method used, or -1 on bad input.
+ * Needs no GPU. */
+int spq_component_order_host(int k, const long long* adj_ptr, const int* adj, const int* weight, int method,
+                             int* order_out, double* cost_out);
+
 /* Number of kernels this library has launched in this process so far (all entry
  * points, all devices; the micro-benchmark above excluded). */
 unsigned long long spq_kernel_launches(void);

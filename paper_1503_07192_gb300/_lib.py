@@ -39,6 +39,7 @@ SIGNATURES = {
     "spq_peak_minplus": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(f64),
                                         ctypes.POINTER(f64)]),
     "spq_kernel_launches": (ctypes.c_ulonglong, []),
+    "spq_component_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, ctypes.c_int, P, P]),
     "spq_get_meta": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "spq_get_apsp": (ctypes.c_int, [P, i32, P, P]),
     "spq_get_bg": (ctypes.c_int, [P, P, P]),

@@ -368,8 +368,9 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     }
     double cu = 0.0;
     for (int32_t c = 0; c < k; ++c) {
+        // per round: the diagonal tile, R - 1 row tiles, R(R - 1)/2 upper-triangle tiles
         double R = (double)((h->h_descs[c].n + kTile - 1) / kTile);
-        cu += R * R * R * (double)kTile * kTile * kTile;
+        cu += R * (1.0 + (R - 1.0) + R * (R - 1.0) / 2.0) * (double)kTile * kTile * kTile;
     }
     h->comp_updates = cu;
     CK(cudaStreamSynchronize(st));

@@ -309,7 +309,30 @@ __global__ void __launch_bounds__(NTH, 2) k_phase2(T* __restrict__ base, const M
     }
 }
 
-// ---------------- phase 3, batched form: every tile (I, J), I, J != r ----------------
+// Upper-triangle task t (0 <= t < c(c+1)/2) -> pair (x, y), 0 <= x <= y < c, row-major.
+__device__ __forceinline__ void tri_pair(int64_t t, int64_t c, int64_t& x, int64_t& y) {
+    const double b = 2.0 * (double)c + 1.0;
+    int64_t xx = (int64_t)((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+    xx = xx < 0 ? 0 : (xx > c - 1 ? c - 1 : xx);
+    while (xx > 0 && xx * c - xx * (xx - 1) / 2 > t) --xx;
+    while (xx + 1 < c && (xx + 1) * c - (xx + 1) * xx / 2 <= t) ++xx;
+    x = xx;
+    y = xx + (t - (xx * c - xx * (xx - 1) / 2));
+}
+
+// Phase-3 update of tile (I, J), I <= J, and, by symmetry, of (J, I) = (I, J)^T.
+template <typename T>
+__device__ __forceinline__ void phase3_tile(T* __restrict__ M, int64_t n, int64_t o, int64_t I, int64_t J,
+                                            PanelSmem<T>& sm, int tid, int tx, int ty) {
+    const int64_t ci = I * T_, cj = J * T_;
+    T acc[8][8];
+    load_c<T>(acc, M, n, ci, cj, tx, ty);
+    minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+    store_c<T>(acc, M, n, ci, cj, tx, ty);
+    if (I != J) store_c_transposed<T>(acc, M, n, ci, cj, tx, ty);
+}
+
+// ---------------- phase 3, batched form: tiles (I, J), I <= J, I, J != r ----------------
 template <typename T>
 __global__ void __launch_bounds__(NTH, 2) k_phase3_batched(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                            int32_t nmat, int32_t r) {
@@ -320,23 +343,21 @@ __global__ void __launch_bounds__(NTH, 2) k_phase3_batched(T* __restrict__ base,
         const MatDesc d = descs[mi];
         const int64_t n = d.n;
         const int32_t R = (int32_t)((n + T_ - 1) / T_);
-        const int32_t Rm = R - 1;
-        if (r >= R || (int64_t)blockIdx.x >= (int64_t)Rm * Rm) continue;
-        int32_t I = (int32_t)blockIdx.x / Rm, J = (int32_t)blockIdx.x % Rm;
+        const int64_t Rm = R - 1;
+        if (r >= R || (int64_t)blockIdx.x >= Rm * (Rm + 1) / 2) continue;
+        int64_t I, J;
+        tri_pair((int64_t)blockIdx.x, Rm, I, J);
         I += (I >= r);
         J += (J >= r);
-        T* M = base + d.off;
-        const int64_t o = (int64_t)r * T_, ci = (int64_t)I * T_, cj = (int64_t)J * T_;
-        T acc[8][8];
-        load_c<T>(acc, M, n, ci, cj, tx, ty);
-        minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
-        store_c<T>(acc, M, n, ci, cj, tx, ty);
+        phase3_tile<T>(base + d.off, n, (int64_t)r * T_, I, J, sm, tid, tx, ty);
     }
 }
 
 // ---------------- phase 3, single large matrix: persistent over a tile list ----------------
-// list[0] = count c, list[1..c] = tile indices J != r whose row tile (r, J) holds a
-// finite entry; every (I, J) in list x list is updated.
+// list[0] = count c, list[1..c] = ascending tile indices J != r whose row tile (r, J)
+// holds a finite entry; every (I, J) in list x list is updated, the pairs I < J once
+// for both triangles.  Tiles outside list x list keep their values: their pivot panel
+// is entirely infinite, so min(D, inf + x) = D.
 template <typename T>
 __global__ void __launch_bounds__(NTH, 2) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
                                                         const uint32_t* __restrict__ list) {
@@ -345,13 +366,10 @@ __global__ void __launch_bounds__(NTH, 2) k_phase3_list(T* __restrict__ M, int64
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t c = list[0];
     const int64_t o = (int64_t)r * T_;
-    for (int64_t t = blockIdx.x; t < c * c; t += gridDim.x) {
-        const int64_t I = list[1 + t / c], J = list[1 + t % c];
-        const int64_t ci = I * T_, cj = J * T_;
-        T acc[8][8];
-        load_c<T>(acc, M, n, ci, cj, tx, ty);
-        minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
-        store_c<T>(acc, M, n, ci, cj, tx, ty);
+    for (int64_t t = blockIdx.x; t < c * (c + 1) / 2; t += gridDim.x) {
+        int64_t x, y;
+        tri_pair(t, c, x, y);
+        phase3_tile<T>(M, n, o, (int64_t)list[1 + x], (int64_t)list[1 + y], sm, tid, tx, ty);
     }
 }
 
@@ -385,7 +403,7 @@ __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, ui
     for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
     if (threadIdx.x == 0) {
         list[0] = cnt;
-        *tiles += (unsigned long long)cnt * cnt;
+        *tiles += (unsigned long long)cnt * (cnt + 1) / 2;
     }
 }
 
@@ -433,7 +451,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t ma
         count_launches(1);
         if (R > 1) {
             k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, nullptr);
-            k_phase3_batched<T><<<dim3((R - 1) * (R - 1), gy), NTH, psm, st>>>(base, d_descs, nmat, r);
+            k_phase3_batched<T><<<dim3((R - 1) * R / 2, gy), NTH, psm, st>>>(base, d_descs, nmat, r);
             count_launches(2);
         }
         e = cudaGetLastError();

@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "order.h"
+#include "spq_bench.h"
 
 namespace spq {
 
@@ -179,6 +180,137 @@ struct ND {
     }
 };
 
+// Nested dissection by id ranges: the node set is split at its weighted median id;
+// the separator is the side (of the two) whose nodes adjacent to the other side weigh
+// less.  Partitions numbered along a recursive bisection (recursive coordinate
+// bisection, recursive graph bisection) get their own cut lines back this way.
+void id_split_nd(const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj, const std::vector<int32_t>& wt,
+                 int32_t k, std::vector<int32_t>* out) {
+    std::vector<int32_t> side(k, 0);  // subset label during one split
+    int32_t next = 1;
+    struct Work {
+        std::vector<int32_t> nodes;  // ascending ids
+        std::vector<int32_t> sep;
+        bool emit;
+    };
+    std::vector<Work> stack;
+    {
+        std::vector<int32_t> all(k);
+        for (int32_t c = 0; c < k; ++c) all[c] = c;
+        stack.push_back({std::move(all), {}, false});
+    }
+    while (!stack.empty()) {
+        Work wk = std::move(stack.back());
+        stack.pop_back();
+        if (wk.emit) {
+            out->insert(out->end(), wk.sep.begin(), wk.sep.end());
+            continue;
+        }
+        std::vector<int32_t>& S = wk.nodes;
+        if (S.size() <= 2) {
+            out->insert(out->end(), S.begin(), S.end());
+            continue;
+        }
+        int64_t total = 0;
+        for (int32_t x : S) total += wt[x];
+        int64_t cum = 0;
+        size_t cut = 1;
+        for (size_t i = 0; i < S.size(); ++i) {
+            cum += wt[S[i]];
+            if (2 * cum >= total) {
+                cut = i + 1;
+                break;
+            }
+        }
+        if (cut >= S.size()) cut = S.size() - 1;
+        const int32_t la = next++, lb = next++;
+        for (size_t i = 0; i < S.size(); ++i) side[S[i]] = i < cut ? la : lb;
+        std::vector<int32_t> sa, sb;  // nodes of each side adjacent to the other side
+        int64_t wa = 0, wb = 0;
+        for (int32_t x : S) {
+            const int32_t other = side[x] == la ? lb : la;
+            bool touches = false;
+            for (int64_t e = ptr[x]; e < ptr[x + 1] && !touches; ++e) touches = side[adj[e]] == other;
+            if (!touches) continue;
+            if (side[x] == la) {
+                sa.push_back(x);
+                wa += wt[x];
+            } else {
+                sb.push_back(x);
+                wb += wt[x];
+            }
+        }
+        const bool use_a = wa <= wb;
+        std::vector<int32_t>& sep = use_a ? sa : sb;
+        for (int32_t x : sep) side[x] = 0;
+        std::vector<int32_t> A, B;
+        for (int32_t x : S) {
+            if (side[x] == la) A.push_back(x);
+            else if (side[x] == lb) B.push_back(x);
+            side[x] = 0;
+        }
+        stack.push_back({{}, std::move(sep), true});
+        stack.push_back({std::move(B), {}, false});
+        stack.push_back({std::move(A), {}, false});
+    }
+}
+
+// Symbolic cost of Floyd-Warshall with infinite-panel skipping, at component
+// granularity: when component p's rows are the pivots, the finite rows are those of
+// the components joined to p through components already eliminated, plus their
+// uneliminated neighbours; the work is w(p) * (their weight)^2 / 2.
+double fw_order_cost(const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
+                     const std::vector<int32_t>& wt, const std::vector<int32_t>& order) {
+    const int32_t k = (int32_t)order.size();
+    std::vector<int32_t> parent(k), elim(k, 0);
+    std::vector<int64_t> inner(k, 0), frontw(k, 0);
+    std::vector<std::vector<int32_t>> front(k);  // sorted frontier (uneliminated neighbours)
+    for (int32_t c = 0; c < k; ++c) parent[c] = c;
+    auto find = [&](int32_t x) {
+        while (parent[x] != x) {
+            parent[x] = parent[parent[x]];
+            x = parent[x];
+        }
+        return x;
+    };
+    double cost = 0.0;
+    std::vector<int32_t> merged;
+    for (int32_t p : order) {
+        elim[p] = 1;
+        int32_t rp = p;
+        inner[rp] = wt[p];
+        front[rp].clear();
+        for (int64_t e = ptr[p]; e < ptr[p + 1]; ++e)
+            if (!elim[adj[e]]) front[rp].push_back(adj[e]);
+        std::sort(front[rp].begin(), front[rp].end());
+        front[rp].erase(std::unique(front[rp].begin(), front[rp].end()), front[rp].end());
+        for (int64_t e = ptr[p]; e < ptr[p + 1]; ++e) {
+            int32_t q = adj[e];
+            if (!elim[q] || q == p) continue;
+            int32_t rq = find(q);
+            rp = find(rp);
+            if (rq == rp) continue;
+            if (front[rq].size() > front[rp].size()) std::swap(rq, rp);
+            parent[rq] = rp;
+            inner[rp] += inner[rq];
+            merged.clear();
+            std::set_union(front[rp].begin(), front[rp].end(), front[rq].begin(), front[rq].end(),
+                           std::back_inserter(merged));
+            front[rp].swap(merged);
+            std::vector<int32_t>().swap(front[rq]);
+        }
+        rp = find(rp);
+        // drop eliminated nodes (p itself) from the frontier
+        auto& F = front[rp];
+        F.erase(std::remove_if(F.begin(), F.end(), [&](int32_t x) { return elim[x] != 0; }), F.end());
+        int64_t fw = 0;
+        for (int32_t x : F) fw += wt[x];
+        const double reach = (double)(inner[rp] + fw);
+        cost += (double)wt[p] * reach * reach * 0.5;
+    }
+    return cost;
+}
+
 }  // namespace
 
 void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std::vector<int32_t>& adj,
@@ -196,7 +328,7 @@ spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int3
                            std::vector<int32_t>* order) {
     order->resize(k);
     for (int32_t c = 0; c < k; ++c) (*order)[c] = c;
-    const bool want = ord == SPQ_ORDER_DISSECTION || (ord == SPQ_ORDER_AUTO && k >= 8);
+    const bool want = ord == SPQ_ORDER_DISSECTION || (ord == SPQ_ORDER_AUTO && k >= 4);
     if (!want || k > 65536 || m == 0) return SPQ_OK;
     uint32_t *keys = nullptr, *vals = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr, *cnt = nullptr;
     const int64_t hist_words = radix_hist_words(m);
@@ -243,9 +375,55 @@ spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int3
     for (size_t i = 0; i < hk.size(); ++i) adj[i] = (int32_t)(hk[i] % (uint32_t)k);  // sorted by source
     std::vector<int32_t> w(k);
     for (int32_t c = 0; c < k; ++c) w[c] = nb[c] > 0 ? nb[c] : 1;
-    nested_dissection(k, ptr, adj, w, order);
+    // candidates: id order, level-structure nested dissection, id-range nested
+    // dissection; keep the one of least symbolic cost (ties: the earlier)
+    std::vector<std::vector<int32_t>> cand(3);
+    cand[0] = *order;
+    nested_dissection(k, ptr, adj, w, &cand[1]);
+    id_split_nd(ptr, adj, w, k, &cand[2]);
+    const size_t first = ord == SPQ_ORDER_DISSECTION ? 1 : 0;
+    size_t best = first;
+    double best_cost = fw_order_cost(ptr, adj, w, cand[first]);
+    for (size_t i = first + 1; i < cand.size(); ++i) {
+        double c = fw_order_cost(ptr, adj, w, cand[i]);
+        if (c < best_cost) {
+            best_cost = c;
+            best = i;
+        }
+    }
+    *order = std::move(cand[best]);
     return SPQ_OK;
 }
+
+}  // namespace spq
+
+extern "C" int spq_component_order_host(int k, const long long* adj_ptr, const int* adj, const int* weight,
+                                        int method, int* order_out, double* cost_out) {
+    using namespace spq;
+    if (k <= 0 || !adj_ptr || !weight || !order_out || method < 0 || method > 3) return -1;
+    std::vector<int64_t> ptr(adj_ptr, adj_ptr + k + 1);
+    std::vector<int32_t> ad(adj, adj + ptr[k]);
+    std::vector<int32_t> w(weight, weight + k);
+    std::vector<std::vector<int32_t>> cand(3);
+    cand[0].resize(k);
+    for (int32_t c = 0; c < k; ++c) cand[0][c] = c;
+    nested_dissection(k, ptr, ad, w, &cand[1]);
+    id_split_nd(ptr, ad, w, k, &cand[2]);
+    double costs[3];
+    for (int i = 0; i < 3; ++i) costs[i] = fw_order_cost(ptr, ad, w, cand[i]);
+    int pick = method;
+    if (method == 3) {
+        pick = 0;
+        for (int i = 1; i < 3; ++i)
+            if (costs[i] < costs[pick]) pick = i;
+    }
+    for (int32_t c = 0; c < k; ++c) order_out[c] = cand[pick][c];
+    if (cost_out)
+        for (int i = 0; i < 3; ++i) cost_out[i] = costs[i];
+    return pick;
+}
+
+namespace spq {
 
 cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t cols, int64_t ld, void* out,
                            cudaStream_t st) {
