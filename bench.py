@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="delaunay1m", choices=["delaunay1m", "grid64", "delaunay65k"])
+    p.add_argument("--workload", default="delaunay1m",
+                   choices=["delaunay1m", "grid64", "delaunay65k", "delaunay262k", "grid1024diag"])
     p.add_argument("--queries", type=int, default=None, help="override the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     p.add_argument("--e2e-steps", type=int, default=1)
@@ -65,6 +66,14 @@ def make_workload(name, q):
         desc = {"workload": "delaunay1m", "vertices": w.graph.n, "edges": w.graph.m // 2,
                 "components": w.k, "partition": "recursive coordinate bisection, 10 levels",
                 "weights": "int32 round(1e6 * Euclidean length)", "queries_per_step": int(w.pairs.shape[0])}
+    elif name == "delaunay262k":
+        w = gen.configs.delaunay_rcb(1 << 18, 8, q or 2_500_000, seed=1241)
+        desc = {"workload": "delaunay262k", "vertices": w.graph.n, "components": w.k,
+                "queries_per_step": int(w.pairs.shape[0])}
+    elif name == "grid1024diag":
+        w = gen.configs.grid1024diag(q=q or 10_000_000)
+        desc = {"workload": "grid1024diag", "vertices": w.graph.n, "components": w.k,
+                "partition": "32x32-vertex blocks", "queries_per_step": int(w.pairs.shape[0])}
     elif name == "delaunay65k":
         w = gen.configs.delaunay_rcb(1 << 16, 6, q or 1_000_000, seed=1240)
         desc = {"workload": "delaunay65k", "vertices": w.graph.n, "components": w.k,
@@ -250,7 +259,8 @@ def main():
 
     for i in range(args.warmup):
         st, pf, qms = step()
-        log(f"[rank {rank}] warmup {i}: build stages {[round(pf[k], 1) for k in list(pf)[:6]]} ms, query {qms:.1f} ms")
+        log(f"[rank {rank}] warmup {i}: build stages {[round(pf[k], 1) for k in list(pf)[:6]]} ms, query {qms:.1f} ms"
+            f", bg updates {st['bg_updates']:.3e}, order {int(pf.get('order_method', -1))}")
 
     # correctness spot check outside the timed region (CUDA path vs the last step's output)
     clocks = ClockSampler(local_rank)
@@ -318,6 +328,7 @@ def main():
         "build_gops": total_updates / (statistics.mean(build_ms) * 1e-3) / 1e9,
         "build_updates": total_updates,
         "n_bg": st0["n_bg"],
+        "bg_order": int(per[0][1].get("order_method", -1)),
         "query_ms": statistics.mean(query_ms),
         "query_qps": q / (statistics.mean(query_ms) * 1e-3),
         "build_stage_ms": {k: round(statistics.mean(pf[k] for _, pf, _ in per), 2)

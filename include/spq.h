@@ -68,12 +68,17 @@ typedef enum {
     SPQ_ARITH_F32 = 2,  /* float32 add and min over exact integers, falling back to int32 */
 } spq_arith;
 
-/* Order of the components along the boundary-graph matrix (its rows and columns stay
- * grouped by component, as in the paper's Fig. 1). */
+/* Order of the boundary vertices along the boundary-graph matrix.  Floyd-Warshall gives
+ * the same distances for any order of its intermediate vertices; the order decides how
+ * many tile updates are provably no-ops (an all-infinite pivot panel) and skipped. */
 typedef enum {
-    SPQ_ORDER_AUTO = 0,      /* nested dissection when it pays, else by component id */
-    SPQ_ORDER_ID = 1,        /* components in id order */
-    SPQ_ORDER_DISSECTION = 2 /* nested-dissection order of the component adjacency graph */
+    SPQ_ORDER_AUTO = 0,       /* the cheapest of the orders below, by a symbolic cost model */
+    SPQ_ORDER_ID = 1,         /* grouped by component, components in id order (the
+                                 paper's Fig. 1 layout) */
+    SPQ_ORDER_DISSECTION = 2, /* grouped by component, components in nested-dissection
+                                 order of the component adjacency graph */
+    SPQ_ORDER_VERTEX_DISSECTION = 3 /* the same bisections refined to vertex level: only
+                                 the boundary vertices on a cut become separator vertices */
 } spq_order;
 
 typedef struct spq_opts {
@@ -176,8 +181,11 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
  * and, when the build ran with opts.profile_kernels = 1:
  *   [6] summed device ms of the phase-3 kernel launches of the boundary-graph
  *   Floyd-Warshall, [7] their number, [8] the min-plus updates they issued (128^3 per
- *   updated tile).
- * Writes min(count, 9) values; returns how many it wrote (0 if h is NULL).  With the
+ *   updated tile);
+ * and [9] the order used along the boundary-graph matrix: 0 components in id order,
+ *   1 / 2 components in level-structure / id-range nested-dissection order, 3 / 4 the
+ *   vertex-level refinements of 1 / 2.
+ * Writes min(count, 10) values; returns how many it wrote (0 if h is NULL).  With the
  * float32 arithmetic falling back to int32, stages 2-5 hold the int32 run's times. */
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count);
 

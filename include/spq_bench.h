@@ -31,6 +31,14 @@ int spq_peak_minplus(int mode, int iters, int blocks_per_sm, double* updates_per
 int spq_component_order_host(int k, const long long* adj_ptr, const int* adj, const int* weight, int method,
                              int* order_out, double* cost_out);
 
+/* Host-only: the vertex-level nested-dissection order of the boundary slots for one of
+ * the component bisection rules (1 level structure, 2 id ranges).  Slots are numbered
+ * component by component (slot_off[k+1]); snb_ptr[nslots+1] / snb list, per slot, the
+ * other components its vertex has an edge into.  Writes the slots in elimination order.
+ * Returns 0, or a negative value on bad input.  Needs no GPU. */
+int spq_boundary_order_host(int k, const long long* adj_ptr, const int* adj, const long long* slot_off,
+                            const long long* snb_ptr, const int* snb, int rule, int* slot_order_out);
+
 /* Number of kernels this library has launched in this process so far (all entry
  * points, all devices; the micro-benchmark above excluded). */
 unsigned long long spq_kernel_launches(void);

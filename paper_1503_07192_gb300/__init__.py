@@ -32,6 +32,7 @@ from ._lib import (  # noqa: F401
     SPQ_ORDER_AUTO,
     SPQ_ORDER_DISSECTION,
     SPQ_ORDER_ID,
+    SPQ_ORDER_VERTEX_DISSECTION,
     SpqError,
     SpqOpts,
 )
@@ -93,10 +94,10 @@ class SpqHandle:
     def profile(self) -> dict:
         """Device milliseconds of the build stages (CUDA events), and the phase-3 kernel
         timing of the boundary-graph Floyd-Warshall when built with profile_kernels."""
-        ms = (ctypes.c_double * 9)()
-        cnt = _lib.load().spq_build_profile(self.ptr, ms, 9)
+        ms = (ctypes.c_double * 10)()
+        cnt = _lib.load().spq_build_profile(self.ptr, ms, 10)
         names = ["validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check", "p3_ms", "p3_launches",
-                 "p3_updates"]
+                 "p3_updates", "order_method"]
         return {names[i]: ms[i] for i in range(cnt)}
 
     def meta(self) -> dict:

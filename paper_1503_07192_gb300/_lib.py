@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libspq.so")
 SPQ_OK, SPQ_EINVAL, SPQ_ENOMEM, SPQ_ECUDA, SPQ_ETIMEOUT, SPQ_EUNSUPPORTED = range(6)
 SPQ_I32, SPQ_F32 = 0, 1
 SPQ_ARITH_AUTO, SPQ_ARITH_I32, SPQ_ARITH_F32 = 0, 1, 2
-SPQ_ORDER_AUTO, SPQ_ORDER_ID, SPQ_ORDER_DISSECTION = 0, 1, 2
+SPQ_ORDER_AUTO, SPQ_ORDER_ID, SPQ_ORDER_DISSECTION, SPQ_ORDER_VERTEX_DISSECTION = 0, 1, 2, 3
 SPQ_INF_I32 = 0x20000000
 
 # Every symbol include/spq.h declares, with (restype, argtypes).
@@ -40,6 +40,7 @@ SIGNATURES = {
                                         ctypes.POINTER(f64)]),
     "spq_kernel_launches": (ctypes.c_ulonglong, []),
     "spq_component_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, ctypes.c_int, P, P]),
+    "spq_boundary_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.c_int, P]),
     "spq_get_meta": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "spq_get_apsp": (ctypes.c_int, [P, i32, P, P]),
     "spq_get_bg": (ctypes.c_int, [P, P, P]),

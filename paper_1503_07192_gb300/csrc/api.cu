@@ -32,7 +32,9 @@ struct spq_handle {
     int32_t* local = nullptr;
     MatDesc* descs = nullptr;
     int32_t* nb = nullptr;
-    int32_t* bg_off = nullptr;
+    int32_t* bg_off = nullptr;  // first slot of each component (component-grouped numbering)
+    int32_t* bgpos = nullptr;   // matrix position of each slot
+    int32_t order_method = 0;
     int32_t* csize = nullptr;
     void* apsp = nullptr;
     void* D = nullptr;
@@ -92,7 +94,7 @@ struct Temps {
 };
 
 void free_handle_memory(spq_handle* h) {
-    void* ps[] = {h->comp, h->local, h->descs, h->nb, h->bg_off, h->csize, h->apsp, h->D, h->err};
+    void* ps[] = {h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, h->csize, h->apsp, h->D, h->err};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -164,9 +166,10 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
     evs.mark(3, st);
     if (h->N > 0) {
         if ((e = launch_bg_fill<T>(D, h->N, st)) != cudaSuccess) return e;
-        if ((e = launch_bg_clique<T>(apsp, h->descs, h->nb, h->bg_off, h->k, D, h->N, st)) != cudaSuccess) return e;
-        if ((e = launch_bg_inter<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->bg_off, D, h->N, st)) !=
-            cudaSuccess)
+        if ((e = launch_bg_clique<T>(apsp, h->descs, h->nb, h->bg_off, h->bgpos, h->k, D, h->N, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_bg_inter<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->bg_off, h->bgpos, D,
+                                    h->N, st)) != cudaSuccess)
             return e;
     }
     evs.mark(4, st);
@@ -274,23 +277,11 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         max_n = std::max(max_n, ld);
     }
     h->apsp_elems = acc;
-    // component order along the boundary-graph matrix
-    std::vector<int32_t> corder;
-    {
-        spq_order ord = (spq_order)opts.order;
-        if (ord == SPQ_ORDER_ID) {
-            corder.resize(k);
-            for (int32_t c = 0; c < k; ++c) corder[c] = c;
-        } else {
-            // adjacency of components (pairs joined by an inter-component edge), from the GPU
-            spq_status s = component_order(n, m, d_rp, d_col, d_part, k, h->h_nb, ord, st, &corder);
-            if (s != SPQ_OK) return s;
-        }
-    }
+    // boundary slots, numbered component by component (their matrix positions, bgpos,
+    // are chosen after the reordering below)
     h->h_bgoff.assign(k, 0);
     int64_t bo = 0;
-    for (int32_t i = 0; i < k; ++i) {
-        int32_t c = corder[i];
+    for (int32_t c = 0; c < k; ++c) {
         h->h_bgoff[c] = (int32_t)bo;
         bo += h->h_nb[c];
     }
@@ -312,6 +303,7 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     CK(dev_alloc(&h->descs, (size_t)k, &bytes));
     CK(dev_alloc(&h->nb, (size_t)k, &bytes));
     CK(dev_alloc(&h->bg_off, (size_t)k, &bytes));
+    CK(dev_alloc(&h->bgpos, (size_t)h->nbg, &bytes));
     CK(dev_alloc(&h->csize, (size_t)k, &bytes));
     CK(dev_alloc(&h->err, 4, &bytes));
     CK(dev_alloc((uint32_t**)&h->apsp, (size_t)h->apsp_elems, &bytes));
@@ -339,6 +331,16 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         int key_bits = bits_for(2 * (uint64_t)k - 1);
         CK(radix_sort_pairs(k0, v0, k1, v1, hist, n, key_bits, &in_k1, st));
         CK(launch_assign_local(n, in_k1 ? v1 : v0, d_part, d_vstart, h->local, h->comp, st));
+    }
+
+    // ---- positions of the boundary slots along the boundary-graph matrix ----
+    if (h->nbg > 0) {
+        std::vector<int32_t> bgpos;
+        spq_status s = boundary_order(n, m, d_rp, d_col, d_part, h->local, h->bg_off, k, h->h_nb,
+                                      (spq_order)opts.order, st, &bgpos, &h->order_method);
+        if (s != SPQ_OK) return s;
+        CK(cudaMemcpyAsync(h->bgpos, bgpos.data(), bgpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // bgpos (host) goes out of scope
     }
 
     // ---- tables: component APSP, boundary graph, boundary-graph APSP ----
@@ -403,7 +405,7 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
         if (opts->struct_size < (int32_t)sizeof(spq_opts)) return SPQ_EINVAL;
         o = *opts;
         if (o.arith < SPQ_ARITH_AUTO || o.arith > SPQ_ARITH_F32) return SPQ_EINVAL;
-        if (o.order < SPQ_ORDER_AUTO || o.order > SPQ_ORDER_DISSECTION) return SPQ_EINVAL;
+        if (o.order < SPQ_ORDER_AUTO || o.order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
     }
     spq_handle* h = new (std::nothrow) spq_handle();
     if (!h) return SPQ_ENOMEM;
@@ -436,11 +438,11 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
     const bool out_f32 = h->wt == SPQ_F32;
     auto launch = [&](const int32_t* p, void* o) -> cudaError_t {
         if (h->f32store) {
-            QueryCtx<float> c{h->n, h->comp, h->local, h->descs, h->nb, h->bg_off, (const float*)h->apsp,
+            QueryCtx<float> c{h->n,   h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
                               (const float*)h->D, h->N, h->err};
             return launch_query<float>(c, p, q, o, out_f32, st);
         }
-        QueryCtx<int32_t> c{h->n, h->comp, h->local, h->descs, h->nb, h->bg_off, (const int32_t*)h->apsp,
+        QueryCtx<int32_t> c{h->n,     h->comp,   h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
                             (const int32_t*)h->D, h->N, h->err};
         return launch_query<int32_t>(c, p, q, o, out_f32, st);
     };
@@ -515,12 +517,13 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
 
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     if (!h || !ms || count <= 0) return 0;
-    double v[9];
+    double v[10];
     for (int i = 0; i < 6; ++i) v[i] = h->prof_ms[i];
     v[6] = h->fwprof.p3_ms;
     v[7] = (double)h->fwprof.p3_launches;
     v[8] = h->fwprof.p3_updates;
-    int32_t c = count < 9 ? count : 9;
+    v[9] = (double)h->order_method;
+    int32_t c = count < 10 ? count : 10;
     for (int32_t i = 0; i < c; ++i) ms[i] = v[i];
     return c;
 }
@@ -556,7 +559,7 @@ spq_status spq_get_apsp(const spq_handle* h, int32_t c, void* out, void* stream)
     if (sz == 0) return SPQ_OK;
     const MatDesc d = h->h_descs[c];
     const void* src = (const char*)h->apsp + d.off * 4;
-    return copy_table_out(h->f32store && h->wt == SPQ_I32, src, sz, sz, d.n, out, st) == cudaSuccess
+    return copy_table_out(h->f32store && h->wt == SPQ_I32, src, sz, sz, d.n, nullptr, out, st) == cudaSuccess
                ? SPQ_OK
                : cuda_fail(cudaGetLastError());
 }
@@ -565,7 +568,7 @@ spq_status spq_get_bg(const spq_handle* h, void* out, void* stream) {
     if (!h || !out) return SPQ_EINVAL;
     if (h->nbg == 0) return SPQ_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    return copy_table_out(h->f32store && h->wt == SPQ_I32, h->D, h->nbg, h->nbg, h->N, out, st) == cudaSuccess
+    return copy_table_out(h->f32store && h->wt == SPQ_I32, h->D, h->nbg, h->nbg, h->N, h->bgpos, out, st) == cudaSuccess
                ? SPQ_OK
                : cuda_fail(cudaGetLastError());
 }

@@ -99,19 +99,22 @@ __global__ void k_bg_fill(T* __restrict__ D, int64_t N) {
 }
 
 // Clique edges of Algorithm 1, line 4: D[B(C), B(C)] = APSP(C)[0:|B|, 0:|B|] (the
-// boundary vertices have the lowest local indices).  One CTA per component at a time.
+// boundary vertices have the lowest local indices), at the slots' matrix positions.
+// One CTA per component at a time.
 template <typename T>
 __global__ void k_bg_clique(const T* __restrict__ apsp, const MatDesc* __restrict__ descs,
-                            const int32_t* __restrict__ nb, const int32_t* __restrict__ bg_off, int32_t k,
-                            T* __restrict__ D, int64_t N) {
+                            const int32_t* __restrict__ nb, const int32_t* __restrict__ bg_off,
+                            const int32_t* __restrict__ bgpos, int32_t k, T* __restrict__ D, int64_t N) {
     for (int32_t c = blockIdx.x; c < k; c += gridDim.x) {
         int32_t b = nb[c];
         if (b == 0) continue;
         MatDesc d = descs[c];
         const T* A = apsp + d.off;
-        int64_t o = bg_off[c];
-        for (int32_t i = threadIdx.y; i < b; i += blockDim.y)
-            for (int32_t j = threadIdx.x; j < b; j += blockDim.x) D[(o + i) * N + o + j] = A[(int64_t)i * d.n + j];
+        const int32_t* pos = bgpos + bg_off[c];
+        for (int32_t i = threadIdx.y; i < b; i += blockDim.y) {
+            T* row = D + (int64_t)pos[i] * N;
+            for (int32_t j = threadIdx.x; j < b; j += blockDim.x) row[pos[j]] = A[(int64_t)i * d.n + j];
+        }
     }
 }
 
@@ -120,8 +123,8 @@ __global__ void k_bg_clique(const T* __restrict__ apsp, const MatDesc* __restric
 template <typename T>
 __global__ void k_bg_inter(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const void* __restrict__ w, bool f32w, const int32_t* __restrict__ part,
-                           const int32_t* __restrict__ local, const int32_t* __restrict__ bg_off, T* __restrict__ D,
-                           int64_t N) {
+                           const int32_t* __restrict__ local, const int32_t* __restrict__ bg_off,
+                           const int32_t* __restrict__ bgpos, T* __restrict__ D, int64_t N) {
     int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
     int32_t cu = part[u];
@@ -130,8 +133,8 @@ __global__ void k_bg_inter(int32_t n, const int64_t* __restrict__ rp, const int3
         int32_t v = col[e];
         int32_t cv = part[v];
         if (cv == cu) continue;
-        if (bu < 0) bu = (int64_t)bg_off[cu] + local[u];
-        int64_t bv = (int64_t)bg_off[cv] + local[v];
+        if (bu < 0) bu = bgpos[bg_off[cu] + local[u]];
+        int64_t bv = bgpos[bg_off[cv] + local[v]];
         atomic_min_cell<T>(D + bu * N + bv, weight_as<T>(w, e, f32w));
     }
 }
@@ -193,21 +196,21 @@ cudaError_t launch_bg_fill(T* D, int64_t N, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t launch_bg_clique(const T* apsp, const MatDesc* descs, const int32_t* nb, const int32_t* bg_off, int32_t k,
-                             T* D, int64_t N, cudaStream_t st) {
+cudaError_t launch_bg_clique(const T* apsp, const MatDesc* descs, const int32_t* nb, const int32_t* bg_off,
+                             const int32_t* bgpos, int32_t k, T* D, int64_t N, cudaStream_t st) {
     if (k <= 0 || N <= 0) return cudaSuccess;
     int blocks = k < 65535 ? k : 65535;
-    k_bg_clique<T><<<blocks, dim3(32, 8), 0, st>>>(apsp, descs, nb, bg_off, k, D, N);
+    k_bg_clique<T><<<blocks, dim3(32, 8), 0, st>>>(apsp, descs, nb, bg_off, bgpos, k, D, N);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_bg_inter(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
-                            const int32_t* part, const int32_t* local, const int32_t* bg_off, T* D, int64_t N,
-                            cudaStream_t st) {
+                            const int32_t* part, const int32_t* local, const int32_t* bg_off, const int32_t* bgpos, T* D,
+                            int64_t N, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    k_bg_inter<T><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, w, f32w, part, local, bg_off, D, N);
+    k_bg_inter<T><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, w, f32w, part, local, bg_off, bgpos, D, N);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -228,10 +231,11 @@ cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStr
     template cudaError_t launch_scatter_intra<T>(bool, int32_t, const int64_t*, const int32_t*, const void*,       \
                                                  const int32_t*, const int32_t*, const MatDesc*, T*, cudaStream_t); \
     template cudaError_t launch_bg_fill<T>(T*, int64_t, cudaStream_t);                                             \
-    template cudaError_t launch_bg_clique<T>(const T*, const MatDesc*, const int32_t*, const int32_t*, int32_t, T*, \
-                                             int64_t, cudaStream_t);                                               \
+    template cudaError_t launch_bg_clique<T>(const T*, const MatDesc*, const int32_t*, const int32_t*,           \
+                                             const int32_t*, int32_t, T*, int64_t, cudaStream_t);                 \
     template cudaError_t launch_bg_inter<T>(bool, int32_t, const int64_t*, const int32_t*, const void*,            \
-                                            const int32_t*, const int32_t*, const int32_t*, T*, int64_t, cudaStream_t);
+                                            const int32_t*, const int32_t*, const int32_t*, const int32_t*, T*,   \
+                                            int64_t, cudaStream_t);
 SPQ_INST(int32_t)
 SPQ_INST(float)
 

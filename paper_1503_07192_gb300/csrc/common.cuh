@@ -78,12 +78,12 @@ cudaError_t launch_scatter_intra(bool f32w, int32_t n, const int64_t* rp, const 
 template <typename T>
 cudaError_t launch_bg_fill(T* D, int64_t N, cudaStream_t st);
 template <typename T>
-cudaError_t launch_bg_clique(const T* apsp, const MatDesc* descs, const int32_t* nb, const int32_t* bg_off, int32_t k,
-                             T* D, int64_t N, cudaStream_t st);
+cudaError_t launch_bg_clique(const T* apsp, const MatDesc* descs, const int32_t* nb, const int32_t* bg_off,
+                             const int32_t* bgpos, int32_t k, T* D, int64_t N, cudaStream_t st);
 template <typename T>
 cudaError_t launch_bg_inter(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
-                            const int32_t* part, const int32_t* local, const int32_t* bg_off, T* D, int64_t N,
-                            cudaStream_t st);
+                            const int32_t* part, const int32_t* local, const int32_t* bg_off, const int32_t* bgpos, T* D,
+                            int64_t N, cudaStream_t st);
 // In place: float32 table -> int32 (+inf -> SPQ_INF_I32), flagging kErrExact if a
 // finite entry is >= 2^24 (then the converted values are not used).
 cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStream_t st);
@@ -107,6 +107,7 @@ struct QueryCtx {
     const MatDesc* descs;
     const int32_t* nb;
     const int32_t* bg_off;
+    const int32_t* bgpos;
     const T* apsp;
     const T* D;
     int64_t N;

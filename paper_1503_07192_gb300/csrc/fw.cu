@@ -195,6 +195,42 @@ __device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>
     }
 }
 
+// float32 form: the sums of two neighbouring columns come from one packed f32x2 add
+// (sm_100 family), and a three-input min folds two k steps into each accumulator.
+template <>
+__device__ __forceinline__ void compute_chunk<float>(float (&acc)[8][8], const PanelSmem<float>& sm, int s, int tx,
+                                                     int ty) {
+#pragma unroll 1
+    for (int kk = 0; kk < KC; kk += 2) {
+        const float4 x0 = *reinterpret_cast<const float4*>(&sm.a[s][kk][ty * 4]);
+        const float4 x1 = *reinterpret_cast<const float4*>(&sm.a[s][kk][64 + ty * 4]);
+        const float4 y0 = *reinterpret_cast<const float4*>(&sm.a[s][kk + 1][ty * 4]);
+        const float4 y1 = *reinterpret_cast<const float4*>(&sm.a[s][kk + 1][64 + ty * 4]);
+        const float4 z0 = *reinterpret_cast<const float4*>(&sm.b[s][kk][tx * 4]);
+        const float4 z1 = *reinterpret_cast<const float4*>(&sm.b[s][kk][64 + tx * 4]);
+        const float4 w0 = *reinterpret_cast<const float4*>(&sm.b[s][kk + 1][tx * 4]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&sm.b[s][kk + 1][64 + tx * 4]);
+        const float a0[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const float a1[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+        const float2 b0[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
+                              make_float2(z1.z, z1.w)};
+        const float2 b1[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                              make_float2(w1.z, w1.w)};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2 p0 = make_float2(a0[i], a0[i]);
+            const float2 p1 = make_float2(a1[i], a1[i]);
+#pragma unroll
+            for (int jp = 0; jp < 4; ++jp) {
+                const float2 s0 = __fadd2_rn(p0, b0[jp]);
+                const float2 s1 = __fadd2_rn(p1, b1[jp]);
+                acc[i][2 * jp] = fmin3(acc[i][2 * jp], s0.x, s1.x);
+                acc[i][2 * jp + 1] = fmin3(acc[i][2 * jp + 1], s0.y, s1.y);
+            }
+        }
+    }
+}
+
 // acc = min(acc, A (x) B) with A[i][k] = M[arow0 + k][acol0 + i] and
 // B[k][j] = M[arow0 + k][bcol0 + j], k over the pivot block [arow0, arow0 + 128).
 template <typename T>
@@ -310,14 +346,16 @@ __global__ void __launch_bounds__(NTH, 2) k_phase2(T* __restrict__ base, const M
 }
 
 // Upper-triangle task t (0 <= t < c(c+1)/2) -> pair (x, y), 0 <= x <= y < c, row-major.
+// (float estimate of the row, then exact integer correction; c < 2^16 tiles.)
 __device__ __forceinline__ void tri_pair(int64_t t, int64_t c, int64_t& x, int64_t& y) {
-    const double b = 2.0 * (double)c + 1.0;
-    int64_t xx = (int64_t)((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
-    xx = xx < 0 ? 0 : (xx > c - 1 ? c - 1 : xx);
-    while (xx > 0 && xx * c - xx * (xx - 1) / 2 > t) --xx;
-    while (xx + 1 < c && (xx + 1) * c - (xx + 1) * xx / 2 <= t) ++xx;
+    const int32_t ti = (int32_t)t, ci = (int32_t)c;
+    const float b = 2.0f * (float)ci + 1.0f;
+    int32_t xx = (int32_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)ti, 0.0f))) * 0.5f);
+    xx = xx < 0 ? 0 : (xx > ci - 1 ? ci - 1 : xx);
+    while (xx > 0 && xx * ci - xx * (xx - 1) / 2 > ti) --xx;
+    while (xx + 1 < ci && (xx + 1) * ci - (xx + 1) * xx / 2 <= ti) ++xx;
     x = xx;
-    y = xx + (t - (xx * c - xx * (xx - 1) / 2));
+    y = xx + (ti - (xx * ci - xx * (xx - 1) / 2));
 }
 
 // Phase-3 update of tile (I, J), I <= J, and, by symmetry, of (J, I) = (I, J)^T.

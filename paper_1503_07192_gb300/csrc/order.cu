@@ -30,6 +30,41 @@ __global__ void k_emit_comp_pairs(int32_t n, const int64_t* __restrict__ rp, con
     }
 }
 
+// One pair (slot of u, component of v) per slot u -> v joining two components; the slot
+// of boundary vertex u is slot_off[part[u]] + local[u] (component-grouped numbering).
+__global__ void k_emit_slot_pairs(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ part, const int32_t* __restrict__ local,
+                                  const int32_t* __restrict__ slot_off, int32_t* __restrict__ slots,
+                                  int32_t* __restrict__ comps, uint32_t* __restrict__ count) {
+    int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t cu = part[u];
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+        const int32_t cv = part[col[e]];
+        if (cv == cu) continue;
+        uint32_t i = atomicAdd(count, 1u);
+        slots[i] = slot_off[cu] + local[u];
+        comps[i] = cv;
+    }
+}
+
+// out[i][j] = src[pos[i]][pos[j]] (i, j < rows): the boundary-graph matrix in slot order.
+template <bool CONV>
+__global__ void k_gather_out(const uint32_t* __restrict__ src, int64_t rows, int64_t ld,
+                             const int32_t* __restrict__ pos, uint32_t* __restrict__ dst) {
+    for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+        const int64_t ri = pos[i];
+        for (int64_t j = threadIdx.x; j < rows; j += blockDim.x) {
+            uint32_t x = src[ri * ld + pos[j]];
+            if (CONV) {
+                float f = __uint_as_float(x);
+                x = isinf(f) ? (uint32_t)SPQ_INF_I32 : (uint32_t)(int32_t)f;
+            }
+            dst[i * rows + j] = x;
+        }
+    }
+}
+
 template <bool CONV>
 __global__ void k_copy_out(const uint32_t* __restrict__ src, int64_t rows, int64_t cols, int64_t ld,
                            uint32_t* __restrict__ dst) {
@@ -311,6 +346,161 @@ double fw_order_cost(const std::vector<int64_t>& ptr, const std::vector<int32_t>
     return cost;
 }
 
+// Vertex-level nested dissection of the boundary graph, following a bisection of the
+// component set (rule 1: level structure, rule 2: id ranges).  At each split (A, B)
+// the separator is the lighter of: the remaining boundary slots of A-components with an
+// edge into a B-component, or the same for B.  Every path of the boundary graph between
+// the two sides uses an edge of G between an A-component and a B-component, whose two
+// ends are such slots, so either set separates (the clique edges stay inside one
+// component, hence inside one side).  Slots: component-grouped numbering, slot_off[c]
+// .. slot_off[c+1]-1 for component c in local order.  Emits every slot once.
+void vertex_nd(int rule, int32_t k, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
+               const std::vector<int64_t>& slot_off, const std::vector<int64_t>& snb_ptr,
+               const std::vector<int32_t>& snb, std::vector<int32_t>* out) {
+    const int64_t nslots = slot_off[k];
+    std::vector<uint8_t> removed(nslots, 0);
+    std::vector<int32_t> remain(k);
+    for (int32_t c = 0; c < k; ++c) remain[c] = (int32_t)(slot_off[c + 1] - slot_off[c]);
+    std::vector<int32_t> side(k, 0), level(k, -1);
+    int32_t next = 1;
+    auto emit_comp = [&](int32_t c) {
+        for (int64_t sl = slot_off[c]; sl < slot_off[c + 1]; ++sl)
+            if (!removed[sl]) {
+                removed[sl] = 1;
+                out->push_back((int32_t)sl);
+            }
+        remain[c] = 0;
+    };
+    struct Work {
+        std::vector<int32_t> comps;  // ascending ids
+        std::vector<int32_t> sep;    // slots to emit
+        bool emit;
+    };
+    std::vector<Work> stack;
+    {
+        std::vector<int32_t> all(k);
+        for (int32_t c = 0; c < k; ++c) all[c] = c;
+        stack.push_back({std::move(all), {}, false});
+    }
+    std::vector<int32_t> q;
+    while (!stack.empty()) {
+        Work wk = std::move(stack.back());
+        stack.pop_back();
+        if (wk.emit) {
+            out->insert(out->end(), wk.sep.begin(), wk.sep.end());
+            continue;
+        }
+        std::vector<int32_t>& S = wk.comps;
+        int64_t total = 0;
+        for (int32_t c : S) total += remain[c];
+        if (S.size() <= 1 || total == 0) {
+            for (int32_t c : S) emit_comp(c);
+            continue;
+        }
+        const int32_t la = next++, lb = next++;
+        bool ok = true;
+        if (rule == 2) {
+            int64_t cum = 0;
+            size_t cut = S.size() - 1;
+            for (size_t i = 0; i < S.size(); ++i) {
+                cum += remain[S[i]];
+                if (2 * cum >= total) {
+                    cut = i + 1;
+                    break;
+                }
+            }
+            if (cut >= S.size()) cut = S.size() - 1;
+            if (cut == 0) cut = 1;
+            for (size_t i = 0; i < S.size(); ++i) side[S[i]] = i < cut ? la : lb;
+        } else {
+            for (int32_t c : S) side[c] = la;  // membership mark for the BFS
+            auto bfs = [&](int32_t s0) {
+                q.clear();
+                q.push_back(s0);
+                level[s0] = 0;
+                for (size_t h = 0; h < q.size(); ++h) {
+                    int32_t x = q[h];
+                    for (int64_t e = ptr[x]; e < ptr[x + 1]; ++e) {
+                        int32_t y = adj[e];
+                        if (side[y] == la && level[y] < 0) {
+                            level[y] = level[x] + 1;
+                            q.push_back(y);
+                        }
+                    }
+                }
+            };
+            auto clear = [&]() {
+                for (int32_t x : q) level[x] = -1;
+            };
+            bfs(S[0]);
+            if (q.size() < S.size()) {  // disconnected: one piece against the rest
+                for (int32_t c : S) side[c] = level[c] >= 0 ? la : lb;
+                clear();
+            } else {
+                int32_t far = q.back();
+                clear();
+                bfs(far);
+                int32_t far2 = q.back();
+                clear();
+                bfs(far2);
+                const int32_t hmax = level[q.back()];
+                if (hmax < 1) {
+                    ok = false;
+                    clear();
+                } else {
+                    std::vector<int64_t> lw(hmax + 1, 0);
+                    for (int32_t x : q) lw[level[x]] += remain[x];
+                    int64_t cum = 0;
+                    int32_t L = 0;
+                    for (int32_t l = 0; l <= hmax; ++l) {
+                        cum += lw[l];
+                        if (2 * cum >= total) {
+                            L = l;
+                            break;
+                        }
+                    }
+                    if (L > hmax - 1) L = hmax - 1;
+                    for (int32_t x : q) side[x] = level[x] <= L ? la : lb;
+                    clear();
+                }
+            }
+        }
+        if (!ok) {
+            for (int32_t c : S) {
+                side[c] = 0;
+                emit_comp(c);
+            }
+            continue;
+        }
+        std::vector<int32_t> sa, sb;
+        for (int32_t c : S) {
+            const int32_t other = side[c] == la ? lb : la;
+            std::vector<int32_t>& dst = side[c] == la ? sa : sb;
+            for (int64_t sl = slot_off[c]; sl < slot_off[c + 1]; ++sl) {
+                if (removed[sl]) continue;
+                bool touches = false;
+                for (int64_t e = snb_ptr[sl]; e < snb_ptr[sl + 1] && !touches; ++e) touches = side[snb[e]] == other;
+                if (touches) dst.push_back((int32_t)sl);
+            }
+        }
+        std::vector<int32_t>& sep = sa.size() <= sb.size() ? sa : sb;
+        for (int32_t sl : sep) removed[sl] = 1;
+        // remaining counts per component
+        for (int32_t sl : sep) {
+            int32_t c = (int32_t)(std::upper_bound(slot_off.begin(), slot_off.end(), (int64_t)sl) - slot_off.begin()) - 1;
+            remain[c]--;
+        }
+        std::vector<int32_t> A, B;
+        for (int32_t c : S) {
+            (side[c] == la ? A : B).push_back(c);
+            side[c] = 0;
+        }
+        stack.push_back({{}, std::move(sep), true});
+        stack.push_back({std::move(B), {}, false});
+        stack.push_back({std::move(A), {}, false});
+    }
+}
+
 }  // namespace
 
 void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std::vector<int32_t>& adj,
@@ -323,16 +513,21 @@ void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std
     nd.run(std::move(all));
 }
 
-spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
-                           int32_t k, const std::vector<int32_t>& nb, spq_order ord, cudaStream_t st,
-                           std::vector<int32_t>* order) {
-    order->resize(k);
-    for (int32_t c = 0; c < k; ++c) (*order)[c] = c;
-    const bool want = ord == SPQ_ORDER_DISSECTION || (ord == SPQ_ORDER_AUTO && k >= 4);
-    if (!want || k > 65536 || m == 0) return SPQ_OK;
+spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
+                          const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
+                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method) {
+    std::vector<int64_t> slot_off(k + 1, 0);
+    for (int32_t c = 0; c < k; ++c) slot_off[c + 1] = slot_off[c] + nb[c];
+    const int64_t nslots = slot_off[k];
+    bgpos->resize(nslots);
+    for (int64_t i = 0; i < nslots; ++i) (*bgpos)[i] = (int32_t)i;
+    *method = 0;
+    const bool want = ord != SPQ_ORDER_ID && k >= 4;
+    if (!want || k > 65536 || m == 0 || nslots == 0) return SPQ_OK;
+    cudaError_t e = cudaSuccess;
+    // ---- component adjacency (GPU emit, GPU radix sort, host unique) ----
     uint32_t *keys = nullptr, *vals = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr, *cnt = nullptr;
     const int64_t hist_words = radix_hist_words(m);
-    cudaError_t e = cudaSuccess;
     auto A = [&](uint32_t** p, size_t c) {
         if (e == cudaSuccess) e = cudaMallocAsync((void**)p, (c ? c : 1) * sizeof(uint32_t), st);
     };
@@ -363,10 +558,32 @@ spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int3
             e = cudaMemcpyAsync(hk.data(), in_k1 ? k1 : keys, hc * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
+    // ---- (slot, neighbour component) pairs for the vertex-level separators ----
+    std::vector<int32_t> hs, hcmp;
+    if (e == cudaSuccess && hc > 0 && ord != SPQ_ORDER_DISSECTION) {
+        int32_t* ps = (int32_t*)k1;  // reuse: hc <= m words each
+        int32_t* pc = (int32_t*)v1;
+        e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
+        if (e == cudaSuccess) {
+            k_emit_slot_pairs<<<(n + 255) / 256, 256, 0, st>>>(n, d_rp, d_col, d_part, d_local, d_slot_off, ps, pc,
+                                                                 cnt);
+            count_launches(1);
+            e = cudaGetLastError();
+        }
+        uint32_t hc2 = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc2, cnt, sizeof(hc2), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        hs.resize(hc2);
+        hcmp.resize(hc2);
+        if (e == cudaSuccess && hc2 > 0) e = cudaMemcpyAsync(hs.data(), ps, hc2 * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && hc2 > 0) e = cudaMemcpyAsync(hcmp.data(), pc, hc2 * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     uint32_t* ps[] = {keys, vals, k1, v1, hist, cnt};
     for (uint32_t* p : ps)
         if (p) cudaFreeAsync(p, st);
     if (e != cudaSuccess) return SPQ_ECUDA;
+    if (hc == 0) return SPQ_OK;
     hk.erase(std::unique(hk.begin(), hk.end()), hk.end());
     std::vector<int64_t> ptr(k + 1, 0);
     for (uint32_t key : hk) ptr[key / (uint32_t)k + 1]++;
@@ -376,12 +593,13 @@ spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int3
     std::vector<int32_t> w(k);
     for (int32_t c = 0; c < k; ++c) w[c] = nb[c] > 0 ? nb[c] : 1;
     // candidates: id order, level-structure nested dissection, id-range nested
-    // dissection; keep the one of least symbolic cost (ties: the earlier)
+    // dissection of the components; keep the one of least symbolic cost
     std::vector<std::vector<int32_t>> cand(3);
-    cand[0] = *order;
+    cand[0].resize(k);
+    for (int32_t c = 0; c < k; ++c) cand[0][c] = c;
     nested_dissection(k, ptr, adj, w, &cand[1]);
     id_split_nd(ptr, adj, w, k, &cand[2]);
-    const size_t first = ord == SPQ_ORDER_DISSECTION ? 1 : 0;
+    const size_t first = (ord == SPQ_ORDER_AUTO) ? 0 : 1;
     size_t best = first;
     double best_cost = fw_order_cost(ptr, adj, w, cand[first]);
     for (size_t i = first + 1; i < cand.size(); ++i) {
@@ -391,7 +609,36 @@ spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int3
             best = i;
         }
     }
-    *order = std::move(cand[best]);
+    *method = (int32_t)best;
+    if (best == 0) return SPQ_OK;
+    std::vector<int32_t> slot_order;
+    slot_order.reserve(nslots);
+    if (ord == SPQ_ORDER_DISSECTION) {
+        for (int32_t c : cand[best])
+            for (int64_t sl = slot_off[c]; sl < slot_off[c + 1]; ++sl) slot_order.push_back((int32_t)sl);
+    } else {
+        // per-slot neighbour components (counting sort by slot, then unique per slot)
+        std::vector<int64_t> snb_ptr(nslots + 1, 0);
+        for (int32_t sl : hs) snb_ptr[sl + 1]++;
+        for (int64_t i = 0; i < nslots; ++i) snb_ptr[i + 1] += snb_ptr[i];
+        std::vector<int32_t> snb(hs.size());
+        std::vector<int64_t> fill(snb_ptr.begin(), snb_ptr.end() - 1);
+        for (size_t i = 0; i < hs.size(); ++i) snb[fill[hs[i]]++] = hcmp[i];
+        std::vector<int64_t> uptr(nslots + 1, 0);
+        int64_t wpos = 0;
+        for (int64_t sl = 0; sl < nslots; ++sl) {
+            auto b = snb.begin() + snb_ptr[sl], en = snb.begin() + snb_ptr[sl + 1];
+            std::sort(b, en);
+            auto u = std::unique(b, en);
+            uptr[sl] = wpos;
+            for (auto it = b; it != u; ++it) snb[wpos++] = *it;
+        }
+        uptr[nslots] = wpos;
+        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order);
+        *method = (int32_t)best + 2;
+    }
+    if ((int64_t)slot_order.size() != nslots) return SPQ_EINVAL;  // cannot happen: every slot is emitted once
+    for (int64_t i = 0; i < nslots; ++i) (*bgpos)[slot_order[i]] = (int32_t)i;
     return SPQ_OK;
 }
 
@@ -423,10 +670,27 @@ extern "C" int spq_component_order_host(int k, const long long* adj_ptr, const i
     return pick;
 }
 
+extern "C" int spq_boundary_order_host(int k, const long long* adj_ptr, const int* adj, const long long* slot_off,
+                                       const long long* snb_ptr, const int* snb, int rule, int* slot_order_out) {
+    using namespace spq;
+    if (k <= 0 || !adj_ptr || !slot_off || !snb_ptr || !slot_order_out || rule < 1 || rule > 2) return -1;
+    std::vector<int64_t> ptr(adj_ptr, adj_ptr + k + 1);
+    std::vector<int32_t> ad(adj, adj + ptr[k]);
+    std::vector<int64_t> so(slot_off, slot_off + k + 1);
+    const int64_t ns = so[k];
+    std::vector<int64_t> sp(snb_ptr, snb_ptr + ns + 1);
+    std::vector<int32_t> sn(snb, snb + sp[ns]);
+    std::vector<int32_t> out;
+    vertex_nd(rule, k, ptr, ad, so, sp, sn, &out);
+    if ((int64_t)out.size() != ns) return -2;
+    for (int64_t i = 0; i < ns; ++i) slot_order_out[i] = out[i];
+    return 0;
+}
+
 namespace spq {
 
-cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t cols, int64_t ld, void* out,
-                           cudaStream_t st) {
+cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t cols, int64_t ld, const int32_t* pos,
+                           void* out, cudaStream_t st) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     const bool od = dev_ptr(out);
     uint32_t* dst = (uint32_t*)out;
@@ -434,10 +698,16 @@ cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t c
     if (!od) e = cudaMallocAsync((void**)&dst, (size_t)(rows * cols) * 4, st);
     if (e != cudaSuccess) return e;
     int64_t blocks = rows < 65535 ? rows : 65535;
-    if (to_i32)
+    if (pos) {
+        if (to_i32)
+            k_gather_out<true><<<(unsigned)blocks, 256, 0, st>>>((const uint32_t*)src, rows, ld, pos, dst);
+        else
+            k_gather_out<false><<<(unsigned)blocks, 256, 0, st>>>((const uint32_t*)src, rows, ld, pos, dst);
+    } else if (to_i32) {
         k_copy_out<true><<<(unsigned)blocks, 256, 0, st>>>((const uint32_t*)src, rows, cols, ld, dst);
-    else
+    } else {
         k_copy_out<false><<<(unsigned)blocks, 256, 0, st>>>((const uint32_t*)src, rows, cols, ld, dst);
+    }
     count_launches(1);
     e = cudaGetLastError();
     if (!od) {

@@ -10,17 +10,20 @@
 
 namespace spq {
 
-// Fills *order with a permutation of the k components.  SPQ_ORDER_DISSECTION (and
-// AUTO, when it applies) orders them by nested dissection of the component adjacency
-// graph (two components are adjacent when an edge of G joins them), each component
-// weighted by its boundary size nb[c]: the two sides of a separator come first, each
-// ordered recursively, and the separator last.  Floyd-Warshall is correct for any
-// order of the intermediate vertices; in this order the pivot panels of the early
-// rounds stay infinite outside the current sub-region, so those tile updates are
-// provably no-ops and are skipped.
-spq_status component_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
-                           int32_t k, const std::vector<int32_t>& nb, spq_order ord, cudaStream_t st,
-                           std::vector<int32_t>* order);
+// Position of every boundary slot along the boundary-graph matrix.  Slots are numbered
+// component by component (slot_off[c] + local index, boundary vertices first in each
+// component); bgpos[slot] is the matrix row/column of that slot.  Floyd-Warshall is
+// correct for any order of the intermediate vertices; the order decides how many tile
+// updates are provably no-ops and skipped.  The component order is the cheapest, by a
+// symbolic cost model, of: id order, level-structure nested dissection and id-range
+// nested dissection of the component adjacency graph.  SPQ_ORDER_DISSECTION keeps each
+// component's slots contiguous in that order; SPQ_ORDER_AUTO and
+// SPQ_ORDER_VERTEX_DISSECTION refine the chosen bisections to vertex level (only the
+// boundary vertices on a cut become separator vertices).  *method: 0 id order, 1 / 2
+// component-level level-structure / id-range dissection, 3 / 4 their vertex-level forms.
+spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
+                          const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
+                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method);
 
 // Host-only nested dissection of a graph given as adjacency lists (exposed for tests).
 void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std::vector<int32_t>& adj,
@@ -28,7 +31,9 @@ void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std
 
 // Copy a rows x cols block (row stride ld, elements of 4 bytes) to dense `out` (host or
 // device), converting float32 exact integers to int32 (+inf -> SPQ_INF_I32) if to_i32.
-cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t cols, int64_t ld, void* out,
-                           cudaStream_t st);
+// With pos != NULL (device, rows == cols entries) element (i, j) is taken from
+// src[pos[i]][pos[j]] instead.
+cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t cols, int64_t ld, const int32_t* pos,
+                           void* out, cudaStream_t st);
 
 }  // namespace spq

@@ -44,14 +44,15 @@ __device__ __forceinline__ T warp_min(T x) {
 // sums at or above 2^24 may have rounded).  Every table entry is an exact integer.
 template <typename T>
 __device__ int64_t exact_query(const T* __restrict__ A1, const T* __restrict__ A2, const T* __restrict__ D, int64_t N,
-                               int64_t bo1, int64_t bo2, int32_t nb1, int32_t nb2, bool same, int32_t l2, int lane) {
+                               const int32_t* pos1, const int32_t* pos2, int32_t nb1, int32_t nb2, bool same,
+                               int32_t l2, int lane) {
     const int64_t big = (int64_t)1 << 40;
     int64_t best = big;
     for (int32_t j = lane; j < nb2; j += 32) {
         float cj = (float)A2[j];
         if (isinf(cj)) continue;
         for (int32_t i = 0; i < nb1; ++i) {
-            float ai = (float)A1[i], dij = (float)D[(bo1 + i) * N + bo2 + j];
+            float ai = (float)A1[i], dij = (float)D[(int64_t)pos1[i] * N + pos2[j]];
             if (isinf(ai) || isinf(dij)) continue;
             int64_t s = (int64_t)ai + (int64_t)dij + (int64_t)cj;
             best = s < best ? s : best;
@@ -105,28 +106,32 @@ __global__ void __launch_bounds__(QTH) k_query(const QueryCtx<T> ctx, const int2
         const int64_t bo1 = ctx.bg_off[c1], bo2 = ctx.bg_off[c2];
         const T* A1 = ctx.apsp + d1.off + (int64_t)l1 * d1.n;
         const T* A2 = ctx.apsp + d2.off + (int64_t)l2 * d2.n;
+        // matrix positions of the boundary slots: rows of C1's, columns of C2's
+        const int32_t* pos1 = ctx.bgpos + bo1;
+        const int32_t* pos2 = ctx.bgpos + bo2;
         T r = inf;
         for (int32_t jb = 0; jb < nb2; jb += 32 * JPL) {
             T t[JPL], cj[JPL];
+            int32_t colj[JPL];
 #pragma unroll
             for (int jj = 0; jj < JPL; ++jj) {
                 const int32_t j = jb + jj * 32 + lane;
                 t[jj] = inf;
                 cj[jj] = j < nb2 ? A2[j] : inf;
+                colj[jj] = j < nb2 ? pos2[j] : 0;
             }
-            const T* Dblk = ctx.D + bo1 * ctx.N + bo2 + jb + lane;
             for (int32_t ib = 0; ib < nb1; ib += 32) {
                 const T areg = (ib + lane < nb1) ? A1[ib + lane] : inf;
+                const int32_t rreg = (ib + lane < nb1) ? pos1[ib + lane] : 0;
                 const int32_t iend = (nb1 - ib) < 32 ? (nb1 - ib) : 32;
-                const T* rowp = Dblk + (int64_t)ib * ctx.N;
 #pragma unroll 2
                 for (int32_t ii = 0; ii < iend; ++ii) {
                     const T ai = __shfl_sync(0xffffffffu, areg, ii);
+                    const T* rowp = ctx.D + (int64_t)__shfl_sync(0xffffffffu, rreg, ii) * ctx.N;
 #pragma unroll
                     for (int jj = 0; jj < JPL; ++jj) {
-                        if (jb + jj * 32 + lane < nb2) t[jj] = tmin(t[jj], ai + rowp[jj * 32]);
+                        if (jb + jj * 32 + lane < nb2) t[jj] = tmin(t[jj], ai + rowp[colj[jj]]);
                     }
-                    rowp += ctx.N;
                 }
             }
 #pragma unroll
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(QTH) k_query(const QueryCtx<T> ctx, const int2
             } else if (rf < 16777216.0f) {
                 res = (int32_t)rf;
             } else {
-                int64_t ex = exact_query<T>(A1, A2, ctx.D, ctx.N, bo1, bo2, nb1, nb2, c1 == c2, l2, lane);
+                int64_t ex = exact_query<T>(A1, A2, ctx.D, ctx.N, pos1, pos2, nb1, nb2, c1 == c2, l2, lane);
                 res = ex >= SPQ_INF_I32 ? SPQ_INF_I32 : (int32_t)ex;
             }
             if (lane == 0) ((int32_t*)out)[qi] = res;

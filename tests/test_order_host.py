@@ -106,3 +106,86 @@ def test_grid_of_components(lib):
     n = float(w.sum())
     assert cost[0] / n ** 3 > 0.15
     assert min(cost[1], cost[2]) / n ** 3 < 0.05
+
+
+def bg_structure(w):
+    """Boundary slots of a workload (component-grouped, ascending vertex id inside each
+    component as the library numbers them), the component adjacency and, per slot, the
+    other components its vertex touches."""
+    g, part, k = w.graph, w.part, w.k
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    cross = part[src] != part[g.col]
+    bnd = np.zeros(g.n, bool)
+    bnd[src[cross]] = True
+    slots = []
+    slot_off = np.zeros(k + 1, np.int64)
+    for c in range(k):
+        ids = np.nonzero((part == c) & bnd)[0]
+        slots.extend(ids.tolist())
+        slot_off[c + 1] = slot_off[c] + ids.size
+    slot_of = {v: i for i, v in enumerate(slots)}
+    nbrs = [set() for _ in slots]
+    edges = set()
+    for a, b in zip(src[cross], g.col[cross]):
+        nbrs[slot_of[int(a)]].add(int(part[b]))
+        edges.add((int(part[a]), int(part[b])))
+    ptr, flat, adj = csr(k, list(edges))
+    snb_ptr = np.zeros(len(slots) + 1, np.int64)
+    for i, s in enumerate(nbrs):
+        snb_ptr[i + 1] = snb_ptr[i] + len(s)
+    snb = np.array([c for s in nbrs for c in sorted(s)], np.int32)
+    return slots, slot_off, ptr, flat, snb_ptr, snb, slot_of
+
+
+def vertex_cost(w, slots, slot_off, order):
+    """Symbolic vertex-level Floyd-Warshall cost (sum over pivots of finite rows^2 / 2)
+    on the boundary graph with its clique edges."""
+    g, part = w.graph, w.part
+    k = w.k
+    comp_of_slot = np.repeat(np.arange(k), np.diff(slot_off))
+    members = [list(range(slot_off[c], slot_off[c + 1])) for c in range(k)]
+    slot_of = {v: i for i, v in enumerate(slots)}
+    inter = [set() for _ in slots]
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    for a, b in zip(src, g.col):
+        if part[a] != part[b]:
+            inter[slot_of[int(a)]].add(slot_of[int(b)])
+    elim = np.zeros(len(slots), bool)
+    total = 0.0
+    for p in order:
+        elim[p] = True
+        seen = {p}
+        stack = [p]
+        reach = set()
+        while stack:
+            x = stack.pop()
+            for y in list(inter[x]) + members[comp_of_slot[x]]:
+                if elim[y]:
+                    if y not in seen:
+                        seen.add(y)
+                        stack.append(y)
+                else:
+                    reach.add(y)
+        total += (len(seen) + len(reach)) ** 2 * 0.5
+    return total
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+def test_vertex_order_is_a_permutation_and_cheaper(lib, rule):
+    w = gen.configs.delaunay_rcb(1500, 3, 10, seed=3)
+    slots, slot_off, ptr, flat, snb_ptr, snb, _ = bg_structure(w)
+    out = np.empty(len(slots), np.int32)
+    rc = lib.spq_boundary_order_host(w.k, ptr.ctypes.data, flat.ctypes.data, slot_off.ctypes.data,
+                                     snb_ptr.ctypes.data, snb.ctypes.data, rule, out.ctypes.data)
+    assert rc == 0
+    assert sorted(out.tolist()) == list(range(len(slots)))
+    comp_order = []
+    nb = np.diff(slot_off).astype(np.int32)
+    _, corder, _ = order_of(lib, w.k, ptr, flat, nb, rule)
+    for c in corder:
+        comp_order.extend(range(slot_off[c], slot_off[c + 1]))
+    ident = list(range(len(slots)))
+    c_id = vertex_cost(w, slots, slot_off, ident)
+    c_comp = vertex_cost(w, slots, slot_off, comp_order)
+    c_vert = vertex_cost(w, slots, slot_off, out.tolist())
+    assert c_vert < c_comp < c_id, (c_vert, c_comp, c_id)

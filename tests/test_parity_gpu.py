@@ -23,7 +23,7 @@ from make_golden import FIXTURES, load
 pytestmark = pytest.mark.gpu
 
 ARITHS = [1, 2]  # SPQ_ARITH_I32, SPQ_ARITH_F32
-ORDERS = [1, 2]  # SPQ_ORDER_ID, SPQ_ORDER_DISSECTION
+ORDERS = [0, 1, 2, 3]  # SPQ_ORDER_AUTO, _ID, _DISSECTION, _VERTEX_DISSECTION
 
 
 @pytest.mark.parametrize("name", sorted(FIXTURES))
