@@ -92,6 +92,10 @@ typedef struct spq_opts {
     int32_t profile_kernels; /* 1: time every launch of the boundary-graph
                                Floyd-Warshall's phase-3 kernel with CUDA events (see
                                spq_build_profile); 0 (default): no per-launch events */
+    int32_t query_grouped;  /* 1 (default): spq_query batches of >= 4096 pairs are sorted
+                               by component pair (stream-ordered scratch of 16 bytes per
+                               pair) so that each boundary-graph block is read once per
+                               group; 0: one warp per pair in input order, no scratch */
 } spq_opts;
 
 /* Fill *opts with the defaults (also what opts == NULL means). */

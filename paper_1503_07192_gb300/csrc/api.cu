@@ -35,6 +35,7 @@ struct spq_handle {
     int32_t* bg_off = nullptr;  // first slot of each component (component-grouped numbering)
     int32_t* bgpos = nullptr;   // matrix position of each slot
     int32_t order_method = 0;
+    int32_t query_grouped = 1;
     int32_t* csize = nullptr;
     void* apsp = nullptr;
     void* D = nullptr;
@@ -52,6 +53,9 @@ struct spq_handle {
 namespace {
 
 thread_local int g_last_cuda = 0;
+
+// Below this many pairs a query batch is answered in input order (no sort).
+constexpr int64_t kGroupedMinQueries = 4096;
 
 spq_status cuda_fail(cudaError_t e) {
     g_last_cuda = (int)e;
@@ -391,6 +395,7 @@ void spq_opts_default(spq_opts* o) {
     o->order = SPQ_ORDER_AUTO;
     o->skip_inf_tiles = 1;
     o->profile_kernels = 0;
+    o->query_grouped = 1;
 }
 
 spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
@@ -417,6 +422,7 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
     h->n = n;
     h->k = k;
     h->wt = wt;
+    h->query_grouped = o.query_grouped;
     spq_status s = build_impl(n, row_ptr, col, w, wt, part, k, o, (cudaStream_t)stream, h);
     if (s != SPQ_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -436,22 +442,26 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
     const bool pd = is_device_ptr(pairs), od = is_device_ptr(dist_out);
     if (pd != od) return SPQ_EINVAL;
     const bool out_f32 = h->wt == SPQ_F32;
+    Temps tmp(st);
+    // the grouped form sorts the pairs by component pair in stream-ordered scratch
+    uint32_t* scratch = nullptr;
+    if (h->query_grouped && q >= kGroupedMinQueries && h->k <= 65535)
+        CK(tmp.alloc(&scratch, (size_t)query_scratch_words(q)));
     auto launch = [&](const int32_t* p, void* o) -> cudaError_t {
         if (h->f32store) {
             QueryCtx<float> c{h->n,   h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
                               (const float*)h->D, h->N, h->err};
-            return launch_query<float>(c, p, q, o, out_f32, st);
+            return launch_query<float>(c, p, q, o, out_f32, (uint32_t)h->k, scratch, st);
         }
         QueryCtx<int32_t> c{h->n,     h->comp,   h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
                             (const int32_t*)h->D, h->N, h->err};
-        return launch_query<int32_t>(c, p, q, o, out_f32, st);
+        return launch_query<int32_t>(c, p, q, o, out_f32, (uint32_t)h->k, scratch, st);
     };
     if (pd) {
         if (((uintptr_t)pairs & 7u) || ((uintptr_t)dist_out & 3u)) return SPQ_EINVAL;
         CK(launch(pairs, dist_out));
         return SPQ_OK;
     }
-    Temps tmp(st);
     int32_t* dp;
     int32_t* dout;
     CK(tmp.alloc(&dp, 2 * (size_t)q));

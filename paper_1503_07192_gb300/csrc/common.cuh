@@ -113,8 +113,11 @@ struct QueryCtx {
     int64_t N;
     uint32_t* err;
 };
+// Queries; with scratch (query_scratch_words(q) words) and k <= 65535 the grouped form
+// (sorted by component pair), else one warp per query in input order.
+int64_t query_scratch_words(int64_t q);
 template <typename T>
 cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
-                         cudaStream_t st);
+                         uint32_t k, uint32_t* scratch, cudaStream_t st);
 
 }  // namespace spq

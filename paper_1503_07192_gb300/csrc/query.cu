@@ -26,7 +26,7 @@ constexpr int QTH = 256;
 constexpr int JPL = 8;  // columns per lane per pass: 256 columns of the block per pass
 
 // Output modes.
-enum { kOutI32 = 0, kOutI32FromF32 = 1, kOutF32 = 2 };
+enum { kOutI32 = 0, kOutF32 = 2 };
 
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) {
@@ -38,36 +38,6 @@ __device__ __forceinline__ T warp_min(T x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x = tmin(x, __shfl_xor_sync(0xffffffffu, x, o));
     return x;
-}
-
-// Exact int64 recomputation for float tables whose float answer reached 2^24 (float
-// sums at or above 2^24 may have rounded).  Every table entry is an exact integer.
-template <typename T>
-__device__ int64_t exact_query(const T* __restrict__ A1, const T* __restrict__ A2, const T* __restrict__ D, int64_t N,
-                               const int32_t* pos1, const int32_t* pos2, int32_t nb1, int32_t nb2, bool same,
-                               int32_t l2, int lane) {
-    const int64_t big = (int64_t)1 << 40;
-    int64_t best = big;
-    for (int32_t j = lane; j < nb2; j += 32) {
-        float cj = (float)A2[j];
-        if (isinf(cj)) continue;
-        for (int32_t i = 0; i < nb1; ++i) {
-            float ai = (float)A1[i], dij = (float)D[(int64_t)pos1[i] * N + pos2[j]];
-            if (isinf(ai) || isinf(dij)) continue;
-            int64_t s = (int64_t)ai + (int64_t)dij + (int64_t)cj;
-            best = s < best ? s : best;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        int64_t y = __shfl_xor_sync(0xffffffffu, best, o);
-        best = y < best ? y : best;
-    }
-    if (same) {
-        float s = (float)A1[l2];
-        if (!isinf(s) && (int64_t)s < best) best = (int64_t)s;
-    }
-    return best;
 }
 
 template <typename T, int MODE>
@@ -141,20 +111,8 @@ __global__ void __launch_bounds__(QTH) k_query(const QueryCtx<T> ctx, const int2
         if (c1 == c2) r = tmin(r, A1[l2]);
         if (MODE == kOutI32) {
             if (lane == 0) ((int32_t*)out)[qi] = (int32_t)tmin<int32_t>((int32_t)r, SPQ_INF_I32);
-        } else if (MODE == kOutF32) {
-            if (lane == 0) ((float*)out)[qi] = (float)r;
         } else {
-            const float rf = (float)r;
-            int32_t res;
-            if (isinf(rf)) {
-                res = SPQ_INF_I32;
-            } else if (rf < 16777216.0f) {
-                res = (int32_t)rf;
-            } else {
-                int64_t ex = exact_query<T>(A1, A2, ctx.D, ctx.N, pos1, pos2, nb1, nb2, c1 == c2, l2, lane);
-                res = ex >= SPQ_INF_I32 ? SPQ_INF_I32 : (int32_t)ex;
-            }
-            if (lane == 0) ((int32_t*)out)[qi] = res;
+            if (lane == 0) ((float*)out)[qi] = (float)r;
         }
     }
 }
@@ -172,28 +130,232 @@ int query_sms() {
 
 }  // namespace
 
+// ---------------- grouped form ----------------
+// Queries sorted by their unordered component pair {C1, C2}: every segment of equal keys
+// shares one block dist_BG(B(C1), B(C2)), which is staged into shared memory in chunks of
+// rows (gathered through the slot positions) and reused by all of the segment's queries.
+// Segments never cross a 64-position tile of the sorted order (a key change or a tile
+// start begins a segment), so one CTA owns each tile.  dist is symmetric, so a pair is
+// answered as (v, w) with comp(v) = C1 <= C2 = comp(w).
+constexpr int GTH = 256;  // 8 warps
+constexpr int GTILE = 64;
+constexpr int GQPW = 4;               // queries per warp per batch
+constexpr int GBATCH = 8 * GQPW;      // queries per batch
+constexpr int GRC = 64;               // block rows per staged chunk
+constexpr int GCOLS = 256;            // block columns per pass (8 per lane)
+
+__global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t n, const int32_t* __restrict__ comp,
+                             uint32_t k, uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q) return;
+    int2 p = pairs[i];
+    uint32_t key = k * k;  // sentinel: invalid pair, sorted last
+    if (p.x >= 0 && p.x < n && p.y >= 0 && p.y < n) {
+        uint32_t a = (uint32_t)comp[p.x], b = (uint32_t)comp[p.y];
+        key = a <= b ? a * k + b : b * k + a;
+    }
+    keys[i] = key;
+    idx[i] = (uint32_t)i;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(GTH) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
+                                                       const uint32_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ idx, int64_t q, uint32_t k,
+                                                       void* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T(*S)[GCOLS] = reinterpret_cast<T(*)[GCOLS]>(smem_raw);
+    __shared__ int32_t heads[GTILE + 1];
+    __shared__ uint32_t hb[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * GTILE;
+    const int tn = (int)((q - t0) < GTILE ? (q - t0) : GTILE);
+    const T inf = Inf<T>::value();
+    bool h = false;
+    if (tid < GTILE) {
+        h = tid < tn && (tid == 0 || keys[t0 + tid] != keys[t0 + tid - 1]);
+        unsigned b = __ballot_sync(0xffffffffu, h);
+        if (lane == 0) hb[warp] = b;
+    }
+    __syncthreads();
+    if (tid < GTILE && h) {
+        int pos = __popc(hb[warp] & ((1u << lane) - 1u)) + (warp == 1 ? __popc(hb[0]) : 0);
+        heads[pos] = tid;
+    }
+    const int nh = __popc(hb[0]) + __popc(hb[1]);
+    if (tid == 0) heads[nh] = tn;
+    __syncthreads();
+    for (int sg = 0; sg < nh; ++sg) {
+        const int s0 = heads[sg], s1 = heads[sg + 1];
+        const uint32_t key = keys[t0 + s0];
+        if (key >= k * k) {  // out-of-range pairs
+            for (int u = tid; u < s1 - s0; u += GTH) {
+                const uint32_t qi = idx[t0 + s0 + u];
+                if (MODE == kOutF32)
+                    ((float*)out)[qi] = __int_as_float(0x7fc00000);
+                else
+                    ((int32_t*)out)[qi] = -1;
+                atomicOr(ctx.err, kErrPair);
+            }
+            continue;
+        }
+        const int32_t c1 = (int32_t)(key / k), c2 = (int32_t)(key % k);
+        const MatDesc d1 = ctx.descs[c1], d2 = ctx.descs[c2];
+        const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];
+        const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
+        const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
+        for (int bq = s0; bq < s1; bq += GBATCH) {
+            // this warp's queries: bq + u * 8 + warp
+            const T* A1[GQPW];
+            const T* A2[GQPW];
+            int32_t l2s[GQPW];
+            uint32_t qis[GQPW];
+            bool val[GQPW], same_v[GQPW];
+            T r[GQPW];
+#pragma unroll
+            for (int u = 0; u < GQPW; ++u) {
+                const int sp = bq + u * 8 + warp;
+                val[u] = sp < s1;
+                qis[u] = 0;
+                A1[u] = A2[u] = nullptr;
+                l2s[u] = 0;
+                same_v[u] = false;
+                r[u] = inf;
+                if (val[u]) {
+                    qis[u] = idx[t0 + sp];
+                    int2 p = pairs[qis[u]];
+                    if (ctx.comp[p.x] != c1) {
+                        const int32_t tmp = p.x;
+                        p.x = p.y;
+                        p.y = tmp;
+                    }
+                    same_v[u] = p.x == p.y;
+                    l2s[u] = ctx.local[p.y];
+                    A1[u] = ctx.apsp + d1.off + (int64_t)ctx.local[p.x] * d1.n;
+                    A2[u] = ctx.apsp + d2.off + (int64_t)l2s[u] * d2.n;
+                }
+            }
+            for (int32_t jb = 0; jb < nb2; jb += GCOLS) {
+                const int cols = (nb2 - jb) < GCOLS ? (nb2 - jb) : GCOLS;
+                T t[GQPW][8], cj[GQPW][8];
+#pragma unroll
+                for (int u = 0; u < GQPW; ++u)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = jj * 32 + lane;
+                        t[u][jj] = inf;
+                        cj[u][jj] = (val[u] && j < cols) ? A2[u][jb + j] : inf;
+                    }
+                for (int32_t rc = 0; rc < nb1; rc += GRC) {
+                    const int rows = (nb1 - rc) < GRC ? (nb1 - rc) : GRC;
+                    __syncthreads();
+                    for (int ii = warp; ii < rows; ii += 8) {
+                        const T* src = ctx.D + (int64_t)pos1[rc + ii] * ctx.N;
+                        for (int jj = lane; jj < cols; jj += 32) S[ii][jj] = src[pos2[jb + jj]];
+                    }
+                    __syncthreads();
+                    T alo[GQPW], ahi[GQPW];
+#pragma unroll
+                    for (int u = 0; u < GQPW; ++u) {
+                        alo[u] = (val[u] && lane < rows) ? A1[u][rc + lane] : inf;
+                        ahi[u] = (val[u] && 32 + lane < rows) ? A1[u][rc + 32 + lane] : inf;
+                    }
+                    const int jmax = (cols + 31) >> 5;
+                    for (int ii = 0; ii < rows; ++ii) {
+                        T ai[GQPW];
+#pragma unroll
+                        for (int u = 0; u < GQPW; ++u) ai[u] = __shfl_sync(0xffffffffu, ii < 32 ? alo[u] : ahi[u], ii & 31);
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            if (jj < jmax) {
+                                const T sv = S[ii][jj * 32 + lane];
+#pragma unroll
+                                for (int u = 0; u < GQPW; ++u) t[u][jj] = tmin(t[u][jj], ai[u] + sv);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < GQPW; ++u)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) r[u] = tmin(r[u], t[u][jj] + cj[u][jj]);
+            }
+#pragma unroll
+            for (int u = 0; u < GQPW; ++u) {
+                T x = warp_min(r[u]);
+                if (val[u]) {
+                    if (c1 == c2) x = tmin(x, A1[u][l2s[u]]);
+                    if (same_v[u]) x = T(0);
+                    if (lane == 0) {
+                        if (MODE == kOutF32)
+                            ((float*)out)[qis[u]] = (float)x;
+                        else
+                            ((int32_t*)out)[qis[u]] = (int32_t)tmin<int32_t>((int32_t)x, SPQ_INF_I32);
+                    }
+                }
+            }
+        }
+    }
+}
+
+int64_t query_scratch_words(int64_t q) { return 4 * q + radix_hist_words(q) + 4; }
+
 template <typename T>
 cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
-                         cudaStream_t st) {
+                         uint32_t k, uint32_t* scratch, cudaStream_t st) {
     if (q <= 0) return cudaSuccess;
+    const int2* p2 = reinterpret_cast<const int2*>(pairs);
+    const bool mode_f32 = !std::is_same<T, int32_t>::value;
+    if (scratch && k <= 65535u && q <= (int64_t)UINT32_MAX) {
+        uint32_t* keys = scratch;
+        uint32_t* vals = scratch + q;
+        uint32_t* k1 = scratch + 2 * q;
+        uint32_t* v1 = scratch + 3 * q;
+        uint32_t* hist = scratch + 4 * q;
+        k_query_keys<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(p2, q, ctx.n, ctx.comp, k, keys, vals);
+        count_launches(1);
+        int bits = 0;
+        const uint64_t mx = (uint64_t)k * k;
+        while (bits < 32 && (mx >> bits)) ++bits;
+        bool in_k1 = false;
+        cudaError_t e = radix_sort_pairs(keys, vals, k1, v1, hist, q, bits, &in_k1, st);
+        if (e != cudaSuccess) return e;
+        const uint32_t* sk = in_k1 ? k1 : keys;
+        const uint32_t* sv = in_k1 ? v1 : vals;
+        const size_t smem = sizeof(T) * GRC * GCOLS;
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[mode_f32]) {
+            if (mode_f32)
+                e = cudaFuncSetAttribute(k_query_grouped<T, kOutF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+            else
+                e = cudaFuncSetAttribute(k_query_grouped<T, kOutI32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set[mode_f32] = true;
+        }
+        const unsigned blocks = (unsigned)((q + GTILE - 1) / GTILE);
+        if (mode_f32)
+            k_query_grouped<T, kOutF32><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, out);
+        else
+            k_query_grouped<T, kOutI32><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, out);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     int64_t blocks = (q + (QTH / 32) - 1) / (QTH / 32);
     int64_t cap = (int64_t)query_sms() * 16;
     if (blocks > cap) blocks = cap;
-    const int2* p2 = reinterpret_cast<const int2*>(pairs);
-    if (sizeof(T) == 4 && !out_f32) {
-        if (std::is_same<T, int32_t>::value)
-            k_query<T, kOutI32><<<(unsigned)blocks, QTH, 0, st>>>(ctx, p2, q, out);
-        else
-            k_query<T, kOutI32FromF32><<<(unsigned)blocks, QTH, 0, st>>>(ctx, p2, q, out);
-    } else {
+    if (!mode_f32 && !out_f32)
+        k_query<T, kOutI32><<<(unsigned)blocks, QTH, 0, st>>>(ctx, p2, q, out);
+    else
         k_query<T, kOutF32><<<(unsigned)blocks, QTH, 0, st>>>(ctx, p2, q, out);
-    }
     count_launches(1);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_query<int32_t>(const QueryCtx<int32_t>&, const int32_t*, int64_t, void*, bool,
-                                           cudaStream_t);
-template cudaError_t launch_query<float>(const QueryCtx<float>&, const int32_t*, int64_t, void*, bool, cudaStream_t);
+template cudaError_t launch_query<int32_t>(const QueryCtx<int32_t>&, const int32_t*, int64_t, void*, bool, uint32_t,
+                                           uint32_t*, cudaStream_t);
+template cudaError_t launch_query<float>(const QueryCtx<float>&, const int32_t*, int64_t, void*, bool, uint32_t,
+                                         uint32_t*, cudaStream_t);
 
 }  // namespace spq

@@ -248,3 +248,53 @@ def test_delaunay16k_sampled_and_full_rows():
         pairs = np.stack([np.full(g.n, s), np.arange(g.n)], 1).astype(np.int32)
         assert np.array_equal(query(h, pairs).astype(np.int64), rows[i])
     h.free()
+
+
+def _build_with(w, grouped):
+    return build(w.graph, w.part, w.k, query_grouped=grouped)
+
+
+def test_grouped_and_input_order_queries_agree():
+    """The grouped query form (pairs sorted by component pair, blocks staged in shared
+    memory) and the one-warp-per-pair form give the same bit-exact answers, including
+    long runs of one component pair (split across 64-pair tiles), reversed pairs,
+    same-component pairs and v == w."""
+    w = gen.configs.grid_blocks_workload(64, 48, 16, 16, 100, 20000, seed=17)
+    g = w.graph
+    rng = np.random.default_rng(17)
+    same_pair = np.tile(np.array([[5, 3000]], np.int32), (5000, 1))
+    one_block = np.stack([rng.integers(0, 256, 3000), 2048 + rng.integers(0, 256, 3000)], 1).astype(np.int32)
+    same_comp = np.stack([rng.integers(0, 16, 2000) * 64 + rng.integers(0, 16, 2000),
+                          rng.integers(0, 16, 2000) * 64 + rng.integers(0, 16, 2000)], 1).astype(np.int32)
+    pairs = np.concatenate([w.pairs, same_pair, one_block, one_block[:, ::-1], same_comp,
+                            np.repeat(np.arange(0, g.n, 97)[:, None], 2, 1).astype(np.int32)])
+    pairs = pairs[rng.permutation(pairs.shape[0])]
+    hg = _build_with(w, 1)
+    hu = _build_with(w, 0)
+    a = query(hg, pairs)
+    b = query(hu, pairs)
+    assert np.array_equal(a, b)
+    assert_pairs_exact(hg, g, pairs[:20000])
+    hg.free()
+    hu.free()
+
+
+def test_grouped_queries_mark_invalid_pairs():
+    m = spq()
+    w = gen.configs.grid_blocks_workload(32, 32, 8, 8, 50, 10000, seed=19)
+    h = build(w.graph, w.part, w.k)
+    pairs = w.pairs.copy()
+    bad = np.array([3, 777, 9999])
+    pairs[bad, 1] = w.graph.n + 5
+    torch, dev = __import__("_util").torch_dev()
+    d = m.spq_query(h, torch.from_numpy(pairs).to(dev))
+    torch.cuda.synchronize()
+    with pytest.raises(m.SpqError):
+        m.spq_query_status(h)
+    got = d.cpu().numpy().astype(np.int64)
+    assert np.all(got[bad] == -1)
+    ok = np.setdiff1d(np.arange(pairs.shape[0]), bad)
+    ref = oracle_i32(oracle.pairs_dist(w.graph.row_ptr, w.graph.col, w.graph.w, pairs[ok]))
+    assert np.array_equal(got[ok], ref)
+    m.spq_query_status(h)  # the mark was cleared
+    h.free()
