@@ -249,9 +249,12 @@ __global__ void __launch_bounds__(GTH) k_query_grouped(const QueryCtx<T> ctx, co
                 for (int32_t rc = 0; rc < nb1; rc += GRC) {
                     const int rows = (nb1 - rc) < GRC ? (nb1 - rc) : GRC;
                     __syncthreads();
+                    // columns up to the next multiple of 32 are filled (infinity past
+                    // the block) so that every lane reads a defined value below
+                    const int cols32 = (cols + 31) & ~31;
                     for (int ii = warp; ii < rows; ii += 8) {
                         const T* src = ctx.D + (int64_t)pos1[rc + ii] * ctx.N;
-                        for (int jj = lane; jj < cols; jj += 32) S[ii][jj] = src[pos2[jb + jj]];
+                        for (int jj = lane; jj < cols32; jj += 32) S[ii][jj] = jj < cols ? src[pos2[jb + jj]] : inf;
                     }
                     __syncthreads();
                     T alo[GQPW], ahi[GQPW];
