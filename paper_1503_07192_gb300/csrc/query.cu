@@ -141,8 +141,8 @@ constexpr int GTH = 256;  // 8 warps
 constexpr int GTILE = 64;
 constexpr int GQPW = 4;               // queries per warp per batch
 constexpr int GBATCH = 8 * GQPW;      // queries per batch
-constexpr int GRC = 64;               // block rows per staged chunk
 constexpr int GCOLS = 256;            // block columns per pass (8 per lane)
+constexpr int GSMEM = 24 * 1024;      // staged elements per CTA (96 KB): two CTAs per SM
 
 __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t n, const int32_t* __restrict__ comp,
                              uint32_t k, uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
@@ -159,12 +159,12 @@ __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t 
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(GTH) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
+__global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
                                                        const uint32_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ idx, int64_t q, uint32_t k,
                                                        void* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*S)[GCOLS] = reinterpret_cast<T(*)[GCOLS]>(smem_raw);
+    T* S = reinterpret_cast<T*>(smem_raw);  // GSMEM elements, rows of `ld` = cols rounded up to 32
     __shared__ int32_t heads[GTILE + 1];
     __shared__ uint32_t hb[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -206,8 +206,7 @@ __global__ void __launch_bounds__(GTH) k_query_grouped(const QueryCtx<T> ctx, co
         const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
         for (int bq = s0; bq < s1; bq += GBATCH) {
             // this warp's queries: bq + u * 8 + warp
-            const T* A1[GQPW];
-            const T* A2[GQPW];
+            int64_t a1off[GQPW], a2off[GQPW];
             int32_t l2s[GQPW];
             uint32_t qis[GQPW];
             bool val[GQPW], same_v[GQPW];
@@ -217,7 +216,7 @@ __global__ void __launch_bounds__(GTH) k_query_grouped(const QueryCtx<T> ctx, co
                 const int sp = bq + u * 8 + warp;
                 val[u] = sp < s1;
                 qis[u] = 0;
-                A1[u] = A2[u] = nullptr;
+                a1off[u] = a2off[u] = 0;
                 l2s[u] = 0;
                 same_v[u] = false;
                 r[u] = inf;
@@ -231,63 +230,91 @@ __global__ void __launch_bounds__(GTH) k_query_grouped(const QueryCtx<T> ctx, co
                     }
                     same_v[u] = p.x == p.y;
                     l2s[u] = ctx.local[p.y];
-                    A1[u] = ctx.apsp + d1.off + (int64_t)ctx.local[p.x] * d1.n;
-                    A2[u] = ctx.apsp + d2.off + (int64_t)l2s[u] * d2.n;
+                    a1off[u] = d1.off + (int64_t)ctx.local[p.x] * d1.n;
+                    a2off[u] = d2.off + (int64_t)l2s[u] * d2.n;
                 }
             }
             for (int32_t jb = 0; jb < nb2; jb += GCOLS) {
                 const int cols = (nb2 - jb) < GCOLS ? (nb2 - jb) : GCOLS;
-                T t[GQPW][8], cj[GQPW][8];
+                const int ld = (cols + 31) & ~31;  // staged row length
+                const int jmax = ld >> 5;
+                const int rows_per_chunk = GSMEM / ld;
+                int32_t colpos[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = jj * 32 + lane;
+                    colpos[jj] = j < cols ? pos2[jb + j] : -1;
+                }
+                T t[GQPW][8];
+#pragma unroll
+                for (int u = 0; u < GQPW; ++u)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) t[u][jj] = inf;
+                for (int32_t rc = 0; rc < nb1; rc += rows_per_chunk) {
+                    const int rows = (nb1 - rc) < rows_per_chunk ? (nb1 - rc) : rows_per_chunk;
+                    __syncthreads();
+                    // stage the chunk: 4 rows x 8 column groups of independent loads per lane
+                    for (int i0 = warp; i0 < rows; i0 += 32) {
+                        int64_t rb[4];
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr) {
+                            const int ii = i0 + 8 * rr;
+                            rb[rr] = ii < rows ? (int64_t)pos1[rc + ii] * ctx.N : -1;
+                        }
+                        T v[4][8];
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj)
+                                v[rr][jj] = (rb[rr] >= 0 && colpos[jj] >= 0) ? ctx.D[rb[rr] + colpos[jj]] : inf;
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr) {
+                            const int ii = i0 + 8 * rr;
+                            if (ii < rows) {
+#pragma unroll
+                                for (int jj = 0; jj < 8; ++jj)
+                                    if (jj < jmax) S[ii * ld + jj * 32 + lane] = v[rr][jj];
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    for (int ib = 0; ib < rows; ib += 32) {
+                        T areg[GQPW];
+#pragma unroll
+                        for (int u = 0; u < GQPW; ++u)
+                            areg[u] = (val[u] && ib + lane < rows) ? ctx.apsp[a1off[u] + rc + ib + lane] : inf;
+                        const int iend = (rows - ib) < 32 ? (rows - ib) : 32;
+                        for (int ii = 0; ii < iend; ++ii) {
+                            T ai[GQPW];
+#pragma unroll
+                            for (int u = 0; u < GQPW; ++u) ai[u] = __shfl_sync(0xffffffffu, areg[u], ii);
+                            const T* srow = S + (ib + ii) * ld + lane;
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {
+                                if (jj < jmax) {
+                                    const T sv = srow[jj * 32];
+#pragma unroll
+                                    for (int u = 0; u < GQPW; ++u) t[u][jj] = tmin(t[u][jj], ai[u] + sv);
+                                }
+                            }
+                        }
+                    }
+                }
+                // dist_C2(b2, v2) for this pass's columns
 #pragma unroll
                 for (int u = 0; u < GQPW; ++u)
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
                         const int j = jj * 32 + lane;
-                        t[u][jj] = inf;
-                        cj[u][jj] = (val[u] && j < cols) ? A2[u][jb + j] : inf;
+                        const T c = (val[u] && j < cols) ? ctx.apsp[a2off[u] + jb + j] : inf;
+                        r[u] = tmin(r[u], t[u][jj] + c);
                     }
-                for (int32_t rc = 0; rc < nb1; rc += GRC) {
-                    const int rows = (nb1 - rc) < GRC ? (nb1 - rc) : GRC;
-                    __syncthreads();
-                    // columns up to the next multiple of 32 are filled (infinity past
-                    // the block) so that every lane reads a defined value below
-                    const int cols32 = (cols + 31) & ~31;
-                    for (int ii = warp; ii < rows; ii += 8) {
-                        const T* src = ctx.D + (int64_t)pos1[rc + ii] * ctx.N;
-                        for (int jj = lane; jj < cols32; jj += 32) S[ii][jj] = jj < cols ? src[pos2[jb + jj]] : inf;
-                    }
-                    __syncthreads();
-                    T alo[GQPW], ahi[GQPW];
-#pragma unroll
-                    for (int u = 0; u < GQPW; ++u) {
-                        alo[u] = (val[u] && lane < rows) ? A1[u][rc + lane] : inf;
-                        ahi[u] = (val[u] && 32 + lane < rows) ? A1[u][rc + 32 + lane] : inf;
-                    }
-                    const int jmax = (cols + 31) >> 5;
-                    for (int ii = 0; ii < rows; ++ii) {
-                        T ai[GQPW];
-#pragma unroll
-                        for (int u = 0; u < GQPW; ++u) ai[u] = __shfl_sync(0xffffffffu, ii < 32 ? alo[u] : ahi[u], ii & 31);
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            if (jj < jmax) {
-                                const T sv = S[ii][jj * 32 + lane];
-#pragma unroll
-                                for (int u = 0; u < GQPW; ++u) t[u][jj] = tmin(t[u][jj], ai[u] + sv);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < GQPW; ++u)
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) r[u] = tmin(r[u], t[u][jj] + cj[u][jj]);
             }
 #pragma unroll
             for (int u = 0; u < GQPW; ++u) {
                 T x = warp_min(r[u]);
                 if (val[u]) {
-                    if (c1 == c2) x = tmin(x, A1[u][l2s[u]]);
+                    if (c1 == c2) x = tmin(x, ctx.apsp[a1off[u] + l2s[u]]);
                     if (same_v[u]) x = T(0);
                     if (lane == 0) {
                         if (MODE == kOutF32)
@@ -325,7 +352,7 @@ cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q
         if (e != cudaSuccess) return e;
         const uint32_t* sk = in_k1 ? k1 : keys;
         const uint32_t* sv = in_k1 ? v1 : vals;
-        const size_t smem = sizeof(T) * GRC * GCOLS;
+        const size_t smem = sizeof(T) * GSMEM;
         static bool attr_set[2] = {false, false};
         if (!attr_set[mode_f32]) {
             if (mode_f32)
