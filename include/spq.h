@@ -152,6 +152,27 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
  */
 spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream);
 
+/*
+ * spq_query without memory allocation (the paper has no counterpart: it is for callers
+ * of this library that cannot let it allocate device memory on their request path, such
+ * as a serving process that has given all free device memory to its own pool or runs
+ * under a fixed budget where an allocation could fail or stall).
+ *
+ * Same results and rules as spq_query, except:
+ *   - q <= SPQ_NOALLOC_MAX_PAIRS (a larger q returns SPQ_EINVAL and queues nothing);
+ *   - pairs and dist_out must be device memory (else SPQ_EINVAL); the call returns once
+ *     the work is queued, and spq_query_status reports out-of-range pairs;
+ *   - its scratch is one fixed array of about 4.3 MB in the library's device memory,
+ *     present on every GPU that loads the library until the process exits.  The first
+ *     call on a device looks up that array's address (cudaGetSymbolAddress, once per
+ *     device); make that first call before any stream capture.  All calls share the
+ *     array, so calls whose work overlaps on the GPU race: order them (one stream, or
+ *     events).
+ * It calls no allocation routine (no cudaMalloc, cudaMallocAsync or cudaFree).
+ */
+#define SPQ_NOALLOC_MAX_PAIRS 262144
+spq_status spq_query_noalloc(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream);
+
 /* Synchronise `stream`, return SPQ_EINVAL if any spq_query on h since the last call
  * met an out-of-range pair (and clear the mark), else SPQ_OK (or SPQ_ECUDA). */
 spq_status spq_query_status(spq_handle* h, void* stream);

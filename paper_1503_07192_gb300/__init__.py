@@ -29,6 +29,7 @@ from ._lib import (  # noqa: F401
     SPQ_F32,
     SPQ_I32,
     SPQ_INF_I32,
+    SPQ_NOALLOC_MAX_PAIRS,
     SPQ_ORDER_AUTO,
     SPQ_ORDER_DISSECTION,
     SPQ_ORDER_ID,
@@ -175,6 +176,25 @@ def spq_query(h: SpqHandle, pairs, out=None, stream=None):
     st = lib.spq_query(h.ptr, p_p, q, o_p, _stream(stream, p_dev))
     if st:
         raise SpqError(st, "spq_query")
+    return o_k
+
+
+def spq_query_noalloc(h: SpqHandle, pairs, out=None, stream=None):
+    """spq_query for callers that cannot let the library allocate device memory: pairs
+    (int32[q, 2], q <= SPQ_NOALLOC_MAX_PAIRS) and out must be CUDA tensors; the
+    library's fixed device scratch array is used instead of an allocation (the output,
+    if not given, is allocated here by torch, outside the library)."""
+    lib = _lib.load()
+    p_p, p_k, p_dev = _ptr(pairs, np.int32)
+    if not p_dev:
+        raise ValueError("spq_query_noalloc takes device tensors")
+    q = int(p_k.shape[0]) if p_k.ndim > 1 else int(p_k.shape[0]) // 2
+    if out is None:
+        out = torch.empty(q, dtype=torch.float32 if h.wt == SPQ_F32 else torch.int32, device=p_k.device)
+    o_p, o_k, _ = _ptr(out, np.float32 if h.wt == SPQ_F32 else np.int32)
+    st = lib.spq_query_noalloc(h.ptr, p_p, q, o_p, _stream(stream, True))
+    if st:
+        raise SpqError(st, "spq_query_noalloc")
     return o_k
 
 

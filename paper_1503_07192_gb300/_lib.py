@@ -13,6 +13,7 @@ SPQ_I32, SPQ_F32 = 0, 1
 SPQ_ARITH_AUTO, SPQ_ARITH_I32, SPQ_ARITH_F32 = 0, 1, 2
 SPQ_ORDER_AUTO, SPQ_ORDER_ID, SPQ_ORDER_DISSECTION, SPQ_ORDER_VERTEX_DISSECTION = 0, 1, 2, 3
 SPQ_INF_I32 = 0x20000000
+SPQ_NOALLOC_MAX_PAIRS = 262144
 
 # Every symbol include/spq.h declares, with (restype, argtypes).
 P = ctypes.c_void_p
@@ -30,6 +31,7 @@ SIGNATURES = {
                                  ctypes.POINTER(P)]),
     "spq_query": (ctypes.c_int, [P, P, i64, P, P]),
     "spq_query_status": (ctypes.c_int, [P, P]),
+    "spq_query_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
     "spq_free": (None, [P]),
     "spq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "spq_last_cuda_error": (ctypes.c_int, []),

@@ -584,3 +584,19 @@ spq_status spq_get_bg(const spq_handle* h, void* out, void* stream) {
 }
 
 }  // extern "C"
+
+namespace spq {
+
+// Read-only view of a handle's device tables for entry points defined in other files.
+void handle_query_view(const spq_handle* h, QueryCtx<int32_t>* ci, QueryCtx<float>* cf, bool* f32store, bool* out_f32,
+                       int32_t* k) {
+    *ci = QueryCtx<int32_t>{h->n,     h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
+                            (const int32_t*)h->D, h->N, h->err};
+    *cf = QueryCtx<float>{h->n,   h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
+                          (const float*)h->D, h->N, h->err};
+    *f32store = h->f32store;
+    *out_f32 = h->wt == SPQ_F32;
+    *k = h->k;
+}
+
+}  // namespace spq

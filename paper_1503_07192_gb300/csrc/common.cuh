@@ -120,4 +120,8 @@ template <typename T>
 cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
                          uint32_t k, uint32_t* scratch, cudaStream_t st);
 
+// Read-only view of a handle's device tables (api.cu), for other entry points.
+void handle_query_view(const spq_handle* h, QueryCtx<int32_t>* ci, QueryCtx<float>* cf, bool* f32store, bool* out_f32,
+                       int32_t* k);
+
 }  // namespace spq
