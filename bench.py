@@ -145,7 +145,8 @@ class ClockSampler:
 
 def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
     """Time the oracle (Dijkstra per pair, all host cores) on a bounded sample of the
-    workload's pairs; returns (queries/s, sample size, seconds, cores)."""
+    workload's pairs: chunks of uniformly drawn pairs until budget_s has elapsed.
+    Returns (queries/s, sample size, seconds, cores)."""
     import numpy as np
 
     import oracle
@@ -154,14 +155,12 @@ def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
     cores = os.cpu_count() or 1
     g = w.graph
     rng = np.random.default_rng(seed)
-    probe = w.pairs[rng.integers(0, w.pairs.shape[0], size=4 * cores)]
-    t0 = time.perf_counter()
-    oracle.pairs_dist(g.row_ptr, g.col, g.w, probe, nthreads=cores)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    n = int(min(max(probe.shape[0] * budget_s / dt, probe.shape[0]), w.pairs.shape[0], 200_000))
-    sample = w.pairs[rng.integers(0, w.pairs.shape[0], size=n)]
-    t0 = time.perf_counter()
-    oracle.pairs_dist(g.row_ptr, g.col, g.w, sample, nthreads=cores)
+    oracle.pairs_dist(g.row_ptr, g.col, g.w, w.pairs[:cores], nthreads=cores)  # load, spin up threads
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and n < w.pairs.shape[0]:
+        chunk = w.pairs[rng.integers(0, w.pairs.shape[0], size=8 * cores)]
+        oracle.pairs_dist(g.row_ptr, g.col, g.w, chunk, nthreads=cores)
+        n += chunk.shape[0]
     dt = time.perf_counter() - t0
     return n / dt, n, dt, cores
 

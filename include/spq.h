@@ -3,14 +3,14 @@
  *
  * The data structure is the one of Chapuis & Djidjev, "Shortest-Path Queries in Planar
  * Graphs on GPU-Accelerated Architectures" (arXiv 1503.07192):
- *   - Algorithm 1, line 3: for every component C of a given k-partition, the table
+ *   - Algorithm 1, per-component step: for every component C of a given k-partition, the table
  *     APSP(C) of distances dist_C inside the subgraph induced by C (Sec. 2 defines
  *     dist_H for a subgraph H);
- *   - Algorithm 1, lines 4-6: the boundary graph BG on all boundary vertices (Sec. 2:
+ *   - Algorithm 1, clique edges and BG: the boundary graph BG on all boundary vertices (Sec. 2:
  *     vertices with a neighbour in another component), with G's edges between boundary
  *     vertices plus one edge per pair of boundary vertices of a component, weighted
  *     dist_C;
- *   - Algorithm 1, lines 7-9: all-pairs distances in BG (Lemma 1: they equal the
+ *   - Algorithm 1, APSP of BG: all-pairs distances in BG (Lemma 1: they equal the
  *     distances in G), held as one |BG| x |BG| matrix, rows and columns grouped by
  *     component (Sec. 4, Fig. 1);
  *   - Algorithm 2 (correct by Lemma 3): dist(v1, v2) = min over b1 in B(C1), b2 in B(C2)

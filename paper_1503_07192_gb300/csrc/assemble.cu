@@ -1,5 +1,5 @@
 // Table initialisation (Sec. 4: cell (i, j) holds wt(i, j) if the edge exists, else
-// infinity, and 0 on the diagonal) and boundary-graph assembly (Algorithm 1, lines 4-6).
+// infinity, and 0 on the diagonal) and boundary-graph assembly (Algorithm 1: clique edges, BG).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -98,7 +98,7 @@ __global__ void k_bg_fill(T* __restrict__ D, int64_t N) {
     }
 }
 
-// Clique edges of Algorithm 1, line 4: D[B(C), B(C)] = APSP(C)[0:|B|, 0:|B|] (the
+// Clique edges of Algorithm 1: D[B(C), B(C)] = APSP(C)[0:|B|, 0:|B|] (the
 // boundary vertices have the lowest local indices), at the slots' matrix positions.
 // One CTA per component at a time.
 template <typename T>

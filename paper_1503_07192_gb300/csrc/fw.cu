@@ -1,5 +1,5 @@
 // Blocked Floyd-Warshall in the (min, +) semiring, for the component tables APSP(C)
-// (Algorithm 1, line 3) and for the boundary graph (Algorithm 1, lines 7-9).
+// (Algorithm 1, per-component APSP) and for the boundary graph (Algorithm 1, APSP of BG).
 //
 // The paper computes APSP(C) with the GPU algorithm of its reference [ipdps-apsp] and
 // the boundary-graph rows with Dijkstra's algorithm; both are exact all-pairs distance

@@ -1,16 +1,16 @@
 // Distance queries: Algorithm 2 of the paper, one warp per query pair.
 //
-// For (v1, v2) with components C1, C2 (Algorithm 2, line 1):
-//   t(b2)  = min over b1 in B(C1) of dist_C1(v1, b1) + dist_BG(b1, b2)   (lines 2-7)
-//   dist   = min over b2 in B(C2) of t(b2) + dist_C2(b2, v2)              (lines 9-12)
-//   if C1 = C2: dist = min(dist, dist_C1(v1, v2))                         (line 13)
+// For (v1, v2) with components C1, C2:
+//   t(b2)  = min over b1 in B(C1) of dist_C1(v1, b1) + dist_BG(b1, b2)   (first loop)
+//   dist   = min over b2 in B(C2) of t(b2) + dist_C2(b2, v2)              (second loop)
+//   if C1 = C2: dist = min(dist, dist_C1(v1, v2))                         (same component)
 // dist_C1(v1, b1) is row v1 of APSP(C1) restricted to its first |B(C1)| columns (the
 // boundary vertices come first in the local order); dist_C2(b2, v2) is row v2 of
 // APSP(C2) (the tables are symmetric); dist_BG(b1, b2) is the |B(C1)| x |B(C2)| block of
 // the boundary-graph matrix at (bg_off[C1], bg_off[C2]) (the paper's Fig. 2: two
 // diagonal submatrices and one off-diagonal one).  Lanes own columns b2 (coalesced
 // reads of each block row), rows b1 are walked in order with dist_C1(v1, b1) broadcast
-// by shuffle, and a butterfly min-reduction over the warp finishes line 10-12.
+// by shuffle, and a butterfly min-reduction over the warp finishes the second loop.
 #include <cuda_runtime.h>
 #include <math.h>
 
