@@ -330,18 +330,19 @@ __global__ void __launch_bounds__(NTH, 2) k_phase2(T* __restrict__ base, const M
         const int64_t o = (int64_t)r * T_, cj = (int64_t)J * T_;
         T acc[8][8];
         load_c<T>(acc, M, n, o, cj, tx, ty);
+        // An all-infinite row tile stays all-infinite (D*(r,r) (x) inf = inf), and so
+        // does its transpose: nothing to compute or store.
+        bool fin = false;
+        const T inf = Inf<T>::value();
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
+        if (!__syncthreads_or(fin)) continue;
         minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
         store_c<T>(acc, M, n, o, cj, tx, ty);
         store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
-        if (row_finite) {
-            bool fin = false;
-            const T inf = Inf<T>::value();
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
-            if (__syncthreads_or(fin) && tid == 0) row_finite[J] = 1u;
-        }
+        if (row_finite && tid == 0) row_finite[J] = 1u;
     }
 }
 
@@ -412,7 +413,8 @@ __global__ void __launch_bounds__(NTH, 2) k_phase3_list(T* __restrict__ M, int64
 }
 
 // Build the tile list of round r from the flags phase 2 set (and clear the flags).
-// Also accumulates the number of phase-3 tiles into *tiles.
+// Also accumulates the number of phase-3 tiles into tiles[0] and of phase-2 tiles with a
+// finite entry (the ones phase 2 computed) into tiles[1].
 __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, uint32_t* __restrict__ list,
                           unsigned long long* __restrict__ tiles) {
     __shared__ uint32_t cnt;
@@ -441,7 +443,8 @@ __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, ui
     for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
     if (threadIdx.x == 0) {
         list[0] = cnt;
-        *tiles += (unsigned long long)cnt * (cnt + 1) / 2;
+        tiles[0] += (unsigned long long)cnt * (cnt + 1) / 2;  // phase-3 tiles of this round
+        tiles[1] += (unsigned long long)cnt;                  // phase-2 tiles computed (finite)
     }
 }
 
@@ -500,7 +503,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t ma
 
 int64_t fw_single_scratch_words(int64_t N) {
     int64_t R = (N + T_ - 1) / T_;
-    return 2 * R + 2 + 2;  // flags[R], list[1 + R], tile counter (u64)
+    return 2 * R + 2 + 4;  // flags[R], list[1 + R] (+1 pad), two tile counters (u64)
 }
 
 template <typename T>
@@ -547,8 +550,8 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
         }
         e = cudaGetLastError();
     }
-    unsigned long long ht = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ht, tiles, sizeof(ht), cudaMemcpyDeviceToHost, st);
+    unsigned long long htv[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(htv, tiles, sizeof(htv), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(dd, st);
     if (prof) {
@@ -561,13 +564,13 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
                 prof->p3_launches += 1;
             }
         }
-        prof->p3_updates = (double)ht * (double)T_ * T_ * T_;
+        prof->p3_updates = (double)htv[0] * (double)T_ * T_ * T_;
     }
     for (auto& ev : evs)
         if (ev) cudaEventDestroy(ev);
     if (updates) {
         double t3 = (double)T_ * T_ * T_;
-        *updates = ((double)ht + (double)R * R) * t3;  // phase-3 tiles + R phase-1 and R(R-1) phase-2 tiles
+        *updates = ((double)htv[0] + (double)htv[1] + (double)R) * t3;  // phase 3, phase 2, phase 1 tiles
     }
     return e;
 }
