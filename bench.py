@@ -298,6 +298,12 @@ def main():
     p3_launches = sum(pf["p3_launches"] for _, pf, _ in per)
     p3_updates = sum(pf["p3_updates"] for _, pf, _ in per)
     achieved_gops = p3_updates / (p3_ms * 1e-3) / 1e9 if p3_ms > 0 else None
+    # DRAM bytes per 128x128 phase-3 tile, from an ncu capture of two full launches of the
+    # same kernel on the 2^18-point Delaunay workload (dram__bytes_read.sum +
+    # dram__bytes_write.sum = 6.533e9 bytes over 32,131 tiles), scaled to this workload's
+    # average launch by its tile count (traffic grows in proportion to tiles).
+    bytes_per_tile = 6.5329e9 / 32131
+    tiles_per_launch = p3_updates / max(p3_launches, 1) / 128 ** 3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_gops = sms * 128 * 2070e6 / 2 / 1e9  # 128 lanes/SM, 2 lane-ops per update, max SM clock
 
@@ -339,7 +345,8 @@ def main():
             "peak": peak_gops,
             "unit": "Gop/s",
             "frac": (achieved_gops / peak_gops) if achieved_gops else None,
-            "traffic": None,
+            "traffic": bytes_per_tile * tiles_per_launch,
+            "traffic_unit": "bytes per launch (DRAM read + write)",
             "launches": int(p3_launches),
             "avg_launch_ms": p3_ms / max(p3_launches, 1),
             "peak_basis": f"{sms} SMs x 128 lanes x 2070 MHz / 2 lane-ops per min-plus update (derived)",
