@@ -25,6 +25,16 @@ namespace spq {
 
 namespace {
 
+// Compile-time tuning of the phase-2/3 kernels: resident CTAs per SM requested from the
+// register allocator, and unrolling of the float32 inner loop (two k steps per trip).
+#ifndef SPQ_FW_MIN_CTAS
+#define SPQ_FW_MIN_CTAS 2
+#endif
+#ifndef SPQ_FW_UNROLL
+#define SPQ_FW_UNROLL 1
+#endif
+
+constexpr int kInnerUnroll = SPQ_FW_UNROLL;
 constexpr int T_ = kTile;  // 128
 constexpr int KC = 32;     // k rows per staged panel chunk
 constexpr int NTH = 256;   // threads per CTA; each owns an 8 x 8 block of the tile
@@ -200,7 +210,7 @@ __device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>
 template <>
 __device__ __forceinline__ void compute_chunk<float>(float (&acc)[8][8], const PanelSmem<float>& sm, int s, int tx,
                                                      int ty) {
-#pragma unroll 1
+#pragma unroll kInnerUnroll
     for (int kk = 0; kk < KC; kk += 2) {
         const float4 x0 = *reinterpret_cast<const float4*>(&sm.a[s][kk][ty * 4]);
         const float4 x1 = *reinterpret_cast<const float4*>(&sm.a[s][kk][64 + ty * 4]);
@@ -315,7 +325,7 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 
 // ---------------- phase 2: pivot row tiles (and their transposes) ----------------
 template <typename T>
-__global__ void __launch_bounds__(NTH, 2) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                    int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
@@ -373,7 +383,7 @@ __device__ __forceinline__ void phase3_tile(T* __restrict__ M, int64_t n, int64_
 
 // ---------------- phase 3, batched form: tiles (I, J), I <= J, I, J != r ----------------
 template <typename T>
-__global__ void __launch_bounds__(NTH, 2) k_phase3_batched(T* __restrict__ base, const MatDesc* __restrict__ descs,
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_batched(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                            int32_t nmat, int32_t r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(NTH, 2) k_phase3_batched(T* __restrict__ base,
 // for both triangles.  Tiles outside list x list keep their values: their pivot panel
 // is entirely infinite, so min(D, inf + x) = D.
 template <typename T>
-__global__ void __launch_bounds__(NTH, 2) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
                                                         const uint32_t* __restrict__ list) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
