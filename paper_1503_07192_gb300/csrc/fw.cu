@@ -17,7 +17,6 @@
 // Arithmetic: int32 (add, min) or float32 (add, three-input min over two k steps).
 #include <cuda_runtime.h>
 
-#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -33,11 +32,6 @@ namespace {
 #endif
 #ifndef SPQ_FW_UNROLL
 #define SPQ_FW_UNROLL 1
-#endif
-// 1: the float32 kernels stage a copy of the A panel with every value written twice, so
-// the (a_i, a_i) operand pairs of the packed adds come straight from shared memory.
-#ifndef SPQ_FW_DUPA
-#define SPQ_FW_DUPA 0
 #endif
 
 constexpr int kInnerUnroll = SPQ_FW_UNROLL;
@@ -91,9 +85,6 @@ template <typename T>
 struct alignas(16) PanelSmem {
     T a[2][KC][T_];
     T b[2][KC][T_];
-#if SPQ_FW_DUPA
-    T adup[KC][2 * T_];  // adup[k][2i] = adup[k][2i+1] = a[s][k][i] of the chunk in use
-#endif
 };
 
 // Thread-owned rows / columns inside a tile: {q*4 .. q*4+3} and {64 + q*4 .. 64+q*4+3}.
@@ -250,65 +241,6 @@ __device__ __forceinline__ void compute_chunk<float>(float (&acc)[8][8], const P
     }
 }
 
-#if SPQ_FW_DUPA
-// Write stage s of the A panel twice over into adup (one float4 in, two out per item).
-__device__ __forceinline__ void duplicate_a(PanelSmem<float>& sm, int s, int tid) {
-#pragma unroll
-    for (int it = 0; it < (KC * T_ / 4) / NTH; ++it) {
-        const int idx = it * NTH + tid;
-        const int kk = idx >> 5, c4 = idx & 31;
-        const float4 v = *reinterpret_cast<const float4*>(&sm.a[s][kk][c4 * 4]);
-        *reinterpret_cast<float4*>(&sm.adup[kk][c4 * 8]) = make_float4(v.x, v.x, v.y, v.y);
-        *reinterpret_cast<float4*>(&sm.adup[kk][c4 * 8 + 4]) = make_float4(v.z, v.z, v.w, v.w);
-    }
-}
-
-// compute_chunk<float> reading the (a_i, a_i) pairs from the duplicated A panel.
-__device__ __forceinline__ void compute_chunk_dup(float (&acc)[8][8], const PanelSmem<float>& sm, int s, int tx,
-                                                  int ty) {
-#pragma unroll 1
-    for (int kk = 0; kk < KC; kk += 2) {
-        float2 p0[8], p1[8];
-        {
-            const float4 q0 = *reinterpret_cast<const float4*>(&sm.adup[kk][ty * 8]);
-            const float4 q1 = *reinterpret_cast<const float4*>(&sm.adup[kk][ty * 8 + 4]);
-            const float4 q2 = *reinterpret_cast<const float4*>(&sm.adup[kk][128 + ty * 8]);
-            const float4 q3 = *reinterpret_cast<const float4*>(&sm.adup[kk][128 + ty * 8 + 4]);
-            const float4 r0 = *reinterpret_cast<const float4*>(&sm.adup[kk + 1][ty * 8]);
-            const float4 r1 = *reinterpret_cast<const float4*>(&sm.adup[kk + 1][ty * 8 + 4]);
-            const float4 r2 = *reinterpret_cast<const float4*>(&sm.adup[kk + 1][128 + ty * 8]);
-            const float4 r3 = *reinterpret_cast<const float4*>(&sm.adup[kk + 1][128 + ty * 8 + 4]);
-            p0[0] = make_float2(q0.x, q0.y); p0[1] = make_float2(q0.z, q0.w);
-            p0[2] = make_float2(q1.x, q1.y); p0[3] = make_float2(q1.z, q1.w);
-            p0[4] = make_float2(q2.x, q2.y); p0[5] = make_float2(q2.z, q2.w);
-            p0[6] = make_float2(q3.x, q3.y); p0[7] = make_float2(q3.z, q3.w);
-            p1[0] = make_float2(r0.x, r0.y); p1[1] = make_float2(r0.z, r0.w);
-            p1[2] = make_float2(r1.x, r1.y); p1[3] = make_float2(r1.z, r1.w);
-            p1[4] = make_float2(r2.x, r2.y); p1[5] = make_float2(r2.z, r2.w);
-            p1[6] = make_float2(r3.x, r3.y); p1[7] = make_float2(r3.z, r3.w);
-        }
-        const float4 z0 = *reinterpret_cast<const float4*>(&sm.b[s][kk][tx * 4]);
-        const float4 z1 = *reinterpret_cast<const float4*>(&sm.b[s][kk][64 + tx * 4]);
-        const float4 w0 = *reinterpret_cast<const float4*>(&sm.b[s][kk + 1][tx * 4]);
-        const float4 w1 = *reinterpret_cast<const float4*>(&sm.b[s][kk + 1][64 + tx * 4]);
-        const float2 b0[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
-                              make_float2(z1.z, z1.w)};
-        const float2 b1[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
-                              make_float2(w1.z, w1.w)};
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-#pragma unroll
-            for (int jp = 0; jp < 4; ++jp) {
-                const float2 s0 = __fadd2_rn(p0[i], b0[jp]);
-                const float2 s1 = __fadd2_rn(p1[i], b1[jp]);
-                acc[i][2 * jp] = fmin3(acc[i][2 * jp], s0.x, s1.x);
-                acc[i][2 * jp + 1] = fmin3(acc[i][2 * jp + 1], s0.y, s1.y);
-            }
-        }
-    }
-}
-#endif
-
 // acc = min(acc, A (x) B) with A[i][k] = M[arow0 + k][acol0 + i] and
 // B[k][j] = M[arow0 + k][bcol0 + j], k over the pivot block [arow0, arow0 + 128).
 template <typename T>
@@ -330,17 +262,7 @@ __device__ __forceinline__ void minplus_panels(T (&acc)[8][8], const T* __restri
             cp_async_wait<0>();
         }
         __syncthreads();
-#if SPQ_FW_DUPA
-        if constexpr (std::is_same<T, float>::value) {
-            duplicate_a(sm, ch & 1, tid);
-            __syncthreads();
-            compute_chunk_dup(acc, sm, ch & 1, tx, ty);
-        } else {
-            compute_chunk<T>(acc, sm, ch & 1, tx, ty);
-        }
-#else
         compute_chunk<T>(acc, sm, ch & 1, tx, ty);
-#endif
         __syncthreads();
     }
 }
