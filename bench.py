@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="delaunay1m",
-                   choices=["delaunay1m", "grid64", "delaunay65k", "delaunay262k", "grid1024diag"])
+                   choices=["delaunay1m", "grid64", "delaunay65k", "delaunay262k", "grid1024diag", "batch512"])
+    p.add_argument("--instances", type=int, default=512, help="batch512: number of instances")
     p.add_argument("--queries", type=int, default=None, help="override the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     p.add_argument("--e2e-steps", type=int, default=1)
@@ -205,6 +206,107 @@ def run_reference(args, rank):
     return 0
 
 
+def _gen_instance(args):
+    import gen
+
+    seed, i, q_per = args
+    return gen.configs.batch_instances(count=i + 1, seed=seed, q_per=q_per, only=i)[0]
+
+
+def run_batch(args, rank, local_rank):
+    """The batching pattern: many independent instances (grids with 10% of the vertices
+    removed and Delaunay triangulations, n log-uniform in [1,000, 65,536], kd-tree
+    components with a leaf cap log-uniform in [128, 2,048], 100,000 pairs each).
+    Batched form: spq_build_many + spq_query_many, all instances in shared launches.
+    Per-graph form: spq_build + spq_query + spq_free per instance, one after another.
+    One step = every instance built and queried once (device buffers); value = pairs
+    answered per second of the batched form."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    G = args.instances
+    q_per = args.queries or 100_000
+    t0 = time.time()
+    with cf.ProcessPoolExecutor(max_workers=os.cpu_count() or 4, mp_context=mp.get_context("spawn")) as ex:
+        ins = list(ex.map(_gen_instance, [(1237, i, q_per) for i in range(G)]))
+    log(f"[rank {rank}] {G} instances, {sum(w.graph.n for w in ins)} vertices ({time.time() - t0:.1f}s)")
+
+    import numpy as np
+    import torch
+
+    import paper_1503_07192_gb300 as spq
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    spq.build()
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    graphs = [(w.graph.n, T(w.graph.row_ptr), T(w.graph.col), T(w.graph.w), T(w.part), w.k) for w in ins]
+    pairs = [T(w.pairs) for w in ins]
+    outs = [torch.empty(p.shape[0], dtype=torch.int32, device=dev) for p in pairs]
+    q_tot = sum(int(p.shape[0]) for p in pairs)
+    stream = torch.cuda.current_stream(dev)
+
+    def batched():
+        hs = spq.spq_build_many(graphs)
+        spq.spq_query_many(hs, pairs, outs=outs)
+        torch.cuda.synchronize()
+        st = hs[0].stats()
+        pf = hs[0].profile()
+        for h in hs:
+            h.free()
+        return st, pf
+
+    def per_graph():
+        for g, p, o in zip(graphs, pairs, outs):
+            h = spq.spq_build(*g)
+            spq.spq_query(h, p, out=o)
+            h.free()
+        torch.cuda.synchronize()
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = None
+        for _ in range(k):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k, r
+
+    for _ in range(args.warmup):
+        batched()
+    ref = [o.clone() for o in outs]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = spq.spq_kernel_launches()
+    ms_b, (st, pf) = timed(batched, args.steps)
+    launches = spq.spq_kernel_launches() - launches0
+    clk = clocks.stop()
+    per_graph()  # warm-up of the per-graph form
+    ms_p, _ = timed(per_graph, max(1, args.steps // 2))
+    same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    upd = sum(w.graph.n for w in ins)
+    line = {
+        "metric": METRIC, "value": q_tot / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if st["arith"] == spq.SPQ_ARITH_F32 else "int32", "data": "synthetic",
+        "config": {"workload": f"batch{G}", "instances": G, "vertices": upd, "queries_per_step": q_tot,
+                   "l2": "tables of all instances (tens of GB) rebuilt every step"},
+        "batched_ms": ms_b, "per_graph_ms": ms_p, "speedup_vs_per_graph": ms_p / ms_b,
+        "per_graph_qps": q_tot / (ms_p * 1e-3), "results_identical": bool(same),
+        "batch_stage_ms": {k: round(pf[k], 2) for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw",
+                                                         "check")},
+        "bg_updates": st["bg_updates"], "gpu_launches": int(launches) // max(1, args.steps), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -212,6 +314,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "batch512":
+        return run_batch(args, rank, local_rank)
 
     import numpy as np
     import torch

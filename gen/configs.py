@@ -61,13 +61,17 @@ def delaunay1m(q: int = 10_000_000, seed: int = 1236) -> Workload:
 
 
 def batch_instances(count: int = 512, seed: int = 1237, q_per: int = 100_000,
-                    n_lo: int = 1000, n_hi: int = 65536, leaf_lo: int = 128, leaf_hi: int = 2048) -> list:
-    """Instances of the batching workload (kd-tree components, uneven sizes)."""
+                    n_lo: int = 1000, n_hi: int = 65536, leaf_lo: int = 128, leaf_hi: int = 2048,
+                    only: Optional[int] = None) -> list:
+    """Instances of the batching workload (kd-tree components, uneven sizes).  With
+    `only`, just instance number `only` (same sizes and seeds as in the full list)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
         leaf = int(round(math.exp(rng.uniform(math.log(leaf_lo), math.log(leaf_hi)))))
+        if only is not None and i != only:
+            continue
         s = seed * 1000 + i
         if i % 2 == 0:
             g = graphs.grid_holes(n, 0.1, wmax=1000, seed=s)

@@ -173,6 +173,39 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
 #define SPQ_NOALLOC_MAX_PAIRS 262144
 spq_status spq_query_noalloc(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream);
 
+/*
+ * Many independent graphs at once (the batching pattern: many small planar instances of
+ * uneven size).  graphs[i] describes instance i exactly as spq_build's arguments do (all
+ * with the same weight type); outs[i] receives its handle.  The instances share one
+ * device allocation (released with the last of their handles) and, where the work
+ * allows, the same kernel launches: validation with one readback for all, one stable
+ * sort of every instance's vertices, the component Floyd-Warshall of all components of
+ * all instances, and the boundary-graph Floyd-Warshall of all instances round by round.
+ * Results are identical to building each instance with spq_build.  On error no handle is
+ * returned (every outs[i] is NULL).  spq_stats of such a handle reports the whole batch's
+ * boundary-graph update count.
+ */
+typedef struct spq_graph {
+    int32_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* w;
+    spq_dtype wt;
+    const int32_t* part;
+    int32_t k;
+} spq_graph;
+spq_status spq_build_many(int32_t count, const spq_graph* graphs, const spq_opts* opts, void* stream,
+                          spq_handle** outs);
+
+/*
+ * spq_query for `count` handles at once: pairs[i] (int32[q[i]][2]) against hs[i], answers
+ * in dist_out[i].  All buffers host memory (synchronous; SPQ_EINVAL if any pair was out of
+ * range) or all device memory (queued; spq_query_status per handle).  One scratch
+ * allocation serves every instance, reused in stream order.
+ */
+spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* const* pairs, const int64_t* q,
+                          void* const* dist_out, void* stream);
+
 /* Synchronise `stream`, return SPQ_EINVAL if any spq_query on h since the last call
  * met an out-of-range pair (and clear the mark), else SPQ_OK (or SPQ_ECUDA). */
 spq_status spq_query_status(spq_handle* h, void* stream);

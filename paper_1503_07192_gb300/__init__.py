@@ -160,6 +160,64 @@ def spq_build(n: int, row_ptr, col, w, part, k: int, opts: SpqOpts | None = None
     return SpqHandle(out, int(n), int(k), wt)
 
 
+def spq_build_many(graphs, opts: SpqOpts | None = None, stream=None) -> list:
+    """Build many independent graphs at once.  graphs: sequence of (n, row_ptr, col, w,
+    part, k) tuples (numpy arrays or tensors, host or device, one weight type for all).
+    Returns one SpqHandle per graph (they share one device allocation)."""
+    lib = _lib.load()
+    keep = []
+    arr = (_lib.SpqGraph * len(graphs))()
+    wt0 = None
+    dev = False
+    for i, (n, row_ptr, col, w, part, k) in enumerate(graphs):
+        wt = SPQ_F32 if (getattr(w, "dtype", None) in (np.float32, np.float64) or
+                         (_is_torch(w) and w.is_floating_point())) else SPQ_I32
+        wt0 = wt if wt0 is None else wt0
+        rp_p, rp_k, rp_d = _ptr(row_ptr, np.int64)
+        col_p, col_k, _ = _ptr(col, np.int32)
+        w_p, w_k, _ = _ptr(w, np.float32 if wt == SPQ_F32 else np.int32)
+        pt_p, pt_k, _ = _ptr(part, np.int32)
+        dev = dev or rp_d
+        keep += [rp_k, col_k, w_k, pt_k]
+        arr[i] = _lib.SpqGraph(int(n), rp_p, col_p, w_p, wt, pt_p, int(k))
+    outs = (ctypes.c_void_p * len(graphs))()
+    st = lib.spq_build_many(len(graphs), arr, ctypes.byref(opts) if opts is not None else None,
+                            _stream(stream, dev), outs)
+    del keep
+    if st:
+        raise SpqError(st, "spq_build_many")
+    return [SpqHandle(ctypes.c_void_p(outs[i]), int(graphs[i][0]), int(graphs[i][5]), arr[i].wt)
+            for i in range(len(graphs))]
+
+
+def spq_query_many(handles, pairs_list, outs=None, stream=None) -> list:
+    """spq_query for many handles at once (all pairs host or all device)."""
+    lib = _lib.load()
+    n = len(handles)
+    keep, outs_k = [], []
+    hp = (ctypes.c_void_p * n)()
+    pp = (ctypes.c_void_p * n)()
+    qq = (ctypes.c_int64 * n)()
+    op = (ctypes.c_void_p * n)()
+    dev = False
+    for i, (h, pairs) in enumerate(zip(handles, pairs_list)):
+        p_p, p_k, p_dev = _ptr(pairs, np.int32)
+        dev = dev or p_dev
+        q = int(p_k.shape[0]) if p_k.ndim > 1 else int(p_k.shape[0]) // 2
+        odt = np.float32 if h.wt == SPQ_F32 else np.int32
+        o = outs[i] if outs is not None else (
+            torch.empty(q, dtype=torch.float32 if h.wt == SPQ_F32 else torch.int32, device=p_k.device)
+            if p_dev else np.empty(q, odt))
+        o_p, o_k, _ = _ptr(o, odt)
+        keep.append(p_k)
+        outs_k.append(o_k)
+        hp[i], pp[i], qq[i], op[i] = h.ptr, p_p, q, o_p
+    st = lib.spq_query_many(n, hp, pp, qq, op, _stream(stream, dev))
+    if st:
+        raise SpqError(st, "spq_query_many")
+    return outs_k
+
+
 def spq_query(h: SpqHandle, pairs, out=None, stream=None):
     """dist(v1, v2) for each row of pairs (int32[q, 2]); returns int32[q] (float32 for
     float-weight graphs) in the same memory space as pairs."""

@@ -25,12 +25,19 @@ class SpqOpts(ctypes.Structure):
                 ("profile_kernels", i32), ("query_grouped", i32)]
 
 
+class SpqGraph(ctypes.Structure):
+    _fields_ = [("n", i32), ("row_ptr", P), ("col", P), ("w", P), ("wt", ctypes.c_int), ("part", P), ("k", i32)]
+
+
 SIGNATURES = {
     "spq_opts_default": (None, [ctypes.POINTER(SpqOpts)]),
     "spq_build": (ctypes.c_int, [i32, P, P, P, ctypes.c_int, P, i32, ctypes.POINTER(SpqOpts), P,
                                  ctypes.POINTER(P)]),
     "spq_query": (ctypes.c_int, [P, P, i64, P, P]),
     "spq_query_status": (ctypes.c_int, [P, P]),
+    "spq_build_many": (ctypes.c_int, [i32, ctypes.POINTER(SpqGraph), ctypes.POINTER(SpqOpts), P, ctypes.POINTER(P)]),
+    "spq_query_many": (ctypes.c_int, [i32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(i64),
+                                      ctypes.POINTER(P), P]),
     "spq_query_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
     "spq_free": (None, [P]),
     "spq_strerror": (ctypes.c_char_p, [ctypes.c_int]),

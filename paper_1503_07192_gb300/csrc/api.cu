@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "handle.h"
 #include "order.h"
 
 using namespace spq;
@@ -21,34 +22,6 @@ extern std::atomic<unsigned long long> g_kernel_launches;
 std::atomic<unsigned long long> g_kernel_launches{0};
 void count_launches(int n) { g_kernel_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 }  // namespace spq
-
-struct spq_handle {
-    int device = 0;
-    int32_t n = 0, k = 0;
-    spq_dtype wt = SPQ_I32;
-    bool f32store = false;  // tables hold float32 values
-    int32_t arith = SPQ_ARITH_I32;
-    int32_t* comp = nullptr;
-    int32_t* local = nullptr;
-    MatDesc* descs = nullptr;
-    int32_t* nb = nullptr;
-    int32_t* bg_off = nullptr;  // first slot of each component (component-grouped numbering)
-    int32_t* bgpos = nullptr;   // matrix position of each slot
-    int32_t order_method = 0;
-    int32_t query_grouped = 1;
-    int32_t* csize = nullptr;
-    void* apsp = nullptr;
-    void* D = nullptr;
-    uint32_t* err = nullptr;
-    int64_t N = 0, nbg = 0;
-    int64_t apsp_elems = 0;
-    size_t bytes = 0;
-    double comp_updates = 0.0, bg_updates = 0.0;
-    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-    FwProfile fwprof;
-    std::vector<int32_t> h_csize, h_nb, h_bgoff;
-    std::vector<MatDesc> h_descs;
-};
 
 namespace {
 
@@ -98,6 +71,14 @@ struct Temps {
 };
 
 void free_handle_memory(spq_handle* h) {
+    if (h->arena) {
+        if (h->arena->refs.fetch_sub(1) == 1) {
+            cudaFree(h->arena->base);
+            delete h->arena;
+        }
+        h->arena = nullptr;
+        return;
+    }
     void* ps[] = {h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, h->csize, h->apsp, h->D, h->err};
     for (void* p : ps)
         if (p) cudaFree(p);

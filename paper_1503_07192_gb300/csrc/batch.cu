@@ -1,0 +1,678 @@
+// Many graphs at once: spq_build_many (Algorithm 1 for a batch of independent
+// instances) and spq_query_many (Algorithm 2 for a query stream per instance).
+//
+// The instances share every launch where the work allows: one validation readback, one
+// device arena for all tables, one stable sort over every instance's vertices, one
+// readback of every instance's component adjacency (the host orders the instances'
+// boundary vertices in parallel threads), the component Floyd-Warshall of all
+// components of all instances in the same launches, and the boundary-graph
+// Floyd-Warshall of all instances round by round in the same launches (each instance
+// with its own list of tiles with a finite pivot panel).  The per-instance work left is
+// a handful of O(n + m) kernels (edge scatter, boundary-graph assembly).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+#include "order.h"
+
+using namespace spq;
+
+namespace {
+
+thread_local int g_batch_cuda_error = 0;
+
+spq_status batch_cuda_fail(cudaError_t e) {
+    g_batch_cuda_error = (int)e;
+    return SPQ_ECUDA;
+}
+
+#define BCK(call)                                          \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return batch_cuda_fail(e_); \
+    } while (0)
+
+bool dev_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct TempList {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit TempList(cudaStream_t s) : st(s) {}
+    ~TempList() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count) {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)p, (count ? count : 1) * sizeof(T), st);
+        if (e == cudaSuccess) ptrs.push_back((void*)*p);
+        return e;
+    }
+};
+
+// keys[vbase + v] = 2 * (kbase + part[v]) + (interior ? 1 : 0), vals = vbase + v.
+__global__ void k_make_keys_many(int32_t n, const int32_t* __restrict__ part, const uint8_t* __restrict__ bflag,
+                                 uint32_t kbase, uint32_t vbase, uint32_t* __restrict__ keys,
+                                 uint32_t* __restrict__ vals) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    keys[vbase + v] = 2u * (kbase + (uint32_t)part[v]) + (bflag[v] ? 0u : 1u);
+    vals[vbase + v] = vbase + (uint32_t)v;
+}
+
+// After the stable sort by (global component, interior): the vertex at sorted position
+// pos gets its index inside its component and its instance-local component id.
+__global__ void k_assign_local_many(int64_t ntot, const uint32_t* __restrict__ skeys,
+                                    const uint32_t* __restrict__ svals, const int64_t* __restrict__ cstart,
+                                    const int32_t* __restrict__ ckbase, int32_t* __restrict__ local,
+                                    int32_t* __restrict__ comp) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= ntot) return;
+    const uint32_t gv = svals[pos];
+    const uint32_t gc = skeys[pos] >> 1;
+    local[gv] = (int32_t)(pos - cstart[gc]);
+    comp[gv] = (int32_t)gc - ckbase[gc];
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+namespace {
+
+// One instance of the batch: its device inputs and the place of its tables.
+struct Inst {
+    int32_t n = 0, k = 0;
+    int64_t m = 0;
+    const int64_t* rp = nullptr;
+    const int32_t* col = nullptr;
+    const void* w = nullptr;
+    const int32_t* part = nullptr;
+    int64_t vbase = 0, kbase = 0, mbase = 0, slotbase = 0;  // offsets in the batch-wide arrays
+    int64_t apsp_off = 0, apsp_elems = 0, d_off = 0, N = 0, nbg = 0;
+    int32_t max_ld = 0;
+    std::vector<int32_t> csize, nb, bgoff;
+    std::vector<MatDesc> descs;  // relative to the instance's own APSP base
+};
+
+// Batch-wide device arrays (all inside the arena).
+struct BatchPtrs {
+    int32_t* comp = nullptr;
+    int32_t* local = nullptr;
+    MatDesc* descs = nullptr;
+    int32_t* nb = nullptr;
+    int32_t* bgoff = nullptr;
+    int32_t* csize = nullptr;
+    int32_t* bgpos = nullptr;
+    uint32_t* err = nullptr;
+    uint32_t* tables = nullptr;  // every APSP(C), then every boundary-graph matrix
+    int64_t table_elems = 0;
+};
+
+// Tables of every instance in element type T (Algorithm 1 after the reordering).
+template <typename T>
+cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs, int64_t ktot,
+                         int32_t max_ld, const MatDesc* d_bdescs, int32_t nbmat, int32_t max_N, bool f32w,
+                         uint32_t* fw_scratch, uint32_t* d_flag, bool check, bool* inexact, double* bg_updates,
+                         cudaEvent_t* ev, cudaStream_t st) {
+    *inexact = false;
+    T* base = reinterpret_cast<T*>(P.tables);
+    cudaError_t e;
+    cudaEventRecord(ev[2], st);
+    if ((e = launch_fill_blocks<T>(base, d_cdescs, (int32_t)ktot, st)) != cudaSuccess) return e;
+    for (auto& x : I) {
+        if (x.n == 0) continue;
+        e = launch_scatter_intra<T>(f32w, x.n, x.rp, x.col, x.w, x.part, P.local + x.vbase, P.descs + x.kbase,
+                                    base + x.apsp_off, st);
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = fw_batched<T>(base, d_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess) return e;
+    cudaEventRecord(ev[3], st);
+    for (auto& x : I) {
+        if (x.N == 0) continue;
+        T* D = base + x.d_off;
+        if ((e = launch_bg_fill<T>(D, x.N, st)) != cudaSuccess) return e;
+        e = launch_bg_clique<T>(base + x.apsp_off, P.descs + x.kbase, P.nb + x.kbase, P.bgoff + x.kbase,
+                                P.bgpos + x.slotbase, x.k, D, x.N, st);
+        if (e != cudaSuccess) return e;
+        e = launch_bg_inter<T>(f32w, x.n, x.rp, x.col, x.w, x.part, P.local + x.vbase, P.bgoff + x.kbase,
+                               P.bgpos + x.slotbase, D, x.N, st);
+        if (e != cudaSuccess) return e;
+    }
+    cudaEventRecord(ev[4], st);
+    if (nbmat > 0 && (e = fw_many_skip<T>(base, d_bdescs, nbmat, max_N, fw_scratch, bg_updates, st)) != cudaSuccess)
+        return e;
+    cudaEventRecord(ev[5], st);
+    if (check) {
+        if ((e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        if ((e = launch_check_convert(reinterpret_cast<float*>(P.tables), P.table_elems, d_flag, st)) != cudaSuccess)
+            return e;
+        uint32_t f = 0;
+        if ((e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        *inexact = (f & kErrExact) != 0;
+    }
+    cudaEventRecord(ev[6], st);
+    return cudaSuccess;
+}
+
+int bits_of(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace
+
+namespace {
+
+spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cudaStream_t st,
+                           std::vector<spq_handle*>* out) {
+    TempList tmp(st);
+    const spq_dtype wt = gs[0].wt;
+    const bool f32w = wt == SPQ_F32;
+    std::vector<Inst> I(G);
+    int64_t ntot = 0, ktot = 0, mtot = 0;
+    // ---- inputs on the device ----
+    for (int32_t g = 0; g < G; ++g) {
+        const spq_graph& a = gs[g];
+        if (a.n < 1 || a.k < 1 || !a.row_ptr || !a.part || a.wt != wt) return SPQ_EINVAL;
+        Inst& x = I[g];
+        x.n = a.n;
+        x.k = a.k;
+        int64_t ends[2] = {0, 0};
+        const bool rp_dev = dev_pointer(a.row_ptr);
+        if (rp_dev) {
+            BCK(cudaMemcpyAsync(&ends[0], a.row_ptr, 8, cudaMemcpyDeviceToHost, st));
+            BCK(cudaMemcpyAsync(&ends[1], a.row_ptr + a.n, 8, cudaMemcpyDeviceToHost, st));
+            BCK(cudaStreamSynchronize(st));
+        } else {
+            ends[0] = a.row_ptr[0];
+            ends[1] = a.row_ptr[a.n];
+        }
+        x.m = ends[1];
+        if (ends[0] != 0 || x.m < 0 || x.m > INT32_MAX || (x.m > 0 && (!a.col || !a.w))) return SPQ_EINVAL;
+        x.rp = a.row_ptr;
+        x.col = a.col;
+        x.w = a.w;
+        x.part = a.part;
+        if (!rp_dev) {
+            int64_t* p;
+            BCK(tmp.alloc(&p, (size_t)a.n + 1));
+            BCK(cudaMemcpyAsync(p, a.row_ptr, ((size_t)a.n + 1) * 8, cudaMemcpyHostToDevice, st));
+            x.rp = p;
+        }
+        if (x.m > 0 && !dev_pointer(a.col)) {
+            int32_t* p;
+            BCK(tmp.alloc(&p, (size_t)x.m));
+            BCK(cudaMemcpyAsync(p, a.col, (size_t)x.m * 4, cudaMemcpyHostToDevice, st));
+            x.col = p;
+        }
+        if (x.m > 0 && !dev_pointer(a.w)) {
+            uint32_t* p;
+            BCK(tmp.alloc(&p, (size_t)x.m));
+            BCK(cudaMemcpyAsync(p, a.w, (size_t)x.m * 4, cudaMemcpyHostToDevice, st));
+            x.w = p;
+        }
+        if (!dev_pointer(a.part)) {
+            int32_t* p;
+            BCK(tmp.alloc(&p, (size_t)a.n));
+            BCK(cudaMemcpyAsync(p, a.part, (size_t)a.n * 4, cudaMemcpyHostToDevice, st));
+            x.part = p;
+        }
+        x.vbase = ntot;
+        x.kbase = ktot;
+        x.mbase = mtot;
+        ntot += a.n;
+        ktot += a.k;
+        mtot += x.m;
+    }
+    if (ntot >= ((int64_t)1 << 31) || 2 * ktot >= ((int64_t)1 << 32)) return SPQ_EUNSUPPORTED;
+    cudaEvent_t ev[7] = {};
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 7; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } evguard{ev};
+    for (auto& e : ev) BCK(cudaEventCreate(&e));
+    cudaEventRecord(ev[0], st);
+
+    // ---- validation, boundary flags and counts of every instance; one readback ----
+    uint8_t* bflag;
+    int32_t* cnt;
+    uint32_t* errs;
+    BCK(tmp.alloc(&bflag, (size_t)ntot));
+    BCK(tmp.alloc(&cnt, 2 * (size_t)ktot));
+    BCK(tmp.alloc(&errs, (size_t)G + 1));
+    BCK(cudaMemsetAsync(cnt, 0, 2 * (size_t)ktot * 4, st));
+    BCK(cudaMemsetAsync(errs, 0, ((size_t)G + 1) * 4, st));
+    for (auto& x : I)
+        BCK(launch_validate(f32w, x.n, x.m, x.rp, x.col, x.w, x.part, x.k, bflag + x.vbase, cnt + x.kbase,
+                            cnt + ktot + x.kbase, errs + (&x - I.data()), st));
+    std::vector<int32_t> hcnt(2 * (size_t)ktot);
+    std::vector<uint32_t> herr(G);
+    BCK(cudaMemcpyAsync(hcnt.data(), cnt, hcnt.size() * 4, cudaMemcpyDeviceToHost, st));
+    BCK(cudaMemcpyAsync(herr.data(), errs, (size_t)G * 4, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    for (uint32_t f : herr)
+        if (f) return SPQ_EINVAL;
+    cudaEventRecord(ev[1], st);
+
+    // ---- plan: sizes and offsets of every table ----
+    int64_t apsp_tot = 0, slot_tot = 0;
+    int32_t max_ld = 0;
+    for (auto& x : I) {
+        x.csize.assign(hcnt.begin() + x.kbase, hcnt.begin() + x.kbase + x.k);
+        x.nb.assign(hcnt.begin() + ktot + x.kbase, hcnt.begin() + ktot + x.kbase + x.k);
+        x.descs.resize(x.k);
+        x.bgoff.resize(x.k);
+        int64_t acc = 0, bo = 0;
+        for (int32_t c = 0; c < x.k; ++c) {
+            const int32_t ld = (int32_t)round_up(x.csize[c], 4);
+            x.descs[c] = MatDesc{acc, ld, 0};
+            acc += (int64_t)ld * ld;
+            x.max_ld = std::max(x.max_ld, ld);
+            x.bgoff[c] = (int32_t)bo;
+            bo += x.nb[c];
+        }
+        x.apsp_elems = acc;
+        x.apsp_off = apsp_tot;
+        apsp_tot += acc;
+        x.nbg = bo;
+        x.N = round_up(bo, 4);
+        x.slotbase = slot_tot;
+        slot_tot += bo;
+        max_ld = std::max(max_ld, x.max_ld);
+    }
+    int64_t d_tot = 0;
+    int32_t max_N = 0, nbmat = 0;
+    for (auto& x : I) {
+        x.d_off = apsp_tot + d_tot;
+        d_tot += x.N * x.N;
+        if (x.N > 0) {
+            ++nbmat;
+            max_N = std::max(max_N, (int32_t)x.N);
+        }
+    }
+    // arena: metadata arrays, then the tables (16-byte aligned)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off = align256(off + bytes);
+        return o2;
+    };
+    const size_t o_comp = take(4 * (size_t)ntot), o_local = take(4 * (size_t)ntot);
+    const size_t o_descs = take(sizeof(MatDesc) * (size_t)ktot), o_nb = take(4 * (size_t)ktot);
+    const size_t o_bgoff = take(4 * (size_t)ktot), o_csize = take(4 * (size_t)ktot);
+    const size_t o_bgpos = take(4 * (size_t)slot_tot), o_err = take(16 * (size_t)G);
+    const int64_t table_elems = apsp_tot + d_tot;
+    const size_t o_tables = take(4 * (size_t)table_elems);
+    const size_t arena_bytes = off;
+    const int64_t fw_words = nbmat > 0 ? fw_many_scratch_words(nbmat, max_N) : 1;
+    const size_t temp_bytes = 16 * (size_t)ntot + 4 * (size_t)radix_hist_words(ntot) + 12 * (size_t)mtot +
+                              4 * (size_t)fw_words + (64u << 20);
+    size_t free_b = 0, total_b = 0;
+    BCK(cudaMemGetInfo(&free_b, &total_b));
+    if (arena_bytes + temp_bytes > free_b) return SPQ_ENOMEM;
+    void* arena_base = nullptr;
+    {
+        cudaError_t e = cudaMalloc(&arena_base, arena_bytes);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SPQ_ENOMEM : batch_cuda_fail(e);
+    }
+    struct ArenaGuard {
+        void* p;
+        ~ArenaGuard() {
+            if (p) cudaFree(p);
+        }
+    } aguard{arena_base};
+    char* ab = static_cast<char*>(arena_base);
+    BatchPtrs P;
+    P.comp = reinterpret_cast<int32_t*>(ab + o_comp);
+    P.local = reinterpret_cast<int32_t*>(ab + o_local);
+    P.descs = reinterpret_cast<MatDesc*>(ab + o_descs);
+    P.nb = reinterpret_cast<int32_t*>(ab + o_nb);
+    P.bgoff = reinterpret_cast<int32_t*>(ab + o_bgoff);
+    P.csize = reinterpret_cast<int32_t*>(ab + o_csize);
+    P.bgpos = reinterpret_cast<int32_t*>(ab + o_bgpos);
+    P.err = reinterpret_cast<uint32_t*>(ab + o_err);
+    P.tables = reinterpret_cast<uint32_t*>(ab + o_tables);
+    P.table_elems = table_elems;
+    {
+        std::vector<MatDesc> hd;
+        std::vector<int32_t> hnb, hbo, hcs;
+        hd.reserve(ktot);
+        for (auto& x : I) {
+            hd.insert(hd.end(), x.descs.begin(), x.descs.end());
+            hnb.insert(hnb.end(), x.nb.begin(), x.nb.end());
+            hbo.insert(hbo.end(), x.bgoff.begin(), x.bgoff.end());
+            hcs.insert(hcs.end(), x.csize.begin(), x.csize.end());
+        }
+        BCK(cudaMemcpyAsync(P.descs, hd.data(), hd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(P.nb, hnb.data(), hnb.size() * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(P.bgoff, hbo.data(), hbo.size() * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(P.csize, hcs.data(), hcs.size() * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemsetAsync(P.err, 0, 16 * (size_t)G, st));
+        BCK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    }
+
+    // ---- one stable sort of every instance's vertices by (global component, interior) ----
+    {
+        uint32_t *k0, *v0, *k1, *v1, *hist;
+        BCK(tmp.alloc(&k0, (size_t)ntot));
+        BCK(tmp.alloc(&v0, (size_t)ntot));
+        BCK(tmp.alloc(&k1, (size_t)ntot));
+        BCK(tmp.alloc(&v1, (size_t)ntot));
+        BCK(tmp.alloc(&hist, (size_t)radix_hist_words(ntot)));
+        for (auto& x : I) {
+            k_make_keys_many<<<(x.n + 255) / 256, 256, 0, st>>>(x.n, x.part, bflag + x.vbase, (uint32_t)x.kbase,
+                                                                (uint32_t)x.vbase, k0, v0);
+            count_launches(1);
+        }
+        BCK(cudaGetLastError());
+        bool in_k1 = false;
+        BCK(radix_sort_pairs(k0, v0, k1, v1, hist, ntot, bits_of(2 * (uint64_t)ktot - 1), &in_k1, st));
+        std::vector<int64_t> cstart(ktot);
+        std::vector<int32_t> ckbase(ktot);
+        int64_t pos = 0;
+        for (auto& x : I)
+            for (int32_t c = 0; c < x.k; ++c) {
+                cstart[x.kbase + c] = pos;
+                ckbase[x.kbase + c] = (int32_t)x.kbase;
+                pos += x.csize[c];
+            }
+        int64_t* d_cstart;
+        int32_t* d_ckbase;
+        BCK(tmp.alloc(&d_cstart, (size_t)ktot));
+        BCK(tmp.alloc(&d_ckbase, (size_t)ktot));
+        BCK(cudaMemcpyAsync(d_cstart, cstart.data(), (size_t)ktot * 8, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(d_ckbase, ckbase.data(), (size_t)ktot * 4, cudaMemcpyHostToDevice, st));
+        k_assign_local_many<<<(unsigned)((ntot + 255) / 256), 256, 0, st>>>(
+            ntot, in_k1 ? k1 : k0, in_k1 ? v1 : v0, d_cstart, d_ckbase, P.local, P.comp);
+        count_launches(1);
+        BCK(cudaGetLastError());
+        BCK(cudaStreamSynchronize(st));  // cstart / ckbase go out of scope
+    }
+
+    // ---- boundary-slot order of every instance: one gather, host ordering in threads ----
+    std::vector<int32_t> bgpos(slot_tot);
+    std::vector<int32_t> methods(G, 0);
+    for (auto& x : I)
+        for (int64_t i = 0; i < x.nbg; ++i) bgpos[x.slotbase + i] = (int32_t)i;
+    if ((spq_order)o.order != SPQ_ORDER_ID && mtot > 0) {
+        uint32_t *keys, *counters;
+        int32_t *slots, *comps;
+        BCK(tmp.alloc(&keys, (size_t)mtot));
+        BCK(tmp.alloc(&slots, (size_t)mtot));
+        BCK(tmp.alloc(&comps, (size_t)mtot));
+        BCK(tmp.alloc(&counters, 2 * (size_t)G));
+        BCK(cudaMemsetAsync(counters, 0, 2 * (size_t)G * 4, st));
+        for (int32_t g = 0; g < G; ++g) {
+            const Inst& x = I[g];
+            if (x.m == 0 || x.k < 4 || x.k > 65536 || x.nbg == 0) continue;
+            BCK(launch_emit_comp_pairs(x.n, x.rp, x.col, x.part, x.k, keys + x.mbase, counters + 2 * g, st));
+            BCK(launch_emit_slot_pairs(x.n, x.rp, x.col, x.part, P.local + x.vbase, P.bgoff + x.kbase,
+                                       slots + x.mbase, comps + x.mbase, counters + 2 * g + 1, st));
+        }
+        std::vector<uint32_t> hc(2 * (size_t)G);
+        BCK(cudaMemcpyAsync(hc.data(), counters, hc.size() * 4, cudaMemcpyDeviceToHost, st));
+        BCK(cudaStreamSynchronize(st));
+        std::vector<std::vector<uint32_t>> hk(G);
+        std::vector<std::vector<int32_t>> hs(G), hcm(G);
+        for (int32_t g = 0; g < G; ++g) {
+            const Inst& x = I[g];
+            hk[g].resize(hc[2 * g]);
+            hs[g].resize(hc[2 * g + 1]);
+            hcm[g].resize(hc[2 * g + 1]);
+            if (hc[2 * g])
+                BCK(cudaMemcpyAsync(hk[g].data(), keys + x.mbase, hc[2 * g] * 4, cudaMemcpyDeviceToHost, st));
+            if (hc[2 * g + 1]) {
+                BCK(cudaMemcpyAsync(hs[g].data(), slots + x.mbase, hc[2 * g + 1] * 4, cudaMemcpyDeviceToHost, st));
+                BCK(cudaMemcpyAsync(hcm[g].data(), comps + x.mbase, hc[2 * g + 1] * 4, cudaMemcpyDeviceToHost, st));
+            }
+        }
+        BCK(cudaStreamSynchronize(st));
+        std::atomic<int32_t> next{0};
+        std::atomic<int> bad{0};
+        auto worker = [&]() {
+            for (;;) {
+                const int32_t g = next.fetch_add(1);
+                if (g >= G) return;
+                const Inst& x = I[g];
+                if (hk[g].empty()) continue;
+                std::vector<int32_t> bp;
+                int32_t meth = 0;
+                if (boundary_order_host(x.k, x.nb, std::move(hk[g]), hs[g], hcm[g], (spq_order)o.order, &bp,
+                                        &meth) != SPQ_OK ||
+                    (int64_t)bp.size() != x.nbg) {
+                    bad = 1;
+                    continue;
+                }
+                std::copy(bp.begin(), bp.end(), bgpos.begin() + x.slotbase);
+                methods[g] = meth;
+            }
+        };
+        const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 16));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(worker);
+        worker();
+        for (auto& t : pool) t.join();
+        if (bad) return SPQ_EINVAL;
+    }
+    if (slot_tot > 0) BCK(cudaMemcpyAsync(P.bgpos, bgpos.data(), (size_t)slot_tot * 4, cudaMemcpyHostToDevice, st));
+
+    // ---- tables of every instance ----
+    std::vector<MatDesc> cd, bd;
+    cd.reserve(ktot);
+    for (auto& x : I) {
+        for (const MatDesc& d : x.descs) cd.push_back(MatDesc{x.apsp_off + d.off, d.n, 0});
+        if (x.N > 0) bd.push_back(MatDesc{x.d_off, (int32_t)x.N, 0});
+    }
+    MatDesc *d_cd, *d_bd;
+    uint32_t *fw_scratch, *d_flag;
+    BCK(tmp.alloc(&d_cd, cd.size()));
+    BCK(tmp.alloc(&d_bd, bd.size()));
+    BCK(tmp.alloc(&fw_scratch, (size_t)fw_words));
+    BCK(tmp.alloc(&d_flag, 1));
+    BCK(cudaMemcpyAsync(d_cd, cd.data(), cd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+    if (!bd.empty()) BCK(cudaMemcpyAsync(d_bd, bd.data(), bd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+    double bg_updates = 0.0;
+    bool f32store = false;
+    int32_t arith = SPQ_ARITH_I32;
+    bool inexact = false;
+    if (f32w) {
+        f32store = true;
+        arith = SPQ_ARITH_F32;
+        BCK(batch_tables<float>(I, P, d_cd, ktot, max_ld, d_bd, nbmat, max_N, true, fw_scratch, d_flag, false,
+                                &inexact, &bg_updates, ev, st));
+    } else {
+        const bool try_f32 = o.arith != SPQ_ARITH_I32;
+        if (try_f32) {
+            arith = SPQ_ARITH_F32;
+            BCK(batch_tables<float>(I, P, d_cd, ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag, true,
+                                    &inexact, &bg_updates, ev, st));
+        }
+        if (!try_f32 || inexact) {
+            arith = SPQ_ARITH_I32;
+            BCK(batch_tables<int32_t>(I, P, d_cd, ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag,
+                                      false, &inexact, &bg_updates, ev, st));
+        }
+    }
+    BCK(cudaStreamSynchronize(st));
+    double prof[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 6; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) prof[i] = t;
+    }
+    cudaGetLastError();
+
+    // ---- one handle per instance, all pointing into the arena ----
+    int dev = 0;
+    BCK(cudaGetDevice(&dev));
+    Arena* ar = new (std::nothrow) Arena();
+    if (!ar) return SPQ_ENOMEM;
+    ar->base = arena_base;
+    ar->refs = G;
+    aguard.p = nullptr;  // owned by the handles from here on
+    out->resize(G, nullptr);
+    for (int32_t g = 0; g < G; ++g) {
+        const Inst& x = I[g];
+        spq_handle* h = new (std::nothrow) spq_handle();
+        if (!h) {  // nothing was handed out yet: release everything
+            for (int32_t j = 0; j < g; ++j) delete (*out)[j];
+            cudaFree(ar->base);
+            delete ar;
+            out->clear();
+            return SPQ_ENOMEM;
+        }
+        h->device = dev;
+        h->n = x.n;
+        h->k = x.k;
+        h->wt = wt;
+        h->f32store = f32store;
+        h->arith = arith;
+        h->query_grouped = o.query_grouped;
+        h->order_method = methods[g];
+        h->comp = P.comp + x.vbase;
+        h->local = P.local + x.vbase;
+        h->descs = P.descs + x.kbase;
+        h->nb = P.nb + x.kbase;
+        h->bg_off = P.bgoff + x.kbase;
+        h->csize = P.csize + x.kbase;
+        h->bgpos = P.bgpos + x.slotbase;
+        h->err = P.err + 4 * (int64_t)g;
+        h->apsp = P.tables + x.apsp_off;
+        h->D = x.N > 0 ? (void*)(P.tables + x.d_off) : nullptr;
+        h->N = x.N;
+        h->nbg = x.nbg;
+        h->apsp_elems = x.apsp_elems;
+        h->bytes = 4 * (size_t)(x.apsp_elems + x.N * x.N) + 8 * (size_t)x.n + 16 * (size_t)x.k + 4 * (size_t)x.nbg;
+        double cu = 0.0;
+        for (const MatDesc& d : x.descs) {
+            const double R = (double)((d.n + kTile - 1) / kTile);
+            cu += R * (1.0 + (R - 1.0) + R * (R - 1.0) / 2.0) * (double)kTile * kTile * kTile;
+        }
+        h->comp_updates = cu;
+        h->bg_updates = bg_updates;  // the whole batch's boundary-graph updates
+        for (int i = 0; i < 6; ++i) h->prof_ms[i] = prof[i];
+        h->h_csize = x.csize;
+        h->h_nb = x.nb;
+        h->h_bgoff = x.bgoff;
+        h->h_descs = x.descs;
+        h->arena = ar;
+        (*out)[g] = h;
+    }
+    return SPQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spq_status spq_build_many(int32_t count, const spq_graph* graphs, const spq_opts* opts, void* stream,
+                          spq_handle** outs) {
+    if (count < 1 || !graphs || !outs) return SPQ_EINVAL;
+    for (int32_t g = 0; g < count; ++g) outs[g] = nullptr;
+    spq_opts o;
+    spq_opts_default(&o);
+    if (opts) {
+        if (opts->struct_size < (int32_t)sizeof(spq_opts)) return SPQ_EINVAL;
+        o = *opts;
+        if (o.arith < SPQ_ARITH_AUTO || o.arith > SPQ_ARITH_F32) return SPQ_EINVAL;
+        if (o.order < SPQ_ORDER_AUTO || o.order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
+    }
+    std::vector<spq_handle*> hs;
+    const spq_status s = build_many_impl(count, graphs, o, (cudaStream_t)stream, &hs);
+    if (s != SPQ_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        return s;
+    }
+    for (int32_t g = 0; g < count; ++g) outs[g] = hs[g];
+    return SPQ_OK;
+}
+
+spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* const* pairs, const int64_t* q,
+                          void* const* dist_out, void* stream) {
+    if (count < 0 || (count > 0 && (!hs || !pairs || !q || !dist_out))) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t qmax = 0, qtot = 0;
+    bool any_dev = false, any_host = false;
+    for (int32_t i = 0; i < count; ++i) {
+        if (!hs[i] || q[i] < 0 || (q[i] > 0 && (!pairs[i] || !dist_out[i]))) return SPQ_EINVAL;
+        if (q[i] == 0) continue;
+        const bool pd = dev_pointer(pairs[i]), od = dev_pointer(dist_out[i]);
+        if (pd != od) return SPQ_EINVAL;
+        if (pd && (((uintptr_t)pairs[i] & 7u) || ((uintptr_t)dist_out[i] & 3u))) return SPQ_EINVAL;
+        (pd ? any_dev : any_host) = true;
+        qmax = std::max(qmax, q[i]);
+        qtot += q[i];
+    }
+    if (qtot == 0) return SPQ_OK;
+    if (any_dev && any_host) return SPQ_EINVAL;
+    TempList tmp(st);
+    // one scratch for every instance's grouped form, reused in stream order
+    uint32_t* scratch;
+    BCK(tmp.alloc(&scratch, (size_t)query_scratch_words(qmax)));
+    int32_t* dpairs = nullptr;
+    int32_t* dout = nullptr;
+    if (any_host) {
+        BCK(tmp.alloc(&dpairs, 2 * (size_t)qtot));
+        BCK(tmp.alloc(&dout, (size_t)qtot));
+    }
+    int64_t base = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (q[i] == 0) continue;
+        const int32_t* p = pairs[i];
+        void* o = dist_out[i];
+        if (any_host) {
+            BCK(cudaMemcpyAsync(dpairs + 2 * base, pairs[i], 2 * (size_t)q[i] * 4, cudaMemcpyHostToDevice, st));
+            p = dpairs + 2 * base;
+            o = dout + base;
+        }
+        QueryCtx<int32_t> ci;
+        QueryCtx<float> cf;
+        bool f32store = false, out_f32 = false;
+        int32_t k = 0;
+        handle_query_view(hs[i], &ci, &cf, &f32store, &out_f32, &k);
+        uint32_t* sc = hs[i]->query_grouped ? scratch : nullptr;
+        BCK(f32store ? launch_query<float>(cf, p, q[i], o, out_f32, (uint32_t)k, sc, st)
+                     : launch_query<int32_t>(ci, p, q[i], o, out_f32, (uint32_t)k, sc, st));
+        if (any_host)
+            BCK(cudaMemcpyAsync(dist_out[i], dout + base, (size_t)q[i] * 4, cudaMemcpyDeviceToHost, st));
+        base += q[i];
+    }
+    if (any_host) {
+        BCK(cudaStreamSynchronize(st));
+        bool bad = false;
+        for (int32_t i = 0; i < count; ++i) {
+            if (q[i] == 0) continue;
+            uint32_t f = 0;
+            BCK(cudaMemcpy(&f, hs[i]->err, sizeof(f), cudaMemcpyDeviceToHost));
+            if (f & kErrPair) {
+                bad = true;
+                BCK(cudaMemset(hs[i]->err, 0, sizeof(uint32_t)));
+            }
+        }
+        if (bad) return SPQ_EINVAL;
+    }
+    return SPQ_OK;
+}
+
+}  // extern "C"

@@ -61,6 +61,8 @@ cudaError_t launch_validate(bool f32, int32_t n, int64_t m, const int64_t* rp, c
 // the input, k1/v1 are scratch of the same size; hist needs radix_hist_words(n) words.
 // Returns (via *in_k1) whether the sorted result ended in k1/v1.
 int64_t radix_hist_words(int64_t n);
+// In-place exclusive prefix sum of len words (one CTA; for short arrays).
+cudaError_t launch_scan_excl(uint32_t* a, int64_t len, cudaStream_t st);
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist, int64_t n,
                              int key_bits, bool* in_k1, cudaStream_t st);
 cudaError_t launch_make_keys(int32_t n, const int32_t* part, const uint8_t* bflag, uint32_t* keys, uint32_t* vals,
@@ -97,6 +99,12 @@ template <typename T>
 cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, double* updates, FwProfile* prof,
                       cudaStream_t st);
 int64_t fw_single_scratch_words(int64_t N);
+// Many matrices (sizes up to max_n) at once, with infinite-panel skipping per matrix;
+// *updates receives the phase-2 and phase-3 min-plus updates issued.
+template <typename T>
+cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
+                         double* updates, cudaStream_t st);
+int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n);
 
 // ---- query.cu ----
 template <typename T>

@@ -326,7 +326,8 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 // ---------------- phase 2: pivot row tiles (and their transposes) ----------------
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
-                                                   int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite) {
+                                                   int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite,
+                                                   int32_t flag_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
         minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
         store_c<T>(acc, M, n, o, cj, tx, ty);
         store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
-        if (row_finite && tid == 0) row_finite[J] = 1u;
+        if (row_finite && tid == 0) row_finite[(int64_t)mi * flag_stride + J] = 1u;
     }
 }
 
@@ -458,6 +459,77 @@ __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, ui
     }
 }
 
+// ---------------- many matrices with infinite-panel skipping ----------------
+// Per matrix mi (one CTA each): compact the flags of round r into the list at
+// lists[mi * lstride] (count, then tile indices) and write the matrix's phase-3 task
+// count c(c+1)/2 into offs[mi] (offs is scanned to task offsets afterwards).
+__global__ void k_compact_many(uint32_t* __restrict__ flags, int32_t fstride, const MatDesc* __restrict__ descs,
+                               int32_t nmat, int32_t r, uint32_t* __restrict__ lists, int32_t lstride,
+                               uint32_t* __restrict__ offs, unsigned long long* __restrict__ tiles) {
+    __shared__ uint32_t cnt;
+    __shared__ uint32_t wsum[32];
+    const int32_t mi = blockIdx.x;
+    if (mi >= nmat) return;
+    const int32_t R = (descs[mi].n + T_ - 1) / T_;
+    uint32_t* f = flags + (int64_t)mi * fstride;
+    uint32_t* list = lists + (int64_t)mi * lstride;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int32_t base = 0; base < R && r < R; base += blockDim.x) {
+        const int32_t J = base + threadIdx.x;
+        const bool take = J < R && J != r && f[J] != 0u;
+        const unsigned ballot = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) wsum[warp] = __popc(ballot);
+        __syncthreads();
+        uint32_t off = cnt;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (take) list[1 + off + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)J;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+            cnt += tot;
+        }
+        __syncthreads();
+    }
+    for (int32_t J = threadIdx.x; J < R; J += blockDim.x) f[J] = 0u;
+    if (threadIdx.x == 0) {
+        const uint32_t c = r < R ? cnt : 0u;
+        list[0] = c;
+        offs[mi] = c * (c + 1) / 2;
+        atomicAdd(&tiles[0], (unsigned long long)c * (c + 1) / 2);
+        atomicAdd(&tiles[1], (unsigned long long)c);
+    }
+}
+
+// Phase 3 over the task lists of every matrix: offs[0..nmat] holds the exclusive task
+// offsets (offs[nmat] = total); task t belongs to the matrix whose range holds it.
+template <typename T>
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_many(T* __restrict__ base,
+                                                                      const MatDesc* __restrict__ descs, int32_t nmat,
+                                                                      int32_t r, const uint32_t* __restrict__ lists,
+                                                                      int32_t lstride,
+                                                                      const uint32_t* __restrict__ offs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t total = offs[nmat];
+    const int64_t o = (int64_t)r * T_;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int32_t lo = 0, hi = nmat;  // largest mi with offs[mi] <= t
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if ((int64_t)offs[mid] <= t) lo = mid; else hi = mid;
+        }
+        const MatDesc d = descs[lo];
+        const uint32_t* list = lists + (int64_t)lo * lstride;
+        int64_t x, y;
+        tri_pair(t - (int64_t)offs[lo], (int64_t)list[0], x, y);
+        phase3_tile<T>(base + d.off, d.n, o, (int64_t)list[1 + x], (int64_t)list[1 + y], sm, tid, tx, ty);
+    }
+}
+
 int g_sms = 0;
 int sms() {
     if (g_sms == 0) {
@@ -483,6 +555,8 @@ cudaError_t set_smem_attrs() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase3_many<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
     done = true;
     return cudaSuccess;
 }
@@ -501,7 +575,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t ma
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, nullptr);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, nullptr, 0);
             k_phase3_batched<T><<<dim3((R - 1) * R / 2, gy), NTH, psm, st>>>(base, d_descs, nmat, r);
             count_launches(2);
         }
@@ -547,7 +621,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
         k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags);
+            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags, 0);
             if (!skip_inf) {
                 // mark every tile: the compaction then lists all J != r
                 cudaMemsetAsync(flags, 0xff, R * sizeof(uint32_t), st);
@@ -584,6 +658,54 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
     }
     return e;
 }
+
+int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n) {
+    const int64_t R = (max_n + T_ - 1) / T_;
+    return (int64_t)nmat * R + (int64_t)nmat * (R + 1) + nmat + 1 + 1 + 4;
+}
+
+template <typename T>
+cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
+                         double* updates, cudaStream_t st) {
+    if (updates) *updates = 0.0;
+    if (nmat <= 0 || max_n <= 0) return cudaSuccess;
+    cudaError_t e = set_smem_attrs<T>();
+    if (e != cudaSuccess) return e;
+    const int32_t R = (max_n + T_ - 1) / T_;
+    uint32_t* flags = scratch;
+    uint32_t* lists = flags + (int64_t)nmat * R;
+    uint32_t* offs = lists + (int64_t)nmat * (R + 1);
+    int64_t toff = (int64_t)nmat * R + (int64_t)nmat * (R + 1) + nmat + 1;
+    toff += toff & 1;  // 8-byte alignment of the counters
+    unsigned long long* tiles = reinterpret_cast<unsigned long long*>(scratch + toff);
+    e = cudaMemsetAsync(scratch, 0, fw_many_scratch_words(nmat, max_n) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const unsigned gy = (unsigned)(nmat < 65535 ? nmat : 65535);
+    const size_t psm = sizeof(PanelSmem<T>);
+    const int p3_grid = sms() * 2;
+    for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
+        k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r);
+        count_launches(1);
+        if (R > 1) {
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R);
+            k_compact_many<<<nmat, 1024, 0, st>>>(flags, R, d_descs, nmat, r, lists, R + 1, offs, tiles);
+            launch_scan_excl(offs, nmat + 1, st);
+            k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs);
+            count_launches(4);
+        }
+        e = cudaGetLastError();
+    }
+    unsigned long long htv[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(htv, tiles, sizeof(htv), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // phase-3 and phase-2 tiles; the caller adds the phase-1 (diagonal) tiles
+    if (updates) *updates = ((double)htv[0] + (double)htv[1]) * (double)T_ * T_ * T_;
+    return e;
+}
+
+template cudaError_t fw_many_skip<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, uint32_t*, double*,
+                                           cudaStream_t);
+template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_t, uint32_t*, double*, cudaStream_t);
 
 template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_batched<float>(float*, const MatDesc*, int32_t, int32_t, cudaStream_t);

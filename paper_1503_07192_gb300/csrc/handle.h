@@ -1,0 +1,50 @@
+// The query structure of one graph (definition shared by the library's host files).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "common.cuh"
+
+namespace spq {
+
+// One device allocation shared by the handles of a batch (spq_build_many); freed with
+// the last of them.
+struct Arena {
+    void* base = nullptr;
+    std::atomic<int> refs{0};
+};
+
+}  // namespace spq
+
+struct spq_handle {
+    int device = 0;
+    int32_t n = 0, k = 0;
+    spq_dtype wt = SPQ_I32;
+    bool f32store = false;  // tables hold float32 values
+    int32_t arith = SPQ_ARITH_I32;
+    int32_t* comp = nullptr;
+    int32_t* local = nullptr;
+    spq::MatDesc* descs = nullptr;
+    int32_t* nb = nullptr;
+    int32_t* bg_off = nullptr;  // first slot of each component (component-grouped numbering)
+    int32_t* bgpos = nullptr;   // matrix position of each slot
+    int32_t order_method = 0;
+    int32_t query_grouped = 1;
+    int32_t* csize = nullptr;
+    void* apsp = nullptr;
+    void* D = nullptr;
+    uint32_t* err = nullptr;
+    int64_t N = 0, nbg = 0;
+    int64_t apsp_elems = 0;
+    size_t bytes = 0;
+    double comp_updates = 0.0, bg_updates = 0.0;
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    spq::FwProfile fwprof;
+    std::vector<int32_t> h_csize, h_nb, h_bgoff;
+    std::vector<spq::MatDesc> h_descs;
+    spq::Arena* arena = nullptr;  // set: every device pointer above lies in the arena
+};

@@ -26,7 +26,7 @@ __global__ void k_emit_comp_pairs(int32_t n, const int64_t* __restrict__ rp, con
         if (cv == cu) continue;
         uint32_t i = atomicAdd(count, 1u);
         keys[i] = cu * k + cv;
-        vals[i] = 0u;
+        if (vals) vals[i] = 0u;
     }
 }
 
@@ -503,6 +503,23 @@ void vertex_nd(int rule, int32_t k, const std::vector<int64_t>& ptr, const std::
 
 }  // namespace
 
+cudaError_t launch_emit_comp_pairs(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part, int32_t k,
+                                   uint32_t* keys, uint32_t* count, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_emit_comp_pairs<<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, part, (uint32_t)k, keys, nullptr, count);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_slot_pairs(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part,
+                                   const int32_t* local, const int32_t* slot_off, int32_t* slots, int32_t* comps,
+                                   uint32_t* count, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_emit_slot_pairs<<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, part, local, slot_off, slots, comps, count);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std::vector<int32_t>& adj,
                        const std::vector<int32_t>& weight, std::vector<int32_t>* order) {
     order->clear();
@@ -511,6 +528,75 @@ void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std
     std::vector<int32_t> all(k);
     for (int32_t c = 0; c < k; ++c) all[c] = c;
     nd.run(std::move(all));
+}
+
+spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::vector<uint32_t> hk,
+                               const std::vector<int32_t>& hs, const std::vector<int32_t>& hcmp, spq_order ord,
+                               std::vector<int32_t>* bgpos, int32_t* method) {
+    std::vector<int64_t> slot_off(k + 1, 0);
+    for (int32_t c = 0; c < k; ++c) slot_off[c + 1] = slot_off[c] + nb[c];
+    const int64_t nslots = slot_off[k];
+    bgpos->resize(nslots);
+    for (int64_t i = 0; i < nslots; ++i) (*bgpos)[i] = (int32_t)i;
+    *method = 0;
+    if (ord == SPQ_ORDER_ID || k < 4 || k > 65536 || hk.empty() || nslots == 0) return SPQ_OK;
+    if (!std::is_sorted(hk.begin(), hk.end())) std::sort(hk.begin(), hk.end());
+    hk.erase(std::unique(hk.begin(), hk.end()), hk.end());
+    std::vector<int64_t> ptr(k + 1, 0);
+    for (uint32_t key : hk) ptr[key / (uint32_t)k + 1]++;
+    for (int32_t c = 0; c < k; ++c) ptr[c + 1] += ptr[c];
+    std::vector<int32_t> adj(hk.size());
+    for (size_t i = 0; i < hk.size(); ++i) adj[i] = (int32_t)(hk[i] % (uint32_t)k);  // sorted by source
+    std::vector<int32_t> w(k);
+    for (int32_t c = 0; c < k; ++c) w[c] = nb[c] > 0 ? nb[c] : 1;
+    // candidates: id order, level-structure nested dissection, id-range nested
+    // dissection of the components; keep the one of least symbolic cost
+    std::vector<std::vector<int32_t>> cand(3);
+    cand[0].resize(k);
+    for (int32_t c = 0; c < k; ++c) cand[0][c] = c;
+    nested_dissection(k, ptr, adj, w, &cand[1]);
+    id_split_nd(ptr, adj, w, k, &cand[2]);
+    const size_t first = (ord == SPQ_ORDER_AUTO) ? 0 : 1;
+    size_t best = first;
+    double best_cost = fw_order_cost(ptr, adj, w, cand[first]);
+    for (size_t i = first + 1; i < cand.size(); ++i) {
+        double c = fw_order_cost(ptr, adj, w, cand[i]);
+        if (c < best_cost) {
+            best_cost = c;
+            best = i;
+        }
+    }
+    *method = (int32_t)best;
+    if (best == 0) return SPQ_OK;
+    std::vector<int32_t> slot_order;
+    slot_order.reserve(nslots);
+    if (ord == SPQ_ORDER_DISSECTION) {
+        for (int32_t c : cand[best])
+            for (int64_t sl = slot_off[c]; sl < slot_off[c + 1]; ++sl) slot_order.push_back((int32_t)sl);
+    } else {
+        // per-slot neighbour components (counting sort by slot, then unique per slot)
+        std::vector<int64_t> snb_ptr(nslots + 1, 0);
+        for (int32_t sl : hs) snb_ptr[sl + 1]++;
+        for (int64_t i = 0; i < nslots; ++i) snb_ptr[i + 1] += snb_ptr[i];
+        std::vector<int32_t> snb(hs.size());
+        std::vector<int64_t> fill(snb_ptr.begin(), snb_ptr.end() - 1);
+        for (size_t i = 0; i < hs.size(); ++i) snb[fill[hs[i]]++] = hcmp[i];
+        std::vector<int64_t> uptr(nslots + 1, 0);
+        int64_t wpos = 0;
+        for (int64_t sl = 0; sl < nslots; ++sl) {
+            auto b = snb.begin() + snb_ptr[sl], en = snb.begin() + snb_ptr[sl + 1];
+            std::sort(b, en);
+            auto u = std::unique(b, en);
+            uptr[sl] = wpos;
+            for (auto it = b; it != u; ++it) snb[wpos++] = *it;
+        }
+        uptr[nslots] = wpos;
+        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order);
+        *method = (int32_t)best + 2;
+    }
+    if ((int64_t)slot_order.size() != nslots) return SPQ_EINVAL;  // cannot happen: every slot is emitted once
+    for (int64_t i = 0; i < nslots; ++i) (*bgpos)[slot_order[i]] = (int32_t)i;
+    return SPQ_OK;
 }
 
 spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
@@ -583,63 +669,7 @@ spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32
     for (uint32_t* p : ps)
         if (p) cudaFreeAsync(p, st);
     if (e != cudaSuccess) return SPQ_ECUDA;
-    if (hc == 0) return SPQ_OK;
-    hk.erase(std::unique(hk.begin(), hk.end()), hk.end());
-    std::vector<int64_t> ptr(k + 1, 0);
-    for (uint32_t key : hk) ptr[key / (uint32_t)k + 1]++;
-    for (int32_t c = 0; c < k; ++c) ptr[c + 1] += ptr[c];
-    std::vector<int32_t> adj(hk.size());
-    for (size_t i = 0; i < hk.size(); ++i) adj[i] = (int32_t)(hk[i] % (uint32_t)k);  // sorted by source
-    std::vector<int32_t> w(k);
-    for (int32_t c = 0; c < k; ++c) w[c] = nb[c] > 0 ? nb[c] : 1;
-    // candidates: id order, level-structure nested dissection, id-range nested
-    // dissection of the components; keep the one of least symbolic cost
-    std::vector<std::vector<int32_t>> cand(3);
-    cand[0].resize(k);
-    for (int32_t c = 0; c < k; ++c) cand[0][c] = c;
-    nested_dissection(k, ptr, adj, w, &cand[1]);
-    id_split_nd(ptr, adj, w, k, &cand[2]);
-    const size_t first = (ord == SPQ_ORDER_AUTO) ? 0 : 1;
-    size_t best = first;
-    double best_cost = fw_order_cost(ptr, adj, w, cand[first]);
-    for (size_t i = first + 1; i < cand.size(); ++i) {
-        double c = fw_order_cost(ptr, adj, w, cand[i]);
-        if (c < best_cost) {
-            best_cost = c;
-            best = i;
-        }
-    }
-    *method = (int32_t)best;
-    if (best == 0) return SPQ_OK;
-    std::vector<int32_t> slot_order;
-    slot_order.reserve(nslots);
-    if (ord == SPQ_ORDER_DISSECTION) {
-        for (int32_t c : cand[best])
-            for (int64_t sl = slot_off[c]; sl < slot_off[c + 1]; ++sl) slot_order.push_back((int32_t)sl);
-    } else {
-        // per-slot neighbour components (counting sort by slot, then unique per slot)
-        std::vector<int64_t> snb_ptr(nslots + 1, 0);
-        for (int32_t sl : hs) snb_ptr[sl + 1]++;
-        for (int64_t i = 0; i < nslots; ++i) snb_ptr[i + 1] += snb_ptr[i];
-        std::vector<int32_t> snb(hs.size());
-        std::vector<int64_t> fill(snb_ptr.begin(), snb_ptr.end() - 1);
-        for (size_t i = 0; i < hs.size(); ++i) snb[fill[hs[i]]++] = hcmp[i];
-        std::vector<int64_t> uptr(nslots + 1, 0);
-        int64_t wpos = 0;
-        for (int64_t sl = 0; sl < nslots; ++sl) {
-            auto b = snb.begin() + snb_ptr[sl], en = snb.begin() + snb_ptr[sl + 1];
-            std::sort(b, en);
-            auto u = std::unique(b, en);
-            uptr[sl] = wpos;
-            for (auto it = b; it != u; ++it) snb[wpos++] = *it;
-        }
-        uptr[nslots] = wpos;
-        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order);
-        *method = (int32_t)best + 2;
-    }
-    if ((int64_t)slot_order.size() != nslots) return SPQ_EINVAL;  // cannot happen: every slot is emitted once
-    for (int64_t i = 0; i < nslots; ++i) (*bgpos)[slot_order[i]] = (int32_t)i;
-    return SPQ_OK;
+    return boundary_order_host(k, nb, std::move(hk), hs, hcmp, ord, bgpos, method);
 }
 
 }  // namespace spq

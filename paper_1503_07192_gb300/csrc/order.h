@@ -25,6 +25,20 @@ spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32
                           const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
                           spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method);
 
+// Host part of boundary_order: hk = component pair keys cu * k + cv (any order,
+// duplicates allowed), (hs[i], hcmp[i]) = (slot, neighbouring component) pairs.
+spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::vector<uint32_t> hk,
+                               const std::vector<int32_t>& hs, const std::vector<int32_t>& hcmp, spq_order ord,
+                               std::vector<int32_t>* bgpos, int32_t* method);
+
+// One key cu * k + cv per CSR slot joining components cu != cv (appended at *count).
+cudaError_t launch_emit_comp_pairs(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part, int32_t k,
+                                   uint32_t* keys, uint32_t* count, cudaStream_t st);
+// One (slot of u, component of v) pair per CSR slot u -> v joining two components.
+cudaError_t launch_emit_slot_pairs(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part,
+                                   const int32_t* local, const int32_t* slot_off, int32_t* slots, int32_t* comps,
+                                   uint32_t* count, cudaStream_t st);
+
 // Host-only nested dissection of a graph given as adjacency lists (exposed for tests).
 void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std::vector<int32_t>& adj,
                        const std::vector<int32_t>& weight, std::vector<int32_t>* order);

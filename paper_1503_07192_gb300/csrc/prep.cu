@@ -221,6 +221,12 @@ cudaError_t launch_assign_local(int32_t n, const uint32_t* sorted_vals, const in
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan_excl(uint32_t* a, int64_t len, cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    k_scan_excl<<<1, 1024, 0, st>>>(a, len);
+    return cudaGetLastError();
+}
+
 int64_t radix_hist_words(int64_t n) {
     int64_t ntiles = (n + kRsTile - 1) / kRsTile;
     return 256 * (ntiles > 0 ? ntiles : 1);
