@@ -147,7 +147,7 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
     if ((e = launch_scatter_intra<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->descs, apsp, st)) !=
         cudaSuccess)
         return e;
-    if ((e = fw_batched<T>(apsp, h->descs, h->k, max_n, st)) != cudaSuccess) return e;
+    if ((e = fw_batched<T>(apsp, h->descs, h->h_descs.data(), h->k, max_n, st)) != cudaSuccess) return e;
     evs.mark(3, st);
     if (h->N > 0) {
         if ((e = launch_bg_fill<T>(D, h->N, st)) != cudaSuccess) return e;

@@ -127,7 +127,8 @@ struct BatchPtrs {
 
 // Tables of every instance in element type T (Algorithm 1 after the reordering).
 template <typename T>
-cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs, int64_t ktot,
+cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs,
+                         const MatDesc* h_cdescs, int64_t ktot,
                          int32_t max_ld, const MatDesc* d_bdescs, int32_t nbmat, int32_t max_N, bool f32w,
                          uint32_t* fw_scratch, uint32_t* d_flag, bool check, bool* inexact, double* bg_updates,
                          cudaEvent_t* ev, cudaStream_t st) {
@@ -142,7 +143,7 @@ cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc
                                     base + x.apsp_off, st);
         if (e != cudaSuccess) return e;
     }
-    if ((e = fw_batched<T>(base, d_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess) return e;
+    if ((e = fw_batched<T>(base, d_cdescs, h_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess) return e;
     cudaEventRecord(ev[3], st);
     for (auto& x : I) {
         if (x.N == 0) continue;
@@ -500,18 +501,18 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     if (f32w) {
         f32store = true;
         arith = SPQ_ARITH_F32;
-        BCK(batch_tables<float>(I, P, d_cd, ktot, max_ld, d_bd, nbmat, max_N, true, fw_scratch, d_flag, false,
+        BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, nbmat, max_N, true, fw_scratch, d_flag, false,
                                 &inexact, &bg_updates, ev, st));
     } else {
         const bool try_f32 = o.arith != SPQ_ARITH_I32;
         if (try_f32) {
             arith = SPQ_ARITH_F32;
-            BCK(batch_tables<float>(I, P, d_cd, ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag, true,
+            BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag, true,
                                     &inexact, &bg_updates, ev, st));
         }
         if (!try_f32 || inexact) {
             arith = SPQ_ARITH_I32;
-            BCK(batch_tables<int32_t>(I, P, d_cd, ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag,
+            BCK(batch_tables<int32_t>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag,
                                       false, &inexact, &bg_updates, ev, st));
         }
     }

@@ -91,8 +91,11 @@ cudaError_t launch_bg_inter(bool f32w, int32_t n, const int64_t* rp, const int32
 cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStream_t st);
 
 // ---- fw.cu: blocked Floyd-Warshall (Venkataraman, Sahni & Mukhopadhyaya 2003) ----
+// Many matrices (descs on the device and on the host); each round touches only the
+// matrices that still have tiles left.
 template <typename T>
-cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, cudaStream_t st);
+cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, int32_t nmat, int32_t max_n,
+                       cudaStream_t st);
 // One matrix of size N, optionally skipping tiles whose pivot panel is all infinite.
 // *updates receives the number of min-plus updates issued (host-side count).
 template <typename T>

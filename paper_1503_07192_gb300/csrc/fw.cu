@@ -17,6 +17,8 @@
 // Arithmetic: int32 (add, min) or float32 (add, three-input min over two k steps).
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <vector>
 
 #include "common.cuh"
@@ -270,12 +272,12 @@ __device__ __forceinline__ void minplus_panels(T (&acc)[8][8], const T* __restri
 // ---------------- phase 1: closure of the diagonal tile ----------------
 template <typename T>
 __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatDesc* __restrict__ descs,
-                                                int32_t nmat, int32_t r) {
+                                                int32_t nmat, int32_t r, const int32_t* __restrict__ sel) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T(*S)[T_] = reinterpret_cast<T(*)[T_]>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (int32_t mi = blockIdx.y; mi < nmat; mi += gridDim.y) {
-        const MatDesc d = descs[mi];
+        const MatDesc d = descs[sel ? sel[mi] : mi];
         const int64_t n = d.n;
         const int32_t R = (int32_t)((n + T_ - 1) / T_);
         if (r >= R) continue;
@@ -327,12 +329,12 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                    int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite,
-                                                   int32_t flag_stride) {
+                                                   int32_t flag_stride, const int32_t* __restrict__ sel) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (int32_t mi = blockIdx.y; mi < nmat; mi += gridDim.y) {
-        const MatDesc d = descs[mi];
+        const MatDesc d = descs[sel ? sel[mi] : mi];
         const int64_t n = d.n;
         const int32_t R = (int32_t)((n + T_ - 1) / T_);
         if (r >= R || (int32_t)blockIdx.x >= R - 1) continue;
@@ -400,6 +402,34 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_batched(T* __re
         I += (I >= r);
         J += (J >= r);
         phase3_tile<T>(base + d.off, n, (int64_t)r * T_, I, J, sm, tid, tx, ty);
+    }
+}
+
+// ---------------- phase 3 over the matrices active in round r ----------------
+// sel[0..nsel) = matrices with more than r + 1 tile rows; p3off[0..nsel] = exclusive
+// prefix of their task counts Rm(Rm + 1)/2 (Rm = tiles per side minus the pivot).
+template <typename T>
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_sel(T* __restrict__ base,
+                                                                     const MatDesc* __restrict__ descs,
+                                                                     const int32_t* __restrict__ sel, int32_t nsel,
+                                                                     const int64_t* __restrict__ p3off, int32_t r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t total = p3off[nsel];
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int32_t lo = 0, hi = nsel;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (p3off[mid] <= t) lo = mid; else hi = mid;
+        }
+        const MatDesc d = descs[sel[lo]];
+        const int64_t Rm = (d.n + T_ - 1) / T_ - 1;
+        int64_t I, J;
+        tri_pair(t - p3off[lo], Rm, I, J);
+        I += (I >= r);
+        J += (J >= r);
+        phase3_tile<T>(base + d.off, d.n, (int64_t)r * T_, I, J, sm, tid, tx, ty);
     }
 }
 
@@ -557,6 +587,8 @@ cudaError_t set_smem_attrs() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_many<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase3_sel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
     done = true;
     return cudaSuccess;
 }
@@ -564,25 +596,60 @@ cudaError_t set_smem_attrs() {
 }  // namespace
 
 template <typename T>
-cudaError_t fw_batched(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, cudaStream_t st) {
+cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, int32_t nmat, int32_t max_n,
+                       cudaStream_t st) {
     if (nmat <= 0 || max_n <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
     if (e != cudaSuccess) return e;
     const int32_t R = (max_n + T_ - 1) / T_;
-    const unsigned gy = (unsigned)(nmat < 65535 ? nmat : 65535);
-    const size_t psm = sizeof(PanelSmem<T>);
+    // per round: the matrices still active (more than r tile rows), in one host buffer
+    //   [sel_0 | p3off_0 (as two int32 words each) | sel_1 | ...]
+    std::vector<int64_t> start(R + 1, 0);
+    std::vector<int32_t> nsel(R, 0);
+    std::vector<int32_t> buf;
     for (int32_t r = 0; r < R; ++r) {
-        k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r);
+        start[r] = (int64_t)buf.size();
+        std::vector<int32_t> sel;
+        for (int32_t m = 0; m < nmat; ++m)
+            if ((h_descs[m].n + T_ - 1) / T_ > r) sel.push_back(m);
+        nsel[r] = (int32_t)sel.size();
+        buf.insert(buf.end(), sel.begin(), sel.end());
+        if (buf.size() & 1) buf.push_back(0);  // 8-byte alignment of the offsets
+        int64_t acc = 0;
+        for (size_t i = 0; i <= sel.size(); ++i) {
+            int32_t w2[2];
+            memcpy(w2, &acc, 8);
+            buf.push_back(w2[0]);
+            buf.push_back(w2[1]);
+            if (i < sel.size()) {
+                const int64_t Rm = (h_descs[sel[i]].n + T_ - 1) / T_ - 1;
+                acc += Rm * (Rm + 1) / 2;
+            }
+        }
+    }
+    int32_t* d_buf = nullptr;
+    e = cudaMallocAsync(&d_buf, buf.size() * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_buf, buf.data(), buf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    const size_t psm = sizeof(PanelSmem<T>);
+    const int p3_grid = sms() * 2;
+    for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
+        const int32_t ns = nsel[r];
+        if (ns == 0) break;
+        const int32_t* sel = d_buf + start[r];
+        const int64_t* p3off = reinterpret_cast<const int64_t*>(d_buf + start[r] + ns + (ns & 1));
+        const unsigned gy = (unsigned)(ns < 65535 ? ns : 65535);
+        k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, ns, r, sel);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, nullptr, 0);
-            k_phase3_batched<T><<<dim3((R - 1) * R / 2, gy), NTH, psm, st>>>(base, d_descs, nmat, r);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, ns, r, nullptr, 0, sel);
+            k_phase3_sel<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, sel, ns, p3off, r);
             count_launches(2);
         }
         e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    cudaFreeAsync(d_buf, st);  // (the pageable upload above completed before it returned)
+    return e;
 }
 
 int64_t fw_single_scratch_words(int64_t N) {
@@ -618,10 +685,10 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
-        k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r);
+        k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags, 0);
+            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags, 0, nullptr);
             if (!skip_inf) {
                 // mark every tile: the compaction then lists all J != r
                 cudaMemsetAsync(flags, 0xff, R * sizeof(uint32_t), st);
@@ -684,10 +751,10 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
     const size_t psm = sizeof(PanelSmem<T>);
     const int p3_grid = sms() * 2;
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
-        k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r);
+        k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r, nullptr);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr);
             k_compact_many<<<nmat, 1024, 0, st>>>(flags, R, d_descs, nmat, r, lists, R + 1, offs, tiles);
             launch_scan_excl(offs, nmat + 1, st);
             k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs);
@@ -707,8 +774,8 @@ template cudaError_t fw_many_skip<int32_t>(int32_t*, const MatDesc*, int32_t, in
                                            cudaStream_t);
 template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_t, uint32_t*, double*, cudaStream_t);
 
-template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, cudaStream_t);
-template cudaError_t fw_batched<float>(float*, const MatDesc*, int32_t, int32_t, cudaStream_t);
+template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
+template cudaError_t fw_batched<float>(float*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, double*, FwProfile*, cudaStream_t);
 template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, double*, FwProfile*, cudaStream_t);
 
