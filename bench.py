@@ -326,6 +326,7 @@ def run_serve(args, rank, local_rank):
 
     torch.cuda.set_device(local_rank)
     spq.build()
+    sys.setswitchinterval(1e-4)  # the scheduler thread shares the interpreter with the producer
     t0 = time.time()
     ws = [gen.configs.grid1024diag()] + gen.configs.batch_instances(count=8, q_per=10)
     srv = QueryServer(device=local_rank, slots=4, max_pairs=1 << 20)
@@ -349,8 +350,11 @@ def run_serve(args, rank, local_rank):
         t_arr = start + np.cumsum(gaps)
         futs = []
         for (gid, p), ta in zip(reqs, t_arr):
-            while time.perf_counter() < ta:
-                pass
+            # sleep until just before the arrival (a Python spin would hold the
+            # interpreter lock the scheduler thread needs), then submit
+            dt = ta - time.perf_counter()
+            if dt > 2e-4:
+                time.sleep(dt - 1e-4)
             futs.append(srv.submit(gid, p, t_arrival=float(ta)))
         outs = [f.result(timeout=600) for f in futs]
         t_end = time.perf_counter()
