@@ -206,8 +206,33 @@ spq_status spq_build_many(int32_t count, const spq_graph* graphs, const spq_opts
 spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* const* pairs, const int64_t* q,
                           void* const* dist_out, void* stream);
 
+/*
+ * Distances with the path witness, and their gradients (the differentiation pattern;
+ * meant for SPQ_F32 graphs, also defined for SPQ_I32).  Device buffers only.
+ *
+ * spq_query_saved: like spq_query, and saved[i] (int32[2]) receives the local boundary
+ * indices (b1, b2) of the minimising pair of Algorithm 2 (ties: the smallest (b1, b2)),
+ * or (-1, -1) when the same-component distance dist_C1(v1, v2) is the answer, (-2, -2)
+ * when v1 = v2, (-3, -3) when v2 is unreachable or the pair is out of range.
+ *
+ * spq_query_backward: adds grad_dist[i] to grad_w[e] (float[m], accumulated, not
+ * cleared) for every CSR slot e on the shortest path of pair i, in the direction of
+ * travel from v1 to v2.  The path is not stored: it is walked again from the tables (next
+ * hop = the neighbour minimising edge weight + table distance to the target).  Where the
+ * path is unique this is the derivative of sum_i grad_dist[i] * dist_i with respect to the
+ * slot weights (an undirected edge's derivative is the sum over its two slots).
+ * pairs and saved must be those of the forward call on the same handle.  A walk that
+ * cannot reach its target (zero-length cycles) sets a mark reported by spq_query_status.
+ * Handles from spq_build_many return SPQ_EUNSUPPORTED.
+ */
+spq_status spq_query_saved(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, int32_t* saved,
+                           void* stream);
+spq_status spq_query_backward(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved,
+                              const float* grad_dist, float* grad_w, void* stream);
+
 /* Synchronise `stream`, return SPQ_EINVAL if any spq_query on h since the last call
- * met an out-of-range pair (and clear the mark), else SPQ_OK (or SPQ_ECUDA). */
+ * met an out-of-range pair, or SPQ_ETIMEOUT if a gradient walk did not reach its target
+ * (and clear the marks), else SPQ_OK (or SPQ_ECUDA). */
 spq_status spq_query_status(spq_handle* h, void* stream);
 
 /* Release every device table of h.  NULL-safe.  Synchronises the device. */

@@ -256,6 +256,69 @@ def spq_query_noalloc(h: SpqHandle, pairs, out=None, stream=None):
     return o_k
 
 
+def spq_query_saved(h: SpqHandle, pairs, stream=None):
+    """(dist, saved) for CUDA int32[q, 2] pairs: the distances and, per pair, the
+    minimising boundary pair (int32[q, 2]; negative markers, see include/spq.h)."""
+    lib = _lib.load()
+    p_p, p_k, p_dev = _ptr(pairs, np.int32)
+    if not p_dev:
+        raise ValueError("spq_query_saved takes device tensors")
+    q = int(p_k.shape[0])
+    dist = torch.empty(q, dtype=torch.float32 if h.wt == SPQ_F32 else torch.int32, device=p_k.device)
+    saved = torch.empty((q, 2), dtype=torch.int32, device=p_k.device)
+    st = lib.spq_query_saved(h.ptr, p_p, q, ctypes.c_void_p(dist.data_ptr()), ctypes.c_void_p(saved.data_ptr()),
+                             _stream(stream, True))
+    if st:
+        raise SpqError(st, "spq_query_saved")
+    return dist, saved
+
+
+def spq_query_backward(h: SpqHandle, pairs, saved, grad_dist, grad_w, stream=None):
+    """grad_w[e] += grad_dist[i] for every CSR slot e on pair i's shortest path (CUDA
+    tensors: pairs/saved int32[q, 2], grad_dist float32[q], grad_w float32[m])."""
+    lib = _lib.load()
+    p_p, p_k, _ = _ptr(pairs, np.int32)
+    s_p, s_k, _ = _ptr(saved, np.int32)
+    g_p, g_k, _ = _ptr(grad_dist, np.float32)
+    if not (grad_w.is_cuda and grad_w.dtype == torch.float32 and grad_w.is_contiguous()):
+        raise ValueError("grad_w must be a contiguous CUDA float32 tensor")
+    st = lib.spq_query_backward(h.ptr, p_p, int(p_k.shape[0]), s_p, g_p, ctypes.c_void_p(grad_w.data_ptr()),
+                                _stream(stream, True))
+    if st:
+        raise SpqError(st, "spq_query_backward")
+    return grad_w
+
+
+if torch is not None:
+
+    class ShortestPathDistance(torch.autograd.Function):
+        """dist = ShortestPathDistance.apply(w, row_ptr, col, part, k, pairs): distances of
+        the pairs in the graph whose CSR slot weights are w (float32, CUDA, one entry per
+        slot; give both slots of an undirected edge the same value).  The forward builds the
+        query structure (Algorithm 1) and answers the pairs keeping each one's minimising
+        boundary pair; the backward walks every pair's shortest path again and accumulates
+        the upstream gradient on the slots it uses."""
+
+        @staticmethod
+        def forward(ctx, w, row_ptr, col, part, k, pairs):
+            h = spq_build(int(row_ptr.shape[0] - 1), row_ptr, col, w.detach().contiguous(), part, int(k))
+            dist, saved = spq_query_saved(h, pairs)
+            spq_query_status(h)
+            ctx.h = h
+            ctx.m = int(w.shape[0])
+            ctx.save_for_backward(pairs, saved)
+            return dist
+
+        @staticmethod
+        def backward(ctx, g):
+            pairs, saved = ctx.saved_tensors
+            grad_w = torch.zeros(ctx.m, dtype=torch.float32, device=pairs.device)
+            spq_query_backward(ctx.h, pairs, saved, g.contiguous().to(torch.float32), grad_w)
+            spq_query_status(ctx.h)
+            ctx.h.free()
+            return grad_w, None, None, None, None, None
+
+
 def spq_query_status(h: SpqHandle, stream=None):
     st = _lib.load().spq_query_status(h.ptr, _stream(stream, True))
     if st:

@@ -39,6 +39,8 @@ SIGNATURES = {
     "spq_query_many": (ctypes.c_int, [i32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(i64),
                                       ctypes.POINTER(P), P]),
     "spq_query_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
+    "spq_query_saved": (ctypes.c_int, [P, P, i64, P, P, P]),
+    "spq_query_backward": (ctypes.c_int, [P, P, i64, P, P, P, P]),
     "spq_free": (None, [P]),
     "spq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "spq_last_cuda_error": (ctypes.c_int, []),

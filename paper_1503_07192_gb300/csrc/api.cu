@@ -79,7 +79,8 @@ void free_handle_memory(spq_handle* h) {
         h->arena = nullptr;
         return;
     }
-    void* ps[] = {h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, h->csize, h->apsp, h->D, h->err};
+    void* ps[] = {h->comp,   h->local,   h->descs,   h->nb,  h->bg_off, h->bgpos,  h->csize, h->apsp,
+                  h->D,      h->err,     h->csr_rp,  h->csr_col, h->csr_w, h->vorder, h->vstart};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -278,7 +279,8 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
     const int64_t hist_words = radix_hist_words(n);
     size_t need = 4 * (size_t)h->apsp_elems + 4 * (size_t)h->N * (size_t)h->N + 8 * (size_t)n +
-                  (size_t)k * (sizeof(MatDesc) + 12) + 16 * (size_t)n + 4 * (size_t)(fw_words + hist_words) + (64u << 20);
+                  (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words + hist_words) +
+                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + (64u << 20);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     if (need > free_b) return SPQ_ENOMEM;
@@ -291,6 +293,12 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     CK(dev_alloc(&h->bgpos, (size_t)h->nbg, &bytes));
     CK(dev_alloc(&h->csize, (size_t)k, &bytes));
     CK(dev_alloc(&h->err, 4, &bytes));
+    CK(dev_alloc(&h->csr_rp, (size_t)n + 1, &bytes));
+    CK(dev_alloc(&h->csr_col, (size_t)m, &bytes));
+    CK(dev_alloc((uint32_t**)&h->csr_w, (size_t)m, &bytes));
+    CK(dev_alloc(&h->vorder, (size_t)n, &bytes));
+    CK(dev_alloc(&h->vstart, (size_t)k, &bytes));
+    h->m = m;
     CK(dev_alloc((uint32_t**)&h->apsp, (size_t)h->apsp_elems, &bytes));
     if (h->N > 0) CK(dev_alloc((uint32_t**)&h->D, (size_t)(h->N * h->N), &bytes));
     h->bytes = bytes;
@@ -316,6 +324,14 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         int key_bits = bits_for(2 * (uint64_t)k - 1);
         CK(radix_sort_pairs(k0, v0, k1, v1, hist, n, key_bits, &in_k1, st));
         CK(launch_assign_local(n, in_k1 ? v1 : v0, d_part, d_vstart, h->local, h->comp, st));
+        // kept for path walks: vertices in (component, local) order, component starts, CSR
+        CK(cudaMemcpyAsync(h->vorder, in_k1 ? v1 : v0, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->vstart, d_vstart, (size_t)k * 4, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->csr_rp, d_rp, ((size_t)n + 1) * 8, cudaMemcpyDeviceToDevice, st));
+        if (m > 0) {
+            CK(cudaMemcpyAsync(h->csr_col, d_col, (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(h->csr_w, d_w, (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
+        }
     }
 
     // ---- positions of the boundary slots along the boundary-graph matrix ----
@@ -467,10 +483,10 @@ spq_status spq_query_status(spq_handle* h, void* stream) {
     uint32_t f = 0;
     CK(cudaMemcpyAsync(&f, h->err, sizeof(f), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (f & kErrPair) {
+    if (f & (kErrPair | kErrWalk)) {
         CK(cudaMemsetAsync(h->err, 0, sizeof(uint32_t), st));
         CK(cudaStreamSynchronize(st));
-        return SPQ_EINVAL;
+        return (f & kErrPair) ? SPQ_EINVAL : SPQ_ETIMEOUT;
     }
     return SPQ_OK;
 }

@@ -16,6 +16,7 @@ enum : uint32_t {
     kErrAsym = 8u,    // slot u->v without a matching v->u of the same smallest weight
     kErrPair = 16u,   // query pair id outside [0, n)
     kErrExact = 32u,  // float32 tables hold a finite entry >= 2^24 (not provably exact)
+    kErrWalk = 64u,   // a gradient path walk did not reach its target (ties of zero length)
 };
 
 constexpr int kTile = 128;  // Floyd-Warshall tile edge (rows = columns = pivot block)

@@ -47,4 +47,12 @@ struct spq_handle {
     std::vector<int32_t> h_csize, h_nb, h_bgoff;
     std::vector<spq::MatDesc> h_descs;
     spq::Arena* arena = nullptr;  // set: every device pointer above lies in the arena
+    // kept for path walks (gradients): the graph's CSR and, per component, the vertices
+    // in local order (vorder[vstart[c] + i] = vertex with local index i in component c)
+    int64_t m = 0;
+    int64_t* csr_rp = nullptr;
+    int32_t* csr_col = nullptr;
+    void* csr_w = nullptr;
+    int32_t* vorder = nullptr;
+    int32_t* vstart = nullptr;
 };
