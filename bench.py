@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="delaunay1m",
                    choices=["delaunay1m", "grid64", "delaunay65k", "delaunay262k", "grid1024diag", "batch512",
-                            "serve"])
+                            "serve", "grad256k"])
     p.add_argument("--rates", default="500,2000,8000", help="serve: request arrival rates (1/s) to sweep")
     p.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals per rate")
     p.add_argument("--instances", type=int, default=512, help="batch512: number of instances")
@@ -379,6 +379,91 @@ def run_serve(args, rank, local_rank):
     return 0
 
 
+def run_grad(args, rank, local_rank):
+    """The differentiation pattern: Delaunay of 2^18 uniform points, float32 weights =
+    length x lognormal(0, 0.25), recursive coordinate bisection into 256 components of
+    1,024, 1,000,000 pairs with upstream gradients N(0, 1).  One step = forward (build +
+    distances with the minimising boundary pairs) + backward (path walks, gradient
+    scatter onto the 1.5M CSR slots).  A seeded sample of 2,000 pairs is checked against
+    the CPU reference gradient (the oracle's Dijkstra paths, FP64)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import oracle
+    import paper_1503_07192_gb300 as spq
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    spq.build()
+    t0 = time.time()
+    w = gen.configs.delaunay256k(q=args.queries or 1_000_000)
+    g = w.graph
+    rng = np.random.default_rng(1238)
+    up = rng.normal(size=w.pairs.shape[0]).astype(np.float32)
+    log(f"[rank {rank}] grad workload n={g.n} m={g.m} k={w.k} ({time.time() - t0:.1f}s)")
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    d_rp, d_col, d_w, d_part, d_pairs, d_up = T(g.row_ptr), T(g.col), T(g.w), T(w.part), T(w.pairs), T(up)
+    grad = torch.zeros(g.m, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        h = spq.spq_build(g.n, d_rp, d_col, d_w, d_part, w.k)
+        e[1].record(stream)
+        dist, saved = spq.spq_query_saved(h, d_pairs)
+        e[2].record(stream)
+        grad.zero_()
+        spq.spq_query_backward(h, d_pairs, saved, d_up, grad)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        spq.spq_query_status(h)
+        h.free()
+        return [e[i].elapsed_time(e[i + 1]) for i in range(3)]
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    times = [step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    build_ms, fwd_ms, bwd_ms = (statistics.mean(t[i] for t in times) for i in range(3))
+    # correctness on a sample of pairs: GPU gradient of the sample vs the CPU reference
+    idx = rng.choice(w.pairs.shape[0], size=2000, replace=False)
+    sp, su = w.pairs[idx], up[idx].astype(np.float64)
+    h = spq.spq_build(g.n, d_rp, d_col, d_w, d_part, w.k)
+    dist_s, saved_s = spq.spq_query_saved(h, T(sp))
+    gs = torch.zeros(g.m, dtype=torch.float32, device=dev)
+    spq.spq_query_backward(h, T(sp), saved_s, T(su.astype(np.float32)), gs)
+    torch.cuda.synchronize()
+    h.free()
+    ref_d, ref_g = oracle.pairs_dist_f64(g.row_ptr, g.col, g.w.astype(np.float64), sp, g=su)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    key = np.minimum(src, g.col).astype(np.int64) * g.n + np.maximum(src, g.col)
+    _, inv = np.unique(key, return_inverse=True)
+    gu = np.bincount(inv, weights=gs.cpu().numpy().astype(np.float64))
+    ru = np.bincount(inv, weights=ref_g)
+    err = np.abs(gu - ru).max() / max(1.0, np.abs(ru).max())
+    derr = float(np.max(np.abs(dist_s.cpu().numpy() - ref_d) / np.maximum(ref_d, 1e-30)))
+    q = int(w.pairs.shape[0])
+    step_ms = build_ms + fwd_ms + bwd_ms
+    line = {"metric": METRIC, "value": q / (step_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grad256k", "vertices": g.n, "components": w.k, "pairs": q,
+                       "weights": "float32 length x lognormal(0, 0.25)"},
+            "build_ms": build_ms, "forward_query_ms": fwd_ms, "backward_ms": bwd_ms,
+            "sample_check": {"pairs": 2000, "dist_max_rel_err_vs_fp64": derr,
+                             "grad_max_err_vs_cpu_reference_rel_to_max": float(err), "pass": bool(err <= 1e-4)},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -390,6 +475,8 @@ def main():
         return run_batch(args, rank, local_rank)
     if args.workload == "serve":
         return run_serve(args, rank, local_rank)
+    if args.workload == "grad256k":
+        return run_grad(args, rank, local_rank)
 
     import numpy as np
     import torch
