@@ -37,6 +37,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "queries/s + build min-plus Gop/s (1M-vertex planar), vs INT32/HBM roofline, 1xGB300"
+# DRAM bytes (read + write) per min-plus update of k_backsub, measured with ncu on the
+# delaunay1m build (None until measured)
+BACKSUB_BYTES_PER_UPDATE = None
 UNIT = "queries/s"
 
 
@@ -562,15 +565,37 @@ def main():
     p3_ms = sum(pf["p3_ms"] for _, pf, _ in per)
     p3_launches = sum(pf["p3_launches"] for _, pf, _ in per)
     p3_updates = sum(pf["p3_updates"] for _, pf, _ in per)
-    achieved_gops = p3_updates / (p3_ms * 1e-3) / 1e9 if p3_ms > 0 else None
-    # DRAM bytes per 128x128 phase-3 tile, from an ncu capture of two full launches of the
-    # same kernel on the 2^18-point Delaunay workload (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 6.533e9 bytes over 32,131 tiles), scaled to this workload's
-    # average launch by its tile count (traffic grows in proportion to tiles).
-    bytes_per_tile = 6.5329e9 / 32131
-    tiles_per_launch = p3_updates / max(p3_launches, 1) / 128 ** 3
+    bs_ms = sum(pf.get("bs_ms", 0.0) for _, pf, _ in per)
+    bs_launches = sum(pf.get("bs_launches", 0.0) for _, pf, _ in per)
+    bs_updates = sum(pf.get("bs_updates", 0.0) for _, pf, _ in per)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_gops = sms * 128 * 2070e6 / 2 / 1e9  # 128 lanes/SM, 2 lane-ops per update, max SM clock
+    kern = {
+        # DRAM bytes per 128x128 phase-3 tile, from an ncu capture of two full launches on
+        # the 2^18-point Delaunay workload (Floyd-Warshall form: 6.533e9 bytes over 32,131
+        # tiles), scaled to this workload's average launch by its tile count (traffic grows
+        # in proportion to tiles).
+        "k_phase3_list": {"what": "k_phase3_list (boundary-graph elimination / Floyd-Warshall, phase 3)",
+                          "ms": p3_ms, "launches": p3_launches, "updates": p3_updates,
+                          "traffic": 6.5329e9 / 32131 * p3_updates / max(p3_launches, 1) / 128 ** 3},
+        # DRAM bytes per min-plus update of the back-substitution, from an ncu capture of
+        # its launch on delaunay1m itself (see profiles/), times this launch's updates
+        "k_backsub": {"what": "k_backsub (boundary-graph back-substitution, persistent)",
+                      "ms": bs_ms, "launches": bs_launches, "updates": bs_updates,
+                      "traffic": BACKSUB_BYTES_PER_UPDATE * bs_updates / max(bs_launches, 1)
+                      if BACKSUB_BYTES_PER_UPDATE else None},
+    }
+    top = max(kern, key=lambda x: kern[x]["ms"])
+    other = [x for x in kern if x != top and kern[x]["ms"] > 0]
+
+    def roof(name):
+        kd = kern[name]
+        ach = kd["updates"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
+        return {"kernel": kd["what"], "bound": "alu", "achieved": ach, "peak": peak_gops, "unit": "Gop/s",
+                "frac": (ach / peak_gops) if ach else None, "traffic": kd["traffic"],
+                "traffic_unit": "bytes per launch (DRAM read + write)", "launches": int(kd["launches"]),
+                "avg_launch_ms": kd["ms"] / max(kd["launches"], 1),
+                "share_of_bg_ms": kd["ms"] / K / max(statistics.mean(pf["bg_fw"] for _, pf, _ in per), 1e-9)}
 
     # measured issue peak of the update (same process, after the timed region)
     ups, pms = ctypes.c_double(), ctypes.c_double()
@@ -599,24 +624,15 @@ def main():
         "build_updates": total_updates,
         "n_bg": st0["n_bg"],
         "bg_order": int(per[0][1].get("order_method", -1)),
+        "bg_method": {1: "floyd-warshall", 2: "elimination + back-substitution"}.get(
+            int(per[0][1].get("bg_method", 1)), "?"),
         "query_ms": statistics.mean(query_ms),
         "query_qps": q / (statistics.mean(query_ms) * 1e-3),
         "build_stage_ms": {k: round(statistics.mean(pf[k] for _, pf, _ in per), 2)
                            for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check")},
-        "roofline": {
-            "kernel": "k_phase3_list (boundary-graph Floyd-Warshall, phase 3)",
-            "bound": "alu",
-            "achieved": achieved_gops,
-            "peak": peak_gops,
-            "unit": "Gop/s",
-            "frac": (achieved_gops / peak_gops) if achieved_gops else None,
-            "traffic": bytes_per_tile * tiles_per_launch,
-            "traffic_unit": "bytes per launch (DRAM read + write)",
-            "launches": int(p3_launches),
-            "avg_launch_ms": p3_ms / max(p3_launches, 1),
-            "peak_basis": f"{sms} SMs x 128 lanes x 2070 MHz / 2 lane-ops per min-plus update (derived)",
-            "microbench_gops": micro,
-        },
+        "roofline": dict(roof(top), peak_basis=f"{sms} SMs x 128 lanes x 2070 MHz / 2 lane-ops per min-plus "
+                                                 "update (derived)", microbench_gops=micro),
+        "roofline_other": [roof(x) for x in other],
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,

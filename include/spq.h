@@ -81,6 +81,23 @@ typedef enum {
                                  the boundary vertices on a cut become separator vertices */
 } spq_order;
 
+/* How the boundary graph's all-pairs distances D are computed (Algorithm 1's APSP of
+ * BG; both give the same D).
+ *   SPQ_BG_FW: three-phase blocked Floyd-Warshall, every round over the whole matrix.
+ *   SPQ_BG_ELIM: the same rounds restricted to the tiles right of and below the pivot
+ *     (block elimination in the (min, +) semiring), then back-substitution from the last
+ *     row block to the first: for row block R, d(R, J) = min over the columns k right of
+ *     R with a finite eliminated entry F(R, k) of F(R, k) + d(k, J).  Exact for any
+ *     order; far fewer updates than Floyd-Warshall when the order is a dissection order
+ *     (few such k per row block).
+ *   SPQ_BG_AUTO (default): SPQ_BG_ELIM when the chosen order is a dissection order,
+ *     else SPQ_BG_FW. */
+typedef enum {
+    SPQ_BG_AUTO = 0,
+    SPQ_BG_FW = 1,
+    SPQ_BG_ELIM = 2
+} spq_bg_method;
+
 typedef struct spq_opts {
     int32_t struct_size; /* sizeof(spq_opts); lets later versions grow the struct */
     int32_t arith;       /* spq_arith */
@@ -96,6 +113,11 @@ typedef struct spq_opts {
                                by component pair (stream-ordered scratch of 16 bytes per
                                pair) so that each boundary-graph block is read once per
                                group; 0: one warp per pair in input order, no scratch */
+    int32_t bg_method;      /* spq_bg_method.  A struct_size that ends before this field
+                               (an earlier version of the struct) means SPQ_BG_AUTO */
+    int32_t bg_panel_mib;   /* SPQ_BG_ELIM: most MiB of device scratch for the gathered
+                               back-substitution panels at a time (the row blocks are
+                               then done in several launches); 0 (default): 1024 */
 } spq_opts;
 
 /* Fill *opts with the defaults (also what opts == NULL means). */
@@ -230,6 +252,25 @@ spq_status spq_query_saved(spq_handle* h, const int32_t* pairs, int64_t q, void*
 spq_status spq_query_backward(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved,
                               const float* grad_dist, float* grad_w, void* stream);
 
+/*
+ * Path retrieval: the vertex sequence of each pair's shortest path, found by the same
+ * walk as spq_query_backward (Section 3's decomposition of a path into an in-component
+ * piece, a boundary-graph piece and an in-component piece, each recovered hop by hop from
+ * the stored distance tables; nothing but the tables is kept per graph).
+ *
+ * pairs, saved: int32[q][2] device, those of a spq_query_saved call on the same handle.
+ * verts: int32[q][max_len] device (row-major; may be NULL when max_len = 0).  Row i gets
+ *   v1, ..., v2, the vertices in order of travel (v1 alone when v1 = v2).
+ * lens: int32[q] device.  lens[i] = number of vertices of the path, or -1 when v2 is
+ *   unreachable or the pair out of range.  A path longer than max_len is counted in full
+ *   but only its first max_len vertices are stored (lens[i] > max_len tells).
+ * Errors: SPQ_EINVAL for NULL or host buffers, misaligned pairs/saved (8 bytes), q or
+ *   max_len < 0; SPQ_EUNSUPPORTED for handles of spq_build_many.  A walk that cannot reach
+ *   its target sets the mark reported by spq_query_status (SPQ_ETIMEOUT).
+ */
+spq_status spq_query_paths(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved, int32_t max_len,
+                           int32_t* verts, int32_t* lens, void* stream);
+
 /* Synchronise `stream`, return SPQ_EINVAL if any spq_query on h since the last call
  * met an out-of-range pair, or SPQ_ETIMEOUT if a gradient walk did not reach its target
  * (and clear the marks), else SPQ_OK (or SPQ_ECUDA). */
@@ -267,8 +308,13 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
  *   updated tile);
  * and [9] the order used along the boundary-graph matrix: 0 components in id order,
  *   1 / 2 components in level-structure / id-range nested-dissection order, 3 / 4 the
- *   vertex-level refinements of 1 / 2.
- * Writes min(count, 10) values; returns how many it wrote (0 if h is NULL).  With the
+ *   vertex-level refinements of 1 / 2;
+ * [10] the spq_bg_method used (SPQ_BG_FW or SPQ_BG_ELIM); for SPQ_BG_ELIM, with
+ *   opts.profile_kernels = 1: [11] summed device ms of the back-substitution kernel's
+ *   launches, [12] its min-plus updates (|K(R)| x 128^2 per tile of row block R), [13]
+ *   its tiles, [14] its launches.  Stage [4] covers elimination and back-substitution,
+ *   and [6]-[8] then describe the elimination's phase-3 launches.
+ * Writes min(count, 15) values; returns how many it wrote (0 if h is NULL).  With the
  * float32 arithmetic falling back to int32, stages 2-5 hold the int32 run's times. */
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count);
 

@@ -30,6 +30,9 @@ from ._lib import (  # noqa: F401
     SPQ_I32,
     SPQ_INF_I32,
     SPQ_NOALLOC_MAX_PAIRS,
+    SPQ_BG_AUTO,
+    SPQ_BG_ELIM,
+    SPQ_BG_FW,
     SPQ_ORDER_AUTO,
     SPQ_ORDER_DISSECTION,
     SPQ_ORDER_ID,
@@ -93,12 +96,13 @@ class SpqHandle:
                 "footprint_bytes": int(_lib.load().spq_footprint_bytes(self.ptr))}
 
     def profile(self) -> dict:
-        """Device milliseconds of the build stages (CUDA events), and the phase-3 kernel
-        timing of the boundary-graph Floyd-Warshall when built with profile_kernels."""
-        ms = (ctypes.c_double * 10)()
-        cnt = _lib.load().spq_build_profile(self.ptr, ms, 10)
+        """Device milliseconds of the build stages (CUDA events), the phase-3 kernel
+        timing of the boundary-graph Floyd-Warshall (or elimination) and of the
+        back-substitution when built with profile_kernels, the order and the method."""
+        ms = (ctypes.c_double * 15)()
+        cnt = _lib.load().spq_build_profile(self.ptr, ms, 15)
         names = ["validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check", "p3_ms", "p3_launches",
-                 "p3_updates", "order_method"]
+                 "p3_updates", "order_method", "bg_method", "bs_ms", "bs_updates", "bs_items", "bs_launches"]
         return {names[i]: ms[i] for i in range(cnt)}
 
     def meta(self) -> dict:
@@ -287,6 +291,24 @@ def spq_query_backward(h: SpqHandle, pairs, saved, grad_dist, grad_w, stream=Non
     if st:
         raise SpqError(st, "spq_query_backward")
     return grad_w
+
+
+def spq_query_paths(h: SpqHandle, pairs, saved, max_len, stream=None):
+    """(verts int32[q, max_len], lens int32[q]) on the device: the vertices of each pair's
+    shortest path in order of travel (lens -1: unreachable; lens > max_len: truncated)."""
+    lib = _lib.load()
+    p_p, p_k, _ = _ptr(pairs, np.int32)
+    s_p, s_k, _ = _ptr(saved, np.int32)
+    if not (p_k.is_cuda and s_k.is_cuda):
+        raise ValueError("spq_query_paths takes device tensors")
+    q = int(p_k.shape[0])
+    verts = torch.empty((q, max(int(max_len), 0)), dtype=torch.int32, device=p_k.device)  # (< 0: EINVAL below)
+    lens = torch.empty(q, dtype=torch.int32, device=p_k.device)
+    st = lib.spq_query_paths(h.ptr, p_p, q, s_p, int(max_len), ctypes.c_void_p(verts.data_ptr()),
+                             ctypes.c_void_p(lens.data_ptr()), _stream(stream, True))
+    if st:
+        raise SpqError(st, "spq_query_paths")
+    return verts, lens
 
 
 if torch is not None:

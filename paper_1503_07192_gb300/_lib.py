@@ -12,6 +12,7 @@ SPQ_OK, SPQ_EINVAL, SPQ_ENOMEM, SPQ_ECUDA, SPQ_ETIMEOUT, SPQ_EUNSUPPORTED = rang
 SPQ_I32, SPQ_F32 = 0, 1
 SPQ_ARITH_AUTO, SPQ_ARITH_I32, SPQ_ARITH_F32 = 0, 1, 2
 SPQ_ORDER_AUTO, SPQ_ORDER_ID, SPQ_ORDER_DISSECTION, SPQ_ORDER_VERTEX_DISSECTION = 0, 1, 2, 3
+SPQ_BG_AUTO, SPQ_BG_FW, SPQ_BG_ELIM = 0, 1, 2
 SPQ_INF_I32 = 0x20000000
 SPQ_NOALLOC_MAX_PAIRS = 262144
 
@@ -22,7 +23,8 @@ i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 
 class SpqOpts(ctypes.Structure):
     _fields_ = [("struct_size", i32), ("arith", i32), ("order", i32), ("skip_inf_tiles", i32),
-                ("profile_kernels", i32), ("query_grouped", i32)]
+                ("profile_kernels", i32), ("query_grouped", i32), ("bg_method", i32),
+                ("bg_panel_mib", i32)]
 
 
 class SpqGraph(ctypes.Structure):
@@ -41,6 +43,7 @@ SIGNATURES = {
     "spq_query_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
     "spq_query_saved": (ctypes.c_int, [P, P, i64, P, P, P]),
     "spq_query_backward": (ctypes.c_int, [P, P, i64, P, P, P, P]),
+    "spq_query_paths": (ctypes.c_int, [P, P, i64, P, ctypes.c_int32, P, P, P]),
     "spq_free": (None, [P]),
     "spq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "spq_last_cuda_error": (ctypes.c_int, []),

@@ -2,6 +2,7 @@
 // (Algorithm 2).  The host only sizes and allocates the tables, orders the components
 // and launches kernels; every per-vertex, per-edge and per-cell step runs on the GPU.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -21,6 +22,22 @@ namespace spq {
 extern std::atomic<unsigned long long> g_kernel_launches;
 std::atomic<unsigned long long> g_kernel_launches{0};
 void count_launches(int n) { g_kernel_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace spq
+
+namespace spq {
+spq_status read_opts(const spq_opts* in, spq_opts* o) {
+    spq_opts_default(o);
+    if (!in) return SPQ_OK;
+    // earlier, shorter versions of the struct end before bg_method
+    const int32_t v1 = (int32_t)offsetof(spq_opts, bg_method);
+    if (in->struct_size < v1) return SPQ_EINVAL;
+    memcpy(o, in, (size_t)std::min<int32_t>(in->struct_size, (int32_t)sizeof(spq_opts)));
+    o->struct_size = (int32_t)sizeof(spq_opts);
+    if (o->arith < SPQ_ARITH_AUTO || o->arith > SPQ_ARITH_F32) return SPQ_EINVAL;
+    if (o->order < SPQ_ORDER_AUTO || o->order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
+    if (o->bg_method < SPQ_BG_AUTO || o->bg_method > SPQ_BG_ELIM || o->bg_panel_mib < 0) return SPQ_EINVAL;
+    return SPQ_OK;
+}
 }  // namespace spq
 
 namespace {
@@ -132,13 +149,22 @@ struct BuildInputs {
     bool f32w;
 };
 
+// How the boundary graph's all-pairs distances are computed: Floyd-Warshall, or the
+// elimination form of its rounds followed by back-substitution (elim.cu).
+struct BgPlan {
+    bool elim = false;
+    uint32_t* rowflags = nullptr;  // R x R words (elimination only)
+    size_t apanel_budget = 0;
+    bool wait_failed = false;      // a bounded wait of the back-substitution gave up
+};
+
 // Tables of Algorithm 1 in element type T: component blocks, their Floyd-Warshall,
-// boundary-graph assembly and its Floyd-Warshall.  Sets *inexact if a float32 table
+// boundary-graph assembly and its all-pairs distances.  Sets *inexact if a float32 table
 // holds a finite entry >= 2^24.
 template <typename T>
 cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact, bool skip_inf, bool profile,
-                         uint32_t* d_flag,
-                         uint32_t* fw_scratch, int32_t max_n, bool* inexact, StageEvents& evs, cudaStream_t st) {
+                         uint32_t* d_flag, uint32_t* fw_scratch, BgPlan& plan, int32_t max_n, bool* inexact,
+                         StageEvents& evs, cudaStream_t st) {
     *inexact = false;
     evs.mark(2, st);
     T* apsp = (T*)h->apsp;
@@ -159,10 +185,28 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
             return e;
     }
     evs.mark(4, st);
-    if (h->N > 0) {
-        if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, &h->bg_updates, profile ? &h->fwprof : nullptr, st)) !=
-            cudaSuccess)
+    if (h->N > 0 && !plan.elim) {
+        if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, nullptr, &h->bg_updates, profile ? &h->fwprof : nullptr,
+                              st)) != cudaSuccess)
             return e;
+    } else if (h->N > 0) {
+        const int64_t R = (h->N + kTile - 1) / kTile;
+        double fwd = 0.0, bs = 0.0;
+        if ((e = cudaMemsetAsync(plan.rowflags, 0, (size_t)(R * R) * 4, st)) != cudaSuccess) return e;
+        if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, plan.rowflags, &fwd, profile ? &h->fwprof : nullptr,
+                              st)) != cudaSuccess)
+            return e;
+        if ((e = bg_backsub<T>(D, h->N, plan.rowflags, h->err, plan.apanel_budget, &bs,
+                               profile ? &h->fwprof : nullptr, st)) != cudaSuccess)
+            return e;
+        h->bg_updates = fwd + bs;
+        uint32_t bits = 0;
+        if ((e = cudaMemcpyAsync(&bits, h->err, sizeof(bits), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if (bits & kErrWait) {
+            plan.wait_failed = true;
+            return cudaSuccess;
+        }
     }
     evs.mark(5, st);
     if (check_exact) {
@@ -278,9 +322,15 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     // ---- memory check, then allocation ----
     const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
     const int64_t hist_words = radix_hist_words(n);
+    // elimination scratch: per-round row flags, back-substitution bookkeeping, A panels
+    const bool may_elim = opts.bg_method != SPQ_BG_FW && h->N > 0;
+    const int64_t nR = (h->N + kTile - 1) / kTile;
+    const size_t panel_cap = opts.bg_panel_mib > 0 ? ((size_t)opts.bg_panel_mib << 20) : ((size_t)1 << 30);
+    const size_t apanel_budget = std::min<size_t>(panel_cap, 4 * (size_t)h->N * (size_t)h->N + (1u << 20));
+    const size_t elim_bytes = may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(h->N) + apanel_budget : 0;
     size_t need = 4 * (size_t)h->apsp_elems + 4 * (size_t)h->N * (size_t)h->N + 8 * (size_t)n +
                   (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words + hist_words) +
-                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + (64u << 20);
+                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + (64u << 20);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     if (need > free_b) return SPQ_ENOMEM;
@@ -347,6 +397,15 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     // ---- tables: component APSP, boundary graph, boundary-graph APSP ----
     uint32_t* fw_scratch;
     CK(tmp.alloc(&fw_scratch, (size_t)fw_words));
+    BgPlan plan;
+    // elimination + back-substitution pays off in a dissection order (small frontiers);
+    // in the id order every row's frontier is most of the matrix
+    plan.elim = may_elim && (opts.bg_method == SPQ_BG_ELIM || h->order_method != 0);
+    h->bg_method = plan.elim ? SPQ_BG_ELIM : SPQ_BG_FW;
+    if (plan.elim) {
+        CK(tmp.alloc(&plan.rowflags, (size_t)(nR * nR)));
+        plan.apanel_budget = apanel_budget;
+    }
     BuildInputs in{n, m, d_rp, d_col, d_w, d_part, f32w};
     const bool skip = opts.skip_inf_tiles != 0;
     const bool prof = opts.profile_kernels != 0;
@@ -354,19 +413,22 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         h->f32store = true;
         h->arith = SPQ_ARITH_F32;
         bool inexact = false;
-        CK(build_tables<float>(h, in, false, skip, prof, d_flag, fw_scratch, max_n, &inexact, evs, st));
+        CK(build_tables<float>(h, in, false, skip, prof, d_flag, fw_scratch, plan, max_n, &inexact, evs, st));
+        if (plan.wait_failed) return SPQ_ETIMEOUT;
     } else {
         bool try_f32 = opts.arith != SPQ_ARITH_I32;
         bool inexact = false;
         if (try_f32) {
             h->f32store = true;
             h->arith = SPQ_ARITH_F32;
-            CK(build_tables<float>(h, in, true, skip, prof, d_flag, fw_scratch, max_n, &inexact, evs, st));
+            CK(build_tables<float>(h, in, true, skip, prof, d_flag, fw_scratch, plan, max_n, &inexact, evs, st));
+            if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
         h->f32store = false;  // converted to int32 by the exactness check
         if (!try_f32 || inexact) {
             h->arith = SPQ_ARITH_I32;
-            CK(build_tables<int32_t>(h, in, false, skip, prof, d_flag, fw_scratch, max_n, &inexact, evs, st));
+            CK(build_tables<int32_t>(h, in, false, skip, prof, d_flag, fw_scratch, plan, max_n, &inexact, evs, st));
+            if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
     }
     double cu = 0.0;
@@ -393,6 +455,8 @@ void spq_opts_default(spq_opts* o) {
     o->skip_inf_tiles = 1;
     o->profile_kernels = 0;
     o->query_grouped = 1;
+    o->bg_method = SPQ_BG_AUTO;
+    o->bg_panel_mib = 0;
 }
 
 spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
@@ -402,13 +466,7 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
     if (n < 1 || k < 1 || !row_ptr || !part) return SPQ_EINVAL;
     if (wt != SPQ_I32 && wt != SPQ_F32) return SPQ_EINVAL;
     spq_opts o;
-    spq_opts_default(&o);
-    if (opts) {
-        if (opts->struct_size < (int32_t)sizeof(spq_opts)) return SPQ_EINVAL;
-        o = *opts;
-        if (o.arith < SPQ_ARITH_AUTO || o.arith > SPQ_ARITH_F32) return SPQ_EINVAL;
-        if (o.order < SPQ_ORDER_AUTO || o.order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
-    }
+    if (spq_status so = read_opts(opts, &o)) return so;
     spq_handle* h = new (std::nothrow) spq_handle();
     if (!h) return SPQ_ENOMEM;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -524,13 +582,18 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
 
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     if (!h || !ms || count <= 0) return 0;
-    double v[10];
+    double v[15];
     for (int i = 0; i < 6; ++i) v[i] = h->prof_ms[i];
     v[6] = h->fwprof.p3_ms;
     v[7] = (double)h->fwprof.p3_launches;
     v[8] = h->fwprof.p3_updates;
     v[9] = (double)h->order_method;
-    int32_t c = count < 10 ? count : 10;
+    v[10] = (double)h->bg_method;
+    v[11] = h->fwprof.bs_ms;
+    v[12] = h->fwprof.bs_updates;
+    v[13] = h->fwprof.bs_items;
+    v[14] = (double)h->fwprof.bs_launches;
+    int32_t c = count < 15 ? count : 15;
     for (int32_t i = 0; i < c; ++i) ms[i] = v[i];
     return c;
 }

@@ -592,13 +592,7 @@ spq_status spq_build_many(int32_t count, const spq_graph* graphs, const spq_opts
     if (count < 1 || !graphs || !outs) return SPQ_EINVAL;
     for (int32_t g = 0; g < count; ++g) outs[g] = nullptr;
     spq_opts o;
-    spq_opts_default(&o);
-    if (opts) {
-        if (opts->struct_size < (int32_t)sizeof(spq_opts)) return SPQ_EINVAL;
-        o = *opts;
-        if (o.arith < SPQ_ARITH_AUTO || o.arith > SPQ_ARITH_F32) return SPQ_EINVAL;
-        if (o.order < SPQ_ORDER_AUTO || o.order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
-    }
+    if (spq_status so = read_opts(opts, &o)) return so;
     std::vector<spq_handle*> hs;
     const spq_status s = build_many_impl(count, graphs, o, (cudaStream_t)stream, &hs);
     if (s != SPQ_OK) {

@@ -17,6 +17,7 @@ enum : uint32_t {
     kErrPair = 16u,   // query pair id outside [0, n)
     kErrExact = 32u,  // float32 tables hold a finite entry >= 2^24 (not provably exact)
     kErrWalk = 64u,   // a gradient path walk did not reach its target (ties of zero length)
+    kErrWait = 128u,  // a bounded device-side wait gave up (back-substitution dependencies)
 };
 
 constexpr int kTile = 128;  // Floyd-Warshall tile edge (rows = columns = pivot block)
@@ -46,12 +47,20 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // Process-wide count of this library's kernel launches (read by spq_kernel_launches).
 void count_launches(int n);
 
+// Validated copy of the caller's options (NULL: the defaults); accepts the shorter
+// earlier versions of the struct (struct_size).
+spq_status read_opts(const spq_opts* in, spq_opts* out);
+
 // Per-launch timing of the boundary-graph Floyd-Warshall's phase-3 kernel (filled only
 // when requested: CUDA events around each launch).
 struct FwProfile {
     double p3_ms = 0.0;
     int64_t p3_launches = 0;
     double p3_updates = 0.0;
+    double bs_ms = 0.0;       // back-substitution kernel time (elimination form)
+    int64_t bs_launches = 0;  // its launches (one per panel budget piece)
+    double bs_updates = 0.0;  // its min-plus updates (unpadded)
+    double bs_items = 0.0;    // its tiles
 };
 
 // ---- prep.cu: input validation, boundary detection, stable radix sort ----
@@ -99,10 +108,24 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
                        cudaStream_t st);
 // One matrix of size N, optionally skipping tiles whose pivot panel is all infinite.
 // *updates receives the number of min-plus updates issued (host-side count).
+// rowflags == NULL: the full Floyd-Warshall.  rowflags = R x R words (R = ceil(N/128)),
+// zeroed: the elimination (forward) form: round r updates only tiles right of and below
+// the pivot (I, J > r), and rowflags[r][J] marks the row tiles (r, J > r) that hold a
+// finite entry; bg_backsub then completes the matrix.
 template <typename T>
-cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, double* updates, FwProfile* prof,
-                      cudaStream_t st);
+cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, uint32_t* rowflags, double* updates,
+                      FwProfile* prof, cudaStream_t st);
 int64_t fw_single_scratch_words(int64_t N);
+
+// ---- elim.cu: back-substitution after the forward form of fw_single ----
+// Completes M (N x N, symmetric storage) to all-pairs distances.  err: device status
+// word (kErrWait if a bounded wait gave up).  *updates: min-plus updates issued.
+// Needs bg_backsub_scratch_bytes(N) bytes of device scratch plus its A panels, which it
+// allocates stream-ordered in pieces of at most apanel_budget bytes.
+template <typename T>
+cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, size_t apanel_budget,
+                       double* updates, FwProfile* prof, cudaStream_t st);
+size_t bg_backsub_scratch_bytes(int64_t N);
 // Many matrices (sizes up to max_n) at once, with infinite-panel skipping per matrix;
 // *updates receives the phase-2 and phase-3 min-plus updates issued.
 template <typename T>

@@ -1,0 +1,414 @@
+// All-pairs distances of the boundary graph by tropical elimination and
+// back-substitution (the boundary-graph APSP of Algorithm 1, computed exactly, with fewer
+// min-plus updates than Floyd-Warshall in a nested-dissection order).
+//
+// Forward (fw_single with rowflags): block elimination in the matrix order.  After it,
+// for row block R and any column j right of R, F(r, j) (r in R) is the length of a
+// shortest r-j path whose inner vertices all lie in blocks <= R, and the diagonal tile
+// (R, R) holds the shortest paths inside blocks <= R.
+//
+// Back-substitution (here), row blocks from the last to the first.  Take a shortest path
+// from r in R to any vertex j, and on it the first vertex k after r that lies right of
+// block R.  The part r..k has its inner vertices in blocks <= R, so it is F(r, k); the
+// rest is d(k, j).  Hence, with K(R) = the columns k right of R with a finite F(r, k) for
+// some r in R (the "frontier" of R, small in a dissection order):
+//   d(R, J) = min over k in K(R) of F(R, k) + d(k, J)       for J right of R,
+//   d(R, R) = min(F(R, R), min over k in K(R) of F(R, k) + d(k, R)),
+// where d(k, J) and d(k, R) = d(R, k) are already final.  Each is a min-plus product of
+// a 128 x |K(R)| panel (gathered once, before the back-substitution overwrites row R)
+// with |K(R)| gathered rows of the matrix.
+//
+// One persistent launch walks the tiles in that order through an atomic work counter:
+// row blocks from the last to the first, inside a row the tiles right of the diagonal,
+// then the diagonal tile.  Tile (R, J) needs the final tiles (min(k, J), max(k, J)) for
+// the blocks k of K(R); the diagonal needs (R, k).  All of them come earlier in the
+// order, so every tile a CTA waits for is held by a CTA that is already running and
+// waits only for tiles earlier still: the waits always end.  Each wait is bounded
+// anyway (2 s of %globaltimer); past that the launch records kErrWait and stops.
+#include <cuda_runtime.h>
+
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "fw_tile.cuh"
+
+namespace spq {
+
+namespace {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of one dependency wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Per row block R: the column tiles J > R holding a finite entry of F (from the forward
+// pass's flags), the 128-bit mask of their finite columns (fblk / masks at R * nR + i),
+// their number and the number of finite columns |K(R)|.
+template <typename T>
+__global__ void __launch_bounds__(256) k_colmask(const T* __restrict__ M, int64_t N, int32_t nR,
+                                                 const uint32_t* __restrict__ rowflags, uint4* __restrict__ masks,
+                                                 int32_t* __restrict__ fblk, int32_t* __restrict__ fcnt,
+                                                 int32_t* __restrict__ kcnt) {
+    __shared__ uint32_t colf[2][T_];
+    __shared__ uint32_t wm[4];
+    const int32_t R = blockIdx.x;
+    const int tid = threadIdx.x, c = tid & (T_ - 1), h = tid >> 7;
+    const T inf = Inf<T>::value();
+    const int64_t r0 = (int64_t)R * T_;
+    const int64_t nrows = (N - r0) < T_ ? (N - r0) : T_;
+    int32_t cnt = 0, kc = 0;
+    for (int32_t J = R + 1; J < nR; ++J) {
+        if (rowflags[(int64_t)R * nR + J] == 0u) continue;
+        const int64_t col = (int64_t)J * T_ + c;
+        uint32_t f = 0;
+        if (col < N)
+            for (int64_t i = h; i < nrows; i += 2) f |= (M[(r0 + i) * N + col] < inf) ? 1u : 0u;
+        colf[h][c] = f;
+        __syncthreads();
+        if (tid < T_) {
+            const unsigned b = __ballot_sync(0xffffffffu, (colf[0][tid] | colf[1][tid]) != 0u);
+            if ((tid & 31) == 0) wm[tid >> 5] = b;
+        }
+        __syncthreads();
+        const uint4 m = make_uint4(wm[0], wm[1], wm[2], wm[3]);
+        const int pc = __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+        if (pc) {
+            if (tid == 0) {
+                fblk[(int64_t)R * nR + cnt] = J;
+                masks[(int64_t)R * nR + cnt] = m;
+            }
+            ++cnt;
+            kc += pc;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        fcnt[R] = cnt;
+        kcnt[R] = kc;
+    }
+}
+
+// K(R) as ascending column indices at klist[koff[R] ..), padded to a multiple of KC with
+// copies of its first entry (their panel rows are infinite, so they change nothing).
+__global__ void __launch_bounds__(T_) k_klist(const uint4* __restrict__ masks, const int32_t* __restrict__ fblk,
+                                              const int32_t* __restrict__ fcnt, const int32_t* __restrict__ kcnt,
+                                              const int64_t* __restrict__ koff, int32_t nR,
+                                              int32_t* __restrict__ klist) {
+    const int32_t R = blockIdx.x;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int64_t base = koff[R];
+    const int32_t nf = fcnt[R];
+    int32_t pos = 0;
+    for (int32_t i = 0; i < nf; ++i) {
+        const uint4 m = masks[(int64_t)R * nR + i];
+        const uint32_t words[4] = {m.x, m.y, m.z, m.w};
+        const uint32_t word = words[w];
+        int32_t woff = 0;
+        for (int x = 0; x < w; ++x) woff += __popc(words[x]);
+        if ((word >> lane) & 1u)
+            klist[base + pos + woff + __popc(word & ((1u << lane) - 1u))] =
+                fblk[(int64_t)R * nR + i] * T_ + w * 32 + lane;
+        pos += __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+    }
+    __syncthreads();
+    const int32_t kc = kcnt[R];
+    const int32_t kp = (kc + KC - 1) / KC * KC;
+    if (kc > 0)
+        for (int32_t j = kc + tid; j < kp; j += T_) klist[base + j] = klist[base];
+}
+
+// A panels: A[(koff[R] - aoff0 + k) * 128 + i] = F(R*128 + i, klist[k]), read as its
+// mirror F(klist[k], R*128 + i) (one contiguous row piece); padding rows infinite.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_a(const T* __restrict__ M, int64_t N, int32_t R0,
+                                                  const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt,
+                                                  const int32_t* __restrict__ klist, int64_t aoff0,
+                                                  T* __restrict__ A) {
+    const int32_t R = R0 + blockIdx.x;
+    const int64_t base = koff[R];
+    const int32_t kc = kcnt[R];
+    const int32_t kp = (kc + KC - 1) / KC * KC;
+    const int64_t col0 = (int64_t)R * T_;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)kp * (T_ / 4); idx += blockDim.x) {
+        const int32_t k = (int32_t)(idx >> 5), c4 = (int32_t)(idx & 31);
+        int4 v = inf4<T>();
+        if (k < kc && col0 + c4 * 4 < N)
+            v = *reinterpret_cast<const int4*>(M + (int64_t)klist[base + k] * N + col0 + c4 * 4);
+        *reinterpret_cast<int4*>(A + (base - aoff0 + k) * T_ + c4 * 4) = v;
+    }
+}
+
+// Stage KC gathered rows klist[kbase ..) of M, columns [col0, col0 + 128), into P.
+template <typename T>
+__device__ __forceinline__ void stage_rows(T (*P)[T_], const T* __restrict__ M, int64_t N,
+                                           const int32_t* __restrict__ rows, int64_t col0, int tid) {
+#pragma unroll
+    for (int it = 0; it < (KC * T_ / 4) / NTH; ++it) {
+        const int idx = it * NTH + tid;
+        const int kk = idx >> 5, c4 = idx & 31;
+        const int64_t c = col0 + c4 * 4;
+        T* dst = &P[kk][c4 * 4];
+        if (c < N)
+            cp_async16(dst, M + (int64_t)rows[kk] * N + c);
+        else
+            *reinterpret_cast<int4*>(dst) = inf4<T>();
+    }
+}
+
+// Stage KC contiguous panel rows (128 wide) into P.
+template <typename T>
+__device__ __forceinline__ void stage_panel(T (*P)[T_], const T* __restrict__ A, int tid) {
+#pragma unroll
+    for (int it = 0; it < (KC * T_ / 4) / NTH; ++it) {
+        const int idx = it * NTH + tid;
+        cp_async16(&P[idx >> 5][(idx & 31) * 4], A + (int64_t)(idx >> 5) * T_ + (idx & 31) * 4);
+    }
+}
+
+// Item g (global order) -> row block R and column block J (J == R: the diagonal tile).
+__device__ __forceinline__ void item_tile(int64_t g, int32_t nR, int32_t& R, int32_t& J) {
+    int64_t m = (int64_t)((sqrt(8.0 * (double)g + 1.0) - 1.0) * 0.5);
+    while (m > 0 && m * (m + 1) / 2 > g) --m;
+    while ((m + 1) * (m + 2) / 2 <= g) ++m;
+    const int64_t p = g - m * (m + 1) / 2;
+    R = nR - 1 - (int32_t)m;
+    J = p < m ? R + 1 + (int32_t)p : R;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
+    k_backsub(T* __restrict__ M, int64_t N, int32_t nR, int64_t g0, int64_t nitems,
+              const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt, const int32_t* __restrict__ klist,
+              const T* __restrict__ A, int64_t aoff0, const int32_t* __restrict__ fblk,
+              const int32_t* __restrict__ fcnt, uint32_t* __restrict__ tflags,
+              unsigned long long* __restrict__ counter, uint32_t* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    __shared__ int64_t s_item;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (;;) {
+        if (tid == 0) {
+            int64_t t = (int64_t)atomicAdd(counter, 1ull);
+            if (*reinterpret_cast<volatile uint32_t*>(err) & kErrWait) t = nitems;
+            s_item = t;
+            s_fail = 0;
+        }
+        __syncthreads();
+        const int64_t t = s_item;
+        if (t >= nitems) break;
+        int32_t R, J;
+        item_tile(g0 + t, nR, R, J);
+        const int32_t kc = kcnt[R];
+        if (kc > 0) {
+            // dependencies: the final tiles this one reads
+            if (tid < 32) {
+                const int32_t nf = fcnt[R];
+                for (int32_t i = tid; i < nf; i += 32) {
+                    const int32_t K = fblk[(int64_t)R * nR + i];
+                    const int32_t a = (J == R) ? R : (K < J ? K : J);
+                    const int32_t b = (J == R) ? K : (K < J ? J : K);
+                    const uint32_t* f = tflags + (int64_t)a * nR + b;
+                    if (ld_acquire(f) == 0u) {
+                        const unsigned long long t0 = global_ns();
+                        while (ld_acquire(f) == 0u) {
+                            __nanosleep(256);
+                            if (global_ns() - t0 > kWaitNs) {
+                                atomicOr(err, kErrWait);
+                                s_fail = 1;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_fail) break;
+            const int64_t r0 = (int64_t)R * T_, c0 = (int64_t)J * T_;
+            T acc[8][8];
+            if (J == R) {
+                load_c<T>(acc, M, N, r0, r0, tx, ty);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = Inf<T>::value();
+            }
+            const int64_t kb = koff[R];
+            const int32_t nch = (kc + KC - 1) / KC;
+            const T* Ap = A + (kb - aoff0) * T_;
+            const int32_t* rows = klist + kb;
+            stage_panel<T>(sm.a[0], Ap, tid);
+            stage_rows<T>(sm.b[0], M, N, rows, c0, tid);
+            cp_async_commit();
+#pragma unroll 1
+            for (int32_t ch = 0; ch < nch; ++ch) {
+                if (ch + 1 < nch) {
+                    const int s = (ch + 1) & 1;
+                    stage_panel<T>(sm.a[s], Ap + (int64_t)(ch + 1) * KC * T_, tid);
+                    stage_rows<T>(sm.b[s], M, N, rows + (ch + 1) * KC, c0, tid);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                compute_chunk<T>(acc, sm, ch & 1, tx, ty);
+                __syncthreads();
+            }
+            store_c<T>(acc, M, N, r0, c0, tx, ty);
+            if (J != R) store_c_transposed<T>(acc, M, N, r0, c0, tx, ty);
+        }
+        // (kc == 0: no finite entry right of R, so d(R, J) = F(R, J) = inf and
+        //  d(R, R) = F(R, R): the stored values are already final)
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release(tflags + (int64_t)R * nR + J, 1u);
+        }
+    }
+}
+
+int g_sms_e = 0;
+int sms_e() {
+    if (g_sms_e == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms_e, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms_e <= 0) g_sms_e = 1;
+    }
+    return g_sms_e;
+}
+
+}  // namespace
+
+size_t bg_backsub_scratch_bytes(int64_t N) {
+    const int64_t nR = (N + T_ - 1) / T_;
+    // masks (16 B), fblk and tile flags (4 B each) per tile pair; per row block: fcnt,
+    // kcnt, koff; the work counter
+    return (size_t)(nR * nR) * 24 + (size_t)nR * 16 + 64;
+}
+
+template <typename T>
+cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, size_t apanel_budget,
+                       double* updates, FwProfile* prof, cudaStream_t st) {
+    if (updates) *updates = 0.0;
+    if (N <= 0) return cudaSuccess;
+    const int32_t nR = (int32_t)((N + T_ - 1) / T_);
+    cudaError_t e = cudaFuncSetAttribute(k_backsub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
+    const int64_t pairs = (int64_t)nR * nR;
+    unsigned char* scratch = nullptr;
+    if ((e = cudaMallocAsync(&scratch, bg_backsub_scratch_bytes(N), st)) != cudaSuccess) return e;
+    uint4* masks = reinterpret_cast<uint4*>(scratch);
+    int32_t* fblk = reinterpret_cast<int32_t*>(scratch + pairs * 16);
+    uint32_t* tflags = reinterpret_cast<uint32_t*>(scratch + pairs * 20);
+    int64_t* koff = reinterpret_cast<int64_t*>(scratch + pairs * 24);
+    int32_t* fcnt = reinterpret_cast<int32_t*>(koff + nR);
+    int32_t* kcnt = fcnt + nR;
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(kcnt + nR);  // 8-byte aligned
+    int32_t* klist = nullptr;
+    T* A = nullptr;
+    std::vector<cudaEvent_t> ev;  // per launch of k_backsub: start, end (profiling only)
+    std::vector<int32_t> hk(nR);
+    std::vector<int64_t> hoff(nR + 1, 0);
+    auto done = [&](cudaError_t r) {
+        if (klist) cudaFreeAsync(klist, st);
+        if (A) cudaFreeAsync(A, st);
+        cudaFreeAsync(scratch, st);
+        for (auto& x : ev)
+            if (x) cudaEventDestroy(x);
+        return r;
+    };
+    if ((e = cudaMemsetAsync(tflags, 0, (size_t)pairs * 4, st)) != cudaSuccess) return done(e);
+    k_colmask<T><<<nR, 256, 0, st>>>(M, N, nR, rowflags, masks, fblk, fcnt, kcnt);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
+    if ((e = cudaMemcpyAsync(hk.data(), kcnt, (size_t)nR * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return done(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
+    double upd = 0.0, items = 0.0;
+    for (int32_t R = 0; R < nR; ++R) {
+        hoff[R + 1] = hoff[R] + round_up(hk[R], KC);
+        upd += (double)hk[R] * T_ * T_ * (double)(nR - R);
+        items += (double)(nR - R);
+    }
+    if (updates) *updates = upd;
+    if (prof) {
+        prof->bs_updates = upd;
+        prof->bs_items = items;
+    }
+    const int64_t ktot = hoff[nR];
+    if ((e = cudaMemcpyAsync(koff, hoff.data(), (size_t)nR * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return done(e);
+    if ((e = cudaMallocAsync(&klist, (size_t)(ktot > 0 ? ktot : 1) * 4, st)) != cudaSuccess) return done(e);
+    k_klist<<<nR, T_, 0, st>>>(masks, fblk, fcnt, kcnt, koff, nR, klist);
+    count_launches(1);
+    // row-block ranges [lo, hi) whose panels fit the budget, from the last rows down
+    const int64_t row_bytes = (int64_t)T_ * sizeof(T);
+    int64_t maxk = 0;
+    std::vector<int32_t> cuts{nR};
+    for (int32_t R = nR - 1; R >= 0; --R) {
+        const int64_t lo_k = hoff[R], hi_k = hoff[cuts.back()];
+        if (R < cuts.back() - 1 && (hi_k - lo_k) * row_bytes > (int64_t)apanel_budget) cuts.push_back(R + 1);
+    }
+    cuts.push_back(0);
+    for (size_t i = 0; i + 1 < cuts.size(); ++i) maxk = std::max(maxk, hoff[cuts[i]] - hoff[cuts[i + 1]]);
+    if ((e = cudaMallocAsync(&A, (size_t)(maxk > 0 ? maxk : 1) * row_bytes, st)) != cudaSuccess) return done(e);
+    if (prof) {
+        ev.assign(2 * (cuts.size() - 1), nullptr);
+        for (auto& x : ev)
+            if ((e = cudaEventCreate(&x)) != cudaSuccess) return done(e);
+    }
+    const size_t psm = sizeof(PanelSmem<T>);
+    const int grid = sms_e() * SPQ_FW_MIN_CTAS;
+    for (size_t i = 0; i + 1 < cuts.size() && e == cudaSuccess; ++i) {
+        const int32_t hi = cuts[i], lo = cuts[i + 1];
+        const int64_t aoff0 = hoff[lo];
+        // A panels of rows [lo, hi): read before the launch overwrites those rows
+        k_gather_a<T><<<hi - lo, 256, 0, st>>>(M, N, lo, koff, kcnt, klist, aoff0, A);
+        const int64_t m0 = nR - hi, m1 = nR - lo;
+        const int64_t g0 = m0 * (m0 + 1) / 2, nit = m1 * (m1 + 1) / 2 - g0;
+        cudaMemsetAsync(counter, 0, 8, st);
+        if (prof) cudaEventRecord(ev[2 * i], st);
+        k_backsub<T><<<grid, NTH, psm, st>>>(M, N, nR, g0, nit, koff, kcnt, klist, A, aoff0, fblk, fcnt, tflags,
+                                             counter, err);
+        if (prof) cudaEventRecord(ev[2 * i + 1], st);
+        count_launches(2);
+        e = cudaGetLastError();
+    }
+    if (prof && e == cudaSuccess && !ev.empty() && (e = cudaEventSynchronize(ev.back())) == cudaSuccess) {
+        prof->bs_ms = 0.0;
+        prof->bs_launches = 0;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
+                prof->bs_ms += ms;
+                prof->bs_launches += 1;
+            }
+        }
+    }
+    return done(e);
+}
+
+template cudaError_t bg_backsub<float>(float*, int64_t, const uint32_t*, uint32_t*, size_t, double*, FwProfile*,
+                                       cudaStream_t);
+template cudaError_t bg_backsub<int32_t>(int32_t*, int64_t, const uint32_t*, uint32_t*, size_t, double*, FwProfile*,
+                                         cudaStream_t);
+
+}  // namespace spq

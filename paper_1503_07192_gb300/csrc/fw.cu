@@ -22,252 +22,11 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fw_tile.cuh"
 
 namespace spq {
 
 namespace {
-
-// Compile-time tuning of the phase-2/3 kernels: resident CTAs per SM requested from the
-// register allocator, and unrolling of the float32 inner loop (two k steps per trip).
-#ifndef SPQ_FW_MIN_CTAS
-#define SPQ_FW_MIN_CTAS 2
-#endif
-#ifndef SPQ_FW_UNROLL
-#define SPQ_FW_UNROLL 1
-#endif
-
-constexpr int kInnerUnroll = SPQ_FW_UNROLL;
-constexpr int T_ = kTile;  // 128
-constexpr int KC = 32;     // k rows per staged panel chunk
-constexpr int NTH = 256;   // threads per CTA; each owns an 8 x 8 block of the tile
-constexpr int NCHUNK = T_ / KC;
-
-__device__ __forceinline__ float fmin3(float a, float b, float c) {
-    float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
-
-template <typename T>
-struct MP;
-template <>
-struct MP<float> {
-    // min(c, a0 + b0, a1 + b1)
-    static __device__ __forceinline__ float upd2(float c, float a0, float b0, float a1, float b1) {
-        return fmin3(c, a0 + b0, a1 + b1);
-    }
-    static __device__ __forceinline__ float upd1(float c, float a, float b) { return fminf(c, a + b); }
-};
-template <>
-struct MP<int32_t> {
-    static __device__ __forceinline__ int32_t upd2(int32_t c, int32_t a0, int32_t b0, int32_t a1, int32_t b1) {
-        return __viaddmin_s32(a0, b0, __viaddmin_s32(a1, b1, c));
-    }
-    static __device__ __forceinline__ int32_t upd1(int32_t c, int32_t a, int32_t b) { return __viaddmin_s32(a, b, c); }
-};
-
-template <typename T>
-__device__ __forceinline__ int4 inf4() {
-    T v = Inf<T>::value();
-    int x = *reinterpret_cast<int*>(&v);
-    return make_int4(x, x, x, x);
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-template <typename T>
-struct alignas(16) PanelSmem {
-    T a[2][KC][T_];
-    T b[2][KC][T_];
-};
-
-// Thread-owned rows / columns inside a tile: {q*4 .. q*4+3} and {64 + q*4 .. 64+q*4+3}.
-__device__ __forceinline__ int own(int q, int i) { return (i < 4) ? q * 4 + i : 64 + q * 4 + (i - 4); }
-
-// Stage rows [row0, row0+KC) x cols [col0, col0+128) of M (n x n) into P; cells outside
-// the matrix read as infinity.
-template <typename T>
-__device__ __forceinline__ void stage_chunk(T (*P)[T_], const T* __restrict__ M, int64_t n, int64_t row0,
-                                            int64_t col0, int tid) {
-#pragma unroll
-    for (int it = 0; it < (KC * T_ / 4) / NTH; ++it) {
-        int idx = it * NTH + tid;
-        int kk = idx >> 5, c4 = idx & 31;
-        int64_t r = row0 + kk, c = col0 + c4 * 4;
-        T* dst = &P[kk][c4 * 4];
-        if (r < n && c < n)
-            cp_async16(dst, M + r * n + c);
-        else
-            *reinterpret_cast<int4*>(dst) = inf4<T>();
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void load_c(T (&acc)[8][8], const T* __restrict__ M, int64_t n, int64_t r0, int64_t c0,
-                                       int tx, int ty) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        int64_t r = r0 + own(ty, i);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int64_t c = c0 + own(tx, h * 4);
-            int4 v = (r < n && c < n) ? *reinterpret_cast<const int4*>(M + r * n + c) : inf4<T>();
-            acc[i][h * 4 + 0] = *reinterpret_cast<T*>(&v.x);
-            acc[i][h * 4 + 1] = *reinterpret_cast<T*>(&v.y);
-            acc[i][h * 4 + 2] = *reinterpret_cast<T*>(&v.z);
-            acc[i][h * 4 + 3] = *reinterpret_cast<T*>(&v.w);
-        }
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void store_c(const T (&acc)[8][8], T* __restrict__ M, int64_t n, int64_t r0, int64_t c0,
-                                        int tx, int ty) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        int64_t r = r0 + own(ty, i);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int64_t c = c0 + own(tx, h * 4);
-            if (r < n && c < n) {
-                int4 v;
-                v.x = *reinterpret_cast<const int*>(&acc[i][h * 4 + 0]);
-                v.y = *reinterpret_cast<const int*>(&acc[i][h * 4 + 1]);
-                v.z = *reinterpret_cast<const int*>(&acc[i][h * 4 + 2]);
-                v.w = *reinterpret_cast<const int*>(&acc[i][h * 4 + 3]);
-                *reinterpret_cast<int4*>(M + r * n + c) = v;
-            }
-        }
-    }
-}
-
-// Transposed store: acc[i][j] -> M[c0 + col(j)][r0 + row(i)].  Each thread writes
-// 4 consecutive transposed columns (its rows q*4..q*4+3) as one 16-byte vector.
-template <typename T>
-__device__ __forceinline__ void store_c_transposed(const T (&acc)[8][8], T* __restrict__ M, int64_t n, int64_t r0,
-                                                   int64_t c0, int tx, int ty) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        int64_t tr = c0 + own(tx, j);  // transposed row
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int64_t tc = r0 + own(ty, h * 4);  // transposed column (multiple of 4)
-            if (tr < n && tc < n) {
-                int4 v;
-                v.x = *reinterpret_cast<const int*>(&acc[h * 4 + 0][j]);
-                v.y = *reinterpret_cast<const int*>(&acc[h * 4 + 1][j]);
-                v.z = *reinterpret_cast<const int*>(&acc[h * 4 + 2][j]);
-                v.w = *reinterpret_cast<const int*>(&acc[h * 4 + 3][j]);
-                *reinterpret_cast<int4*>(M + tr * n + tc) = v;
-            }
-        }
-    }
-}
-
-// acc = min(acc, A (x) B) over the KC-row chunk held in stage s:
-// A[i][k] = a[s][k][i] (the panel is stored k-major), B[k][j] = b[s][k][j].
-template <typename T>
-__device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>& sm, int s, int tx, int ty) {
-#pragma unroll 1
-    for (int kk = 0; kk < KC; kk += 2) {
-        T a0[8], a1[8], b0[8], b1[8];
-        {
-            const int4 x0 = *reinterpret_cast<const int4*>(&sm.a[s][kk][ty * 4]);
-            const int4 x1 = *reinterpret_cast<const int4*>(&sm.a[s][kk][64 + ty * 4]);
-            const int4 y0 = *reinterpret_cast<const int4*>(&sm.a[s][kk + 1][ty * 4]);
-            const int4 y1 = *reinterpret_cast<const int4*>(&sm.a[s][kk + 1][64 + ty * 4]);
-            const int4 z0 = *reinterpret_cast<const int4*>(&sm.b[s][kk][tx * 4]);
-            const int4 z1 = *reinterpret_cast<const int4*>(&sm.b[s][kk][64 + tx * 4]);
-            const int4 w0 = *reinterpret_cast<const int4*>(&sm.b[s][kk + 1][tx * 4]);
-            const int4 w1 = *reinterpret_cast<const int4*>(&sm.b[s][kk + 1][64 + tx * 4]);
-            const int xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-            const int ya[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-            const int zb[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-            const int wb[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                a0[i] = *reinterpret_cast<const T*>(&xa[i]);
-                a1[i] = *reinterpret_cast<const T*>(&ya[i]);
-                b0[i] = *reinterpret_cast<const T*>(&zb[i]);
-                b1[i] = *reinterpret_cast<const T*>(&wb[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = MP<T>::upd2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
-    }
-}
-
-// float32 form: the sums of two neighbouring columns come from one packed f32x2 add
-// (sm_100 family), and a three-input min folds two k steps into each accumulator.
-template <>
-__device__ __forceinline__ void compute_chunk<float>(float (&acc)[8][8], const PanelSmem<float>& sm, int s, int tx,
-                                                     int ty) {
-#pragma unroll kInnerUnroll
-    for (int kk = 0; kk < KC; kk += 2) {
-        const float4 x0 = *reinterpret_cast<const float4*>(&sm.a[s][kk][ty * 4]);
-        const float4 x1 = *reinterpret_cast<const float4*>(&sm.a[s][kk][64 + ty * 4]);
-        const float4 y0 = *reinterpret_cast<const float4*>(&sm.a[s][kk + 1][ty * 4]);
-        const float4 y1 = *reinterpret_cast<const float4*>(&sm.a[s][kk + 1][64 + ty * 4]);
-        const float4 z0 = *reinterpret_cast<const float4*>(&sm.b[s][kk][tx * 4]);
-        const float4 z1 = *reinterpret_cast<const float4*>(&sm.b[s][kk][64 + tx * 4]);
-        const float4 w0 = *reinterpret_cast<const float4*>(&sm.b[s][kk + 1][tx * 4]);
-        const float4 w1 = *reinterpret_cast<const float4*>(&sm.b[s][kk + 1][64 + tx * 4]);
-        const float a0[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        const float a1[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-        const float2 b0[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
-                              make_float2(z1.z, z1.w)};
-        const float2 b1[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
-                              make_float2(w1.z, w1.w)};
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float2 p0 = make_float2(a0[i], a0[i]);
-            const float2 p1 = make_float2(a1[i], a1[i]);
-#pragma unroll
-            for (int jp = 0; jp < 4; ++jp) {
-                const float2 s0 = __fadd2_rn(p0, b0[jp]);
-                const float2 s1 = __fadd2_rn(p1, b1[jp]);
-                acc[i][2 * jp] = fmin3(acc[i][2 * jp], s0.x, s1.x);
-                acc[i][2 * jp + 1] = fmin3(acc[i][2 * jp + 1], s0.y, s1.y);
-            }
-        }
-    }
-}
-
-// acc = min(acc, A (x) B) with A[i][k] = M[arow0 + k][acol0 + i] and
-// B[k][j] = M[arow0 + k][bcol0 + j], k over the pivot block [arow0, arow0 + 128).
-template <typename T>
-__device__ __forceinline__ void minplus_panels(T (&acc)[8][8], const T* __restrict__ M, int64_t n, int64_t prow0,
-                                               int64_t acol0, int64_t bcol0, PanelSmem<T>& sm, int tid, int tx,
-                                               int ty) {
-    stage_chunk<T>(sm.a[0], M, n, prow0, acol0, tid);
-    stage_chunk<T>(sm.b[0], M, n, prow0, bcol0, tid);
-    cp_async_commit();
-#pragma unroll 1
-    for (int ch = 0; ch < NCHUNK; ++ch) {
-        if (ch + 1 < NCHUNK) {
-            const int s = (ch + 1) & 1;
-            stage_chunk<T>(sm.a[s], M, n, prow0 + (ch + 1) * KC, acol0, tid);
-            stage_chunk<T>(sm.b[s], M, n, prow0 + (ch + 1) * KC, bcol0, tid);
-            cp_async_commit();
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        compute_chunk<T>(acc, sm, ch & 1, tx, ty);
-        __syncthreads();
-    }
-}
 
 // ---------------- phase 1: closure of the diagonal tile ----------------
 template <typename T>
@@ -329,7 +88,8 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                    int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite,
-                                                   int32_t flag_stride, const int32_t* __restrict__ sel) {
+                                                   int32_t flag_stride, const int32_t* __restrict__ sel,
+                                                   int32_t trailing) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -337,8 +97,10 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
         const MatDesc d = descs[sel ? sel[mi] : mi];
         const int64_t n = d.n;
         const int32_t R = (int32_t)((n + T_ - 1) / T_);
-        if (r >= R || (int32_t)blockIdx.x >= R - 1) continue;
-        const int32_t J = (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
+        // trailing: only the tiles right of the pivot (J > r; elimination form)
+        const int32_t J = trailing ? r + 1 + (int32_t)blockIdx.x
+                                   : (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
+        if (r >= R || J >= R) continue;
         T* M = base + d.off;
         const int64_t o = (int64_t)r * T_, cj = (int64_t)J * T_;
         T acc[8][8];
@@ -457,7 +219,7 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restr
 // Also accumulates the number of phase-3 tiles into tiles[0] and of phase-2 tiles with a
 // finite entry (the ones phase 2 computed) into tiles[1].
 __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, uint32_t* __restrict__ list,
-                          unsigned long long* __restrict__ tiles) {
+                          unsigned long long* __restrict__ tiles, int32_t clear) {
     __shared__ uint32_t cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -481,7 +243,8 @@ __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, ui
         }
         __syncthreads();
     }
-    for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
+    if (clear)
+        for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
     if (threadIdx.x == 0) {
         list[0] = cnt;
         tiles[0] += (unsigned long long)cnt * (cnt + 1) / 2;  // phase-3 tiles of this round
@@ -642,7 +405,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, ns, r, sel);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, ns, r, nullptr, 0, sel);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, ns, r, nullptr, 0, sel, 0);
             k_phase3_sel<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, sel, ns, p3off, r);
             count_launches(2);
         }
@@ -658,8 +421,8 @@ int64_t fw_single_scratch_words(int64_t N) {
 }
 
 template <typename T>
-cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double* updates, FwProfile* prof,
-                      cudaStream_t st) {
+cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_t* rowflags, double* updates,
+                      FwProfile* prof, cudaStream_t st) {
     if (updates) *updates = 0.0;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
@@ -687,13 +450,19 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
         k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
         count_launches(1);
-        if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags, 0, nullptr);
+        // elimination form: row tiles J > r only, flags kept per round (rowflags[r][J])
+        const int32_t np2 = rowflags ? R - 1 - r : R - 1;
+        uint32_t* fl = rowflags ? rowflags + (int64_t)r * R : flags;
+        if (np2 > 0) {
+            k_phase2<T><<<dim3(np2, 1), NTH, psm, st>>>(M, dd, 1, r, fl, 0, nullptr, rowflags ? 1 : 0);
             if (!skip_inf) {
-                // mark every tile: the compaction then lists all J != r
-                cudaMemsetAsync(flags, 0xff, R * sizeof(uint32_t), st);
+                // mark every tile: the compaction then lists all J != r (J > r)
+                if (rowflags)
+                    cudaMemsetAsync(fl + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
+                else
+                    cudaMemsetAsync(fl, 0xff, R * sizeof(uint32_t), st);
             }
-            k_compact<<<1, 1024, 0, st>>>(flags, R, r, list, tiles);
+            k_compact<<<1, 1024, 0, st>>>(fl, R, r, list, tiles, rowflags ? 0 : 1);
             if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
             k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
             if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
@@ -709,6 +478,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, double*
         prof->p3_ms = 0.0;
         prof->p3_launches = 0;
         for (size_t r = 0; e == cudaSuccess && 2 * r + 1 < evs.size(); ++r) {
+            if (rowflags && (int32_t)r + 1 >= R) break;  // no phase 3 in the last round
             float t = 0.f;
             if (cudaEventElapsedTime(&t, evs[2 * r], evs[2 * r + 1]) == cudaSuccess) {
                 prof->p3_ms += t;
@@ -754,7 +524,7 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r, nullptr);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr, 0);
             k_compact_many<<<nmat, 1024, 0, st>>>(flags, R, d_descs, nmat, r, lists, R + 1, offs, tiles);
             launch_scan_excl(offs, nmat + 1, st);
             k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs);
@@ -776,7 +546,8 @@ template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_
 
 template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_batched<float>(float*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
-template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, double*, FwProfile*, cudaStream_t);
-template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, double*, FwProfile*, cudaStream_t);
+template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*,
+                                        cudaStream_t);
+template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*, cudaStream_t);
 
 }  // namespace spq

@@ -140,8 +140,24 @@ __global__ void __launch_bounds__(GTH) k_query_saved(const View<T> V, const int2
 // Walk inside component c from vertex x to the vertex of local index tl, adding g to
 // every slot taken.  All lanes of the warp take part; returns false if the walk did not
 // reach its target within `limit` steps.
-template <typename T>
-__device__ bool walk_in_component(const View<T>& V, int32_t c, int32_t x, int32_t tl, float g, float* grad,
+// Visitors of the slots a walk takes (called by lane 0 only).
+struct AddGrad {
+    float g;
+    float* grad;
+    __device__ void operator()(int64_t e, int32_t /*to*/) const { atomicAdd(&grad[e], g); }
+};
+struct RecordPath {
+    int32_t* verts;  // this pair's row of max_len vertices
+    int32_t max_len;
+    int32_t* len;    // vertices written so far (may exceed max_len: the path did not fit)
+    __device__ void operator()(int64_t /*e*/, int32_t to) const {
+        const int32_t i = (*len)++;
+        if (i < max_len) verts[i] = to;
+    }
+};
+
+template <typename T, typename Visit>
+__device__ bool walk_in_component(const View<T>& V, int32_t c, int32_t x, int32_t tl, const Visit& visit,
                                   int64_t limit, int lane) {
     const MatDesc d = V.descs[c];
     const T* A = V.apsp + d.off;
@@ -161,15 +177,15 @@ __device__ bool walk_in_component(const View<T>& V, int32_t c, int32_t x, int32_
         }
         warp_argmin(best, be);
         if (be == INT64_MAX) return false;
-        if (lane == 0) atomicAdd(&grad[be], g);
         x = V.col[be];
+        if (lane == 0) visit(be, x);
     }
     return true;
 }
 
 // Walk through the boundary graph from boundary vertex b to boundary vertex b2.
-template <typename T>
-__device__ bool walk_boundary_graph(const View<T>& V, int32_t b, int32_t b2, float g, float* grad, int64_t limit,
+template <typename T, typename Visit>
+__device__ bool walk_boundary_graph(const View<T>& V, int32_t b, int32_t b2, const Visit& visit, int64_t limit,
                                     int lane) {
     const T inf = Inf<T>::value();
     const int64_t pb2 = V.bgpos[V.bg_off[V.comp[b2]] + V.local[b2]];
@@ -204,15 +220,31 @@ __device__ bool walk_boundary_graph(const View<T>& V, int32_t b, int32_t b2, flo
         if (bi == INT64_MAX) return false;
         if (bi < kInter) {
             const int32_t y = (int32_t)bi;
-            if (!walk_in_component(V, cb, b, y, g, grad, limit, lane)) return false;
+            if (!walk_in_component(V, cb, b, y, visit, limit, lane)) return false;
             b = V.vorder[V.vstart[cb] + y];
         } else {
             const int64_t e = bi - kInter;
-            if (lane == 0) atomicAdd(&grad[e], g);
             b = V.col[e];
+            if (lane == 0) visit(e, b);
         }
     }
     return true;
+}
+
+// The whole path of one pair: v1 -> b1* inside C1, b1* -> b2* through the boundary
+// graph, b2* -> v2 inside C2 (or v1 -> v2 inside C1 when the direct distance won).
+template <typename T, typename Visit>
+__device__ bool walk_pair(const View<T>& V, int32_t v, int32_t w, int2 sv, const Visit& visit, int64_t limit,
+                          int lane) {
+    const int32_t c1 = V.comp[v], c2 = V.comp[w];
+    // a witness that is not one this handle's forward call can produce fails the walk
+    if (sv.x == kDirect) return c1 == c2 && walk_in_component(V, c1, v, V.local[w], visit, limit, lane);
+    if (sv.x < 0 || sv.x >= V.nb[c1] || sv.y < 0 || sv.y >= V.nb[c2]) return false;
+    const int32_t b1 = V.vorder[V.vstart[c1] + sv.x];
+    const int32_t b2 = V.vorder[V.vstart[c2] + sv.y];
+    return walk_in_component(V, c1, v, sv.x, visit, limit, lane) &&
+           walk_boundary_graph(V, b1, b2, visit, limit, lane) &&
+           walk_in_component(V, c2, b2, V.local[w], visit, limit, lane);
 }
 
 template <typename T>
@@ -229,19 +261,36 @@ __global__ void __launch_bounds__(GTH) k_query_backward(const View<T> V, const i
         const float g = gdist[qi];
         if (sv.x == kSame || sv.x == kNoPath || g == 0.0f) continue;
         if (pr.x < 0 || pr.x >= V.n || pr.y < 0 || pr.y >= V.n) continue;
-        const int32_t v = pr.x, w = pr.y;
-        const int32_t c1 = V.comp[v], c2 = V.comp[w];
-        bool ok;
-        if (sv.x == kDirect) {
-            ok = walk_in_component(V, c1, v, V.local[w], g, grad, limit, lane);
-        } else {
-            const int32_t b1 = V.vorder[V.vstart[c1] + sv.x];
-            const int32_t b2 = V.vorder[V.vstart[c2] + sv.y];
-            ok = walk_in_component(V, c1, v, sv.x, g, grad, limit, lane) &&
-                 walk_boundary_graph(V, b1, b2, g, grad, limit, lane) &&
-                 walk_in_component(V, c2, b2, V.local[w], g, grad, limit, lane);
+        const AddGrad visit{g, grad};
+        if (!walk_pair(V, pr.x, pr.y, sv, visit, limit, lane) && lane == 0) atomicOr(err, kErrWalk);
+    }
+}
+
+// Vertex sequence of each pair's shortest path: verts[i][0] = v1, ..., up to v2;
+// lens[i] = number of vertices (-1: no path; > max_len: did not fit, truncated).
+template <typename T>
+__global__ void __launch_bounds__(GTH) k_query_paths(const View<T> V, const int2* __restrict__ pairs,
+                                                     const int2* __restrict__ saved, int64_t q, int32_t max_len,
+                                                     int32_t* __restrict__ verts, int32_t* __restrict__ lens,
+                                                     uint32_t* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * GTH) >> 5;
+    const int64_t limit = (int64_t)V.n + 1;
+    for (int64_t qi = ((int64_t)blockIdx.x * GTH + threadIdx.x) >> 5; qi < q; qi += nw) {
+        const int2 pr = pairs[qi];
+        const int2 sv = saved[qi];
+        int32_t* row = verts + qi * (int64_t)max_len;
+        if (sv.x == kNoPath || pr.x < 0 || pr.x >= V.n || pr.y < 0 || pr.y >= V.n) {
+            if (lane == 0) lens[qi] = -1;
+            continue;
         }
-        if (!ok && lane == 0) atomicOr(err, kErrWalk);
+        int32_t len = 1;
+        if (lane == 0 && max_len > 0) row[0] = pr.x;
+        if (sv.x != kSame) {
+            const RecordPath visit{row, max_len, &len};
+            if (!walk_pair(V, pr.x, pr.y, sv, visit, limit, lane) && lane == 0) atomicOr(err, kErrWalk);
+        }
+        if (lane == 0) lens[qi] = len;
     }
 }
 
@@ -318,6 +367,30 @@ spq_status spq_query_backward(spq_handle* h, const int32_t* pairs, int64_t q, co
         k_query_backward<int32_t><<<(unsigned)blocks, GTH, 0, st>>>(view_of<int32_t>(h), (const int2*)pairs,
                                                                      (const int2*)saved, q, grad_dist, grad_w,
                                                                      h->err);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? SPQ_OK : SPQ_ECUDA;
+}
+
+spq_status spq_query_paths(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved, int32_t max_len,
+                           int32_t* verts, int32_t* lens, void* stream) {
+    using namespace spq;
+    if (!h || q < 0 || max_len < 0) return SPQ_EINVAL;
+    if (q == 0) return SPQ_OK;
+    if (!h->vorder || !h->csr_rp) return SPQ_EUNSUPPORTED;
+    if (!on_device(pairs) || !on_device(saved) || !on_device(lens) || (max_len > 0 && !on_device(verts)))
+        return SPQ_EINVAL;
+    if (((uintptr_t)pairs & 7u) || ((uintptr_t)saved & 7u)) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t blocks = (q + 7) / 8;
+    const int64_t cap = (int64_t)grad_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    if (h->f32store)
+        k_query_paths<float><<<(unsigned)blocks, GTH, 0, st>>>(view_of<float>(h), (const int2*)pairs,
+                                                                (const int2*)saved, q, max_len, verts, lens, h->err);
+    else
+        k_query_paths<int32_t><<<(unsigned)blocks, GTH, 0, st>>>(view_of<int32_t>(h), (const int2*)pairs,
+                                                                  (const int2*)saved, q, max_len, verts, lens,
+                                                                  h->err);
     count_launches(1);
     return cudaGetLastError() == cudaSuccess ? SPQ_OK : SPQ_ECUDA;
 }

@@ -33,6 +33,7 @@ struct spq_handle {
     int32_t* bg_off = nullptr;  // first slot of each component (component-grouped numbering)
     int32_t* bgpos = nullptr;   // matrix position of each slot
     int32_t order_method = 0;
+    int32_t bg_method = SPQ_BG_FW;  // how D was computed (spq_bg_method)
     int32_t query_grouped = 1;
     int32_t* csize = nullptr;
     void* apsp = nullptr;

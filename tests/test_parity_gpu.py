@@ -13,8 +13,8 @@ unreachable pairs, v == w, parallel edges, self-loops, zero weights.
 import numpy as np
 import pytest
 
-from _util import (all_pairs, assert_pairs_exact, build, graph_from_edges, oracle_i32, query, random_graph,
-                   spq)
+from _util import (all_pairs, assert_pairs_exact, build, graph_from_edges, opts, oracle_i32, query,
+                   random_graph, spq, torch_dev)
 
 import gen
 import oracle
@@ -24,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 ARITHS = [1, 2]  # SPQ_ARITH_I32, SPQ_ARITH_F32
 ORDERS = [0, 1, 2, 3]  # SPQ_ORDER_AUTO, _ID, _DISSECTION, _VERTEX_DISSECTION
+BGS = [0, 1, 2]  # SPQ_BG_AUTO, _FW, _ELIM
 
 
 @pytest.mark.parametrize("name", sorted(FIXTURES))
@@ -66,9 +67,11 @@ def _check_tables(h, g, part, k):
 
 @pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("order", ORDERS)
-def test_grid64_all_queries_and_tables(arith, order):
+@pytest.mark.parametrize("bg", BGS)
+def test_grid64_all_queries_and_tables(arith, order, bg):
     w = gen.configs.grid64()
-    h = build(w.graph, w.part, w.k, arith=arith, order=order)
+    h = build(w.graph, w.part, w.k, arith=arith, order=order, bg=bg)
+    assert h.profile()["bg_method"] == (2 if bg == 2 or (bg == 0 and h.profile()["order_method"] != 0) else 1)
     st = h.stats()
     assert st["n_bg"] == 732
     assert_pairs_exact(h, w.graph, w.pairs)
@@ -82,9 +85,10 @@ def test_modes_agree_on_delaunay():
     for arith in ARITHS:
         for order in ORDERS:
             for skip in (0, 1):
-                h = build(w.graph, w.part, w.k, arith=arith, order=order, skip=skip)
-                outs.append(query(h, w.pairs))
-                h.free()
+                for bg in (1, 2):
+                    h = build(w.graph, w.part, w.k, arith=arith, order=order, skip=skip, bg=bg)
+                    outs.append(query(h, w.pairs))
+                    h.free()
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
     h = build(w.graph, w.part, w.k)
@@ -298,3 +302,58 @@ def test_grouped_queries_mark_invalid_pairs():
     assert np.array_equal(got[ok], ref)
     m.spq_query_status(h)  # the mark was cleared
     h.free()
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("order", [1, 3])
+def test_elimination_matrix_equals_floyd_warshall(arith, order):
+    """The boundary-graph matrix from elimination + back-substitution is the one
+    Floyd-Warshall gives, entry for entry (60 row blocks, a ragged last block), also
+    when the panels are processed in many launches of 1 MiB each, and it holds Lemma 1's
+    distances."""
+    w = gen.configs.delaunay_rcb(1 << 16, 6, 20000, seed=57)
+    ref = build(w.graph, w.part, w.k, arith=arith, order=order, bg=1)
+    B0 = ref.bg()
+    ref.free()
+    for panel_mib in (0, 1):
+        h = build(w.graph, w.part, w.k, arith=arith, order=order, bg=2, panel_mib=panel_mib)
+        assert h.profile()["bg_method"] == 2
+        assert np.array_equal(h.bg(), B0)
+        assert_pairs_exact(h, w.graph, w.pairs)
+        h.free()
+    n_bg = B0.shape[0]
+    assert n_bg > 59 * 128
+    # a few boundary rows against multi-source Dijkstra (Lemma 1)
+    h = build(w.graph, w.part, w.k, arith=arith, order=order, bg=2)
+    meta = h.meta()
+    comp, local, nb, bg_off = meta["comp"], meta["local"], meta["nb"], meta["bg_off"]
+    bvert = np.empty(n_bg, np.int64)
+    for c in range(w.k):
+        ids = np.nonzero((comp == c) & (local < nb[c]))[0]
+        bvert[bg_off[c] + local[ids]] = ids
+    rows = np.random.default_rng(57).choice(n_bg, size=40, replace=False)
+    ref_rows = oracle_i32(oracle.multi_sssp(w.graph.row_ptr, w.graph.col, w.graph.w, bvert[rows]))
+    assert np.array_equal(B0[rows].astype(np.int64), ref_rows[:, bvert])
+    h.free()
+
+
+def test_elimination_profile_counts():
+    m = spq()
+    torch, dev = torch_dev()
+    w = gen.configs.delaunay_rcb(1 << 15, 5, 10, seed=59)
+    g = w.graph
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    upd = {}
+    for bg in (1, 2):
+        o = opts(bg=bg)
+        o.profile_kernels = 1
+        h = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+        pf, st = h.profile(), h.stats()
+        assert pf["bg_method"] == bg and len(pf) == 15
+        upd[bg] = st["bg_updates"]
+        if bg == 2:
+            nR = -(-st["n_bg"] // 128)
+            assert pf["bs_items"] == nR * (nR + 1) // 2
+            assert 0 < pf["bs_updates"] < st["bg_updates"] and pf["bs_ms"] > 0 and pf["bs_launches"] == 1
+        h.free()
+    assert upd[2] < upd[1]  # dissection order: fewer updates than Floyd-Warshall
