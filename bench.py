@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--queries", type=int, default=None, help="override the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--arith", type=int, default=0, help="spq_arith of the build (0 auto, 1 int32, 2 float32)")
+    p.add_argument("--bg", type=int, default=0, help="spq_bg_method of the build (0 auto, 1 FW, 2 elimination)")
     return p.parse_args()
 
 
@@ -510,6 +512,7 @@ def main():
     d_out = torch.empty(q, dtype=torch.int32, device=dev)
     opts = spq.spq_opts_default()
     opts.profile_kernels = 1
+    opts.arith, opts.bg_method = args.arith, args.bg
     stream = torch.cuda.current_stream(dev)
 
     def step():

@@ -134,13 +134,17 @@ int query_sms() {
 // Queries sorted by their unordered component pair {C1, C2}: every segment of equal keys
 // shares one block dist_BG(B(C1), B(C2)), which is staged into shared memory in chunks of
 // rows (gathered through the slot positions) and reused by all of the segment's queries.
-// Segments never cross a 64-position tile of the sorted order (a key change or a tile
-// start begins a segment), so one CTA owns each tile.  dist is symmetric, so a pair is
+// A segment starts where the key changes or at a multiple of GSEGCAP positions (so no CTA
+// gets an unbounded run), and it is answered by the CTA whose 64-position tile holds its
+// first position, however far it extends past the tile.  dist is symmetric, so a pair is
 // answered as (v, w) with comp(v) = C1 <= C2 = comp(w).
+//
+// Per batch the 8 warps hold 4 queries each; lanes own block columns b2 and walk the rows
+// b1 with dist_C1(v1, b1) broadcast by shuffle (one fused add-min per update for int32).
 constexpr int GTH = 256;  // 8 warps
 constexpr int GTILE = 64;
+constexpr int GSEGCAP = 1024;         // longest segment (a power of two)
 constexpr int GQPW = 4;               // queries per warp per batch
-constexpr int GBATCH = 8 * GQPW;      // queries per batch
 constexpr int GCOLS = 256;            // block columns per pass (8 per lane)
 constexpr int GSMEM = 24 * 1024;      // staged elements per CTA (96 KB): two CTAs per SM
 
@@ -158,6 +162,14 @@ __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t 
     idx[i] = (uint32_t)i;
 }
 
+// t = min(t, a + b): one fused add-min for int32, add then min for float
+__device__ __forceinline__ int32_t addmin(int32_t a, int32_t b, int32_t t) { return __viaddmin_s32(a, b, t); }
+__device__ __forceinline__ float addmin(float a, float b, float t) { return fminf(t, a + b); }
+
+__device__ __forceinline__ bool seg_head(const uint32_t* __restrict__ keys, int64_t p) {
+    return p == 0 || keys[p] != keys[p - 1] || (p & (GSEGCAP - 1)) == 0;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
                                                        const uint32_t* __restrict__ keys,
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
     const T inf = Inf<T>::value();
     bool h = false;
     if (tid < GTILE) {
-        h = tid < tn && (tid == 0 || keys[t0 + tid] != keys[t0 + tid - 1]);
+        h = tid < tn && seg_head(keys, t0 + tid);
         unsigned b = __ballot_sync(0xffffffffu, h);
         if (lane == 0) hb[warp] = b;
     }
@@ -183,7 +195,20 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
         heads[pos] = tid;
     }
     const int nh = __popc(hb[0]) + __popc(hb[1]);
-    if (tid == 0) heads[nh] = tn;
+    if (warp == 0 && nh > 0) {
+        // the last segment runs to the next head at or after the tile's end
+        int64_t e = t0 + tn;
+        for (;;) {
+            const int64_t p = e + lane;
+            const unsigned b = __ballot_sync(0xffffffffu, p >= q || seg_head(keys, p));
+            if (b) {
+                e += __ffs(b) - 1;
+                break;
+            }
+            e += 32;
+        }
+        if (lane == 0) heads[nh] = (int32_t)(e - t0);
+    }
     __syncthreads();
     for (int sg = 0; sg < nh; ++sg) {
         const int s0 = heads[sg], s1 = heads[sg + 1];
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
         const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];
         const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
         const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
-        for (int bq = s0; bq < s1; bq += GBATCH) {
+        for (int bq = s0; bq < s1; bq += 8 * GQPW) {
             // this warp's queries: bq + u * 8 + warp
             int64_t a1off[GQPW], a2off[GQPW];
             int32_t l2s[GQPW];
@@ -294,7 +319,7 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
                                 if (jj < jmax) {
                                     const T sv = srow[jj * 32];
 #pragma unroll
-                                    for (int u = 0; u < GQPW; ++u) t[u][jj] = tmin(t[u][jj], ai[u] + sv);
+                                    for (int u = 0; u < GQPW; ++u) t[u][jj] = addmin(ai[u], sv, t[u][jj]);
                                 }
                             }
                         }
@@ -305,22 +330,24 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
                 for (int u = 0; u < GQPW; ++u)
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
-                        const int j = jj * 32 + lane;
-                        const T c = (val[u] && j < cols) ? ctx.apsp[a2off[u] + jb + j] : inf;
-                        r[u] = tmin(r[u], t[u][jj] + c);
+                        if (jj < jmax) {
+                            const int j = jj * 32 + lane;
+                            const T c = (val[u] && j < cols) ? ctx.apsp[a2off[u] + jb + j] : inf;
+                            r[u] = tmin(r[u], t[u][jj] + c);
+                        }
                     }
             }
 #pragma unroll
             for (int u = 0; u < GQPW; ++u) {
-                T x = warp_min(r[u]);
+                T y = warp_min(r[u]);
                 if (val[u]) {
-                    if (c1 == c2) x = tmin(x, ctx.apsp[a1off[u] + l2s[u]]);
-                    if (same_v[u]) x = T(0);
+                    if (c1 == c2) y = tmin(y, ctx.apsp[a1off[u] + l2s[u]]);
+                    if (same_v[u]) y = T(0);
                     if (lane == 0) {
                         if (MODE == kOutF32)
-                            ((float*)out)[qis[u]] = (float)x;
+                            ((float*)out)[qis[u]] = (float)y;
                         else
-                            ((int32_t*)out)[qis[u]] = (int32_t)tmin<int32_t>((int32_t)x, SPQ_INF_I32);
+                            ((int32_t*)out)[qis[u]] = (int32_t)tmin<int32_t>((int32_t)y, SPQ_INF_I32);
                     }
                 }
             }
