@@ -193,6 +193,9 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
         const int64_t R = (h->N + kTile - 1) / kTile;
         double fwd = 0.0, bs = 0.0;
         if ((e = cudaMemsetAsync(plan.rowflags, 0, (size_t)(R * R) * 4, st)) != cudaSuccess) return e;
+        if ((e = launch_mark_bg_tiles(in.n, in.rp, in.col, in.part, h->local, h->nb, h->bg_off, h->bgpos, h->k, h->N,
+                                      plan.rowflags, st)) != cudaSuccess)
+            return e;
         if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, plan.rowflags, &fwd, profile ? &h->fwprof : nullptr,
                               st)) != cudaSuccess)
             return e;

@@ -126,6 +126,11 @@ template <typename T>
 cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, size_t apanel_budget,
                        double* updates, FwProfile* prof, cudaStream_t st);
 size_t bg_backsub_scratch_bytes(int64_t N);
+// Marks (flags[I * R + J] = 1, I < J, R = ceil(N/128)) of the tiles the assembled
+// boundary-graph matrix may hold a finite entry in: the elimination form's candidates.
+cudaError_t launch_mark_bg_tiles(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part,
+                                 const int32_t* local, const int32_t* nb, const int32_t* bg_off, const int32_t* bgpos,
+                                 int32_t k, int64_t N, uint32_t* flags, cudaStream_t st);
 // Many matrices (sizes up to max_n) at once, with infinite-panel skipping per matrix;
 // *updates receives the phase-2 and phase-3 min-plus updates issued.
 template <typename T>

@@ -55,6 +55,64 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Marks of the tiles (I < J) the assembled boundary-graph matrix may hold a finite entry
+// in (flags[I * nR + J] = 1): every pair of tiles a component's slots fall into (its
+// clique), and the tiles of the edges between components.
+__global__ void __launch_bounds__(256) k_mark_clique(const int32_t* __restrict__ nb, const int32_t* __restrict__ bg_off,
+                                                     const int32_t* __restrict__ bgpos, int32_t k, int32_t nR,
+                                                     uint32_t* __restrict__ flags) {
+    __shared__ int32_t blk[256];
+    __shared__ int32_t nblk;
+    for (int32_t c = blockIdx.x; c < k; c += gridDim.x) {
+        const int32_t b = nb[c];
+        const int32_t* pos = bgpos + bg_off[c];
+        if (threadIdx.x == 0) nblk = 0;
+        __syncthreads();
+        // distinct tiles of the component's slots (a slot's tile differs from the previous
+        // slot's only a few times; duplicates beyond that are harmless)
+        for (int32_t i = threadIdx.x; i < b; i += blockDim.x) {
+            const int32_t t = pos[i] / T_;
+            if (i == 0 || pos[i - 1] / T_ != t) {
+                const int32_t at = atomicAdd(&nblk, 1);
+                if (at < 256) blk[at] = t;
+            }
+        }
+        __syncthreads();
+        const int32_t m = nblk;
+        if (m <= 256) {
+            for (int32_t x = threadIdx.x; x < m * m; x += blockDim.x) {
+                const int32_t I = blk[x / m], J = blk[x % m];
+                if (I < J) flags[(int64_t)I * nR + J] = 1u;
+            }
+        } else {  // many runs: mark from every slot pair
+            for (int32_t x = threadIdx.x; x < b * b; x += blockDim.x) {
+                const int32_t I = pos[x / b] / T_, J = pos[x % b] / T_;
+                if (I < J) flags[(int64_t)I * nR + J] = 1u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_mark_inter(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ part, const int32_t* __restrict__ local,
+                             const int32_t* __restrict__ bg_off, const int32_t* __restrict__ bgpos, int32_t nR,
+                             uint32_t* __restrict__ flags) {
+    const int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const int32_t cu = part[u];
+    int32_t tu = -1;
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+        const int32_t v = col[e];
+        const int32_t cv = part[v];
+        if (cv == cu) continue;
+        if (tu < 0) tu = bgpos[bg_off[cu] + local[u]] / T_;
+        const int32_t tv = bgpos[bg_off[cv] + local[v]] / T_;
+        if (tu < tv) flags[(int64_t)tu * nR + tv] = 1u;
+        else if (tv < tu) flags[(int64_t)tv * nR + tu] = 1u;
+    }
+}
+
 // Per row block R: the column tiles J > R holding a finite entry of F (from the forward
 // pass's flags), the 128-bit mask of their finite columns (fblk / masks at R * nR + i),
 // their number and the number of finite columns |K(R)|.
@@ -295,6 +353,17 @@ int sms_e() {
 }
 
 }  // namespace
+
+cudaError_t launch_mark_bg_tiles(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part,
+                                 const int32_t* local, const int32_t* nb, const int32_t* bg_off, const int32_t* bgpos,
+                                 int32_t k, int64_t N, uint32_t* flags, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const int32_t nR = (int32_t)((N + T_ - 1) / T_);
+    k_mark_clique<<<k < 65535 ? k : 65535, 256, 0, st>>>(nb, bg_off, bgpos, k, nR, flags);
+    k_mark_inter<<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, part, local, bg_off, bgpos, nR, flags);
+    count_launches(2);
+    return cudaGetLastError();
+}
 
 size_t bg_backsub_scratch_bytes(int64_t N) {
     const int64_t nR = (N + T_ - 1) / T_;

@@ -19,6 +19,9 @@
 
 #include <string.h>
 
+#include <algorithm>
+
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -55,8 +58,50 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = S[own(ty, i)][own(tx, j)];
         const int K = (int)((n - o) < T_ ? (n - o) : T_);
+        int k = 0;
+        if constexpr (std::is_same<T, float>::value) {
+            // two pivot steps per barrier: row k + 1 after step k is formed on the fly,
+            // min(D(k+1, x), D(k+1, k) + D(k, x)), and both steps fold into one
+            // three-input min; the owners then publish rows k + 2 and k + 3
+            for (; k + 1 < K; k += 2) {
+                float a0[8], b0[8], a1[8], b1[8];
+                const float4 p0 = *reinterpret_cast<const float4*>(&S[k][ty * 4]);
+                const float4 p1 = *reinterpret_cast<const float4*>(&S[k][64 + ty * 4]);
+                const float4 q0 = *reinterpret_cast<const float4*>(&S[k][tx * 4]);
+                const float4 q1 = *reinterpret_cast<const float4*>(&S[k][64 + tx * 4]);
+                const float4 u0 = *reinterpret_cast<const float4*>(&S[k + 1][ty * 4]);
+                const float4 u1 = *reinterpret_cast<const float4*>(&S[k + 1][64 + ty * 4]);
+                const float4 v0 = *reinterpret_cast<const float4*>(&S[k + 1][tx * 4]);
+                const float4 v1 = *reinterpret_cast<const float4*>(&S[k + 1][64 + tx * 4]);
+                const float skk = S[k][k + 1];
+                const float pa[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                const float qa[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                const float ua[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                const float va[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    a0[i] = pa[i];
+                    b0[i] = qa[i];
+                    a1[i] = fminf(ua[i], skk + pa[i]);
+                    b1[i] = fminf(va[i], skk + qa[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmin3(acc[i][j], a0[i] + b0[j], a1[i] + b1[j]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = own(ty, i);
+                    if (row == k + 2 || row == k + 3) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) S[row][own(tx, j)] = acc[i][j];
+                    }
+                }
+                __syncthreads();
+            }
+        }
 #pragma unroll 1
-        for (int k = 0; k < K; ++k) {
+        for (; k < K; ++k) {
             // row k of S is current: by symmetry it is also column k
             T a[8], b[8];
 #pragma unroll
@@ -88,8 +133,7 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                    int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite,
-                                                   int32_t flag_stride, const int32_t* __restrict__ sel,
-                                                   int32_t trailing) {
+                                                   int32_t flag_stride, const int32_t* __restrict__ sel) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -97,10 +141,8 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
         const MatDesc d = descs[sel ? sel[mi] : mi];
         const int64_t n = d.n;
         const int32_t R = (int32_t)((n + T_ - 1) / T_);
-        // trailing: only the tiles right of the pivot (J > r; elimination form)
-        const int32_t J = trailing ? r + 1 + (int32_t)blockIdx.x
-                                   : (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
-        if (r >= R || J >= R) continue;
+        if (r >= R || (int32_t)blockIdx.x >= R - 1) continue;
+        const int32_t J = (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
         T* M = base + d.off;
         const int64_t o = (int64_t)r * T_, cj = (int64_t)J * T_;
         T acc[8][8];
@@ -119,6 +161,91 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
         store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
         if (row_finite && tid == 0) row_finite[(int64_t)mi * flag_stride + J] = 1u;
     }
+}
+
+// ---------------- phase 2, elimination form: candidate row tiles only ----------------
+// cand[0] = count, cand[1..] = the tiles J > r of row r that may hold a finite entry (the
+// assembly's and earlier rounds' marks).  A candidate that is all-infinite is unmarked
+// (it stays infinite); the others are updated, with their transposes.
+template <typename T>
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restrict__ M, int64_t n, int32_t r,
+                                                                      int32_t R, const uint32_t* __restrict__ cand,
+                                                                      uint32_t* __restrict__ rowflags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t o = (int64_t)r * T_;
+    const uint32_t c = cand[0];
+    const T inf = Inf<T>::value();
+    for (uint32_t ci = blockIdx.x; ci < c; ci += gridDim.x) {
+        const int32_t J = (int32_t)cand[1 + ci];
+        const int64_t cj = (int64_t)J * T_;
+        T acc[8][8];
+        load_c<T>(acc, M, n, o, cj, tx, ty);
+        bool fin = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
+        if (!__syncthreads_or(fin)) {
+            if (tid == 0) rowflags[(int64_t)r * R + J] = 0u;
+            continue;
+        }
+        minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        store_c<T>(acc, M, n, o, cj, tx, ty);
+        store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
+    }
+}
+
+// Ordered list of the marked tiles J in [lo, hi) of one flag row: out[0] = count,
+// out[1..] = J ascending.  Whole block; ends with a barrier.
+__device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t hi, uint32_t* __restrict__ out) {
+    __shared__ uint32_t cnt;
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int32_t base = lo; base < hi; base += blockDim.x) {
+        const int32_t J = base + threadIdx.x;
+        const bool take = J < hi && f[J] != 0u;
+        const unsigned ballot = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) wsum[warp] = __popc(ballot);
+        __syncthreads();
+        uint32_t off = cnt;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (take) out[1 + off + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)J;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+            cnt += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = cnt;
+    __syncthreads();
+}
+
+// Elimination form, after phase 2 of round r (r = -1: before round 0):
+//   list = the finite row tiles J > r of round r (phase 3 updates list x list);
+//   marks every pair of the list as a tile that may hold a finite entry from now on;
+//   cand = the marked tiles J > r + 1 of row r + 1 (phase 2 of the next round).
+__global__ void k_compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int32_t r, uint32_t* __restrict__ list,
+                                uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles) {
+    if (r >= 0) {
+        compact_row(rowflags + (int64_t)r * R, r + 1, R, list);
+        const uint32_t c = list[0];
+        for (uint32_t t = threadIdx.x; t < c * c; t += blockDim.x) {
+            const uint32_t x = t / c, y = t % c;
+            if (y > x) rowflags[(int64_t)list[1 + x] * R + list[1 + y]] = 1u;
+        }
+        if (threadIdx.x == 0) {
+            tiles[0] += (unsigned long long)c * (c + 1) / 2;  // phase-3 tiles of this round
+            tiles[1] += (unsigned long long)c;                // phase-2 tiles computed (finite)
+        }
+        __syncthreads();
+    }
+    if (r + 1 < R) compact_row(rowflags + (int64_t)(r + 1) * R, r + 2, R, cand);
 }
 
 // Upper-triangle task t (0 <= t < c(c+1)/2) -> pair (x, y), 0 <= x <= y < c, row-major.
@@ -219,7 +346,7 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restr
 // Also accumulates the number of phase-3 tiles into tiles[0] and of phase-2 tiles with a
 // finite entry (the ones phase 2 computed) into tiles[1].
 __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, uint32_t* __restrict__ list,
-                          unsigned long long* __restrict__ tiles, int32_t clear) {
+                          unsigned long long* __restrict__ tiles) {
     __shared__ uint32_t cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -243,8 +370,7 @@ __global__ void k_compact(uint32_t* __restrict__ flags, int32_t R, int32_t r, ui
         }
         __syncthreads();
     }
-    if (clear)
-        for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
+    for (int32_t J = threadIdx.x; J < R; J += blockDim.x) flags[J] = 0u;
     if (threadIdx.x == 0) {
         list[0] = cnt;
         tiles[0] += (unsigned long long)cnt * (cnt + 1) / 2;  // phase-3 tiles of this round
@@ -348,6 +474,8 @@ cudaError_t set_smem_attrs() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase2_cand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_many<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_sel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
@@ -405,7 +533,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, ns, r, sel);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, ns, r, nullptr, 0, sel, 0);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, ns, r, nullptr, 0, sel);
             k_phase3_sel<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, sel, ns, p3off, r);
             count_launches(2);
         }
@@ -417,7 +545,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
 
 int64_t fw_single_scratch_words(int64_t N) {
     int64_t R = (N + T_ - 1) / T_;
-    return 2 * R + 2 + 4;  // flags[R], list[1 + R] (+1 pad), two tile counters (u64)
+    return 3 * R + 8;  // flags[R], list[1 + R] (+1 pad), two tile counters (u64), cand[1 + R] (+1)
 }
 
 template <typename T>
@@ -447,22 +575,34 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
         for (auto& ev : evs)
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
+    uint32_t* cand = scratch + 2 * R + 6;
+    if (rowflags && R > 0) {
+        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, -1, list, cand, tiles);  // candidates of round 0
+        count_launches(1);
+    }
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
         k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
         count_launches(1);
-        // elimination form: row tiles J > r only, flags kept per round (rowflags[r][J])
-        const int32_t np2 = rowflags ? R - 1 - r : R - 1;
-        uint32_t* fl = rowflags ? rowflags + (int64_t)r * R : flags;
-        if (np2 > 0) {
-            k_phase2<T><<<dim3(np2, 1), NTH, psm, st>>>(M, dd, 1, r, fl, 0, nullptr, rowflags ? 1 : 0);
-            if (!skip_inf) {
-                // mark every tile: the compaction then lists all J != r (J > r)
-                if (rowflags)
-                    cudaMemsetAsync(fl + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
-                else
-                    cudaMemsetAsync(fl, 0xff, R * sizeof(uint32_t), st);
+        if (rowflags) {
+            // elimination form: row tiles J > r only, among the marked candidates
+            const int32_t np2 = R - 1 - r;
+            if (np2 > 0) {
+                k_phase2_cand<T><<<std::min(np2, p3_grid), NTH, psm, st>>>(M, N, r, R, cand, rowflags);
+                if (!skip_inf)  // mark every tile: the compaction then lists all J > r
+                    cudaMemsetAsync(rowflags + (int64_t)r * R + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
+                k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles);
+                if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
+                k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
+                if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
+                count_launches(3);
             }
-            k_compact<<<1, 1024, 0, st>>>(fl, R, r, list, tiles, rowflags ? 0 : 1);
+        } else if (R > 1) {
+            k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags, 0, nullptr);
+            if (!skip_inf) {
+                // mark every tile: the compaction then lists all J != r
+                cudaMemsetAsync(flags, 0xff, R * sizeof(uint32_t), st);
+            }
+            k_compact<<<1, 1024, 0, st>>>(flags, R, r, list, tiles);
             if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
             k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
             if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
@@ -524,7 +664,7 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r, nullptr);
         count_launches(1);
         if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr, 0);
+            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr);
             k_compact_many<<<nmat, 1024, 0, st>>>(flags, R, d_descs, nmat, r, lists, R + 1, offs, tiles);
             launch_scan_excl(offs, nmat + 1, st);
             k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs);
