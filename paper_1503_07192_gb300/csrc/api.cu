@@ -176,8 +176,20 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
         return e;
     if ((e = fw_batched<T>(apsp, h->descs, h->h_descs.data(), h->k, max_n, st)) != cudaSuccess) return e;
     evs.mark(3, st);
+    const int64_t R = (h->N + kTile - 1) / kTile;
+    // elimination form with skipping: only the marked tiles and the diagonal are read
+    // before the back-substitution writes every tile, so only those are initialised
+    const bool fill_marked = plan.elim && skip_inf;
     if (h->N > 0) {
-        if ((e = launch_bg_fill<T>(D, h->N, st)) != cudaSuccess) return e;
+        if (plan.elim) {
+            if ((e = cudaMemsetAsync(plan.rowflags, 0, (size_t)(R * R) * 4, st)) != cudaSuccess) return e;
+            if ((e = launch_mark_bg_tiles(in.n, in.rp, in.col, in.part, h->local, h->nb, h->bg_off, h->bgpos, h->k,
+                                          h->N, plan.rowflags, st)) != cudaSuccess)
+                return e;
+        }
+        if ((e = fill_marked ? launch_fill_marked<T>(D, h->N, plan.rowflags, st) : launch_bg_fill<T>(D, h->N, st)) !=
+            cudaSuccess)
+            return e;
         if ((e = launch_bg_clique<T>(apsp, h->descs, h->nb, h->bg_off, h->bgpos, h->k, D, h->N, st)) != cudaSuccess)
             return e;
         if ((e = launch_bg_inter<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->bg_off, h->bgpos, D,
@@ -185,21 +197,19 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
             return e;
     }
     evs.mark(4, st);
+    if (check_exact && (e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    // the elimination stores the float32 boundary-graph table as int32 itself (checked)
+    const bool d_converted = plan.elim && check_exact && h->N > 0;
     if (h->N > 0 && !plan.elim) {
         if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, nullptr, &h->bg_updates, profile ? &h->fwprof : nullptr,
                               st)) != cudaSuccess)
             return e;
     } else if (h->N > 0) {
-        const int64_t R = (h->N + kTile - 1) / kTile;
         double fwd = 0.0, bs = 0.0;
-        if ((e = cudaMemsetAsync(plan.rowflags, 0, (size_t)(R * R) * 4, st)) != cudaSuccess) return e;
-        if ((e = launch_mark_bg_tiles(in.n, in.rp, in.col, in.part, h->local, h->nb, h->bg_off, h->bgpos, h->k, h->N,
-                                      plan.rowflags, st)) != cudaSuccess)
-            return e;
         if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, plan.rowflags, &fwd, profile ? &h->fwprof : nullptr,
                               st)) != cudaSuccess)
             return e;
-        if ((e = bg_backsub<T>(D, h->N, plan.rowflags, h->err, plan.apanel_budget, &bs,
+        if ((e = bg_backsub<T>(D, h->N, plan.rowflags, h->err, d_converted ? d_flag : nullptr, plan.apanel_budget, &bs,
                                profile ? &h->fwprof : nullptr, st)) != cudaSuccess)
             return e;
         h->bg_updates = fwd + bs;
@@ -214,9 +224,9 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
     evs.mark(5, st);
     if (check_exact) {
         // the float32 tables become int32 ones (every entry below 2^24 is an exact integer)
-        if ((e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
         if ((e = launch_check_convert((float*)h->apsp, h->apsp_elems, d_flag, st)) != cudaSuccess) return e;
-        if (h->N > 0 && (e = launch_check_convert((float*)h->D, h->N * h->N, d_flag, st)) != cudaSuccess) return e;
+        if (h->N > 0 && !d_converted && (e = launch_check_convert((float*)h->D, h->N * h->N, d_flag, st)) != cudaSuccess)
+            return e;
         uint32_t f = 0;
         if ((e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;

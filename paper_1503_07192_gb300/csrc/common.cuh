@@ -116,15 +116,31 @@ template <typename T>
 cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, uint32_t* rowflags, double* updates,
                       FwProfile* prof, cudaStream_t st);
 int64_t fw_single_scratch_words(int64_t N);
+// Elimination form, after phase 2 of round r (r = -1: before round 0): list = the finite
+// row tiles J > r of round r, marks of its phase-3 targets, cand = the candidates of row
+// r + 1 (count first, then ascending tile indices).
+void launch_compact_trail(uint32_t* rowflags, int32_t R, int32_t r, uint32_t* list, uint32_t* cand,
+                          unsigned long long* tiles, cudaStream_t st);
+// One elimination round r with 1024-thread CTAs (fw_wide.cu): phase 1, phase 2 over cand,
+// the compaction above, phase 3 over list (bracketed by ev0 / ev1 when given).
+template <typename T>
+cudaError_t wide_round(T* M, int64_t N, int32_t r, int32_t R, uint32_t* rowflags, const uint32_t* cand,
+                       uint32_t* list, bool skip_inf, int grid, unsigned long long* tiles, cudaEvent_t ev0,
+                       cudaEvent_t ev1, cudaStream_t st);
 
 // ---- elim.cu: back-substitution after the forward form of fw_single ----
 // Completes M (N x N, symmetric storage) to all-pairs distances.  err: device status
 // word (kErrWait if a bounded wait gave up).  *updates: min-plus updates issued.
 // Needs bg_backsub_scratch_bytes(N) bytes of device scratch plus its A panels, which it
 // allocates stream-ordered in pieces of at most apanel_budget bytes.
+// With exact != NULL (float tables of an int32 graph) the tables are stored as int32 as
+// they become final, and a finite value >= 2^24 sets kErrExact in *exact.
 template <typename T>
-cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, size_t apanel_budget,
+cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
                        double* updates, FwProfile* prof, cudaStream_t st);
+// Infinity (0 on the diagonal) in the marked tiles, their mirrors and the diagonal tiles.
+template <typename T>
+cudaError_t launch_fill_marked(T* M, int64_t N, const uint32_t* flags, cudaStream_t st);
 size_t bg_backsub_scratch_bytes(int64_t N);
 // Marks (flags[I * R + J] = 1, I < J, R = ceil(N/128)) of the tiles the assembled
 // boundary-graph matrix may hold a finite entry in: the elimination form's candidates.

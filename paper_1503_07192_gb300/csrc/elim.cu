@@ -30,6 +30,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -53,6 +54,31 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 }
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Integer encoding of the converted (CONV) back-substitution.  An int32 table value m
+// with 0 <= m < 2^24, read as the bits of a float, is the float m * 2^-149 (a subnormal
+// below 2^23, the smallest binade of normals from 2^23 to 2^24): float addition of two
+// such values is exact integer addition of the bit patterns while the sum stays below
+// 2^24, and float order is integer order.  So the tiles stored as int32 are read back as
+// floats without any conversion; only the forward values (true floats) are converted
+// once, and SPQ_INF_I32 (2^29, read as 2^-63) is infinity (every finite distance of an
+// int32 graph is below it).  Subnormals are kept: no flush-to-zero in these kernels.
+__device__ __forceinline__ float enc(float x) { return __int_as_float(x < 536870912.0f ? (int)x : SPQ_INF_I32); }
+
+// Encoded results -> stored int32: sums of infinities clamp to SPQ_INF_I32; true if a
+// finite value is >= 2^24 (then not provably exact).
+__device__ __forceinline__ bool clamp_enc(float (&acc)[8][8]) {
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int b = __float_as_int(acc[i][j]);
+            bad |= b >= (1 << 24) && b < SPQ_INF_I32;
+            acc[i][j] = __int_as_float(b < SPQ_INF_I32 ? b : SPQ_INF_I32);
+        }
+    return bad;
 }
 
 // Marks of the tiles (I < J) the assembled boundary-graph matrix may hold a finite entry
@@ -110,6 +136,30 @@ __global__ void k_mark_inter(int32_t n, const int64_t* __restrict__ rp, const in
         const int32_t tv = bgpos[bg_off[cv] + local[v]] / T_;
         if (tu < tv) flags[(int64_t)tu * nR + tv] = 1u;
         else if (tv < tu) flags[(int64_t)tv * nR + tu] = 1u;
+    }
+}
+
+// Infinity in the marked tiles (and their mirrors) and the diagonal tiles, 0 on the
+// diagonal: the only tiles the elimination reads before the back-substitution writes
+// every tile.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fill_marked(T* __restrict__ M, int64_t N, int32_t nR,
+                                                     const uint32_t* __restrict__ flags) {
+    const int32_t R = blockIdx.x;
+    const T inf = Inf<T>::value();
+    for (int32_t J = R; J < nR; ++J) {
+        if (J != R && flags[(int64_t)R * nR + J] == 0u) continue;
+        for (int32_t x = threadIdx.x; x < T_ * T_ / 4; x += blockDim.x) {
+            const int64_t i = (int64_t)R * T_ + (x >> 5), c = (int64_t)J * T_ + (x & 31) * 4;
+            if (i < N && c < N) {
+                T v[4] = {inf, inf, inf, inf};
+                if (J == R && i >= c && i < c + 4) v[i - c] = T(0);
+                *reinterpret_cast<int4*>(M + i * N + c) = *reinterpret_cast<const int4*>(v);
+            }
+            // the mirror tile (J, R), all infinite
+            const int64_t mi = (int64_t)J * T_ + (x >> 5), mc = (int64_t)R * T_ + (x & 31) * 4;
+            if (J != R && mi < N && mc < N) *reinterpret_cast<int4*>(M + mi * N + mc) = inf4<T>();
+        }
     }
 }
 
@@ -191,7 +241,7 @@ __global__ void __launch_bounds__(T_) k_klist(const uint4* __restrict__ masks, c
 
 // A panels: A[(koff[R] - aoff0 + k) * 128 + i] = F(R*128 + i, klist[k]), read as its
 // mirror F(klist[k], R*128 + i) (one contiguous row piece); padding rows infinite.
-template <typename T>
+template <typename T, bool CONV>
 __global__ void __launch_bounds__(256) k_gather_a(const T* __restrict__ M, int64_t N, int32_t R0,
                                                   const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt,
                                                   const int32_t* __restrict__ klist, int64_t aoff0,
@@ -206,6 +256,11 @@ __global__ void __launch_bounds__(256) k_gather_a(const T* __restrict__ M, int64
         int4 v = inf4<T>();
         if (k < kc && col0 + c4 * 4 < N)
             v = *reinterpret_cast<const int4*>(M + (int64_t)klist[base + k] * N + col0 + c4 * 4);
+        if constexpr (CONV) {
+            const float4 f = *reinterpret_cast<const float4*>(&v);
+            const float4 g = make_float4(enc(f.x), enc(f.y), enc(f.z), enc(f.w));
+            v = *reinterpret_cast<const int4*>(&g);
+        }
         *reinterpret_cast<int4*>(A + (base - aoff0 + k) * T_ + c4 * 4) = v;
     }
 }
@@ -213,7 +268,7 @@ __global__ void __launch_bounds__(256) k_gather_a(const T* __restrict__ M, int64
 // Stage KC gathered rows klist[kbase ..) of M, columns [col0, col0 + 128), into P.
 template <typename T>
 __device__ __forceinline__ void stage_rows(T (*P)[T_], const T* __restrict__ M, int64_t N,
-                                           const int32_t* __restrict__ rows, int64_t col0, int tid) {
+                                           const int32_t* __restrict__ rows, int64_t col0, int tid, int4 fill) {
 #pragma unroll
     for (int it = 0; it < (KC * T_ / 4) / NTH; ++it) {
         const int idx = it * NTH + tid;
@@ -223,7 +278,7 @@ __device__ __forceinline__ void stage_rows(T (*P)[T_], const T* __restrict__ M, 
         if (c < N)
             cp_async16(dst, M + (int64_t)rows[kk] * N + c);
         else
-            *reinterpret_cast<int4*>(dst) = inf4<T>();
+            *reinterpret_cast<int4*>(dst) = fill;
     }
 }
 
@@ -247,13 +302,16 @@ __device__ __forceinline__ void item_tile(int64_t g, int32_t nR, int32_t& R, int
     J = p < m ? R + 1 + (int32_t)p : R;
 }
 
-template <typename T>
+// CONV (float tables of an int32 graph): every tile is stored as int32 (the final table
+// type) as soon as it is final, and the arithmetic runs on the integer encoding above
+// (tiles read as rows of d need no conversion); a finite value >= 2^24 sets kErrExact.
+template <typename T, bool CONV>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
     k_backsub(T* __restrict__ M, int64_t N, int32_t nR, int64_t g0, int64_t nitems,
               const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt, const int32_t* __restrict__ klist,
               const T* __restrict__ A, int64_t aoff0, const int32_t* __restrict__ fblk,
               const int32_t* __restrict__ fcnt, uint32_t* __restrict__ tflags,
-              unsigned long long* __restrict__ counter, uint32_t* __restrict__ err) {
+              unsigned long long* __restrict__ counter, uint32_t* __restrict__ err, uint32_t* __restrict__ exact) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     __shared__ int64_t s_item;
@@ -272,6 +330,9 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
         int32_t R, J;
         item_tile(g0 + t, nR, R, J);
         const int32_t kc = kcnt[R];
+        const int64_t r0 = (int64_t)R * T_, c0 = (int64_t)J * T_;
+        const int4 fill = CONV ? make_int4(SPQ_INF_I32, SPQ_INF_I32, SPQ_INF_I32, SPQ_INF_I32) : inf4<T>();
+        const T vinf = CONV ? __int_as_float(SPQ_INF_I32) : Inf<T>::value();
         if (kc > 0) {
             // dependencies: the final tiles this one reads
             if (tid < 32) {
@@ -296,29 +357,33 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
             }
             __syncthreads();
             if (s_fail) break;
-            const int64_t r0 = (int64_t)R * T_, c0 = (int64_t)J * T_;
             T acc[8][8];
             if (J == R) {
                 load_c<T>(acc, M, N, r0, r0, tx, ty);
+                if constexpr (CONV)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = enc(acc[i][j]);
             } else {
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = Inf<T>::value();
+                    for (int j = 0; j < 8; ++j) acc[i][j] = vinf;
             }
             const int64_t kb = koff[R];
             const int32_t nch = (kc + KC - 1) / KC;
             const T* Ap = A + (kb - aoff0) * T_;
             const int32_t* rows = klist + kb;
             stage_panel<T>(sm.a[0], Ap, tid);
-            stage_rows<T>(sm.b[0], M, N, rows, c0, tid);
+            stage_rows<T>(sm.b[0], M, N, rows, c0, tid, fill);
             cp_async_commit();
 #pragma unroll 1
             for (int32_t ch = 0; ch < nch; ++ch) {
                 if (ch + 1 < nch) {
                     const int s = (ch + 1) & 1;
                     stage_panel<T>(sm.a[s], Ap + (int64_t)(ch + 1) * KC * T_, tid);
-                    stage_rows<T>(sm.b[s], M, N, rows + (ch + 1) * KC, c0, tid);
+                    stage_rows<T>(sm.b[s], M, N, rows + (ch + 1) * KC, c0, tid, fill);
                     cp_async_commit();
                     cp_async_wait<1>();
                 } else {
@@ -328,11 +393,32 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
                 compute_chunk<T>(acc, sm, ch & 1, tx, ty);
                 __syncthreads();
             }
+            if constexpr (CONV)
+                if (clamp_enc(acc)) atomicOr(exact, kErrExact);
+            store_c<T>(acc, M, N, r0, c0, tx, ty);
+            if (J != R) store_c_transposed<T>(acc, M, N, r0, c0, tx, ty);
+        } else if constexpr (CONV) {
+            // no finite entry right of R: d(R, J) = F(R, J) = inf, d(R, R) = F(R, R); the
+            // values are final but still float: store them as int32
+            T acc[8][8];
+            if (J == R) {
+                load_c<T>(acc, M, N, r0, r0, tx, ty);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = enc(acc[i][j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = vinf;
+            }
+            if (clamp_enc(acc)) atomicOr(exact, kErrExact);
             store_c<T>(acc, M, N, r0, c0, tx, ty);
             if (J != R) store_c_transposed<T>(acc, M, N, r0, c0, tx, ty);
         }
-        // (kc == 0: no finite entry right of R, so d(R, J) = F(R, J) = inf and
-        //  d(R, R) = F(R, R): the stored values are already final)
+        // (kc == 0 without conversion: the stored values d(R, J) = inf and d(R, R) =
+        //  F(R, R) are already final)
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -365,6 +451,15 @@ cudaError_t launch_mark_bg_tiles(int32_t n, const int64_t* rp, const int32_t* co
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_fill_marked(T* M, int64_t N, const uint32_t* flags, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const int32_t nR = (int32_t)((N + T_ - 1) / T_);
+    k_fill_marked<T><<<nR, 256, 0, st>>>(M, N, nR, flags);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 size_t bg_backsub_scratch_bytes(int64_t N) {
     const int64_t nR = (N + T_ - 1) / T_;
     // masks (16 B), fblk and tile flags (4 B each) per tile pair; per row block: fcnt,
@@ -373,13 +468,15 @@ size_t bg_backsub_scratch_bytes(int64_t N) {
 }
 
 template <typename T>
-cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, size_t apanel_budget,
+cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
                        double* updates, FwProfile* prof, cudaStream_t st) {
     if (updates) *updates = 0.0;
     if (N <= 0) return cudaSuccess;
     const int32_t nR = (int32_t)((N + T_ - 1) / T_);
-    cudaError_t e = cudaFuncSetAttribute(k_backsub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PanelSmem<T>));
+    // exact != NULL (float tables only): store int32 tables, checking exactness
+    const bool conv = std::is_same<T, float>::value && exact != nullptr;
+    auto kern = conv ? k_backsub<T, std::is_same<T, float>::value> : k_backsub<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
     const int64_t pairs = (int64_t)nR * nR;
     unsigned char* scratch = nullptr;
@@ -450,13 +547,16 @@ cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err,
         const int32_t hi = cuts[i], lo = cuts[i + 1];
         const int64_t aoff0 = hoff[lo];
         // A panels of rows [lo, hi): read before the launch overwrites those rows
-        k_gather_a<T><<<hi - lo, 256, 0, st>>>(M, N, lo, koff, kcnt, klist, aoff0, A);
+        if (conv)
+            k_gather_a<T, std::is_same<T, float>::value><<<hi - lo, 256, 0, st>>>(M, N, lo, koff, kcnt, klist, aoff0, A);
+        else
+            k_gather_a<T, false><<<hi - lo, 256, 0, st>>>(M, N, lo, koff, kcnt, klist, aoff0, A);
         const int64_t m0 = nR - hi, m1 = nR - lo;
         const int64_t g0 = m0 * (m0 + 1) / 2, nit = m1 * (m1 + 1) / 2 - g0;
         cudaMemsetAsync(counter, 0, 8, st);
         if (prof) cudaEventRecord(ev[2 * i], st);
-        k_backsub<T><<<grid, NTH, psm, st>>>(M, N, nR, g0, nit, koff, kcnt, klist, A, aoff0, fblk, fcnt, tflags,
-                                             counter, err);
+        kern<<<grid, NTH, psm, st>>>(M, N, nR, g0, nit, koff, kcnt, klist, A, aoff0, fblk, fcnt, tflags, counter, err,
+                                     exact);
         if (prof) cudaEventRecord(ev[2 * i + 1], st);
         count_launches(2);
         e = cudaGetLastError();
@@ -475,9 +575,12 @@ cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err,
     return done(e);
 }
 
-template cudaError_t bg_backsub<float>(float*, int64_t, const uint32_t*, uint32_t*, size_t, double*, FwProfile*,
-                                       cudaStream_t);
-template cudaError_t bg_backsub<int32_t>(int32_t*, int64_t, const uint32_t*, uint32_t*, size_t, double*, FwProfile*,
-                                         cudaStream_t);
+template cudaError_t bg_backsub<float>(float*, int64_t, const uint32_t*, uint32_t*, uint32_t*, size_t, double*,
+                                       FwProfile*, cudaStream_t);
+template cudaError_t bg_backsub<int32_t>(int32_t*, int64_t, const uint32_t*, uint32_t*, uint32_t*, size_t, double*,
+                                         FwProfile*, cudaStream_t);
+
+template cudaError_t launch_fill_marked<float>(float*, int64_t, const uint32_t*, cudaStream_t);
+template cudaError_t launch_fill_marked<int32_t>(int32_t*, int64_t, const uint32_t*, cudaStream_t);
 
 }  // namespace spq

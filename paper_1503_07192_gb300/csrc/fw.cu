@@ -163,40 +163,6 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
     }
 }
 
-// ---------------- phase 2, elimination form: candidate row tiles only ----------------
-// cand[0] = count, cand[1..] = the tiles J > r of row r that may hold a finite entry (the
-// assembly's and earlier rounds' marks).  A candidate that is all-infinite is unmarked
-// (it stays infinite); the others are updated, with their transposes.
-template <typename T>
-__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restrict__ M, int64_t n, int32_t r,
-                                                                      int32_t R, const uint32_t* __restrict__ cand,
-                                                                      uint32_t* __restrict__ rowflags) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t o = (int64_t)r * T_;
-    const uint32_t c = cand[0];
-    const T inf = Inf<T>::value();
-    for (uint32_t ci = blockIdx.x; ci < c; ci += gridDim.x) {
-        const int32_t J = (int32_t)cand[1 + ci];
-        const int64_t cj = (int64_t)J * T_;
-        T acc[8][8];
-        load_c<T>(acc, M, n, o, cj, tx, ty);
-        bool fin = false;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
-        if (!__syncthreads_or(fin)) {
-            if (tid == 0) rowflags[(int64_t)r * R + J] = 0u;
-            continue;
-        }
-        minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
-        store_c<T>(acc, M, n, o, cj, tx, ty);
-        store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
-    }
-}
-
 // Ordered list of the marked tiles J in [lo, hi) of one flag row: out[0] = count,
 // out[1..] = J ascending.  Whole block; ends with a barrier.
 __device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t hi, uint32_t* __restrict__ out) {
@@ -228,7 +194,8 @@ __device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t 
 
 // Elimination form, after phase 2 of round r (r = -1: before round 0):
 //   list = the finite row tiles J > r of round r (phase 3 updates list x list);
-//   marks every pair of the list as a tile that may hold a finite entry from now on;
+//   marks every pair of the list as a tile that may hold a finite entry from now on
+//   (2 where it was unmarked: only the marked tiles were initialised);
 //   cand = the marked tiles J > r + 1 of row r + 1 (phase 2 of the next round).
 __global__ void k_compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int32_t r, uint32_t* __restrict__ list,
                                 uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles) {
@@ -237,7 +204,12 @@ __global__ void k_compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int3
         const uint32_t c = list[0];
         for (uint32_t t = threadIdx.x; t < c * c; t += blockDim.x) {
             const uint32_t x = t / c, y = t % c;
-            if (y > x) rowflags[(int64_t)list[1 + x] * R + list[1 + y]] = 1u;
+            if (y > x) {
+                // 2: newly marked, its cells are not initialised yet (phase 3 starts it
+                // from infinity and then marks it 1)
+                uint32_t* f = rowflags + (int64_t)list[1 + x] * R + list[1 + y];
+                if (*f == 0u) *f = 2u;
+            }
         }
         if (threadIdx.x == 0) {
             tiles[0] += (unsigned long long)c * (c + 1) / 2;  // phase-3 tiles of this round
@@ -473,8 +445,7 @@ cudaError_t set_smem_attrs() {
                              (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_phase2_cand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_many<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
@@ -485,6 +456,12 @@ cudaError_t set_smem_attrs() {
 }
 
 }  // namespace
+
+void launch_compact_trail(uint32_t* rowflags, int32_t R, int32_t r, uint32_t* list, uint32_t* cand,
+                          unsigned long long* tiles, cudaStream_t st) {
+    k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles);
+    count_launches(1);
+}
 
 template <typename T>
 cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, int32_t nmat, int32_t max_n,
@@ -576,27 +553,18 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
     uint32_t* cand = scratch + 2 * R + 6;
-    if (rowflags && R > 0) {
-        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, -1, list, cand, tiles);  // candidates of round 0
-        count_launches(1);
-    }
+    if (rowflags && R > 0) launch_compact_trail(rowflags, R, -1, list, cand, tiles, st);  // candidates of round 0
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
+        if (rowflags) {
+            // elimination form: row tiles J > r only, among the marked candidates; one
+            // 1024-thread CTA per tile (latency form)
+            e = wide_round<T>(M, N, r, R, rowflags, cand, list, skip_inf, sms(), tiles,
+                              evs.empty() ? nullptr : evs[2 * r], evs.empty() ? nullptr : evs[2 * r + 1], st);
+            continue;
+        }
         k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
         count_launches(1);
-        if (rowflags) {
-            // elimination form: row tiles J > r only, among the marked candidates
-            const int32_t np2 = R - 1 - r;
-            if (np2 > 0) {
-                k_phase2_cand<T><<<std::min(np2, p3_grid), NTH, psm, st>>>(M, N, r, R, cand, rowflags);
-                if (!skip_inf)  // mark every tile: the compaction then lists all J > r
-                    cudaMemsetAsync(rowflags + (int64_t)r * R + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
-                k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles);
-                if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
-                k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
-                if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
-                count_launches(3);
-            }
-        } else if (R > 1) {
+        if (R > 1) {
             k_phase2<T><<<dim3(R - 1, 1), NTH, psm, st>>>(M, dd, 1, r, flags, 0, nullptr);
             if (!skip_inf) {
                 // mark every tile: the compaction then lists all J != r
