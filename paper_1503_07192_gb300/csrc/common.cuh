@@ -116,18 +116,6 @@ template <typename T>
 cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, uint32_t* rowflags, double* updates,
                       FwProfile* prof, cudaStream_t st);
 int64_t fw_single_scratch_words(int64_t N);
-// Elimination form, after phase 2 of round r (r = -1: before round 0): list = the finite
-// row tiles J > r of round r, marks of its phase-3 targets, cand = the candidates of row
-// r + 1 (count first, then ascending tile indices).
-void launch_compact_trail(uint32_t* rowflags, int32_t R, int32_t r, uint32_t* list, uint32_t* cand,
-                          unsigned long long* tiles, cudaStream_t st);
-// One elimination round r with 1024-thread CTAs (fw_wide.cu): phase 1, phase 2 over cand,
-// the compaction above, phase 3 over list (bracketed by ev0 / ev1 when given).
-template <typename T>
-cudaError_t wide_round(T* M, int64_t N, int32_t r, int32_t R, uint32_t* rowflags, const uint32_t* cand,
-                       uint32_t* list, bool skip_inf, int grid, unsigned long long* tiles, cudaEvent_t ev0,
-                       cudaEvent_t ev1, cudaStream_t st);
-
 // ---- elim.cu: back-substitution after the forward form of fw_single ----
 // Completes M (N x N, symmetric storage) to all-pairs distances.  err: device status
 // word (kErrWait if a bounded wait gave up).  *updates: min-plus updates issued.

@@ -163,6 +163,40 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
     }
 }
 
+// ---------------- phase 2, elimination form: candidate row tiles only ----------------
+// cand[0] = count, cand[1..] = the tiles J > r of row r that may hold a finite entry (the
+// assembly's and earlier rounds' marks).  A candidate that is all-infinite is unmarked
+// (it stays infinite); the others are updated, with their transposes.
+template <typename T>
+__global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restrict__ M, int64_t n, int32_t r,
+                                                                      int32_t R, const uint32_t* __restrict__ cand,
+                                                                      uint32_t* __restrict__ rowflags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t o = (int64_t)r * T_;
+    const uint32_t c = cand[0];
+    const T inf = Inf<T>::value();
+    for (uint32_t ci = blockIdx.x; ci < c; ci += gridDim.x) {
+        const int32_t J = (int32_t)cand[1 + ci];
+        const int64_t cj = (int64_t)J * T_;
+        T acc[8][8];
+        load_c<T>(acc, M, n, o, cj, tx, ty);
+        bool fin = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
+        if (!__syncthreads_or(fin)) {
+            if (tid == 0) rowflags[(int64_t)r * R + J] = 0u;
+            continue;
+        }
+        minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        store_c<T>(acc, M, n, o, cj, tx, ty);
+        store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
+    }
+}
+
 // Ordered list of the marked tiles J in [lo, hi) of one flag row: out[0] = count,
 // out[1..] = J ascending.  Whole block; ends with a barrier.
 __device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t hi, uint32_t* __restrict__ out) {
@@ -299,9 +333,12 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_sel(T* __restri
 // holds a finite entry; every (I, J) in list x list is updated, the pairs I < J once
 // for both triangles.  Tiles outside list x list keep their values: their pivot panel
 // is entirely infinite, so min(D, inf + x) = D.
+// With rowflags (elimination form), a target marked 2 was never initialised: it starts
+// from infinity instead of being loaded, and is marked 1 afterwards.
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
-                                                        const uint32_t* __restrict__ list) {
+                                                        const uint32_t* __restrict__ list,
+                                                        uint32_t* __restrict__ rowflags, int32_t R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -310,7 +347,22 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restr
     for (int64_t t = blockIdx.x; t < c * (c + 1) / 2; t += gridDim.x) {
         int64_t x, y;
         tri_pair(t, c, x, y);
-        phase3_tile<T>(M, n, o, (int64_t)list[1 + x], (int64_t)list[1 + y], sm, tid, tx, ty);
+        const int64_t I = list[1 + x], J = list[1 + y];
+        uint32_t* f = (rowflags && I < J) ? rowflags + I * R + J : nullptr;
+        if (f && *f == 2u) {
+            const int64_t ci = I * T_, cj = J * T_;
+            T acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = Inf<T>::value();
+            minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+            store_c<T>(acc, M, n, ci, cj, tx, ty);
+            store_c_transposed<T>(acc, M, n, ci, cj, tx, ty);
+            if (tid == 0) *f = 1u;  // (every thread read the flag before the panel barriers)
+        } else {
+            phase3_tile<T>(M, n, o, I, J, sm, tid, tx, ty);
+        }
     }
 }
 
@@ -445,6 +497,8 @@ cudaError_t set_smem_attrs() {
                              (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase2_cand<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
 
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_many<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
@@ -457,10 +511,28 @@ cudaError_t set_smem_attrs() {
 
 }  // namespace
 
-void launch_compact_trail(uint32_t* rowflags, int32_t R, int32_t r, uint32_t* list, uint32_t* cand,
-                          unsigned long long* tiles, cudaStream_t st) {
-    k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles);
+// One round r of the elimination form: phase 1, phase 2 over the candidates of row r,
+// the compaction (phase-3 list, marks, next candidates), phase 3 over the list.
+template <typename T>
+cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R, uint32_t* rowflags, uint32_t* cand,
+                       uint32_t* list, bool skip_inf, unsigned long long* tiles, cudaEvent_t ev0, cudaEvent_t ev1,
+                       cudaStream_t st) {
+    const size_t psm = sizeof(PanelSmem<T>);
+    const int grid = sms() * 2;
+    k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
     count_launches(1);
+    const int32_t np2 = R - 1 - r;
+    if (np2 > 0) {
+        k_phase2_cand<T><<<np2 < grid ? np2 : grid, NTH, psm, st>>>(M, N, r, R, cand, rowflags);
+        if (!skip_inf)  // mark every tile: the compaction then lists all J > r
+            cudaMemsetAsync(rowflags + (int64_t)r * R + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
+        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles);
+        if (ev0) cudaEventRecord(ev0, st);
+        k_phase3_list<T><<<grid, NTH, psm, st>>>(M, N, r, list, rowflags, R);
+        if (ev1) cudaEventRecord(ev1, st);
+        count_launches(3);
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -553,12 +625,14 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
     uint32_t* cand = scratch + 2 * R + 6;
-    if (rowflags && R > 0) launch_compact_trail(rowflags, R, -1, list, cand, tiles, st);  // candidates of round 0
+    if (rowflags && R > 0) {
+        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, -1, list, cand, tiles);  // candidates of round 0
+        count_launches(1);
+    }
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
         if (rowflags) {
-            // elimination form: row tiles J > r only, among the marked candidates; one
-            // 1024-thread CTA per tile (latency form)
-            e = wide_round<T>(M, N, r, R, rowflags, cand, list, skip_inf, sms(), tiles,
+            // elimination form: row tiles J > r only, among the marked candidates
+            e = elim_round<T>(M, dd, N, r, R, rowflags, cand, list, skip_inf, tiles,
                               evs.empty() ? nullptr : evs[2 * r], evs.empty() ? nullptr : evs[2 * r + 1], st);
             continue;
         }
@@ -572,7 +646,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
             }
             k_compact<<<1, 1024, 0, st>>>(flags, R, r, list, tiles);
             if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
-            k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list);
+            k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list, nullptr, 0);
             if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
             count_launches(3);
         }

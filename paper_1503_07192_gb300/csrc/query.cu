@@ -145,7 +145,7 @@ constexpr int GTH = 256;  // 8 warps
 constexpr int GTILE = 64;
 constexpr int GSEGCAP = 1024;         // longest segment (a power of two)
 constexpr int GQPW = 4;               // queries per warp per batch
-constexpr int GCOLS = 256;            // block columns per pass (8 per lane)
+constexpr int GCOLS = 256;            // block columns per pass (two groups of 128)
 constexpr int GSMEM = 24 * 1024;      // staged elements per CTA (96 KB): two CTAs per SM
 
 __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t n, const int32_t* __restrict__ comp,
@@ -168,6 +168,102 @@ __device__ __forceinline__ float addmin(float a, float b, float t) { return fmin
 
 __device__ __forceinline__ bool seg_head(const uint32_t* __restrict__ keys, int64_t p) {
     return p == 0 || keys[p] != keys[p - 1] || (p & (GSEGCAP - 1)) == 0;
+}
+
+// One pass over up to NG x 128 block columns [jb, jb + cols) for a warp's GQPW queries:
+// r[u] = min(r[u], min over b1, b2 of dist_C1(v1, b1) + D(b1, b2) + dist_C2(b2, v2)).
+// The block rows are staged in chunks into S (row length NG x 128); each lane owns four
+// consecutive columns per 128-column group (one 16-byte shared load per row and group)
+// and dist_C1(v1, b1) is broadcast by shuffle.
+template <typename T, int NG>
+__device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__ S, const int32_t* __restrict__ pos1,
+                                         const int32_t* __restrict__ pos2, int32_t nb1, int32_t jb, int cols,
+                                         const int64_t (&a1off)[GQPW], const int64_t (&a2off)[GQPW],
+                                         const bool (&val)[GQPW], bool active, T (&r)[GQPW], int tid, int lane,
+                                         int warp) {
+    constexpr int ld = NG * 128;
+    constexpr int rows_per_chunk = GSMEM / ld;
+    const T inf = Inf<T>::value();
+    int32_t colpos[NG * 4];
+#pragma unroll
+    for (int jj = 0; jj < NG * 4; ++jj) {
+        const int j = jj * 32 + lane;
+        colpos[jj] = j < cols ? pos2[jb + j] : -1;
+    }
+    T t[GQPW][NG][4];
+#pragma unroll
+    for (int u = 0; u < GQPW; ++u)
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) t[u][g][e] = inf;
+    for (int32_t rc = 0; rc < nb1; rc += rows_per_chunk) {
+        const int rows = (nb1 - rc) < rows_per_chunk ? (nb1 - rc) : rows_per_chunk;
+        __syncthreads();
+        // stage the chunk: SR rows x (NG x 4) column groups of independent loads per lane
+        constexpr int SR = 8 / NG;
+        for (int i0 = warp; i0 < rows; i0 += 8 * SR) {
+            int64_t rb[SR];
+#pragma unroll
+            for (int rr = 0; rr < SR; ++rr) {
+                const int ii = i0 + 8 * rr;
+                rb[rr] = ii < rows ? (int64_t)pos1[rc + ii] * ctx.N : -1;
+            }
+            T v[SR][NG * 4];
+#pragma unroll
+            for (int rr = 0; rr < SR; ++rr)
+#pragma unroll
+                for (int jj = 0; jj < NG * 4; ++jj)
+                    v[rr][jj] = (rb[rr] >= 0 && colpos[jj] >= 0) ? ctx.D[rb[rr] + colpos[jj]] : inf;
+#pragma unroll
+            for (int rr = 0; rr < SR; ++rr) {
+                const int ii = i0 + 8 * rr;
+                if (ii < rows)
+#pragma unroll
+                    for (int jj = 0; jj < NG * 4; ++jj) S[ii * ld + jj * 32 + lane] = v[rr][jj];
+            }
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int ib = 0; ib < rows; ib += 32) {
+            T areg[GQPW];
+#pragma unroll
+            for (int u = 0; u < GQPW; ++u)
+                areg[u] = (val[u] && ib + lane < rows) ? ctx.apsp[a1off[u] + rc + ib + lane] : inf;
+            const int iend = (rows - ib) < 32 ? (rows - ib) : 32;
+#pragma unroll 2
+            for (int ii = 0; ii < iend; ++ii) {
+                T ai[GQPW];
+#pragma unroll
+                for (int u = 0; u < GQPW; ++u) ai[u] = __shfl_sync(0xffffffffu, areg[u], ii);
+                const T* srow = S + (ib + ii) * ld + lane * 4;
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    const int4 sv = *reinterpret_cast<const int4*>(srow + g * 128);
+                    const T s4[4] = {*reinterpret_cast<const T*>(&sv.x), *reinterpret_cast<const T*>(&sv.y),
+                                     *reinterpret_cast<const T*>(&sv.z), *reinterpret_cast<const T*>(&sv.w)};
+#pragma unroll
+                    for (int u = 0; u < GQPW; ++u)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) t[u][g][e] = addmin(ai[u], s4[e], t[u][g][e]);
+                }
+            }
+        }
+    }
+    if (!active) return;
+    // dist_C2(b2, v2) for this pass's columns (a lane's four consecutive columns)
+#pragma unroll
+    for (int u = 0; u < GQPW; ++u)
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const int j0 = g * 128 + lane * 4;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = j0 + e;
+                const T c = (val[u] && j < cols) ? ctx.apsp[a2off[u] + jb + j] : inf;
+                r[u] = tmin(r[u], t[u][g][e] + c);
+            }
+        }
 }
 
 template <typename T, int MODE>
@@ -230,7 +326,8 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
         const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
         const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
         for (int bq = s0; bq < s1; bq += 8 * GQPW) {
-            // this warp's queries: bq + u * 8 + warp
+            // this warp's queries: bq + warp * GQPW + u (warps past the segment's end idle
+            // through the compute and only help staging)
             int64_t a1off[GQPW], a2off[GQPW];
             int32_t l2s[GQPW];
             uint32_t qis[GQPW];
@@ -238,7 +335,7 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
             T r[GQPW];
 #pragma unroll
             for (int u = 0; u < GQPW; ++u) {
-                const int sp = bq + u * 8 + warp;
+                const int sp = bq + warp * GQPW + u;
                 val[u] = sp < s1;
                 qis[u] = 0;
                 a1off[u] = a2off[u] = 0;
@@ -259,83 +356,13 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
                     a2off[u] = d2.off + (int64_t)l2s[u] * d2.n;
                 }
             }
+            const bool active = val[0];
             for (int32_t jb = 0; jb < nb2; jb += GCOLS) {
                 const int cols = (nb2 - jb) < GCOLS ? (nb2 - jb) : GCOLS;
-                const int ld = (cols + 31) & ~31;  // staged row length
-                const int jmax = ld >> 5;
-                const int rows_per_chunk = GSMEM / ld;
-                int32_t colpos[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = jj * 32 + lane;
-                    colpos[jj] = j < cols ? pos2[jb + j] : -1;
-                }
-                T t[GQPW][8];
-#pragma unroll
-                for (int u = 0; u < GQPW; ++u)
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) t[u][jj] = inf;
-                for (int32_t rc = 0; rc < nb1; rc += rows_per_chunk) {
-                    const int rows = (nb1 - rc) < rows_per_chunk ? (nb1 - rc) : rows_per_chunk;
-                    __syncthreads();
-                    // stage the chunk: 4 rows x 8 column groups of independent loads per lane
-                    for (int i0 = warp; i0 < rows; i0 += 32) {
-                        int64_t rb[4];
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr) {
-                            const int ii = i0 + 8 * rr;
-                            rb[rr] = ii < rows ? (int64_t)pos1[rc + ii] * ctx.N : -1;
-                        }
-                        T v[4][8];
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-                            for (int jj = 0; jj < 8; ++jj)
-                                v[rr][jj] = (rb[rr] >= 0 && colpos[jj] >= 0) ? ctx.D[rb[rr] + colpos[jj]] : inf;
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr) {
-                            const int ii = i0 + 8 * rr;
-                            if (ii < rows) {
-#pragma unroll
-                                for (int jj = 0; jj < 8; ++jj)
-                                    if (jj < jmax) S[ii * ld + jj * 32 + lane] = v[rr][jj];
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    for (int ib = 0; ib < rows; ib += 32) {
-                        T areg[GQPW];
-#pragma unroll
-                        for (int u = 0; u < GQPW; ++u)
-                            areg[u] = (val[u] && ib + lane < rows) ? ctx.apsp[a1off[u] + rc + ib + lane] : inf;
-                        const int iend = (rows - ib) < 32 ? (rows - ib) : 32;
-                        for (int ii = 0; ii < iend; ++ii) {
-                            T ai[GQPW];
-#pragma unroll
-                            for (int u = 0; u < GQPW; ++u) ai[u] = __shfl_sync(0xffffffffu, areg[u], ii);
-                            const T* srow = S + (ib + ii) * ld + lane;
-#pragma unroll
-                            for (int jj = 0; jj < 8; ++jj) {
-                                if (jj < jmax) {
-                                    const T sv = srow[jj * 32];
-#pragma unroll
-                                    for (int u = 0; u < GQPW; ++u) t[u][jj] = addmin(ai[u], sv, t[u][jj]);
-                                }
-                            }
-                        }
-                    }
-                }
-                // dist_C2(b2, v2) for this pass's columns
-#pragma unroll
-                for (int u = 0; u < GQPW; ++u)
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        if (jj < jmax) {
-                            const int j = jj * 32 + lane;
-                            const T c = (val[u] && j < cols) ? ctx.apsp[a2off[u] + jb + j] : inf;
-                            r[u] = tmin(r[u], t[u][jj] + c);
-                        }
-                    }
+                if (cols > 128)
+                    seg_pass<T, 2>(ctx, S, pos1, pos2, nb1, jb, cols, a1off, a2off, val, active, r, tid, lane, warp);
+                else
+                    seg_pass<T, 1>(ctx, S, pos1, pos2, nb1, jb, cols, a1off, a2off, val, active, r, tid, lane, warp);
             }
 #pragma unroll
             for (int u = 0; u < GQPW; ++u) {
