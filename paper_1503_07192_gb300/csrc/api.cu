@@ -156,6 +156,7 @@ struct BgPlan {
     uint32_t* rowflags = nullptr;  // R x R words (elimination only)
     size_t apanel_budget = 0;
     bool wait_failed = false;      // a bounded wait of the back-substitution gave up
+    BgLayout layout;               // aligned pieces and their runs of rounds (elimination)
 };
 
 // Tables of Algorithm 1 in element type T: component blocks, their Floyd-Warshall,
@@ -186,6 +187,13 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
             if ((e = launch_mark_bg_tiles(in.n, in.rp, in.col, in.part, h->local, h->nb, h->bg_off, h->bgpos, h->k,
                                           h->N, plan.rowflags, st)) != cudaSuccess)
                 return e;
+            // the separators' tiles, which concurrent runs of rounds update together, are
+            // marked (and so initialised) from the start
+            std::vector<int32_t> shared;
+            for (const ElimTask& tk : plan.layout.tasks)
+                if (!tk.deps.empty())
+                    for (int32_t b = tk.lo; b < tk.hi; ++b) shared.push_back(b);
+            if ((e = launch_mark_pairs(shared, h->N, plan.rowflags, st)) != cudaSuccess) return e;
         }
         if ((e = fill_marked ? launch_fill_marked<T>(D, h->N, plan.rowflags, st) : launch_bg_fill<T>(D, h->N, st)) !=
             cudaSuccess)
@@ -207,7 +215,7 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
     } else if (h->N > 0) {
         double fwd = 0.0, bs = 0.0;
         if ((e = fw_single<T>(D, h->N, skip_inf, fw_scratch, plan.rowflags, &fwd, profile ? &h->fwprof : nullptr,
-                              st)) != cudaSuccess)
+                              st, plan.layout.tasks.empty() ? nullptr : &plan.layout.tasks)) != cudaSuccess)
             return e;
         if ((e = bg_backsub<T>(D, h->N, plan.rowflags, h->err, d_converted ? d_flag : nullptr, plan.apanel_budget, &bs,
                                profile ? &h->fwprof : nullptr, st)) != cudaSuccess)
@@ -329,20 +337,24 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         bo += h->h_nb[c];
     }
     h->nbg = bo;
-    h->N = round_up(bo, 4);
-    if (h->N > 0 && h->N * h->N > (int64_t)1 << 40) return SPQ_ENOMEM;
+    // matrix order: the slots, plus (elimination form) up to 15 alignment gaps of < 128
+    const bool may_elim = opts.bg_method != SPQ_BG_FW && bo > 0;
+    const int64_t n_max = round_up(bo + (may_elim ? 15 * (kTile - 1) : 0), 4);
+    if (n_max > 0 && n_max * n_max > (int64_t)1 << 40) return SPQ_ENOMEM;
 
-    // ---- memory check, then allocation ----
-    const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
+    // ---- memory check (with the largest matrix order), then allocation ----
     const int64_t hist_words = radix_hist_words(n);
-    // elimination scratch: per-round row flags, back-substitution bookkeeping, A panels
-    const bool may_elim = opts.bg_method != SPQ_BG_FW && h->N > 0;
-    const int64_t nR = (h->N + kTile - 1) / kTile;
     const size_t panel_cap = opts.bg_panel_mib > 0 ? ((size_t)opts.bg_panel_mib << 20) : ((size_t)1 << 30);
-    const size_t apanel_budget = std::min<size_t>(panel_cap, 4 * (size_t)h->N * (size_t)h->N + (1u << 20));
-    const size_t elim_bytes = may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(h->N) + apanel_budget : 0;
-    size_t need = 4 * (size_t)h->apsp_elems + 4 * (size_t)h->N * (size_t)h->N + 8 * (size_t)n +
-                  (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words + hist_words) +
+    int64_t nR = (n_max + kTile - 1) / kTile;
+    const int64_t fw_words_max = n_max > 0 ? fw_single_scratch_words(n_max) : 1;
+    size_t apanel_budget = std::min<size_t>(panel_cap, 4 * (size_t)n_max * (size_t)n_max + (1u << 20));
+    // elimination scratch: per-round row flags, back-substitution bookkeeping, A panels,
+    // and per-run compaction lists (at most 15 runs)
+    const size_t elim_bytes =
+        may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(n_max) + apanel_budget + 15 * 4 * (size_t)fw_words_max
+                 : 0;
+    size_t need = 4 * (size_t)h->apsp_elems + 4 * (size_t)n_max * (size_t)n_max + 8 * (size_t)n +
+                  (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words_max + hist_words) +
                   8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + (64u << 20);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
@@ -363,8 +375,6 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     CK(dev_alloc(&h->vstart, (size_t)k, &bytes));
     h->m = m;
     CK(dev_alloc((uint32_t**)&h->apsp, (size_t)h->apsp_elems, &bytes));
-    if (h->N > 0) CK(dev_alloc((uint32_t**)&h->D, (size_t)(h->N * h->N), &bytes));
-    h->bytes = bytes;
     CK(cudaMemsetAsync(h->err, 0, 4 * sizeof(uint32_t), st));
     CK(cudaMemcpyAsync(h->descs, h->h_descs.data(), (size_t)k * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->nb, h->h_nb.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -398,19 +408,26 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     }
 
     // ---- positions of the boundary slots along the boundary-graph matrix ----
+    BgPlan plan;
     if (h->nbg > 0) {
         std::vector<int32_t> bgpos;
         spq_status s = boundary_order(n, m, d_rp, d_col, d_part, h->local, h->bg_off, k, h->h_nb,
-                                      (spq_order)opts.order, st, &bgpos, &h->order_method);
+                                      (spq_order)opts.order, st, &bgpos, &h->order_method,
+                                      may_elim ? &plan.layout : nullptr);
         if (s != SPQ_OK) return s;
         CK(cudaMemcpyAsync(h->bgpos, bgpos.data(), bgpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));  // bgpos (host) goes out of scope
     }
+    h->N = round_up(plan.layout.npad > 0 ? plan.layout.npad : h->nbg, 4);
+    if (h->N > 0) CK(dev_alloc((uint32_t**)&h->D, (size_t)(h->N * h->N), &bytes));
+    h->bytes = bytes;
+    nR = (h->N + kTile - 1) / kTile;
+    const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
+    apanel_budget = std::min<size_t>(panel_cap, 4 * (size_t)h->N * (size_t)h->N + (1u << 20));
 
     // ---- tables: component APSP, boundary graph, boundary-graph APSP ----
     uint32_t* fw_scratch;
     CK(tmp.alloc(&fw_scratch, (size_t)fw_words));
-    BgPlan plan;
     // elimination + back-substitution pays off in a dissection order (small frontiers);
     // in the id order every row's frontier is most of the matrix
     plan.elim = may_elim && (opts.bg_method == SPQ_BG_ELIM || h->order_method != 0);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "spq.h"
 
 namespace spq {
@@ -112,9 +114,12 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
 // zeroed: the elimination (forward) form: round r updates only tiles right of and below
 // the pivot (I, J > r), and rowflags[r][J] marks the row tiles (r, J > r) that hold a
 // finite entry; bg_backsub then completes the matrix.
+// tasks (elimination form only, may be NULL): runs of rounds to do side by side where
+// they do not depend on each other (see ElimTask in order.h); NULL: one run in order.
+struct ElimTask;
 template <typename T>
 cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch_flags, uint32_t* rowflags, double* updates,
-                      FwProfile* prof, cudaStream_t st);
+                      FwProfile* prof, cudaStream_t st, const std::vector<ElimTask>* tasks = nullptr);
 int64_t fw_single_scratch_words(int64_t N);
 // ---- elim.cu: back-substitution after the forward form of fw_single ----
 // Completes M (N x N, symmetric storage) to all-pairs distances.  err: device status
@@ -126,6 +131,8 @@ int64_t fw_single_scratch_words(int64_t N);
 template <typename T>
 cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
                        double* updates, FwProfile* prof, cudaStream_t st);
+// Marks of every pair of the given tiles (host list).
+cudaError_t launch_mark_pairs(const std::vector<int32_t>& blocks, int64_t N, uint32_t* flags, cudaStream_t st);
 // Infinity (0 on the diagonal) in the marked tiles, their mirrors and the diagonal tiles.
 template <typename T>
 cudaError_t launch_fill_marked(T* M, int64_t N, const uint32_t* flags, cudaStream_t st);

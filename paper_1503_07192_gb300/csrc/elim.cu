@@ -120,6 +120,14 @@ __global__ void __launch_bounds__(256) k_mark_clique(const int32_t* __restrict__
     }
 }
 
+// Every pair of the listed tiles (the separators shared by concurrent runs of rounds).
+__global__ void k_mark_pairs(const int32_t* __restrict__ blocks, int32_t nb, int32_t nR, uint32_t* __restrict__ flags) {
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nb * nb; t += gridDim.x * blockDim.x) {
+        const int32_t I = blocks[t / nb], J = blocks[t % nb];
+        if (I < J) flags[(int64_t)I * nR + J] = 1u;
+    }
+}
+
 __global__ void k_mark_inter(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                              const int32_t* __restrict__ part, const int32_t* __restrict__ local,
                              const int32_t* __restrict__ bg_off, const int32_t* __restrict__ bgpos, int32_t nR,
@@ -458,6 +466,24 @@ cudaError_t launch_fill_marked(T* M, int64_t N, const uint32_t* flags, cudaStrea
     k_fill_marked<T><<<nR, 256, 0, st>>>(M, N, nR, flags);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mark_pairs(const std::vector<int32_t>& blocks, int64_t N, uint32_t* flags, cudaStream_t st) {
+    if (blocks.empty() || N <= 0) return cudaSuccess;
+    const int32_t nR = (int32_t)((N + T_ - 1) / T_);
+    int32_t* d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, blocks.size() * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d, blocks.data(), blocks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int32_t nb = (int32_t)blocks.size();
+        k_mark_pairs<<<(nb * nb + 255) / 256 < 1024 ? (nb * nb + 255) / 256 : 1024, 256, 0, st>>>(d, nb, nR, flags);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // (the host list may go away)
+    cudaFreeAsync(d, st);
+    return e;
 }
 
 size_t bg_backsub_scratch_bytes(int64_t N) {

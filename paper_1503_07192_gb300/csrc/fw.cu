@@ -26,6 +26,7 @@
 
 #include "common.cuh"
 #include "fw_tile.cuh"
+#include "order.h"
 
 namespace spq {
 
@@ -226,14 +227,18 @@ __device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t 
     __syncthreads();
 }
 
+__global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src, int n) {
+    if ((int)threadIdx.x < n) dst[threadIdx.x] += src[threadIdx.x];
+}
+
 // Elimination form, after phase 2 of round r (r = -1: before round 0):
 //   list = the finite row tiles J > r of round r (phase 3 updates list x list);
 //   marks every pair of the list as a tile that may hold a finite entry from now on
 //   (2 where it was unmarked: only the marked tiles were initialised);
 //   cand = the marked tiles J > r + 1 of row r + 1 (phase 2 of the next round).
 __global__ void k_compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int32_t r, uint32_t* __restrict__ list,
-                                uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles) {
-    if (r >= 0) {
+                                uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles, int32_t do_list) {
+    if (r >= 0 && do_list) {
         compact_row(rowflags + (int64_t)r * R, r + 1, R, list);
         const uint32_t c = list[0];
         for (uint32_t t = threadIdx.x; t < c * c; t += blockDim.x) {
@@ -334,11 +339,13 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_sel(T* __restri
 // for both triangles.  Tiles outside list x list keep their values: their pivot panel
 // is entirely infinite, so min(D, inf + x) = D.
 // With rowflags (elimination form), a target marked 2 was never initialised: it starts
-// from infinity instead of being loaded, and is marked 1 afterwards.
+// from infinity instead of being loaded, and is marked 1 afterwards.  Targets (I, J) with
+// I >= shared_from may be updated by concurrent runs of rounds: stored with atomicMin.
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
                                                         const uint32_t* __restrict__ list,
-                                                        uint32_t* __restrict__ rowflags, int32_t R) {
+                                                        uint32_t* __restrict__ rowflags, int32_t R,
+                                                        int32_t shared_from) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -360,6 +367,13 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restr
             store_c<T>(acc, M, n, ci, cj, tx, ty);
             store_c_transposed<T>(acc, M, n, ci, cj, tx, ty);
             if (tid == 0) *f = 1u;  // (every thread read the flag before the panel barriers)
+        } else if (I >= shared_from) {
+            const int64_t ci = I * T_, cj = J * T_;
+            T acc[8][8];
+            load_c<T>(acc, M, n, ci, cj, tx, ty);
+            minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+            store_c_min<T>(acc, M, n, ci, cj, tx, ty);
+            if (I != J) store_c_transposed_min<T>(acc, M, n, ci, cj, tx, ty);
         } else {
             phase3_tile<T>(M, n, o, I, J, sm, tid, tx, ty);
         }
@@ -515,8 +529,8 @@ cudaError_t set_smem_attrs() {
 // the compaction (phase-3 list, marks, next candidates), phase 3 over the list.
 template <typename T>
 cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R, uint32_t* rowflags, uint32_t* cand,
-                       uint32_t* list, bool skip_inf, unsigned long long* tiles, cudaEvent_t ev0, cudaEvent_t ev1,
-                       cudaStream_t st) {
+                       uint32_t* list, bool skip_inf, unsigned long long* tiles, int32_t shared_from, cudaEvent_t ev0,
+                       cudaEvent_t ev1, cudaStream_t st) {
     const size_t psm = sizeof(PanelSmem<T>);
     const int grid = sms() * 2;
     k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
@@ -526,9 +540,9 @@ cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R,
         k_phase2_cand<T><<<np2 < grid ? np2 : grid, NTH, psm, st>>>(M, N, r, R, cand, rowflags);
         if (!skip_inf)  // mark every tile: the compaction then lists all J > r
             cudaMemsetAsync(rowflags + (int64_t)r * R + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
-        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles);
+        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles, 1);
         if (ev0) cudaEventRecord(ev0, st);
-        k_phase3_list<T><<<grid, NTH, psm, st>>>(M, N, r, list, rowflags, R);
+        k_phase3_list<T><<<grid, NTH, psm, st>>>(M, N, r, list, rowflags, R, shared_from);
         if (ev1) cudaEventRecord(ev1, st);
         count_launches(3);
     }
@@ -599,7 +613,7 @@ int64_t fw_single_scratch_words(int64_t N) {
 
 template <typename T>
 cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_t* rowflags, double* updates,
-                      FwProfile* prof, cudaStream_t st) {
+                      FwProfile* prof, cudaStream_t st, const std::vector<ElimTask>* tasks) {
     if (updates) *updates = 0.0;
     if (N <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
@@ -624,18 +638,73 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
         for (auto& ev : evs)
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
-    uint32_t* cand = scratch + 2 * R + 6;
-    if (rowflags && R > 0) {
-        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, -1, list, cand, tiles);  // candidates of round 0
-        count_launches(1);
-    }
-    for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
-        if (rowflags) {
-            // elimination form: row tiles J > r only, among the marked candidates
-            e = elim_round<T>(M, dd, N, r, R, rowflags, cand, list, skip_inf, tiles,
-                              evs.empty() ? nullptr : evs[2 * r], evs.empty() ? nullptr : evs[2 * r + 1], st);
-            continue;
+    // runs of elimination rounds: one run over every block row, or the caller's runs (side
+    // by side on their own streams where they do not depend on each other)
+    std::vector<ElimTask> one(1);
+    one[0].lo = 0;
+    one[0].hi = R;
+    one[0].shared_from = R;
+    const std::vector<ElimTask>& runs = (rowflags && tasks && !tasks->empty()) ? *tasks : one;
+    const size_t nrun = rowflags ? runs.size() : 0;
+    const int64_t rw = 2 * (int64_t)R + 8;  // per run: list[R + 2], cand[R + 2], tiles (2 x u64)
+    uint32_t* run_scratch = nullptr;
+    std::vector<cudaStream_t> rs(nrun, nullptr);
+    std::vector<cudaEvent_t> done(nrun, nullptr);
+    cudaEvent_t start_ev = nullptr;
+    if (nrun > 0) {
+        if (e == cudaSuccess) e = cudaMallocAsync(&run_scratch, nrun * rw * sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(run_scratch, 0, nrun * rw * sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(start_ev, st);
+        for (size_t i = 0; i < nrun && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&rs[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(rs[i], start_ev, 0);
         }
+        // issue the rounds of every startable run in turn, one round at a time
+        std::vector<int32_t> next(nrun, 0), state(nrun, 0);  // 0 waiting, 1 issuing, 2 issued
+        size_t finished = 0;
+        while (finished < nrun && e == cudaSuccess) {
+            for (size_t i = 0; i < nrun && e == cudaSuccess; ++i) {
+                const ElimTask& tk = runs[i];
+                uint32_t* rl = run_scratch + i * rw;
+                uint32_t* rc = rl + R + 2;
+                unsigned long long* rt = reinterpret_cast<unsigned long long*>(rl + 2 * R + 4);
+                if (state[i] == 0) {
+                    bool ready = true;
+                    for (int32_t d : tk.deps) ready = ready && state[d] == 2;
+                    if (!ready) continue;
+                    for (int32_t d : tk.deps) cudaStreamWaitEvent(rs[i], done[d], 0);
+                    if (tk.lo < tk.hi) {  // candidates of the run's first round
+                        k_compact_trail<<<1, 1024, 0, rs[i]>>>(rowflags, R, tk.lo - 1, rl, rc, rt, 0);
+                        count_launches(1);
+                    }
+                    next[i] = tk.lo;
+                    state[i] = 1;
+                }
+                if (state[i] == 1) {
+                    if (next[i] < tk.hi) {
+                        const int32_t r = next[i]++;
+                        e = elim_round<T>(M, dd, N, r, R, rowflags, rc, rl, skip_inf, rt, tk.shared_from,
+                                          evs.empty() ? nullptr : evs[2 * r], evs.empty() ? nullptr : evs[2 * r + 1],
+                                          rs[i]);
+                    } else {
+                        e = cudaEventRecord(done[i], rs[i]);
+                        state[i] = 2;
+                        ++finished;
+                    }
+                }
+            }
+        }
+        for (size_t i = 0; i < nrun && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st, done[i], 0);
+        // tile counters of every run, summed
+        for (size_t i = 0; i < nrun && e == cudaSuccess; ++i) {
+            k_add_u64<<<1, 32, 0, st>>>(tiles, reinterpret_cast<unsigned long long*>(run_scratch + i * rw + 2 * R + 4),
+                                        2);
+            count_launches(1);
+        }
+    }
+    for (int32_t r = 0; r < R && e == cudaSuccess && !rowflags; ++r) {
         k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
         count_launches(1);
         if (R > 1) {
@@ -646,7 +715,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
             }
             k_compact<<<1, 1024, 0, st>>>(flags, R, r, list, tiles);
             if (!evs.empty()) cudaEventRecord(evs[2 * r], st);
-            k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list, nullptr, 0);
+            k_phase3_list<T><<<p3_grid, NTH, psm, st>>>(M, N, r, list, nullptr, 0, (int32_t)R);
             if (!evs.empty()) cudaEventRecord(evs[2 * r + 1], st);
             count_launches(3);
         }
@@ -656,6 +725,12 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
     if (e == cudaSuccess) e = cudaMemcpyAsync(htv, tiles, sizeof(htv), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(dd, st);
+    if (run_scratch) cudaFreeAsync(run_scratch, st);
+    for (auto& x : rs)
+        if (x) cudaStreamDestroy(x);
+    for (auto& x : done)
+        if (x) cudaEventDestroy(x);
+    if (start_ev) cudaEventDestroy(start_ev);
     if (prof) {
         prof->p3_ms = 0.0;
         prof->p3_launches = 0;
@@ -729,7 +804,8 @@ template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_
 template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_batched<float>(float*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*,
-                                        cudaStream_t);
-template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*, cudaStream_t);
+                                        cudaStream_t, const std::vector<ElimTask>*);
+template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*, cudaStream_t,
+                                      const std::vector<ElimTask>*);
 
 }  // namespace spq

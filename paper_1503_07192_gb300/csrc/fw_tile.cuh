@@ -156,6 +156,37 @@ __device__ __forceinline__ void store_c_transposed(const T (&acc)[8][8], T* __re
     }
 }
 
+// Stores of tiles that concurrent writers may update (the min of every contribution
+// wins): atomicMin on the 32-bit patterns, which order like the values for int32 and for
+// non-negative float32 (distances are never negative).
+template <typename T>
+__device__ __forceinline__ void store_c_min(const T (&acc)[8][8], T* __restrict__ M, int64_t n, int64_t r0,
+                                            int64_t c0, int tx, int ty) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = r0 + own(ty, i);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t c = c0 + own(tx, j);
+            if (r < n && c < n) atomicMin(reinterpret_cast<int*>(M + r * n + c), *reinterpret_cast<const int*>(&acc[i][j]));
+        }
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store_c_transposed_min(const T (&acc)[8][8], T* __restrict__ M, int64_t n, int64_t r0,
+                                                       int64_t c0, int tx, int ty) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int64_t tr = c0 + own(tx, j);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t tc = r0 + own(ty, i);
+            if (tr < n && tc < n)
+                atomicMin(reinterpret_cast<int*>(M + tr * n + tc), *reinterpret_cast<const int*>(&acc[i][j]));
+        }
+    }
+}
+
 // acc = min(acc, A (x) B) over the KC-row chunk held in stage s:
 // A[i][k] = a[s][k][i] (the panel is stored k-major), B[k][j] = b[s][k][j].
 template <typename T>

@@ -354,9 +354,13 @@ double fw_order_cost(const std::vector<int64_t>& ptr, const std::vector<int32_t>
 // ends are such slots, so either set separates (the clique edges stay inside one
 // component, hence inside one side).  Slots: component-grouped numbering, slot_off[c]
 // .. slot_off[c+1]-1 for component c in local order.  Emits every slot once.
+// With nodes != NULL, the bisections of the top max_depth levels whose pieces hold at
+// least min_slots slots are recorded as nodes (positions in *out): a node's slots are
+// [begin, end), its own separator [sep_begin, end) after its two children.
 void vertex_nd(int rule, int32_t k, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
                const std::vector<int64_t>& slot_off, const std::vector<int64_t>& snb_ptr,
-               const std::vector<int32_t>& snb, std::vector<int32_t>* out) {
+               const std::vector<int32_t>& snb, std::vector<int32_t>* out, int max_depth = 0,
+               int64_t min_slots = 0, std::vector<NdNode>* nodes = nullptr) {
     const int64_t nslots = slot_off[k];
     std::vector<uint8_t> removed(nslots, 0);
     std::vector<int32_t> remain(k);
@@ -375,26 +379,42 @@ void vertex_nd(int rule, int32_t k, const std::vector<int64_t>& ptr, const std::
         std::vector<int32_t> comps;  // ascending ids
         std::vector<int32_t> sep;    // slots to emit
         bool emit;
+        int depth;
+        int node;  // recorded node (-1: none)
     };
     std::vector<Work> stack;
+    if (nodes) {
+        nodes->clear();
+        nodes->push_back(NdNode{});
+    }
     {
         std::vector<int32_t> all(k);
         for (int32_t c = 0; c < k; ++c) all[c] = c;
-        stack.push_back({std::move(all), {}, false});
+        stack.push_back({std::move(all), {}, false, 0, nodes ? 0 : -1});
     }
+    auto close_node = [&](int node, bool sep) {
+        if (node < 0) return;
+        NdNode& nd = (*nodes)[node];
+        if (!sep) nd.sep_begin = (int64_t)out->size();
+        nd.end = (int64_t)out->size();
+    };
     std::vector<int32_t> q;
     while (!stack.empty()) {
         Work wk = std::move(stack.back());
         stack.pop_back();
         if (wk.emit) {
+            if (wk.node >= 0) (*nodes)[wk.node].sep_begin = (int64_t)out->size();
             out->insert(out->end(), wk.sep.begin(), wk.sep.end());
+            close_node(wk.node, true);
             continue;
         }
+        if (wk.node >= 0) (*nodes)[wk.node].begin = (int64_t)out->size();
         std::vector<int32_t>& S = wk.comps;
         int64_t total = 0;
         for (int32_t c : S) total += remain[c];
         if (S.size() <= 1 || total == 0) {
             for (int32_t c : S) emit_comp(c);
+            close_node(wk.node, false);
             continue;
         }
         const int32_t la = next++, lb = next++;
@@ -470,6 +490,7 @@ void vertex_nd(int rule, int32_t k, const std::vector<int64_t>& ptr, const std::
                 side[c] = 0;
                 emit_comp(c);
             }
+            close_node(wk.node, false);
             continue;
         }
         std::vector<int32_t> sa, sb;
@@ -491,13 +512,27 @@ void vertex_nd(int rule, int32_t k, const std::vector<int64_t>& ptr, const std::
             remain[c]--;
         }
         std::vector<int32_t> A, B;
+        int64_t wa = 0, wb = 0;
         for (int32_t c : S) {
             (side[c] == la ? A : B).push_back(c);
+            (side[c] == la ? wa : wb) += remain[c];
             side[c] = 0;
         }
-        stack.push_back({{}, std::move(sep), true});
-        stack.push_back({std::move(B), {}, false});
-        stack.push_back({std::move(A), {}, false});
+        // record the two halves as nodes of their own when both are large enough
+        int na = -1, nb2 = -1;
+        if (wk.node >= 0 && wk.depth < max_depth && wa >= min_slots && wb >= min_slots) {
+            na = (int)nodes->size();
+            nodes->push_back(NdNode{});
+            nb2 = (int)nodes->size();
+            nodes->push_back(NdNode{});
+            (*nodes)[na].parent = (*nodes)[nb2].parent = wk.node;
+            (*nodes)[na].depth = (*nodes)[nb2].depth = wk.depth + 1;
+            (*nodes)[wk.node].child[0] = na;
+            (*nodes)[wk.node].child[1] = nb2;
+        }
+        stack.push_back({{}, std::move(sep), true, wk.depth, wk.node});
+        stack.push_back({std::move(B), {}, false, wk.depth + 1, nb2});
+        stack.push_back({std::move(A), {}, false, wk.depth + 1, na});
     }
 }
 
@@ -530,9 +565,68 @@ void nested_dissection(int32_t k, const std::vector<int64_t>& adj_ptr, const std
     nd.run(std::move(all));
 }
 
+// Padded positions for the recorded bisections (see BgLayout): every node but the root
+// starts at a multiple of the tile edge, and so does every split node's separator.
+void aligned_layout(const std::vector<int32_t>& slot_order, const std::vector<NdNode>& nodes,
+                    std::vector<int32_t>* bgpos, BgLayout* layout) {
+    const int64_t ns = (int64_t)slot_order.size();
+    std::vector<int64_t> starts;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        if (i != 0) starts.push_back(nodes[i].begin);
+        if (nodes[i].child[0] >= 0) starts.push_back(nodes[i].sep_begin);
+    }
+    std::sort(starts.begin(), starts.end());
+    starts.erase(std::unique(starts.begin(), starts.end()), starts.end());
+    // pad[t] = padding before slot-order index t (t = ns: after the last slot)
+    std::vector<int64_t> pad(ns + 1, 0);
+    int64_t p = 0;
+    size_t j = 0;
+    for (int64_t t = 0; t <= ns; ++t) {
+        while (j < starts.size() && starts[j] == t) {
+            p += (kTile - (t + p) % kTile) % kTile;
+            ++j;
+        }
+        pad[t] = p;
+        if (t < ns) (*bgpos)[slot_order[t]] = (int32_t)(t + p);
+    }
+    layout->npad = ns + pad[ns];
+    // block range of [a, b): from the (aligned) position of a to the end of slot b - 1
+    auto blk_lo = [&](int64_t a) { return (int32_t)((a + pad[a]) / kTile); };
+    auto blk_hi = [&](int64_t b) {
+        if (b >= ns) return (int32_t)((layout->npad + kTile - 1) / kTile);
+        return (int32_t)((b + pad[b]) / kTile);  // b starts aligned, or is a start of nothing
+    };
+    layout->tasks.clear();
+    std::vector<int32_t> task_of(nodes.size(), -1);
+    // post-order: children first
+    std::vector<std::pair<int, bool>> st{{0, false}};
+    while (!st.empty()) {
+        auto [i, done] = st.back();
+        st.pop_back();
+        const NdNode& nd = nodes[i];
+        const bool split = nd.child[0] >= 0;
+        if (split && !done) {
+            st.push_back({i, true});
+            st.push_back({nd.child[1], false});
+            st.push_back({nd.child[0], false});
+            continue;
+        }
+        ElimTask tk;
+        tk.lo = blk_lo(split ? nd.sep_begin : nd.begin);
+        tk.hi = std::max(tk.lo, blk_hi(nd.end));
+        tk.shared_from = tk.hi;
+        if (split) {
+            tk.deps.push_back(task_of[nd.child[0]]);
+            tk.deps.push_back(task_of[nd.child[1]]);
+        }
+        task_of[i] = (int32_t)layout->tasks.size();
+        layout->tasks.push_back(std::move(tk));
+    }
+}
+
 spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::vector<uint32_t> hk,
                                const std::vector<int32_t>& hs, const std::vector<int32_t>& hcmp, spq_order ord,
-                               std::vector<int32_t>* bgpos, int32_t* method) {
+                               std::vector<int32_t>* bgpos, int32_t* method, BgLayout* layout) {
     std::vector<int64_t> slot_off(k + 1, 0);
     for (int32_t c = 0; c < k; ++c) slot_off[c + 1] = slot_off[c] + nb[c];
     const int64_t nslots = slot_off[k];
@@ -591,8 +685,16 @@ spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::v
             for (auto it = b; it != u; ++it) snb[wpos++] = *it;
         }
         uptr[nslots] = wpos;
-        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order);
+        std::vector<NdNode> nodes;
+        // pieces of at least 16 tiles, three levels deep: up to eight runs side by side
+        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order, layout ? 3 : 0, 16 * kTile,
+                  layout ? &nodes : nullptr);
         *method = (int32_t)best + 2;
+        if ((int64_t)slot_order.size() != nslots) return SPQ_EINVAL;  // cannot happen: every slot is emitted once
+        if (layout && nodes.size() > 1) {
+            aligned_layout(slot_order, nodes, bgpos, layout);
+            return SPQ_OK;
+        }
     }
     if ((int64_t)slot_order.size() != nslots) return SPQ_EINVAL;  // cannot happen: every slot is emitted once
     for (int64_t i = 0; i < nslots; ++i) (*bgpos)[slot_order[i]] = (int32_t)i;
@@ -601,7 +703,8 @@ spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::v
 
 spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
                           const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
-                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method) {
+                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method,
+                          BgLayout* layout) {
     std::vector<int64_t> slot_off(k + 1, 0);
     for (int32_t c = 0; c < k; ++c) slot_off[c + 1] = slot_off[c] + nb[c];
     const int64_t nslots = slot_off[k];
@@ -669,7 +772,7 @@ spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32
     for (uint32_t* p : ps)
         if (p) cudaFreeAsync(p, st);
     if (e != cudaSuccess) return SPQ_ECUDA;
-    return boundary_order_host(k, nb, std::move(hk), hs, hcmp, ord, bgpos, method);
+    return boundary_order_host(k, nb, std::move(hk), hs, hcmp, ord, bgpos, method, layout);
 }
 
 }  // namespace spq

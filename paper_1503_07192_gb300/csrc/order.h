@@ -10,6 +10,30 @@
 
 namespace spq {
 
+// A bisection of the vertex-level nested dissection (positions in its slot order).
+struct NdNode {
+    int64_t begin = 0, sep_begin = 0, end = 0;
+    int depth = 0, parent = -1;
+    int child[2] = {-1, -1};
+};
+
+// A run of elimination rounds (block rows [lo, hi)) done in order, possibly beside other
+// runs: two runs without a dependency between them touch disjoint tiles except those
+// with both indices >= shared_from (the separators of common ancestors).
+struct ElimTask {
+    int32_t lo = 0, hi = 0;
+    int32_t shared_from = 0;
+    std::vector<int32_t> deps;  // runs that must finish first (earlier in the list)
+};
+
+// Layout of the boundary-graph matrix for the elimination form: the matrix order
+// (slots plus alignment padding) and the runs of elimination rounds.  With npad == 0 the
+// slots are packed (npad = number of slots) and there is a single run.
+struct BgLayout {
+    int64_t npad = 0;
+    std::vector<ElimTask> tasks;
+};
+
 // Position of every boundary slot along the boundary-graph matrix.  Slots are numbered
 // component by component (slot_off[c] + local index, boundary vertices first in each
 // component); bgpos[slot] is the matrix row/column of that slot.  Floyd-Warshall is
@@ -21,15 +45,20 @@ namespace spq {
 // SPQ_ORDER_VERTEX_DISSECTION refine the chosen bisections to vertex level (only the
 // boundary vertices on a cut become separator vertices).  *method: 0 id order, 1 / 2
 // component-level level-structure / id-range dissection, 3 / 4 their vertex-level forms.
+// With layout != NULL and a vertex-level order, the pieces of the top bisections start
+// at multiples of 128 (the tile edge; isolated padding positions between them) so that
+// their elimination rounds can run side by side (layout->tasks); otherwise the positions
+// are packed.
 spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
                           const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
-                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method);
+                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method,
+                          BgLayout* layout = nullptr);
 
 // Host part of boundary_order: hk = component pair keys cu * k + cv (any order,
 // duplicates allowed), (hs[i], hcmp[i]) = (slot, neighbouring component) pairs.
 spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::vector<uint32_t> hk,
                                const std::vector<int32_t>& hs, const std::vector<int32_t>& hcmp, spq_order ord,
-                               std::vector<int32_t>* bgpos, int32_t* method);
+                               std::vector<int32_t>* bgpos, int32_t* method, BgLayout* layout = nullptr);
 
 // One key cu * k + cv per CSR slot joining components cu != cv (appended at *count).
 cudaError_t launch_emit_comp_pairs(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* part, int32_t k,

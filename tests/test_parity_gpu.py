@@ -337,6 +337,22 @@ def test_elimination_matrix_equals_floyd_warshall(arith, order):
     h.free()
 
 
+@pytest.mark.parametrize("arith", ARITHS)
+def test_concurrent_elimination_runs_match_floyd_warshall(arith):
+    """2^17 points (about 16k boundary vertices): the dissection's top bisections are
+    aligned to tiles and their elimination rounds run on concurrent streams, sharing the
+    separators' tiles; the matrix must still equal Floyd-Warshall's entry for entry."""
+    w = gen.configs.delaunay_rcb(1 << 17, 7, 20000, seed=61)
+    ref = build(w.graph, w.part, w.k, arith=arith, bg=1)
+    B0 = ref.bg()
+    ref.free()
+    h = build(w.graph, w.part, w.k, arith=arith, bg=2)
+    assert h.profile()["bg_method"] == 2
+    assert np.array_equal(h.bg(), B0)
+    assert_pairs_exact(h, w.graph, w.pairs)
+    h.free()
+
+
 def test_elimination_profile_counts():
     m = spq()
     torch, dev = torch_dev()
@@ -353,7 +369,7 @@ def test_elimination_profile_counts():
         upd[bg] = st["bg_updates"]
         if bg == 2:
             nR = -(-st["n_bg"] // 128)
-            assert pf["bs_items"] == nR * (nR + 1) // 2
+            assert pf["bs_items"] >= nR * (nR + 1) // 2  # (alignment padding may add block rows)
             assert 0 < pf["bs_updates"] < st["bg_updates"] and pf["bs_ms"] > 0 and pf["bs_launches"] == 1
         h.free()
     assert upd[2] < upd[1]  # dissection order: fewer updates than Floyd-Warshall
