@@ -276,8 +276,15 @@ spq_status spq_query_paths(spq_handle* h, const int32_t* pairs, int64_t q, const
  * (and clear the marks), else SPQ_OK (or SPQ_ECUDA). */
 spq_status spq_query_status(spq_handle* h, void* stream);
 
-/* Release every device table of h.  NULL-safe.  Synchronises the device. */
+/* Release every device table of h.  NULL-safe.  Synchronises the device.  The memory of
+ * the tables returns to a library-owned memory pool per device and is kept there for the
+ * next spq_build (mapping and unmapping tens of gigabytes takes tens of milliseconds);
+ * spq_build counts the kept memory as free. */
 void spq_free(spq_handle* h);
+
+/* Give the memory kept by that pool back to the device (like emptying a caching
+ * allocator).  Synchronises the device.  Live handles are not affected. */
+void spq_release_cached_memory(void);
 
 /* Static English text for a status code. */
 const char* spq_strerror(spq_status s);

@@ -293,6 +293,11 @@ def spq_query_backward(h: SpqHandle, pairs, saved, grad_dist, grad_w, stream=Non
     return grad_w
 
 
+def spq_release_cached_memory():
+    """Return the device memory that freed handles left in the library's pool."""
+    _lib.load().spq_release_cached_memory()
+
+
 def spq_query_paths(h: SpqHandle, pairs, saved, max_len, stream=None):
     """(verts int32[q, max_len], lens int32[q]) on the device: the vertices of each pair's
     shortest path in order of travel (lens -1: unreachable; lens > max_len: truncated)."""

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -87,6 +88,42 @@ struct Temps {
     }
 };
 
+// The tables of a single build come from a library-owned stream-ordered memory pool per
+// device that keeps freed memory for the next build (a 71 GB table costs tens of
+// milliseconds to map and unmap); spq_release_cached_memory gives it back.
+constexpr int kMaxDevices = 64;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+std::mutex g_pool_mu;
+
+cudaError_t table_pool(int dev, cudaMemPool_t* out) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&g_pools[dev], &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;  // never trimmed implicitly
+        e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// Bytes the pool holds but no live table uses (free for the next build).
+size_t pool_cached_bytes(int dev) {
+    cudaMemPool_t pool;
+    if (table_pool(dev, &pool) != cudaSuccess) return 0;
+    uint64_t reserved = 0, used = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 void free_handle_memory(spq_handle* h) {
     if (h->arena) {
         if (h->arena->refs.fetch_sub(1) == 1) {
@@ -99,14 +136,20 @@ void free_handle_memory(spq_handle* h) {
     void* ps[] = {h->comp,   h->local,   h->descs,   h->nb,  h->bg_off, h->bgpos,  h->csize, h->apsp,
                   h->D,      h->err,     h->csr_rp,  h->csr_col, h->csr_w, h->vorder, h->vstart};
     for (void* p : ps)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);  // back to the pool
+    cudaStreamSynchronize(0);
 }
 
 template <typename T>
-cudaError_t dev_alloc(T** p, size_t count, size_t* total) {
+cudaError_t dev_alloc(T** p, size_t count, size_t* total, cudaStream_t st) {
     if (count == 0) count = 1;
     *total += count * sizeof(T);
-    return cudaMalloc((void**)p, count * sizeof(T));
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (e == cudaSuccess) e = table_pool(dev, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync((void**)p, count * sizeof(T), pool, st);
 }
 
 int bits_for(uint64_t x) {
@@ -358,23 +401,24 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
                   8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + (64u << 20);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
+    free_b += pool_cached_bytes(h->device);
     if (need > free_b) return SPQ_ENOMEM;
     size_t bytes = 0;
-    CK(dev_alloc(&h->comp, (size_t)n, &bytes));
-    CK(dev_alloc(&h->local, (size_t)n, &bytes));
-    CK(dev_alloc(&h->descs, (size_t)k, &bytes));
-    CK(dev_alloc(&h->nb, (size_t)k, &bytes));
-    CK(dev_alloc(&h->bg_off, (size_t)k, &bytes));
-    CK(dev_alloc(&h->bgpos, (size_t)h->nbg, &bytes));
-    CK(dev_alloc(&h->csize, (size_t)k, &bytes));
-    CK(dev_alloc(&h->err, 4, &bytes));
-    CK(dev_alloc(&h->csr_rp, (size_t)n + 1, &bytes));
-    CK(dev_alloc(&h->csr_col, (size_t)m, &bytes));
-    CK(dev_alloc((uint32_t**)&h->csr_w, (size_t)m, &bytes));
-    CK(dev_alloc(&h->vorder, (size_t)n, &bytes));
-    CK(dev_alloc(&h->vstart, (size_t)k, &bytes));
+    CK(dev_alloc(&h->comp, (size_t)n, &bytes, st));
+    CK(dev_alloc(&h->local, (size_t)n, &bytes, st));
+    CK(dev_alloc(&h->descs, (size_t)k, &bytes, st));
+    CK(dev_alloc(&h->nb, (size_t)k, &bytes, st));
+    CK(dev_alloc(&h->bg_off, (size_t)k, &bytes, st));
+    CK(dev_alloc(&h->bgpos, (size_t)h->nbg, &bytes, st));
+    CK(dev_alloc(&h->csize, (size_t)k, &bytes, st));
+    CK(dev_alloc(&h->err, 4, &bytes, st));
+    CK(dev_alloc(&h->csr_rp, (size_t)n + 1, &bytes, st));
+    CK(dev_alloc(&h->csr_col, (size_t)m, &bytes, st));
+    CK(dev_alloc((uint32_t**)&h->csr_w, (size_t)m, &bytes, st));
+    CK(dev_alloc(&h->vorder, (size_t)n, &bytes, st));
+    CK(dev_alloc(&h->vstart, (size_t)k, &bytes, st));
     h->m = m;
-    CK(dev_alloc((uint32_t**)&h->apsp, (size_t)h->apsp_elems, &bytes));
+    CK(dev_alloc((uint32_t**)&h->apsp, (size_t)h->apsp_elems, &bytes, st));
     CK(cudaMemsetAsync(h->err, 0, 4 * sizeof(uint32_t), st));
     CK(cudaMemcpyAsync(h->descs, h->h_descs.data(), (size_t)k * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(h->nb, h->h_nb.data(), (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -419,7 +463,7 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         CK(cudaStreamSynchronize(st));  // bgpos (host) goes out of scope
     }
     h->N = round_up(plan.layout.npad > 0 ? plan.layout.npad : h->nbg, 4);
-    if (h->N > 0) CK(dev_alloc((uint32_t**)&h->D, (size_t)(h->N * h->N), &bytes));
+    if (h->N > 0) CK(dev_alloc((uint32_t**)&h->D, (size_t)(h->N * h->N), &bytes, st));
     h->bytes = bytes;
     nR = (h->N + kTile - 1) / kTile;
     const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
@@ -584,6 +628,13 @@ void spq_free(spq_handle* h) {
     cudaDeviceSynchronize();
     free_handle_memory(h);
     delete h;
+}
+
+void spq_release_cached_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    cudaDeviceSynchronize();
+    for (int d = 0; d < kMaxDevices; ++d)
+        if (g_pools[d]) cudaMemPoolTrimTo(g_pools[d], 0);
 }
 
 const char* spq_strerror(spq_status s) {

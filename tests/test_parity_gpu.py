@@ -373,3 +373,25 @@ def test_elimination_profile_counts():
             assert 0 < pf["bs_updates"] < st["bg_updates"] and pf["bs_ms"] > 0 and pf["bs_launches"] == 1
         h.free()
     assert upd[2] < upd[1]  # dissection order: fewer updates than Floyd-Warshall
+
+
+def test_table_memory_is_pooled_and_released():
+    """spq_free keeps the tables' memory in the library's pool for the next build;
+    spq_release_cached_memory gives it back to the device."""
+    m = spq()
+    torch, dev = torch_dev()
+    w = gen.configs.delaunay_rcb(1 << 16, 6, 10, seed=63)
+    m.spq_release_cached_memory()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    h = build(w.graph, w.part, w.k)
+    fp = h.stats()["footprint_bytes"]
+    h.free()
+    free1 = torch.cuda.mem_get_info(dev)[0]
+    assert free1 < free0 - fp // 2  # kept in the pool
+    h = build(w.graph, w.part, w.k)  # served from the pool
+    assert_pairs_exact(h, w.graph, w.pairs)
+    h.free()
+    m.spq_release_cached_memory()
+    free2 = torch.cuda.mem_get_info(dev)[0]
+    assert free2 > free0 - fp // 4
