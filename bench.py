@@ -37,9 +37,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "queries/s + build min-plus Gop/s (1M-vertex planar), vs INT32/HBM roofline, 1xGB300"
-# DRAM bytes (read + write) per min-plus update of k_backsub, measured with ncu on the
-# delaunay1m build (None until measured)
-BACKSUB_BYTES_PER_UPDATE = None
+# DRAM bytes (read + write) per min-plus update of k_backsub: ncu on the delaunay1m build
+# (dram__bytes_read.sum 132,176,508,160 + dram__bytes_write.sum 73,134,564,096 for one
+# launch of 4.4525e12 updates; profiles/k_backsub_delaunay1m_dram.md)
+BACKSUB_BYTES_PER_UPDATE = (132176508160 + 73134564096) / 4.4525e12
 UNIT = "queries/s"
 
 
