@@ -398,7 +398,9 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
                     cp_async_wait<0>();
                 }
                 __syncthreads();
-                compute_chunk<T>(acc, sm, ch & 1, tx, ty);
+                // the last chunk's rows past |K(R)| are infinite padding: skipped
+                const int kend = ch + 1 < nch ? KC : ((kc - ch * KC) + 1) & ~1;
+                compute_chunk<T>(acc, sm, ch & 1, tx, ty, kend);
                 __syncthreads();
             }
             if constexpr (CONV)

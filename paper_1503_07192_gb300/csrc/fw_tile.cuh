@@ -189,10 +189,12 @@ __device__ __forceinline__ void store_c_transposed_min(const T (&acc)[8][8], T* 
 
 // acc = min(acc, A (x) B) over the KC-row chunk held in stage s:
 // A[i][k] = a[s][k][i] (the panel is stored k-major), B[k][j] = b[s][k][j].
+// (kend: the chunk's rows actually used, even, <= KC)
 template <typename T>
-__device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>& sm, int s, int tx, int ty) {
+__device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>& sm, int s, int tx, int ty,
+                                              int kend = KC) {
 #pragma unroll 1
-    for (int kk = 0; kk < KC; kk += 2) {
+    for (int kk = 0; kk < kend; kk += 2) {
         T a0[8], a1[8], b0[8], b1[8];
         {
             const int4 x0 = *reinterpret_cast<const int4*>(&sm.a[s][kk][ty * 4]);
@@ -226,9 +228,9 @@ __device__ __forceinline__ void compute_chunk(T (&acc)[8][8], const PanelSmem<T>
 // (sm_100 family), and a three-input min folds two k steps into each accumulator.
 template <>
 __device__ __forceinline__ void compute_chunk<float>(float (&acc)[8][8], const PanelSmem<float>& sm, int s, int tx,
-                                                     int ty) {
+                                                     int ty, int kend) {
 #pragma unroll kInnerUnroll
-    for (int kk = 0; kk < KC; kk += 2) {
+    for (int kk = 0; kk < kend; kk += 2) {
         const float4 x0 = *reinterpret_cast<const float4*>(&sm.a[s][kk][ty * 4]);
         const float4 x1 = *reinterpret_cast<const float4*>(&sm.a[s][kk][64 + ty * 4]);
         const float4 y0 = *reinterpret_cast<const float4*>(&sm.a[s][kk + 1][ty * 4]);
