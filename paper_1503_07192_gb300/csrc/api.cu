@@ -205,14 +205,12 @@ struct BgPlan {
 // Tables of Algorithm 1 in element type T: component blocks, their Floyd-Warshall,
 // boundary-graph assembly and its all-pairs distances.  Sets *inexact if a float32 table
 // holds a finite entry >= 2^24.
+// Component tables APSP(C) in element type T (queued on st; no host wait).
 template <typename T>
-cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact, bool skip_inf, bool profile,
-                         uint32_t* d_flag, uint32_t* fw_scratch, BgPlan& plan, int32_t max_n, bool* inexact,
-                         StageEvents& evs, cudaStream_t st) {
-    *inexact = false;
+cudaError_t build_comp_tables(spq_handle* h, const BuildInputs& in, int32_t max_n, StageEvents& evs,
+                              cudaStream_t st) {
     evs.mark(2, st);
     T* apsp = (T*)h->apsp;
-    T* D = (T*)h->D;
     cudaError_t e;
     if ((e = launch_fill_blocks<T>(apsp, h->descs, h->k, st)) != cudaSuccess) return e;
     if ((e = launch_scatter_intra<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->descs, apsp, st)) !=
@@ -220,6 +218,19 @@ cudaError_t build_tables(spq_handle* h, const BuildInputs& in, bool check_exact,
         return e;
     if ((e = fw_batched<T>(apsp, h->descs, h->h_descs.data(), h->k, max_n, st)) != cudaSuccess) return e;
     evs.mark(3, st);
+    return cudaSuccess;
+}
+
+// The boundary graph's table in element type T (after build_comp_tables<T>): assembly,
+// all-pairs distances, and (check_exact) the exactness check of every float32 table.
+template <typename T>
+cudaError_t build_bg_tables(spq_handle* h, const BuildInputs& in, bool check_exact, bool skip_inf, bool profile,
+                            uint32_t* d_flag, uint32_t* fw_scratch, BgPlan& plan, bool* inexact, StageEvents& evs,
+                            cudaStream_t st) {
+    *inexact = false;
+    T* apsp = (T*)h->apsp;
+    T* D = (T*)h->D;
+    cudaError_t e;
     const int64_t R = (h->N + kTile - 1) / kTile;
     // elimination form with skipping: only the marked tiles and the diagonal are read
     // before the back-substitution writes every tile, so only those are initialised
@@ -451,13 +462,27 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         }
     }
 
-    // ---- positions of the boundary slots along the boundary-graph matrix ----
+    // ---- the component tables go to the GPU while the host orders the boundary slots ----
     BgPlan plan;
+    BoundaryPairs bpairs;
+    if (h->nbg > 0) {
+        spq_status s = boundary_pairs(n, m, d_rp, d_col, d_part, h->local, h->bg_off, k, h->h_nb,
+                                      (spq_order)opts.order, st, &bpairs);
+        if (s != SPQ_OK) return s;
+    }
+    BuildInputs in{n, m, d_rp, d_col, d_w, d_part, f32w};
+    const bool skip = opts.skip_inf_tiles != 0;
+    const bool prof = opts.profile_kernels != 0;
+    // float32 arithmetic first (exact below 2^24, checked), int32 if asked or if the check fails
+    const bool first_f32 = f32w || opts.arith != SPQ_ARITH_I32;
+    if (first_f32)
+        CK(build_comp_tables<float>(h, in, max_n, evs, st));
+    else
+        CK(build_comp_tables<int32_t>(h, in, max_n, evs, st));
     if (h->nbg > 0) {
         std::vector<int32_t> bgpos;
-        spq_status s = boundary_order(n, m, d_rp, d_col, d_part, h->local, h->bg_off, k, h->h_nb,
-                                      (spq_order)opts.order, st, &bgpos, &h->order_method,
-                                      may_elim ? &plan.layout : nullptr);
+        spq_status s = boundary_order_from(k, h->h_nb, bpairs, (spq_order)opts.order, &bgpos, &h->order_method,
+                                           may_elim ? &plan.layout : nullptr);
         if (s != SPQ_OK) return s;
         CK(cudaMemcpyAsync(h->bgpos, bgpos.data(), bgpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));  // bgpos (host) goes out of scope
@@ -469,7 +494,7 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const int64_t fw_words = h->N > 0 ? fw_single_scratch_words(h->N) : 1;
     apanel_budget = std::min<size_t>(panel_cap, 4 * (size_t)h->N * (size_t)h->N + (1u << 20));
 
-    // ---- tables: component APSP, boundary graph, boundary-graph APSP ----
+    // ---- boundary graph, its all-pairs distances ----
     uint32_t* fw_scratch;
     CK(tmp.alloc(&fw_scratch, (size_t)fw_words));
     // elimination + back-substitution pays off in a dissection order (small frontiers);
@@ -480,28 +505,25 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         CK(tmp.alloc(&plan.rowflags, (size_t)(nR * nR)));
         plan.apanel_budget = apanel_budget;
     }
-    BuildInputs in{n, m, d_rp, d_col, d_w, d_part, f32w};
-    const bool skip = opts.skip_inf_tiles != 0;
-    const bool prof = opts.profile_kernels != 0;
     if (f32w) {
         h->f32store = true;
         h->arith = SPQ_ARITH_F32;
         bool inexact = false;
-        CK(build_tables<float>(h, in, false, skip, prof, d_flag, fw_scratch, plan, max_n, &inexact, evs, st));
+        CK(build_bg_tables<float>(h, in, false, skip, prof, d_flag, fw_scratch, plan, &inexact, evs, st));
         if (plan.wait_failed) return SPQ_ETIMEOUT;
     } else {
-        bool try_f32 = opts.arith != SPQ_ARITH_I32;
         bool inexact = false;
-        if (try_f32) {
+        if (first_f32) {
             h->f32store = true;
             h->arith = SPQ_ARITH_F32;
-            CK(build_tables<float>(h, in, true, skip, prof, d_flag, fw_scratch, plan, max_n, &inexact, evs, st));
+            CK(build_bg_tables<float>(h, in, true, skip, prof, d_flag, fw_scratch, plan, &inexact, evs, st));
             if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
         h->f32store = false;  // converted to int32 by the exactness check
-        if (!try_f32 || inexact) {
+        if (!first_f32 || inexact) {
             h->arith = SPQ_ARITH_I32;
-            CK(build_tables<int32_t>(h, in, false, skip, prof, d_flag, fw_scratch, plan, max_n, &inexact, evs, st));
+            if (inexact) CK(build_comp_tables<int32_t>(h, in, max_n, evs, st));
+            CK(build_bg_tables<int32_t>(h, in, false, skip, prof, d_flag, fw_scratch, plan, &inexact, evs, st));
             if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
     }

@@ -701,18 +701,15 @@ spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::v
     return SPQ_OK;
 }
 
-spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
+spq_status boundary_pairs(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
                           const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
-                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method,
-                          BgLayout* layout) {
-    std::vector<int64_t> slot_off(k + 1, 0);
-    for (int32_t c = 0; c < k; ++c) slot_off[c + 1] = slot_off[c] + nb[c];
-    const int64_t nslots = slot_off[k];
-    bgpos->resize(nslots);
-    for (int64_t i = 0; i < nslots; ++i) (*bgpos)[i] = (int32_t)i;
-    *method = 0;
+                          spq_order ord, cudaStream_t st, BoundaryPairs* out) {
+    int64_t nslots = 0;
+    for (int32_t c = 0; c < k; ++c) nslots += nb[c];
+    out->want = false;
     const bool want = ord != SPQ_ORDER_ID && k >= 4;
     if (!want || k > 65536 || m == 0 || nslots == 0) return SPQ_OK;
+    out->want = true;
     cudaError_t e = cudaSuccess;
     // ---- component adjacency (GPU emit, GPU radix sort, host unique) ----
     uint32_t *keys = nullptr, *vals = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr, *cnt = nullptr;
@@ -772,8 +769,25 @@ spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32
     for (uint32_t* p : ps)
         if (p) cudaFreeAsync(p, st);
     if (e != cudaSuccess) return SPQ_ECUDA;
-    return boundary_order_host(k, nb, std::move(hk), hs, hcmp, ord, bgpos, method, layout);
+    out->hk = std::move(hk);
+    out->hs = std::move(hs);
+    out->hcmp = std::move(hcmp);
+    return SPQ_OK;
 }
+
+spq_status boundary_order_from(int32_t k, const std::vector<int32_t>& nb, BoundaryPairs& bp, spq_order ord,
+                               std::vector<int32_t>* bgpos, int32_t* method, BgLayout* layout) {
+    int64_t nslots = 0;
+    for (int32_t c = 0; c < k; ++c) nslots += nb[c];
+    if (!bp.want) {
+        bgpos->resize(nslots);
+        for (int64_t i = 0; i < nslots; ++i) (*bgpos)[i] = (int32_t)i;
+        *method = 0;
+        return SPQ_OK;
+    }
+    return boundary_order_host(k, nb, std::move(bp.hk), bp.hs, bp.hcmp, ord, bgpos, method, layout);
+}
+
 
 }  // namespace spq
 

@@ -45,16 +45,25 @@ struct BgLayout {
 // SPQ_ORDER_VERTEX_DISSECTION refine the chosen bisections to vertex level (only the
 // boundary vertices on a cut become separator vertices).  *method: 0 id order, 1 / 2
 // component-level level-structure / id-range dissection, 3 / 4 their vertex-level forms.
-// With layout != NULL and a vertex-level order, the pieces of the top bisections start
-// at multiples of 128 (the tile edge; isolated padding positions between them) so that
-// their elimination rounds can run side by side (layout->tasks); otherwise the positions
-// are packed.
-spq_status boundary_order(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
+// The positions, in two steps so that the host part can overlap other GPU work: the
+// device gathers of the component adjacency and the slots' neighbouring components
+// (boundary_pairs, waits for the stream), then the ordering on the host
+// (boundary_order_from).  With layout != NULL and a vertex-level order, the pieces of the
+// top bisections start at multiples of 128 (the tile edge; isolated padding positions
+// between them) so that their elimination rounds can run side by side (layout->tasks);
+// otherwise the positions are packed.
+struct BoundaryPairs {
+    bool want = false;  // false: the packed component order (no dissection)
+    std::vector<uint32_t> hk;
+    std::vector<int32_t> hs, hcmp;
+};
+spq_status boundary_pairs(int32_t n, int64_t m, const int64_t* d_rp, const int32_t* d_col, const int32_t* d_part,
                           const int32_t* d_local, const int32_t* d_slot_off, int32_t k, const std::vector<int32_t>& nb,
-                          spq_order ord, cudaStream_t st, std::vector<int32_t>* bgpos, int32_t* method,
-                          BgLayout* layout = nullptr);
+                          spq_order ord, cudaStream_t st, BoundaryPairs* out);
+spq_status boundary_order_from(int32_t k, const std::vector<int32_t>& nb, BoundaryPairs& bp, spq_order ord,
+                               std::vector<int32_t>* bgpos, int32_t* method, BgLayout* layout);
 
-// Host part of boundary_order: hk = component pair keys cu * k + cv (any order,
+// The ordering itself (host): hk = component pair keys cu * k + cv (any order,
 // duplicates allowed), (hs[i], hcmp[i]) = (slot, neighbouring component) pairs.
 spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::vector<uint32_t> hk,
                                const std::vector<int32_t>& hs, const std::vector<int32_t>& hcmp, spq_order ord,
