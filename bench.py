@@ -336,8 +336,10 @@ def run_serve(args, rank, local_rank):
     t0 = time.time()
     ws = [gen.configs.grid1024diag()] + gen.configs.batch_instances(count=8, q_per=10)
     srv = QueryServer(device=local_rank, slots=4, max_pairs=1 << 20)
+    gopts = spq.spq_opts_default()
+    gopts.bg_method = args.bg
     for gid, w in enumerate(ws):
-        srv.add_graph(gid, w.graph.n, w.graph.row_ptr, w.graph.col, w.graph.w, w.part, w.k)
+        srv.add_graph(gid, w.graph.n, w.graph.row_ptr, w.graph.col, w.graph.w, w.part, w.k, opts=gopts)
     log(f"[rank {rank}] {len(ws)} graphs resident, {srv.resident_bytes / 1e9:.1f} GB ({time.time() - t0:.1f}s)")
     rng = np.random.default_rng(2026)
     sweep = []

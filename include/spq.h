@@ -229,6 +229,24 @@ spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* c
                           void* const* dist_out, void* stream);
 
 /*
+ * Many-to-many distances: dist_out[i * nt + j] = dist(sources[i], targets[j]) (int32 for
+ * SPQ_I32 graphs, SPQ_INF_I32 if unreachable; float for SPQ_F32).  Algorithm 2 split in
+ * its two stages: for a source v1 in C1 and a target component C2, t(b2) = min over b1 of
+ * dist_C1(v1, b1) + dist_BG(b1, b2) is computed once and reused for every target in C2
+ * (|B1||B2| updates per source and target component, plus |B2| per pair).
+ *   sources int32[ns], targets int32[nt]: vertex ids; duplicates allowed.
+ *   dist_out: ns x nt, row-major, caller-owned; all three buffers on the device
+ *     (asynchronous; out-of-range ids give -1 / NaN and a mark reported by
+ *     spq_query_status) or all on the host (synchronous; ns x nt <= 2^31; SPQ_EINVAL if an
+ *     id is out of range).
+ * Errors: SPQ_EINVAL for NULL buffers, mixed host/device buffers, ns or nt < 0 or above
+ * 2^31 - 1; SPQ_EUNSUPPORTED for handles of spq_build_many or a component with more than
+ * about 3,000 boundary vertices (the reuse buffer of a CTA).
+ */
+spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, int64_t ns, const int32_t* targets, int64_t nt,
+                            void* dist_out, void* stream);
+
+/*
  * Distances with the path witness, and their gradients (the differentiation pattern;
  * meant for SPQ_F32 graphs, also defined for SPQ_I32).  Device buffers only.
  *

@@ -241,6 +241,28 @@ def spq_query(h: SpqHandle, pairs, out=None, stream=None):
     return o_k
 
 
+def spq_query_matrix(h: SpqHandle, sources, targets, out=None, stream=None):
+    """dist(sources[i], targets[j]) as an [ns, nt] array (int32; float32 for float-weight
+    graphs), in the memory space of the inputs (CUDA tensors or numpy arrays)."""
+    lib = _lib.load()
+    s_p, s_k, s_dev = _ptr(sources, np.int32)
+    t_p, t_k, t_dev = _ptr(targets, np.int32)
+    if s_dev != t_dev:
+        raise ValueError("sources and targets must be in the same memory space")
+    ns, nt = int(s_k.reshape(-1).shape[0]), int(t_k.reshape(-1).shape[0])
+    odt = np.float32 if h.wt == SPQ_F32 else np.int32
+    if out is None:
+        if s_dev:
+            out = torch.empty((ns, nt), dtype=torch.float32 if h.wt == SPQ_F32 else torch.int32, device=s_k.device)
+        else:
+            out = np.empty((ns, nt), odt)
+    o_p, o_k, _ = _ptr(out, odt)
+    st = lib.spq_query_matrix(h.ptr, s_p, ns, t_p, nt, o_p, _stream(stream, s_dev))
+    if st:
+        raise SpqError(st, "spq_query_matrix")
+    return o_k
+
+
 def spq_query_noalloc(h: SpqHandle, pairs, out=None, stream=None):
     """spq_query for callers that cannot let the library allocate device memory: pairs
     (int32[q, 2], q <= SPQ_NOALLOC_MAX_PAIRS) and out must be CUDA tensors; the

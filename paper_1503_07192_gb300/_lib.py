@@ -44,6 +44,7 @@ SIGNATURES = {
     "spq_query_saved": (ctypes.c_int, [P, P, i64, P, P, P]),
     "spq_query_backward": (ctypes.c_int, [P, P, i64, P, P, P, P]),
     "spq_query_paths": (ctypes.c_int, [P, P, i64, P, ctypes.c_int32, P, P, P]),
+    "spq_query_matrix": (ctypes.c_int, [P, P, i64, P, i64, P, P]),
     "spq_free": (None, [P]),
     "spq_release_cached_memory": (None, []),
     "spq_strerror": (ctypes.c_char_p, [ctypes.c_int]),

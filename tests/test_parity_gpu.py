@@ -395,3 +395,23 @@ def test_table_memory_is_pooled_and_released():
     m.spq_release_cached_memory()
     free2 = torch.cuda.mem_get_info(dev)[0]
     assert free2 > free0 - fp // 4
+
+
+def test_shorter_opts_struct_is_accepted():
+    """A caller compiled against the earlier spq_opts (ending before bg_method) gets the
+    defaults for the newer fields; a struct_size shorter than that is rejected."""
+    m = spq()
+    torch, dev = torch_dev()
+    w = gen.configs.grid64(q=2000)
+    g = w.graph
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    o = m.spq_opts_default()
+    o.bg_method = 1  # must be ignored: outside the declared size
+    o.struct_size = m.SpqOpts.bg_method.offset
+    h = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+    assert h.profile()["bg_method"] == (2 if h.profile()["order_method"] != 0 else 1)
+    assert_pairs_exact(h, g, w.pairs)
+    h.free()
+    o.struct_size = m.SpqOpts.bg_method.offset - 4
+    with pytest.raises(m.SpqError):
+        m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
