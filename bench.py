@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="delaunay1m",
                    choices=["delaunay1m", "grid64", "delaunay65k", "delaunay262k", "grid1024diag", "batch512",
-                            "serve", "grad256k"])
+                            "serve", "grad256k", "matrix1m"])
     p.add_argument("--rates", default="500,2000,8000", help="serve: request arrival rates (1/s) to sweep")
     p.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals per rate")
     p.add_argument("--instances", type=int, default=512, help="batch512: number of instances")
@@ -387,6 +387,62 @@ def run_serve(args, rank, local_rank):
     return 0
 
 
+def run_matrix(args, rank, local_rank):
+    """Many-to-many distances on delaunay1m: 64 random sources against every vertex
+    (67M distances) with spq_query_matrix (Algorithm 2's first stage done once per source
+    and target component), against spq_query on the same pairs of four sources."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1503_07192_gb300 as spq
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    spq.build()
+    w = gen.configs.delaunay1m(q=10)
+    g = w.graph
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    h = spq.spq_build(g.n, T(g.row_ptr), T(g.col), T(g.w), T(w.part), w.k)
+    rng = np.random.default_rng(1240)
+    src = T(rng.integers(0, g.n, size=64).astype(np.int32))
+    tgt = T(np.arange(g.n, dtype=np.int32))
+    out = torch.empty((64, g.n), dtype=torch.int32, device=dev)
+    pairs = T(np.stack([np.repeat(src.cpu().numpy()[:4], g.n), np.tile(np.arange(g.n), 4)], 1).astype(np.int32))
+    pout = torch.empty(pairs.shape[0], dtype=torch.int32, device=dev)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    mat_ms = timed(lambda: spq.spq_query_matrix(h, src, tgt, out=out), args.steps)
+    pair_ms = timed(lambda: spq.spq_query(h, pairs, out=pout), args.steps)
+    spq.spq_query_status(h)
+    same = bool(torch.equal(out[:4].reshape(-1), pout))
+    line = {
+        "metric": "distances/s (64 sources x all vertices, delaunay1m)",
+        "value": 64 * g.n / (mat_ms * 1e-3), "unit": "distances/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mat_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "matrix1m", "sources": 64, "targets": g.n},
+        "pairwise_query_distances_per_s": pairs.shape[0] / (pair_ms * 1e-3),
+        "speedup_vs_pairwise": (64 * g.n / mat_ms) / (pairs.shape[0] / pair_ms),
+        "first_rows_identical_to_pairwise": same,
+    }
+    h.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_grad(args, rank, local_rank):
     """The differentiation pattern: Delaunay of 2^18 uniform points, float32 weights =
     length x lognormal(0, 0.25), recursive coordinate bisection into 256 components of
@@ -485,6 +541,8 @@ def main():
         return run_serve(args, rank, local_rank)
     if args.workload == "grad256k":
         return run_grad(args, rank, local_rank)
+    if args.workload == "matrix1m":
+        return run_matrix(args, rank, local_rank)
 
     import numpy as np
     import torch

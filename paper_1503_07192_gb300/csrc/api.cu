@@ -42,8 +42,15 @@ spq_status read_opts(const spq_opts* in, spq_opts* o) {
 }  // namespace spq
 
 namespace {
-
 thread_local int g_last_cuda = 0;
+}  // namespace
+
+namespace spq {
+void note_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+}  // namespace spq
+
+namespace {
+
 
 // Below this many pairs a query batch is answered in input order (no sort).
 constexpr int64_t kGroupedMinQueries = 4096;

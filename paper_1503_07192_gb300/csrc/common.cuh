@@ -49,6 +49,9 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // Process-wide count of this library's kernel launches (read by spq_kernel_launches).
 void count_launches(int n);
 
+// Record a CUDA error for spq_last_cuda_error (entry points outside api.cu).
+void note_cuda_error(cudaError_t e);
+
 // Validated copy of the caller's options (NULL: the defaults); accepts the shorter
 // earlier versions of the struct (struct_size).
 spq_status read_opts(const spq_opts* in, spq_opts* out);

@@ -7,9 +7,11 @@
 //   dist = min over b2 of t(b2) + dist_C2(b2, v2), and dist_C1(v1, v2) if C1 = C2,
 // so a (source, target component) pair costs |B1||B2| updates once plus |B2| per target
 // instead of |B1||B2| per pair.  Sources and targets are sorted by component; one CTA
-// takes a (source component, target component) pair: it gathers the block
-// dist_BG(B(C1), B(C2)) into shared memory, computes t for eight sources at a time (one per
-// warp), keeps them in shared memory, and reduces every target of C2 against them.
+// takes a target component and a group of eight sources: each warp computes t for its
+// source from the rows of dist_BG(B(C1), B(C2)) (read in place: the block of a source
+// component is shared by its sources through L2), the eight t rows stay in shared
+// memory, and every target of C2 is reduced against all of them, one target per lane, so
+// a target's row of APSP(C2) is read once per eight sources.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,7 +27,6 @@ namespace {
 constexpr int MTH = 256;           // 8 warps
 constexpr int MSRC = MTH / 32;     // sources per batch: one per warp
 constexpr int MCOLS = 256;         // block columns per pass (8 per lane)
-constexpr int MBLOCK = 16 * 1024;  // staged block elements (64 KB)
 
 template <typename T>
 __device__ __forceinline__ T tmin2(T a, T b) {
@@ -78,81 +79,64 @@ __device__ __forceinline__ void put(void* out, int64_t at, T v) {
         ((int32_t*)out)[at] = (int32_t)tmin2<int32_t>((int32_t)v, SPQ_INF_I32);
 }
 
+// Item (target run jr, group of MSRC consecutive sources in component order).
 template <typename T, bool OUT_F32>
-__global__ void __launch_bounds__(MTH, 1)
+__global__ void __launch_bounds__(MTH)
     k_query_matrix(const QueryCtx<T> ctx, uint32_t k, const int32_t* __restrict__ sid,
-                   const uint32_t* __restrict__ sval, const uint32_t* __restrict__ sstart,
-                   const uint32_t* __restrict__ skey, uint32_t nsrun, const int32_t* __restrict__ tid_,
+                   const uint32_t* __restrict__ sval, int64_t ns, const int32_t* __restrict__ tid_,
                    const uint32_t* __restrict__ tval, const uint32_t* __restrict__ tstart,
                    const uint32_t* __restrict__ tkey, uint32_t ntrun, int64_t nt, int32_t ldt,
                    void* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* S = reinterpret_cast<T*>(smem_raw);           // block chunk, MBLOCK elements
-    T* tb = S + MBLOCK;                               // t of the batch's sources: [MSRC][ldt]
+    T* tb = reinterpret_cast<T*>(smem_raw);  // t of the group's sources: [MSRC][ldt]
+    __shared__ int32_t srcv[MSRC];           // the group's source vertices (-1: out of range)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T inf = Inf<T>::value();
-    for (int64_t item = blockIdx.x; item < (int64_t)nsrun * ntrun; item += gridDim.x) {
-        const uint32_t ir = (uint32_t)(item / ntrun), jr = (uint32_t)(item % ntrun);
-        const uint32_t c1 = skey[ir], c2 = tkey[jr];
-        const uint32_t s0 = sstart[ir], s1 = sstart[ir + 1], w0 = tstart[jr], w1 = tstart[jr + 1];
-        if (c1 >= k || c2 >= k) {  // an id out of range: every pair of the item is invalid
-            for (uint32_t a = s0; a < s1; ++a)
-                for (uint32_t b = w0 + tid; b < w1; b += MTH) {
-                    const int64_t at = (int64_t)sval[a] * nt + tval[b];
-                    if (OUT_F32)
-                        ((float*)out)[at] = __int_as_float(0x7fc00000);
-                    else
-                        ((int32_t*)out)[at] = -1;
-                }
-            if (tid == 0) atomicOr(ctx.err, kErrPair);
-            continue;
+    const int64_t ngroups = (ns + MSRC - 1) / MSRC;
+    for (int64_t item = blockIdx.x; item < ngroups * ntrun; item += gridDim.x) {
+        const uint32_t jr = (uint32_t)(item % ntrun);
+        const int64_t sb = (item / ntrun) * MSRC;
+        const int nsrc = (int)((ns - sb) < MSRC ? (ns - sb) : MSRC);
+        const uint32_t c2 = tkey[jr];
+        const uint32_t w0 = tstart[jr], w1 = tstart[jr + 1];
+        // ---- stage 1: warp w computes t for source sb + w, reading its block rows of D
+        // (lanes over the columns B(C2), through the slot positions) ----
+        int32_t v1 = -1;
+        if (warp < nsrc) {
+            const int32_t v = sid[sval[sb + warp]];
+            v1 = (v >= 0 && v < ctx.n) ? v : -1;
         }
-        const MatDesc d1 = ctx.descs[c1], d2 = ctx.descs[c2];
-        const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];
-        const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
-        const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
-        for (uint32_t sb = s0; sb < s1; sb += MSRC) {
-            // ---- stage 1: t for this warp's source, over all columns, pass by pass ----
-            const uint32_t my = sb + warp;
-            const bool have = my < s1;
-            const int32_t v1 = have ? sid[sval[my]] : 0;
-            const int64_t a1 = d1.off + (int64_t)ctx.local[v1] * d1.n;
+        if (lane == 0) srcv[warp] = v1;
+        if (c2 < k && v1 >= 0) {
+            const uint32_t c1 = (uint32_t)ctx.comp[v1];
+            const MatDesc d1 = ctx.descs[c1];
+            const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];
+            const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
+            const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
+            const T* a1 = ctx.apsp + d1.off + (int64_t)ctx.local[v1] * d1.n;
             for (int32_t jb = 0; jb < nb2; jb += MCOLS) {
                 const int cols = (nb2 - jb) < MCOLS ? (nb2 - jb) : MCOLS;
-                const int ld = (cols + 31) & ~31;
-                const int jmax = ld >> 5;
-                const int rpc = MBLOCK / ld;
+                const int jmax = (cols + 31) >> 5;
                 int32_t colpos[8];
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     const int j = jj * 32 + lane;
-                    colpos[jj] = j < cols ? pos2[jb + j] : -1;
+                    colpos[jj] = j < cols ? pos2[jb + j] : 0;
                 }
                 T t[8];
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) t[jj] = inf;
-                for (int32_t rc = 0; rc < nb1; rc += rpc) {
-                    const int rows = (nb1 - rc) < rpc ? (nb1 - rc) : rpc;
-                    __syncthreads();
-                    for (int ii = warp; ii < rows; ii += MSRC) {
-                        const int64_t rb = (int64_t)pos1[rc + ii] * ctx.N;
+                for (int32_t ib = 0; ib < nb1; ib += 32) {
+                    const T areg = ib + lane < nb1 ? a1[ib + lane] : inf;
+                    const int32_t preg = ib + lane < nb1 ? pos1[ib + lane] : 0;
+                    const int iend = (nb1 - ib) < 32 ? (nb1 - ib) : 32;
+#pragma unroll 2
+                    for (int ii = 0; ii < iend; ++ii) {
+                        const T a = __shfl_sync(0xffffffffu, areg, ii);
+                        const T* drow = ctx.D + (int64_t)__shfl_sync(0xffffffffu, preg, ii) * ctx.N;
 #pragma unroll
                         for (int jj = 0; jj < 8; ++jj)
-                            if (jj < jmax) S[ii * ld + jj * 32 + lane] = colpos[jj] >= 0 ? ctx.D[rb + colpos[jj]] : inf;
-                    }
-                    __syncthreads();
-                    if (have) {
-                        for (int ib = 0; ib < rows; ib += 32) {
-                            const T areg = ib + lane < rows ? ctx.apsp[a1 + rc + ib + lane] : inf;
-                            const int iend = (rows - ib) < 32 ? (rows - ib) : 32;
-                            for (int ii = 0; ii < iend; ++ii) {
-                                const T a = __shfl_sync(0xffffffffu, areg, ii);
-                                const T* srow = S + (ib + ii) * ld + lane;
-#pragma unroll
-                                for (int jj = 0; jj < 8; ++jj)
-                                    if (jj < jmax) t[jj] = add_min(a, srow[jj * 32], t[jj]);
-                            }
-                        }
+                            if (jj < jmax && jj * 32 + lane < cols) t[jj] = add_min(a, drow[colpos[jj]], t[jj]);
                     }
                 }
 #pragma unroll
@@ -161,37 +145,68 @@ __global__ void __launch_bounds__(MTH, 1)
                     if (jj < jmax && j < cols) tb[warp * ldt + jb + j] = t[jj];
                 }
             }
-            __syncthreads();
-            // ---- stage 2: every target of C2 against the batch's t ----
-            const int nsrc = (int)((s1 - sb) < (uint32_t)MSRC ? (s1 - sb) : (uint32_t)MSRC);
-            for (uint32_t b = w0 + warp; b < w1; b += MSRC) {
-                const int32_t v2 = tid_[tval[b]];
-                const int32_t l2 = ctx.local[v2];
-                const int64_t a2 = d2.off + (int64_t)l2 * d2.n;
+        }
+        __syncthreads();
+        // ---- stage 2: one target per lane against the group's t (broadcast from shared
+        // memory), walking the target's row of APSP(C2) ----
+        if (c2 >= k) {  // targets out of range
+            for (uint32_t b = w0 + tid; b < w1; b += MTH)
+                for (int s = 0; s < nsrc; ++s) {
+                    const int64_t at = (int64_t)sval[sb + s] * nt + tval[b];
+                    if (OUT_F32)
+                        ((float*)out)[at] = __int_as_float(0x7fc00000);
+                    else
+                        ((int32_t*)out)[at] = -1;
+                }
+            if (tid == 0) atomicOr(ctx.err, kErrPair);
+        } else {
+            const MatDesc d2 = ctx.descs[c2];
+            const int32_t nb2 = ctx.nb[c2];
+            for (uint32_t b0 = w0 + (uint32_t)warp * 32; b0 < w1; b0 += MSRC * 32) {
+                const uint32_t b = b0 + lane;
+                const bool tv = b < w1;
+                const int32_t v2 = tv ? tid_[tval[b]] : 0;
+                const int32_t l2 = tv ? ctx.local[v2] : 0;
+                const T* a2 = ctx.apsp + d2.off + (int64_t)l2 * d2.n;
                 T acc[MSRC];
 #pragma unroll
                 for (int s = 0; s < MSRC; ++s) acc[s] = inf;
-                for (int32_t c = lane; c < nb2; c += 32) {
-                    const T x = ctx.apsp[a2 + c];
+#pragma unroll 4
+                for (int32_t c = 0; c < nb2; ++c) {
+                    const T x = tv ? a2[c] : inf;
 #pragma unroll
                     for (int s = 0; s < MSRC; ++s)
                         if (s < nsrc) acc[s] = add_min(x, tb[s * ldt + c], acc[s]);
                 }
+                if (tv) {
 #pragma unroll
-                for (int s = 0; s < MSRC; ++s) {
-                    if (s >= nsrc) break;
-                    T y = warp_min2(acc[s]);
-                    if (lane == 0) {
-                        const uint32_t pa = sval[sb + s];
-                        const int32_t v1s = sid[pa];
-                        if (c1 == c2) y = tmin2(y, ctx.apsp[d1.off + (int64_t)ctx.local[v1s] * d1.n + l2]);
+                    for (int s = 0; s < MSRC; ++s) {
+                        if (s >= nsrc) break;
+                        const int64_t at = (int64_t)sval[sb + s] * nt + tval[b];
+                        const int32_t v1s = srcv[s];
+                        if (v1s < 0) {
+                            if (OUT_F32)
+                                ((float*)out)[at] = __int_as_float(0x7fc00000);
+                            else
+                                ((int32_t*)out)[at] = -1;
+                            continue;
+                        }
+                        T y = acc[s];
+                        const uint32_t c1s = (uint32_t)ctx.comp[v1s];
+                        if (c1s == c2) {
+                            const MatDesc d1s = ctx.descs[c1s];
+                            y = tmin2(y, ctx.apsp[d1s.off + (int64_t)ctx.local[v1s] * d1s.n + l2]);
+                        }
                         if (v1s == v2) y = T(0);
-                        put<T, OUT_F32>(out, (int64_t)pa * nt + tval[b], y);
+                        put<T, OUT_F32>(out, at, y);
                     }
                 }
             }
-            __syncthreads();  // tb is rewritten by the next batch
+            if (tid == 0)
+                for (int s = 0; s < nsrc; ++s)
+                    if (srcv[s] < 0) atomicOr(ctx.err, kErrPair);
         }
+        __syncthreads();  // tb and srcv are rewritten by the next item
     }
 }
 
@@ -271,8 +286,8 @@ extern "C" spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, in
     int32_t nbmax = 0;
     for (int32_t c = 0; c < k; ++c) nbmax = std::max(nbmax, h->h_nb[c]);
     const int32_t ldt = ((nbmax > 0 ? nbmax : 1) + 31) & ~31;
-    const size_t smem = (size_t)(MBLOCK + MSRC * ldt) * 4;
-    if (smem > 227 * 1024) return SPQ_EUNSUPPORTED;  // a component with more than ~3,000 boundary vertices
+    const size_t smem = (size_t)(MSRC * ldt) * 4;
+    if (smem > 200 * 1024) return SPQ_EUNSUPPORTED;  // a component with more than ~6,000 boundary vertices
     std::vector<void*> tmp;
     auto alloc = [&](void** p, size_t bytes) {
         cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 4, st);
@@ -283,6 +298,10 @@ extern "C" spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, in
         for (void* p : tmp) cudaFreeAsync(p, st);
         return s;
     };
+    auto fail = [&](cudaError_t err) {
+        note_cuda_error(err);
+        return finish(SPQ_ECUDA);
+    };
     const int32_t *d_s = sources, *d_t = targets;
     void* d_out = dist_out;
     cudaError_t e = cudaSuccess;
@@ -290,7 +309,7 @@ extern "C" spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, in
         void *p1, *p2, *p3;
         if ((e = alloc(&p1, (size_t)ns * 4)) != cudaSuccess || (e = alloc(&p2, (size_t)nt * 4)) != cudaSuccess ||
             (e = alloc(&p3, (size_t)(ns * nt) * 4)) != cudaSuccess)
-            return finish(SPQ_ECUDA);
+            return fail(e);
         cudaMemcpyAsync(p1, sources, (size_t)ns * 4, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(p2, targets, (size_t)nt * 4, cudaMemcpyHostToDevice, st);
         d_s = (const int32_t*)p1;
@@ -300,42 +319,42 @@ extern "C" spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, in
     void *bs, *bt;
     if ((e = alloc(&bs, (size_t)runs_words(ns) * 4)) != cudaSuccess ||
         (e = alloc(&bt, (size_t)runs_words(nt) * 4)) != cudaSuccess)
-        return finish(SPQ_ECUDA);
+        return fail(e);
     uint32_t *sval, *sstart, *skey, *tval, *tstart, *tkey, nsrun = 0, ntrun = 0;
     if ((e = runs_by_component(d_s, ns, h->n, h->comp, (uint32_t)k, (uint32_t*)bs, &sval, &sstart, &skey, &nsrun, st)) !=
             cudaSuccess ||
         (e = runs_by_component(d_t, nt, h->n, h->comp, (uint32_t)k, (uint32_t*)bt, &tval, &tstart, &tkey, &ntrun, st)) !=
             cudaSuccess)
-        return finish(SPQ_ECUDA);
-    const int64_t items = (int64_t)nsrun * ntrun;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)msms() * 8);
+        return fail(e);
+    const int64_t items = ((ns + MSRC - 1) / MSRC) * (int64_t)ntrun;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)msms() * 16);
+    (void)nsrun;
+    (void)sstart;
+    (void)skey;
     if (f32store) {
         auto kern = out_f32 ? k_query_matrix<float, true> : k_query_matrix<float, false>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return finish(SPQ_ECUDA);
-        kern<<<grid, MTH, smem, st>>>(cf, (uint32_t)k, d_s, sval, sstart, skey, nsrun, d_t, tval, tstart, tkey, ntrun, nt,
-                                      ldt, d_out);
+            return fail(e);
+        kern<<<grid, MTH, smem, st>>>(cf, (uint32_t)k, d_s, sval, ns, d_t, tval, tstart, tkey, ntrun, nt, ldt, d_out);
     } else {
         auto kern = out_f32 ? k_query_matrix<int32_t, true> : k_query_matrix<int32_t, false>;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return finish(SPQ_ECUDA);
-        kern<<<grid, MTH, smem, st>>>(ci, (uint32_t)k, d_s, sval, sstart, skey, nsrun, d_t, tval, tstart, tkey, ntrun, nt,
-                                      ldt, d_out);
+            return fail(e);
+        kern<<<grid, MTH, smem, st>>>(ci, (uint32_t)k, d_s, sval, ns, d_t, tval, tstart, tkey, ntrun, nt, ldt, d_out);
     }
     count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return finish(SPQ_ECUDA);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     if (!ds) {
         if ((e = cudaMemcpyAsync(dist_out, d_out, (size_t)(ns * nt) * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return finish(SPQ_ECUDA);
+            return fail(e);
         uint32_t f = 0;
         cudaMemcpyAsync(&f, h->err, sizeof(f), cudaMemcpyDeviceToHost, st);
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return finish(SPQ_ECUDA);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
         if (f & kErrPair) {
             cudaMemsetAsync(h->err, 0, sizeof(uint32_t), st);
             cudaStreamSynchronize(st);
             return finish(SPQ_EINVAL);
         }
     }
-    (void)e;
     return finish(SPQ_OK);
 }
