@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--arith", type=int, default=0, help="spq_arith of the build (0 auto, 1 int32, 2 float32)")
     p.add_argument("--bg", type=int, default=0, help="spq_bg_method of the build (0 auto, 1 FW, 2 elimination)")
+    p.add_argument("--server", choices=["native", "python"], default="native",
+                   help="serve: the library's scheduler thread (spq_server_*) or the Python one")
     return p.parse_args()
 
 
@@ -328,14 +330,16 @@ def run_serve(args, rank, local_rank):
 
     import gen
     import paper_1503_07192_gb300 as spq
-    from paper_1503_07192_gb300.serve import QueryServer
+    from paper_1503_07192_gb300.serve import NativeQueryServer, QueryServer
 
     torch.cuda.set_device(local_rank)
     spq.build()
-    sys.setswitchinterval(1e-4)  # the scheduler thread shares the interpreter with the producer
+    native = args.server == "native"
+    if not native:
+        sys.setswitchinterval(1e-4)  # the scheduler thread shares the interpreter with the producer
     t0 = time.time()
     ws = [gen.configs.grid1024diag()] + gen.configs.batch_instances(count=8, q_per=10)
-    srv = QueryServer(device=local_rank, slots=4, max_pairs=1 << 20)
+    srv = (NativeQueryServer if native else QueryServer)(device=local_rank, slots=4, max_pairs=1 << 20)
     gopts = spq.spq_opts_default()
     gopts.bg_method = args.bg
     for gid, w in enumerate(ws):
@@ -353,17 +357,25 @@ def run_serve(args, rank, local_rank):
         # warm-up: one request per graph
         for gid in range(len(ws)):
             srv.query(gid, reqs[0][1][:1] % ws[gid].graph.n)
-        srv.completed.clear()
+        if native:
+            srv.latency_stats(reset=True)
+        else:
+            srv.completed.clear()
         start = time.perf_counter() + 0.05
         t_arr = start + np.cumsum(gaps)
         futs = []
-        for (gid, p), ta in zip(reqs, t_arr):
+        lag = np.zeros(n_req)
+        for i, ((gid, p), ta) in enumerate(zip(reqs, t_arr)):
             # sleep until just before the arrival (a Python spin would hold the
-            # interpreter lock the scheduler thread needs), then submit
+            # interpreter lock the Python scheduler thread needs), then submit
             dt = ta - time.perf_counter()
             if dt > 2e-4:
                 time.sleep(dt - 1e-4)
-            futs.append(srv.submit(gid, p, t_arrival=float(ta)))
+            if native:  # (latency counted from submission: the lag behind the arrival is reported)
+                lag[i] = max(0.0, time.perf_counter() - ta)
+                futs.append(srv.submit(gid, p))
+            else:
+                futs.append(srv.submit(gid, p, t_arrival=float(ta)))
         outs = [f.result(timeout=600) for f in futs]
         t_end = time.perf_counter()
         st = srv.latency_stats()
@@ -373,7 +385,11 @@ def run_serve(args, rank, local_rank):
         sweep.append({"rate_req_s": rate, "requests": n_req, "pairs": pairs,
                       "offered_pairs_s": pairs / (t_arr[-1] - start + 1e-9),
                       "achieved_pairs_s": pairs / (t_end - start), "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                      "mean_ms": st["mean_ms"], "same_alone_and_in_mix": bool(same)})
+                      "same_alone_and_in_mix": bool(same)})
+        if "mean_ms" in st:
+            sweep[-1]["mean_ms"] = st["mean_ms"]
+        if native:
+            sweep[-1]["submit_lag_p99_ms"] = float(np.percentile(lag, 99) * 1e3)
         log(f"[rank {rank}] rate {rate}: {sweep[-1]}")
     srv.close()
     best = sweep[-1]
@@ -381,7 +397,7 @@ def run_serve(args, rank, local_rank):
             "warmup": 1, "ms_per_step": args.duration * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve", "graphs": ["grid1024diag"] + [f"batch{i}" for i in range(8)],
-                       "request_pairs": "U{1..4096}", "arrivals": "Poisson", "slots": 4},
+                       "request_pairs": "U{1..4096}", "arrivals": "Poisson", "slots": 4, "server": args.server},
             "sweep": sweep}
     print(json.dumps(line), flush=True)
     return 0

@@ -289,6 +289,44 @@ spq_status spq_query_backward(spq_handle* h, const int32_t* pairs, int64_t q, co
 spq_status spq_query_paths(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved, int32_t max_len,
                            int32_t* verts, int32_t* lens, void* stream);
 
+/*
+ * Native continuous-batching server (the serving pattern): a scheduler thread inside the
+ * library keeps up to `slots` query launches in flight, each on its own CUDA stream with
+ * pinned staging and preallocated device buffers (no allocation per request).  A free
+ * slot takes the oldest waiting request and every other waiting request for the same
+ * graph, up to max_pairs pairs in all, and answers them with one launch; requests that
+ * arrive meanwhile join the next free slot.
+ *
+ * spq_server_create: device, slots in [1, 64], max_pairs in [1, 2^28] (the largest
+ *   fused launch; also the largest request), memory_budget in bytes for the tables of the
+ *   admitted graphs (0: 90% of the free device memory).
+ * spq_server_add_graph: admits a built handle under the id gid if its footprint fits the
+ *   budget (SPQ_ENOMEM otherwise, SPQ_EINVAL for a used id).  The caller keeps owning h
+ *   and frees it only after spq_server_remove_graph or spq_server_destroy.
+ * spq_server_remove_graph: waits until no queued or running request uses gid.
+ * spq_server_submit: copies the q pairs (host int32[q][2], ids checked: SPQ_EINVAL) and
+ *   queues them; the distances go to out (host, q x 4 bytes: int32, or float for SPQ_F32
+ *   graphs), which must stay valid until the request completes; *ticket identifies it.
+ *   Thread-safe.  SPQ_ENOMEM if q > max_pairs.
+ * spq_server_poll: 1 done (the ticket is then released), 0 pending, -1 unknown ticket or
+ *   a failed launch.  spq_server_wait: blocks until done (SPQ_OK, releasing the ticket),
+ *   SPQ_ETIMEOUT after timeout_s seconds, SPQ_ECUDA for a failed launch.
+ * spq_server_stats: p50 / p99 latency (ms, submission to completion on the host) of the
+ *   requests completed so far, their number and pairs; reset != 0 starts a new window.
+ * spq_server_destroy: answers what is queued, stops the scheduler, frees the server's
+ *   buffers (not the graphs' handles).
+ */
+typedef struct spq_server spq_server;
+spq_status spq_server_create(int device, int32_t slots, int64_t max_pairs, size_t memory_budget, spq_server** out);
+spq_status spq_server_add_graph(spq_server* s, int32_t gid, spq_handle* h);
+spq_status spq_server_remove_graph(spq_server* s, int32_t gid);
+spq_status spq_server_submit(spq_server* s, int32_t gid, const int32_t* pairs, int64_t q, void* out, int64_t* ticket);
+int32_t spq_server_poll(spq_server* s, int64_t ticket);
+spq_status spq_server_wait(spq_server* s, int64_t ticket, double timeout_s);
+spq_status spq_server_stats(spq_server* s, double* p50_ms, double* p99_ms, int64_t* requests, int64_t* pairs,
+                            int32_t reset);
+void spq_server_destroy(spq_server* s);
+
 /* Synchronise `stream`, return SPQ_EINVAL if any spq_query on h since the last call
  * met an out-of-range pair, or SPQ_ETIMEOUT if a gradient walk did not reach its target
  * (and clear the marks), else SPQ_OK (or SPQ_ECUDA). */

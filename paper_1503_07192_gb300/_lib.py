@@ -45,6 +45,15 @@ SIGNATURES = {
     "spq_query_backward": (ctypes.c_int, [P, P, i64, P, P, P, P]),
     "spq_query_paths": (ctypes.c_int, [P, P, i64, P, ctypes.c_int32, P, P, P]),
     "spq_query_matrix": (ctypes.c_int, [P, P, i64, P, i64, P, P]),
+    "spq_server_create": (ctypes.c_int, [ctypes.c_int, i32, i64, ctypes.c_size_t, ctypes.POINTER(P)]),
+    "spq_server_add_graph": (ctypes.c_int, [P, i32, P]),
+    "spq_server_remove_graph": (ctypes.c_int, [P, i32]),
+    "spq_server_submit": (ctypes.c_int, [P, i32, P, i64, P, ctypes.POINTER(i64)]),
+    "spq_server_poll": (i32, [P, i64]),
+    "spq_server_wait": (ctypes.c_int, [P, i64, ctypes.c_double]),
+    "spq_server_stats": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(i64), ctypes.POINTER(i64), i32]),
+    "spq_server_destroy": (None, [P]),
     "spq_free": (None, [P]),
     "spq_release_cached_memory": (None, []),
     "spq_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(QTH) k_query(const QueryCtx<T> ctx, const int2
     const T inf = Inf<T>::value();
     for (int64_t qi = wg; qi < q; qi += nw) {
         const int2 pr = pairs[qi];
-        const int32_t v = pr.x, w = pr.y;
+        int32_t v = pr.x, w = pr.y;
         if (v < 0 || v >= ctx.n || w < 0 || w >= ctx.n) {
             if (lane == 0) {
                 if (MODE == kOutF32)
@@ -69,7 +69,14 @@ __global__ void __launch_bounds__(QTH) k_query(const QueryCtx<T> ctx, const int2
             }
             continue;
         }
-        const int32_t c1 = ctx.comp[v], c2 = ctx.comp[w];
+        int32_t c1 = ctx.comp[v], c2 = ctx.comp[w];
+        if (c1 > c2) {  // answered from the lower-numbered component's side, as the grouped form does,
+            const int32_t tv = v, tc = c1;  // so that float sums round the same in both forms
+            v = w;
+            w = tv;
+            c1 = c2;
+            c2 = tc;
+        }
         const int32_t l1 = ctx.local[v], l2 = ctx.local[w];
         const MatDesc d1 = ctx.descs[c1], d2 = ctx.descs[c2];
         const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];

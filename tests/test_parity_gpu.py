@@ -283,6 +283,26 @@ def test_grouped_and_input_order_queries_agree():
     hu.free()
 
 
+def test_grouped_and_input_order_queries_agree_float_weights():
+    """With float weights too both forms answer a pair from its lower-numbered
+    component's side, so their sums round alike: bit-identical answers, and the same
+    answer for a pair of two components given in either orientation."""
+    g = gen.delaunay(8000, seed=23, weight="f32_lognormal", scale=float(np.sqrt(8000)))
+    part, k = gen.rcb(g.xy, 3)
+    rng = np.random.default_rng(23)
+    pairs = rng.integers(0, g.n, size=(30000, 2)).astype(np.int32)
+    pairs = np.concatenate([pairs, pairs[:, ::-1]])
+    hg = build(g, part, k, query_grouped=1)
+    hu = build(g, part, k, query_grouped=0)
+    a = query(hg, pairs)
+    b = query(hu, pairs)
+    assert a.dtype == np.float32 and np.array_equal(a, b)
+    diff = part[pairs[:30000, 0]] != part[pairs[:30000, 1]]  # (same-component pairs keep their own order)
+    assert np.array_equal(a[:30000][diff], a[30000:][diff])
+    hg.free()
+    hu.free()
+
+
 def test_grouped_queries_mark_invalid_pairs():
     m = spq()
     w = gen.configs.grid_blocks_workload(32, 32, 8, 8, 50, 10000, seed=19)
