@@ -9,12 +9,20 @@
 // Floyd-Warshall of all instances round by round in the same launches (each instance
 // with its own list of tiles with a finite pivot panel).  The per-instance work left is
 // a handful of O(n + m) kernels (edge scatter, boundary-graph assembly).
+//
+// Instances with a large boundary graph take the elimination form instead, which needs
+// a fraction of the Floyd-Warshall updates there, batched the same way: the forward
+// rounds (restricted to the trailing tiles, in a vertex nested-dissection order) of all
+// of them in the same launches, then one persistent back-substitution over all their
+// tiles, their rows interleaved so that their dependency chains overlap.  Both sets of
+// instances are computed side by side on two streams.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -28,6 +36,11 @@ using namespace spq;
 namespace {
 
 thread_local int g_batch_cuda_error = 0;
+
+// Boundary-graph order from which an instance of a batch takes the elimination form by
+// default: below it the batched Floyd-Warshall rounds cost less than the latency of the
+// elimination's own rounds and back-substitution.
+constexpr int64_t kBatchElimMin = 4096;
 
 spq_status batch_cuda_fail(cudaError_t e) {
     g_batch_cuda_error = (int)e;
@@ -107,6 +120,7 @@ struct Inst {
     int64_t vbase = 0, kbase = 0, mbase = 0, slotbase = 0;  // offsets in the batch-wide arrays
     int64_t apsp_off = 0, apsp_elems = 0, d_off = 0, N = 0, nbg = 0;
     int32_t max_ld = 0;
+    bool elim = false;  // boundary graph by elimination + back-substitution
     std::vector<int32_t> csize, nb, bgoff;
     std::vector<MatDesc> descs;  // relative to the instance's own APSP base
 };
@@ -125,13 +139,25 @@ struct BatchPtrs {
     int64_t table_elems = 0;
 };
 
+// The instances whose boundary graph takes the elimination form: their matrices'
+// descriptors (device), the forward rounds' scratch, the A-panel budget of the
+// back-substitution and its status word.
+struct BatchElim {
+    int dev = 0;
+    int32_t n = 0, max_N = 0;
+    MatDesc* descs = nullptr;
+    uint32_t* scratch = nullptr;
+    uint32_t* err = nullptr;
+    size_t panel_cap = 0;
+};
+
 // Tables of every instance in element type T (Algorithm 1 after the reordering).
 template <typename T>
 cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs,
                          const MatDesc* h_cdescs, int64_t ktot,
                          int32_t max_ld, const MatDesc* d_bdescs, int32_t nbmat, int32_t max_N, bool f32w,
                          uint32_t* fw_scratch, uint32_t* d_flag, bool check, bool* inexact, double* bg_updates,
-                         cudaEvent_t* ev, cudaStream_t st) {
+                         const BatchElim& be, cudaEvent_t* ev, cudaStream_t st) {
     *inexact = false;
     T* base = reinterpret_cast<T*>(P.tables);
     cudaError_t e;
@@ -157,8 +183,51 @@ cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc
         if (e != cudaSuccess) return e;
     }
     cudaEventRecord(ev[4], st);
-    if (nbmat > 0 && (e = fw_many_skip<T>(base, d_bdescs, nbmat, max_N, fw_scratch, bg_updates, st)) != cudaSuccess)
-        return e;
+    // The Floyd-Warshall instances' rounds on a second stream (their host waits on a
+    // helper thread), the elimination instances' forward rounds and back-substitution
+    // here: both sets of launches side by side.
+    double fw_upd = 0.0;
+    cudaError_t fw_err = cudaSuccess;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fw_done = nullptr;
+    std::thread fw_thread;
+    if (nbmat > 0) {
+        if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&fw_done, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaStreamDestroy(s2);
+            return e;
+        }
+        cudaStreamWaitEvent(s2, ev[4], 0);
+        fw_thread = std::thread([&, dev = be.dev]() {
+            fw_err = cudaSetDevice(dev);
+            if (fw_err == cudaSuccess) fw_err = fw_many_skip<T>(base, d_bdescs, nbmat, max_N, fw_scratch, &fw_upd, s2);
+            if (fw_err == cudaSuccess) fw_err = cudaEventRecord(fw_done, s2);
+        });
+    }
+    double el_upd = 0.0;
+    if (be.n > 0) {
+        double fwd = 0.0, bs = 0.0;
+        e = fw_many_skip<T>(base, be.descs, be.n, be.max_N, be.scratch, &fwd, st, true);
+        if (e == cudaSuccess) {
+            std::vector<BsInput<T>> bin;
+            for (auto& x : I)
+                if (x.elim) bin.push_back(BsInput<T>{base + x.d_off, x.N, nullptr});
+            e = bg_backsub_many<T>(bin, be.err, nullptr, be.panel_cap, &bs, nullptr, st);
+        }
+        el_upd = fwd + bs;
+    }
+    if (fw_thread.joinable()) fw_thread.join();
+    if (fw_done) {
+        if (fw_err == cudaSuccess) cudaStreamWaitEvent(st, fw_done, 0);
+        cudaEventDestroy(fw_done);
+    }
+    if (s2) {
+        if (fw_err != cudaSuccess) cudaStreamSynchronize(s2);
+        cudaStreamDestroy(s2);
+    }
+    if (e != cudaSuccess) return e;
+    if (fw_err != cudaSuccess) return fw_err;
+    *bg_updates = fw_upd + el_upd;
     cudaEventRecord(ev[5], st);
     if (check) {
         if ((e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
@@ -456,7 +525,7 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
             for (;;) {
                 const int32_t g = next.fetch_add(1);
                 if (g >= G) return;
-                const Inst& x = I[g];
+                Inst& x = I[g];
                 if (hk[g].empty()) continue;
                 std::vector<int32_t> bp;
                 int32_t meth = 0;
@@ -479,12 +548,35 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     }
     if (slot_tot > 0) BCK(cudaMemcpyAsync(P.bgpos, bgpos.data(), (size_t)slot_tot * 4, cudaMemcpyHostToDevice, st));
 
+    // ---- the form of each boundary graph: elimination + back-substitution when asked
+    // for, or by default from kBatchElimMin slots on in a dissection order ----
+    for (int32_t g = 0; g < G; ++g) {
+        Inst& x = I[g];
+        x.elim = x.nbg > 0 && (o.bg_method == SPQ_BG_ELIM ||
+                               (o.bg_method == SPQ_BG_AUTO && x.nbg >= kBatchElimMin && methods[g] != 0));
+    }
+
     // ---- tables of every instance ----
-    std::vector<MatDesc> cd, bd;
+    std::vector<MatDesc> cd, bd, ed;
     cd.reserve(ktot);
     for (auto& x : I) {
         for (const MatDesc& d : x.descs) cd.push_back(MatDesc{x.apsp_off + d.off, d.n, 0});
-        if (x.N > 0) bd.push_back(MatDesc{x.d_off, (int32_t)x.N, 0});
+        if (x.N > 0) (x.elim ? ed : bd).push_back(MatDesc{x.d_off, (int32_t)x.N, 0});
+    }
+    int32_t max_N_fw = 0, max_N_el = 0;
+    for (const MatDesc& d : bd) max_N_fw = std::max(max_N_fw, d.n);
+    for (const MatDesc& d : ed) max_N_el = std::max(max_N_el, d.n);
+    BatchElim be;
+    BCK(cudaGetDevice(&be.dev));
+    be.n = (int32_t)ed.size();
+    be.max_N = max_N_el;
+    be.panel_cap = o.bg_panel_mib > 0 ? ((size_t)o.bg_panel_mib << 20) : ((size_t)2 << 30);
+    if (be.n > 0) {
+        BCK(tmp.alloc(&be.descs, ed.size()));
+        BCK(tmp.alloc(&be.scratch, (size_t)fw_many_scratch_words(be.n, be.max_N)));
+        BCK(tmp.alloc(&be.err, 1));
+        BCK(cudaMemcpyAsync(be.descs, ed.data(), ed.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+        BCK(cudaMemsetAsync(be.err, 0, 4, st));
     }
     MatDesc *d_cd, *d_bd;
     uint32_t *fw_scratch, *d_flag;
@@ -501,22 +593,28 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     if (f32w) {
         f32store = true;
         arith = SPQ_ARITH_F32;
-        BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, nbmat, max_N, true, fw_scratch, d_flag, false,
-                                &inexact, &bg_updates, ev, st));
+        BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, (int32_t)bd.size(), max_N_fw, true, fw_scratch, d_flag,
+                                false, &inexact, &bg_updates, be, ev, st));
     } else {
         const bool try_f32 = o.arith != SPQ_ARITH_I32;
         if (try_f32) {
             arith = SPQ_ARITH_F32;
-            BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag, true,
-                                    &inexact, &bg_updates, ev, st));
+            BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
+                                    d_flag, true, &inexact, &bg_updates, be, ev, st));
         }
         if (!try_f32 || inexact) {
             arith = SPQ_ARITH_I32;
-            BCK(batch_tables<int32_t>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, nbmat, max_N, false, fw_scratch, d_flag,
-                                      false, &inexact, &bg_updates, ev, st));
+            BCK(batch_tables<int32_t>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
+                                      d_flag, false, &inexact, &bg_updates, be, ev, st));
         }
     }
     BCK(cudaStreamSynchronize(st));
+    if (be.n > 0) {
+        // a bounded wait of the back-substitution that gave up leaves its matrices incomplete
+        uint32_t f = 0;
+        BCK(cudaMemcpy(&f, be.err, 4, cudaMemcpyDeviceToHost));
+        if (f & kErrWait) return SPQ_ETIMEOUT;
+    }
     double prof[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < 6; ++i) {
         float t = 0.f;
@@ -551,6 +649,7 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         h->arith = arith;
         h->query_grouped = o.query_grouped;
         h->order_method = methods[g];
+        h->bg_method = x.elim ? SPQ_BG_ELIM : SPQ_BG_FW;
         h->comp = P.comp + x.vbase;
         h->local = P.local + x.vbase;
         h->descs = P.descs + x.kbase;

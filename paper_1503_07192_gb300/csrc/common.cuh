@@ -134,6 +134,17 @@ int64_t fw_single_scratch_words(int64_t N);
 template <typename T>
 cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
                        double* updates, FwProfile* prof, cudaStream_t st);
+// The same for several independent matrices in the fewest launches (rowflags may be
+// null: every tile right of the diagonal is examined); err and exact are shared.
+template <typename T>
+struct BsInput {
+    T* M;
+    int64_t N;
+    const uint32_t* rowflags;
+};
+template <typename T>
+cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, uint32_t* exact, size_t apanel_budget,
+                            double* updates, FwProfile* prof, cudaStream_t st);
 // Marks of every pair of the given tiles (host list).
 cudaError_t launch_mark_pairs(const std::vector<int32_t>& blocks, int64_t N, uint32_t* flags, cudaStream_t st);
 // Infinity (0 on the diagonal) in the marked tiles, their mirrors and the diagonal tiles.
@@ -146,10 +157,12 @@ cudaError_t launch_mark_bg_tiles(int32_t n, const int64_t* rp, const int32_t* co
                                  const int32_t* local, const int32_t* nb, const int32_t* bg_off, const int32_t* bgpos,
                                  int32_t k, int64_t N, uint32_t* flags, cudaStream_t st);
 // Many matrices (sizes up to max_n) at once, with infinite-panel skipping per matrix;
-// *updates receives the phase-2 and phase-3 min-plus updates issued.
+// *updates receives the phase-2 and phase-3 min-plus updates issued.  trail: the
+// elimination form's forward pass instead (each round's phases 2 and 3 restricted to the
+// tiles right of / below the pivot block), for bg_backsub_many to complete.
 template <typename T>
 cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
-                         double* updates, cudaStream_t st);
+                         double* updates, cudaStream_t st, bool trail = false);
 int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n);
 
 // ---- query.cu ----

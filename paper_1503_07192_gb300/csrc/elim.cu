@@ -171,28 +171,51 @@ __global__ void __launch_bounds__(256) k_fill_marked(T* __restrict__ M, int64_t 
     }
 }
 
-// Per row block R: the column tiles J > R holding a finite entry of F (from the forward
-// pass's flags), the 128-bit mask of their finite columns (fblk / masks at R * nR + i),
-// their number and the number of finite columns |K(R)|.
+// One matrix of a back-substitution launch: its table, order and row blocks, and where
+// its per-tile-pair (masks, fblk, tflags) and per-row-block (fcnt, kcnt, koff) records
+// sit in the launch's arrays.
 template <typename T>
-__global__ void __launch_bounds__(256) k_colmask(const T* __restrict__ M, int64_t N, int32_t nR,
-                                                 const uint32_t* __restrict__ rowflags, uint4* __restrict__ masks,
+struct BsMat {
+    T* M;
+    int64_t N;
+    int32_t nR;
+    const uint32_t* rowflags;  // nR x nR marks of the forward pass, or null (every tile)
+    int64_t pair0;             // offset of its nR x nR records
+    int64_t row0;              // offset of its nR records
+};
+
+// A run of the work order: row block R of matrix mat, its tiles right of the diagonal and
+// then the diagonal tile, as the items [start, start + nR - R).
+struct BsRun {
+    int64_t start;
+    int32_t mat, R;
+};
+
+// Per row block R of matrix blockIdx.y: the column tiles J > R holding a finite entry of
+// F (the forward pass's marks narrow the search), the 128-bit mask of their finite
+// columns (fblk / masks at pair0 + R * nR + i), their number and the number of finite
+// columns |K(R)|.
+template <typename T>
+__global__ void __launch_bounds__(256) k_colmask(const BsMat<T>* __restrict__ mats, uint4* __restrict__ masks,
                                                  int32_t* __restrict__ fblk, int32_t* __restrict__ fcnt,
                                                  int32_t* __restrict__ kcnt) {
     __shared__ uint32_t colf[2][T_];
     __shared__ uint32_t wm[4];
-    const int32_t R = blockIdx.x;
+    const BsMat<T> m = mats[blockIdx.y];
+    const int32_t R = blockIdx.x, nR = m.nR;
+    if (R >= nR) return;
+    const int64_t N = m.N;
     const int tid = threadIdx.x, c = tid & (T_ - 1), h = tid >> 7;
     const T inf = Inf<T>::value();
     const int64_t r0 = (int64_t)R * T_;
     const int64_t nrows = (N - r0) < T_ ? (N - r0) : T_;
     int32_t cnt = 0, kc = 0;
     for (int32_t J = R + 1; J < nR; ++J) {
-        if (rowflags[(int64_t)R * nR + J] == 0u) continue;
+        if (m.rowflags && m.rowflags[(int64_t)R * nR + J] == 0u) continue;
         const int64_t col = (int64_t)J * T_ + c;
         uint32_t f = 0;
         if (col < N)
-            for (int64_t i = h; i < nrows; i += 2) f |= (M[(r0 + i) * N + col] < inf) ? 1u : 0u;
+            for (int64_t i = h; i < nrows; i += 2) f |= (m.M[(r0 + i) * N + col] < inf) ? 1u : 0u;
         colf[h][c] = f;
         __syncthreads();
         if (tid < T_) {
@@ -200,12 +223,12 @@ __global__ void __launch_bounds__(256) k_colmask(const T* __restrict__ M, int64_
             if ((tid & 31) == 0) wm[tid >> 5] = b;
         }
         __syncthreads();
-        const uint4 m = make_uint4(wm[0], wm[1], wm[2], wm[3]);
-        const int pc = __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+        const uint4 mk = make_uint4(wm[0], wm[1], wm[2], wm[3]);
+        const int pc = __popc(mk.x) + __popc(mk.y) + __popc(mk.z) + __popc(mk.w);
         if (pc) {
             if (tid == 0) {
-                fblk[(int64_t)R * nR + cnt] = J;
-                masks[(int64_t)R * nR + cnt] = m;
+                fblk[m.pair0 + (int64_t)R * nR + cnt] = J;
+                masks[m.pair0 + (int64_t)R * nR + cnt] = mk;
             }
             ++cnt;
             kc += pc;
@@ -213,57 +236,65 @@ __global__ void __launch_bounds__(256) k_colmask(const T* __restrict__ M, int64_
         __syncthreads();
     }
     if (tid == 0) {
-        fcnt[R] = cnt;
-        kcnt[R] = kc;
+        fcnt[m.row0 + R] = cnt;
+        kcnt[m.row0 + R] = kc;
     }
 }
 
-// K(R) as ascending column indices at klist[koff[R] ..), padded to a multiple of KC with
-// copies of its first entry (their panel rows are infinite, so they change nothing).
-__global__ void __launch_bounds__(T_) k_klist(const uint4* __restrict__ masks, const int32_t* __restrict__ fblk,
-                                              const int32_t* __restrict__ fcnt, const int32_t* __restrict__ kcnt,
-                                              const int64_t* __restrict__ koff, int32_t nR,
+// K(R) of row block blockIdx.x of matrix blockIdx.y as ascending column indices at
+// klist[koff ..), padded to a multiple of KC with copies of its first entry (their panel
+// rows are infinite, so they change nothing).
+template <typename T>
+__global__ void __launch_bounds__(T_) k_klist(const BsMat<T>* __restrict__ mats, const uint4* __restrict__ masks,
+                                              const int32_t* __restrict__ fblk, const int32_t* __restrict__ fcnt,
+                                              const int32_t* __restrict__ kcnt, const int64_t* __restrict__ koff,
                                               int32_t* __restrict__ klist) {
-    const int32_t R = blockIdx.x;
+    const BsMat<T> m = mats[blockIdx.y];
+    const int32_t R = blockIdx.x, nR = m.nR;
+    if (R >= nR) return;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int64_t base = koff[R];
-    const int32_t nf = fcnt[R];
+    const int64_t base = koff[m.row0 + R];
+    const int32_t nf = fcnt[m.row0 + R];
     int32_t pos = 0;
     for (int32_t i = 0; i < nf; ++i) {
-        const uint4 m = masks[(int64_t)R * nR + i];
-        const uint32_t words[4] = {m.x, m.y, m.z, m.w};
+        const uint4 mk = masks[m.pair0 + (int64_t)R * nR + i];
+        const uint32_t words[4] = {mk.x, mk.y, mk.z, mk.w};
         const uint32_t word = words[w];
         int32_t woff = 0;
         for (int x = 0; x < w; ++x) woff += __popc(words[x]);
         if ((word >> lane) & 1u)
             klist[base + pos + woff + __popc(word & ((1u << lane) - 1u))] =
-                fblk[(int64_t)R * nR + i] * T_ + w * 32 + lane;
-        pos += __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+                fblk[m.pair0 + (int64_t)R * nR + i] * T_ + w * 32 + lane;
+        pos += __popc(mk.x) + __popc(mk.y) + __popc(mk.z) + __popc(mk.w);
     }
     __syncthreads();
-    const int32_t kc = kcnt[R];
+    const int32_t kc = kcnt[m.row0 + R];
     const int32_t kp = (kc + KC - 1) / KC * KC;
     if (kc > 0)
         for (int32_t j = kc + tid; j < kp; j += T_) klist[base + j] = klist[base];
 }
 
-// A panels: A[(koff[R] - aoff0 + k) * 128 + i] = F(R*128 + i, klist[k]), read as its
-// mirror F(klist[k], R*128 + i) (one contiguous row piece); padding rows infinite.
+// A panels of the row blocks [R0, R1) of the matrices mat0 + blockIdx.y:
+// A[(koff - aoff0 + k) * 128 + i] = F(R*128 + i, klist[k]), read as its mirror
+// F(klist[k], R*128 + i) (one contiguous row piece); padding rows infinite.
 template <typename T, bool CONV>
-__global__ void __launch_bounds__(256) k_gather_a(const T* __restrict__ M, int64_t N, int32_t R0,
-                                                  const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt,
-                                                  const int32_t* __restrict__ klist, int64_t aoff0,
-                                                  T* __restrict__ A) {
+__global__ void __launch_bounds__(256) k_gather_a(const BsMat<T>* __restrict__ mats, int32_t mat0, int32_t R0,
+                                                  int32_t R1, const int64_t* __restrict__ koff,
+                                                  const int32_t* __restrict__ kcnt, const int32_t* __restrict__ klist,
+                                                  int64_t aoff0, T* __restrict__ A) {
+    const BsMat<T> m = mats[mat0 + blockIdx.y];
     const int32_t R = R0 + blockIdx.x;
-    const int64_t base = koff[R];
-    const int32_t kc = kcnt[R];
+    if (R >= R1 || R >= m.nR) return;
+    const int64_t N = m.N;
+    const int64_t base = koff[m.row0 + R];
+    const int32_t kc = kcnt[m.row0 + R];
     const int32_t kp = (kc + KC - 1) / KC * KC;
     const int64_t col0 = (int64_t)R * T_;
     for (int64_t idx = threadIdx.x; idx < (int64_t)kp * (T_ / 4); idx += blockDim.x) {
         const int32_t k = (int32_t)(idx >> 5), c4 = (int32_t)(idx & 31);
         int4 v = inf4<T>();
         if (k < kc && col0 + c4 * 4 < N)
-            v = *reinterpret_cast<const int4*>(M + (int64_t)klist[base + k] * N + col0 + c4 * 4);
+            v = *reinterpret_cast<const int4*>(m.M + (int64_t)klist[base + k] * N + col0 + c4 * 4);
         if constexpr (CONV) {
             const float4 f = *reinterpret_cast<const float4*>(&v);
             const float4 g = make_float4(enc(f.x), enc(f.y), enc(f.z), enc(f.w));
@@ -300,22 +331,14 @@ __device__ __forceinline__ void stage_panel(T (*P)[T_], const T* __restrict__ A,
     }
 }
 
-// Item g (global order) -> row block R and column block J (J == R: the diagonal tile).
-__device__ __forceinline__ void item_tile(int64_t g, int32_t nR, int32_t& R, int32_t& J) {
-    int64_t m = (int64_t)((sqrt(8.0 * (double)g + 1.0) - 1.0) * 0.5);
-    while (m > 0 && m * (m + 1) / 2 > g) --m;
-    while ((m + 1) * (m + 2) / 2 <= g) ++m;
-    const int64_t p = g - m * (m + 1) / 2;
-    R = nR - 1 - (int32_t)m;
-    J = p < m ? R + 1 + (int32_t)p : R;
-}
-
 // CONV (float tables of an int32 graph): every tile is stored as int32 (the final table
 // type) as soon as it is final, and the arithmetic runs on the integer encoding above
 // (tiles read as rows of d need no conversion); a finite value >= 2^24 sets kErrExact.
+// Items [0, nitems) follow the runs (ascending starts); one launch may hold the rows of
+// several independent matrices, interleaved.
 template <typename T, bool CONV>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
-    k_backsub(T* __restrict__ M, int64_t N, int32_t nR, int64_t g0, int64_t nitems,
+    k_backsub(const BsMat<T>* __restrict__ mats, const BsRun* __restrict__ runs, int32_t nruns, int64_t nitems,
               const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt, const int32_t* __restrict__ klist,
               const T* __restrict__ A, int64_t aoff0, const int32_t* __restrict__ fblk,
               const int32_t* __restrict__ fcnt, uint32_t* __restrict__ tflags,
@@ -323,6 +346,7 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     __shared__ int64_t s_item;
+    __shared__ int32_t s_mat, s_R, s_J;
     __shared__ int s_fail;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (;;) {
@@ -331,25 +355,40 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
             if (*reinterpret_cast<volatile uint32_t*>(err) & kErrWait) t = nitems;
             s_item = t;
             s_fail = 0;
+            if (t < nitems) {
+                int32_t lo = 0, hi = nruns;  // the last run starting at or before t
+                while (hi - lo > 1) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    if (runs[mid].start <= t) lo = mid; else hi = mid;
+                }
+                const BsRun ru = runs[lo];
+                const int64_t p = t - ru.start;
+                const int32_t last = mats[ru.mat].nR - 1 - ru.R;  // tiles right of the diagonal
+                s_mat = ru.mat;
+                s_R = ru.R;
+                s_J = p < last ? ru.R + 1 + (int32_t)p : ru.R;
+            }
         }
         __syncthreads();
         const int64_t t = s_item;
         if (t >= nitems) break;
-        int32_t R, J;
-        item_tile(g0 + t, nR, R, J);
-        const int32_t kc = kcnt[R];
+        const BsMat<T> m = mats[s_mat];
+        const int32_t R = s_R, J = s_J, nR = m.nR;
+        T* __restrict__ M = m.M;
+        const int64_t N = m.N;
+        const int32_t kc = kcnt[m.row0 + R];
         const int64_t r0 = (int64_t)R * T_, c0 = (int64_t)J * T_;
         const int4 fill = CONV ? make_int4(SPQ_INF_I32, SPQ_INF_I32, SPQ_INF_I32, SPQ_INF_I32) : inf4<T>();
         const T vinf = CONV ? __int_as_float(SPQ_INF_I32) : Inf<T>::value();
         if (kc > 0) {
             // dependencies: the final tiles this one reads
             if (tid < 32) {
-                const int32_t nf = fcnt[R];
+                const int32_t nf = fcnt[m.row0 + R];
                 for (int32_t i = tid; i < nf; i += 32) {
-                    const int32_t K = fblk[(int64_t)R * nR + i];
+                    const int32_t K = fblk[m.pair0 + (int64_t)R * nR + i];
                     const int32_t a = (J == R) ? R : (K < J ? K : J);
                     const int32_t b = (J == R) ? K : (K < J ? J : K);
-                    const uint32_t* f = tflags + (int64_t)a * nR + b;
+                    const uint32_t* f = tflags + m.pair0 + (int64_t)a * nR + b;
                     if (ld_acquire(f) == 0u) {
                         const unsigned long long t0 = global_ns();
                         while (ld_acquire(f) == 0u) {
@@ -379,7 +418,7 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) acc[i][j] = vinf;
             }
-            const int64_t kb = koff[R];
+            const int64_t kb = koff[m.row0 + R];
             const int32_t nch = (kc + KC - 1) / KC;
             const T* Ap = A + (kb - aoff0) * T_;
             const int32_t* rows = klist + kb;
@@ -407,32 +446,32 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
                 if (clamp_enc(acc)) atomicOr(exact, kErrExact);
             store_c<T>(acc, M, N, r0, c0, tx, ty);
             if (J != R) store_c_transposed<T>(acc, M, N, r0, c0, tx, ty);
-        } else if constexpr (CONV) {
-            // no finite entry right of R: d(R, J) = F(R, J) = inf, d(R, R) = F(R, R); the
-            // values are final but still float: store them as int32
+        } else if (CONV || J != R) {
+            // no finite entry right of R: d(R, J) = F(R, J) = inf, stored here (an unmarked
+            // tile was never initialised), and d(R, R) = F(R, R), already in place (with
+            // conversion: final but still float, stored as int32)
             T acc[8][8];
-            if (J == R) {
-                load_c<T>(acc, M, N, r0, r0, tx, ty);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = enc(acc[i][j]);
-            } else {
+                for (int j = 0; j < 8; ++j) acc[i][j] = vinf;
+            if constexpr (CONV) {
+                if (J == R) {
+                    load_c<T>(acc, M, N, r0, r0, tx, ty);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                    for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = vinf;
+                        for (int j = 0; j < 8; ++j) acc[i][j] = enc(acc[i][j]);
+                }
+                if (clamp_enc(acc)) atomicOr(exact, kErrExact);
             }
-            if (clamp_enc(acc)) atomicOr(exact, kErrExact);
             store_c<T>(acc, M, N, r0, c0, tx, ty);
             if (J != R) store_c_transposed<T>(acc, M, N, r0, c0, tx, ty);
         }
-        // (kc == 0 without conversion: the stored values d(R, J) = inf and d(R, R) =
-        //  F(R, R) are already final)
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            st_release(tflags + (int64_t)R * nR + J, 1u);
+            st_release(tflags + m.pair0 + (int64_t)R * nR + J, 1u);
         }
     }
 }
@@ -491,36 +530,57 @@ cudaError_t launch_mark_pairs(const std::vector<int32_t>& blocks, int64_t N, uin
 size_t bg_backsub_scratch_bytes(int64_t N) {
     const int64_t nR = (N + T_ - 1) / T_;
     // masks (16 B), fblk and tile flags (4 B each) per tile pair; per row block: fcnt,
-    // kcnt, koff; the work counter
-    return (size_t)(nR * nR) * 24 + (size_t)nR * 16 + 64;
+    // kcnt, koff and a run of the work order; the work counter and the matrix record
+    return (size_t)(nR * nR) * 24 + (size_t)nR * 32 + 256;
 }
 
 template <typename T>
-cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
-                       double* updates, FwProfile* prof, cudaStream_t st) {
+cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, uint32_t* exact, size_t apanel_budget,
+                            double* updates, FwProfile* prof, cudaStream_t st) {
     if (updates) *updates = 0.0;
-    if (N <= 0) return cudaSuccess;
-    const int32_t nR = (int32_t)((N + T_ - 1) / T_);
+    std::vector<BsMat<T>> hm;
+    int64_t P2 = 0, RR = 0;
+    int32_t nRmax = 0;
+    for (const BsInput<T>& x : in) {
+        if (x.N <= 0) continue;
+        const int32_t nR = (int32_t)((x.N + T_ - 1) / T_);
+        hm.push_back(BsMat<T>{x.M, x.N, nR, x.rowflags, P2, RR});
+        P2 += (int64_t)nR * nR;
+        RR += nR;
+        nRmax = std::max(nRmax, nR);
+    }
+    const int32_t nmat = (int32_t)hm.size();
+    if (nmat == 0) return cudaSuccess;
+    if (nmat > 65535) return cudaErrorInvalidValue;
     // exact != NULL (float tables only): store int32 tables, checking exactness
     const bool conv = std::is_same<T, float>::value && exact != nullptr;
     auto kern = conv ? k_backsub<T, std::is_same<T, float>::value> : k_backsub<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
-    const int64_t pairs = (int64_t)nR * nR;
+    // one scratch block: masks | fblk | tflags | koff | fcnt | kcnt | runs | counter | mats
+    const size_t o_fblk = (size_t)P2 * 16, o_tfl = o_fblk + (size_t)P2 * 4, o_koff = o_tfl + (size_t)P2 * 4;
+    const size_t o_fcnt = o_koff + (size_t)RR * 8, o_kcnt = o_fcnt + (size_t)RR * 4;
+    const size_t o_runs = (o_kcnt + (size_t)RR * 4 + 15) & ~(size_t)15;
+    const size_t o_ctr = o_runs + (size_t)RR * sizeof(BsRun);
+    const size_t o_mats = (o_ctr + 8 + 15) & ~(size_t)15;
+    const size_t bytes = o_mats + (size_t)nmat * sizeof(BsMat<T>);
     unsigned char* scratch = nullptr;
-    if ((e = cudaMallocAsync(&scratch, bg_backsub_scratch_bytes(N), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync(&scratch, bytes, st)) != cudaSuccess) return e;
     uint4* masks = reinterpret_cast<uint4*>(scratch);
-    int32_t* fblk = reinterpret_cast<int32_t*>(scratch + pairs * 16);
-    uint32_t* tflags = reinterpret_cast<uint32_t*>(scratch + pairs * 20);
-    int64_t* koff = reinterpret_cast<int64_t*>(scratch + pairs * 24);
-    int32_t* fcnt = reinterpret_cast<int32_t*>(koff + nR);
-    int32_t* kcnt = fcnt + nR;
-    unsigned long long* counter = reinterpret_cast<unsigned long long*>(kcnt + nR);  // 8-byte aligned
+    int32_t* fblk = reinterpret_cast<int32_t*>(scratch + o_fblk);
+    uint32_t* tflags = reinterpret_cast<uint32_t*>(scratch + o_tfl);
+    int64_t* koff = reinterpret_cast<int64_t*>(scratch + o_koff);
+    int32_t* fcnt = reinterpret_cast<int32_t*>(scratch + o_fcnt);
+    int32_t* kcnt = reinterpret_cast<int32_t*>(scratch + o_kcnt);
+    BsRun* runs = reinterpret_cast<BsRun*>(scratch + o_runs);
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(scratch + o_ctr);
+    BsMat<T>* mats = reinterpret_cast<BsMat<T>*>(scratch + o_mats);
     int32_t* klist = nullptr;
     T* A = nullptr;
     std::vector<cudaEvent_t> ev;  // per launch of k_backsub: start, end (profiling only)
-    std::vector<int32_t> hk(nR);
-    std::vector<int64_t> hoff(nR + 1, 0);
+    std::vector<int32_t> hk(RR);
+    std::vector<int64_t> hoff(RR + 1, 0);
+    std::vector<BsRun> hruns;
     auto done = [&](cudaError_t r) {
         if (klist) cudaFreeAsync(klist, st);
         if (A) cudaFreeAsync(A, st);
@@ -529,63 +589,120 @@ cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err,
             if (x) cudaEventDestroy(x);
         return r;
     };
-    if ((e = cudaMemsetAsync(tflags, 0, (size_t)pairs * 4, st)) != cudaSuccess) return done(e);
-    k_colmask<T><<<nR, 256, 0, st>>>(M, N, nR, rowflags, masks, fblk, fcnt, kcnt);
+    if ((e = cudaMemcpyAsync(mats, hm.data(), hm.size() * sizeof(BsMat<T>), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return done(e);
+    if ((e = cudaMemsetAsync(tflags, 0, (size_t)P2 * 4, st)) != cudaSuccess) return done(e);
+    k_colmask<T><<<dim3(nRmax, nmat), 256, 0, st>>>(mats, masks, fblk, fcnt, kcnt);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
-    if ((e = cudaMemcpyAsync(hk.data(), kcnt, (size_t)nR * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(hk.data(), kcnt, (size_t)RR * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return done(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
     double upd = 0.0, items = 0.0;
-    for (int32_t R = 0; R < nR; ++R) {
-        hoff[R + 1] = hoff[R] + round_up(hk[R], KC);
-        upd += (double)hk[R] * T_ * T_ * (double)(nR - R);
-        items += (double)(nR - R);
-    }
+    for (const BsMat<T>& m : hm)
+        for (int32_t R = 0; R < m.nR; ++R) {
+            const int64_t i = m.row0 + R;
+            hoff[i + 1] = hoff[i] + round_up(hk[i], KC);
+            upd += (double)hk[i] * T_ * T_ * (double)(m.nR - R);
+            items += (double)(m.nR - R);
+        }
     if (updates) *updates = upd;
     if (prof) {
         prof->bs_updates = upd;
         prof->bs_items = items;
     }
-    const int64_t ktot = hoff[nR];
-    if ((e = cudaMemcpyAsync(koff, hoff.data(), (size_t)nR * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    const int64_t ktot = hoff[RR];
+    if ((e = cudaMemcpyAsync(koff, hoff.data(), (size_t)RR * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return done(e);
     if ((e = cudaMallocAsync(&klist, (size_t)(ktot > 0 ? ktot : 1) * 4, st)) != cudaSuccess) return done(e);
-    k_klist<<<nR, T_, 0, st>>>(masks, fblk, fcnt, kcnt, koff, nR, klist);
+    k_klist<T><<<dim3(nRmax, nmat), T_, 0, st>>>(mats, masks, fblk, fcnt, kcnt, koff, klist);
     count_launches(1);
-    // row-block ranges [lo, hi) whose panels fit the budget, from the last rows down
+    // Launches whose A panels fit the budget: whole matrices side by side, or (a matrix
+    // whose panels alone exceed it) ranges of its row blocks from the last rows down.
+    // Each launch's panels are contiguous in the koff order.
+    struct Launch {
+        int32_t mat0, nm, R0, R1;  // matrices [mat0, mat0 + nm), row blocks [R0, R1)
+    };
+    std::vector<Launch> launches;
     const int64_t row_bytes = (int64_t)T_ * sizeof(T);
-    int64_t maxk = 0;
-    std::vector<int32_t> cuts{nR};
-    for (int32_t R = nR - 1; R >= 0; --R) {
-        const int64_t lo_k = hoff[R], hi_k = hoff[cuts.back()];
-        if (R < cuts.back() - 1 && (hi_k - lo_k) * row_bytes > (int64_t)apanel_budget) cuts.push_back(R + 1);
+    {
+        int32_t g0 = 0;
+        int64_t gk = 0;
+        for (int32_t i = 0; i < nmat; ++i) {
+            const BsMat<T>& m = hm[i];
+            const int64_t mk = hoff[m.row0 + m.nR] - hoff[m.row0];
+            if (mk * row_bytes <= (int64_t)apanel_budget) {
+                if (i > g0 && (gk + mk) * row_bytes > (int64_t)apanel_budget) {
+                    launches.push_back(Launch{g0, i - g0, 0, nRmax});
+                    g0 = i;
+                    gk = 0;
+                }
+                gk += mk;
+                continue;
+            }
+            if (i > g0) launches.push_back(Launch{g0, i - g0, 0, nRmax});
+            std::vector<int32_t> cuts{m.nR};
+            for (int32_t R = m.nR - 1; R >= 0; --R) {
+                const int64_t lo_k = hoff[m.row0 + R], hi_k = hoff[m.row0 + cuts.back()];
+                if (R < cuts.back() - 1 && (hi_k - lo_k) * row_bytes > (int64_t)apanel_budget) cuts.push_back(R + 1);
+            }
+            cuts.push_back(0);
+            for (size_t c = 0; c + 1 < cuts.size(); ++c) launches.push_back(Launch{i, 1, cuts[c + 1], cuts[c]});
+            g0 = i + 1;
+            gk = 0;
+        }
+        if (g0 < nmat) launches.push_back(Launch{g0, nmat - g0, 0, nRmax});
     }
-    cuts.push_back(0);
-    for (size_t i = 0; i + 1 < cuts.size(); ++i) maxk = std::max(maxk, hoff[cuts[i]] - hoff[cuts[i + 1]]);
+    // the runs of every launch: row blocks from the last down, the matrices of a launch
+    // interleaved (their q-th rows from the end side by side)
+    std::vector<size_t> run0(launches.size() + 1, 0);
+    std::vector<int64_t> nit(launches.size(), 0);
+    int64_t maxk = 0;
+    for (size_t l = 0; l < launches.size(); ++l) {
+        const Launch& L = launches[l];
+        int64_t start = 0;
+        int32_t depth = 0;
+        for (int32_t i = L.mat0; i < L.mat0 + L.nm; ++i) depth = std::max(depth, std::min(hm[i].nR, L.R1) - L.R0);
+        for (int32_t q = 0; q < depth; ++q)
+            for (int32_t i = L.mat0; i < L.mat0 + L.nm; ++i) {
+                const int32_t R = std::min(hm[i].nR, L.R1) - 1 - q;
+                if (R < L.R0) continue;
+                hruns.push_back(BsRun{start, i, R});
+                start += hm[i].nR - R;
+            }
+        run0[l + 1] = hruns.size();
+        nit[l] = start;
+        const BsMat<T>& a = hm[L.mat0];
+        const BsMat<T>& z = hm[L.mat0 + L.nm - 1];
+        maxk = std::max(maxk, hoff[z.row0 + std::min(z.nR, L.R1)] - hoff[a.row0 + L.R0]);
+    }
+    if ((e = cudaMemcpyAsync(runs, hruns.data(), hruns.size() * sizeof(BsRun), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return done(e);
     if ((e = cudaMallocAsync(&A, (size_t)(maxk > 0 ? maxk : 1) * row_bytes, st)) != cudaSuccess) return done(e);
     if (prof) {
-        ev.assign(2 * (cuts.size() - 1), nullptr);
+        ev.assign(2 * launches.size(), nullptr);
         for (auto& x : ev)
             if ((e = cudaEventCreate(&x)) != cudaSuccess) return done(e);
     }
     const size_t psm = sizeof(PanelSmem<T>);
     const int grid = sms_e() * SPQ_FW_MIN_CTAS;
-    for (size_t i = 0; i + 1 < cuts.size() && e == cudaSuccess; ++i) {
-        const int32_t hi = cuts[i], lo = cuts[i + 1];
-        const int64_t aoff0 = hoff[lo];
-        // A panels of rows [lo, hi): read before the launch overwrites those rows
+    for (size_t l = 0; l < launches.size() && e == cudaSuccess; ++l) {
+        const Launch& L = launches[l];
+        const int64_t aoff0 = hoff[hm[L.mat0].row0 + L.R0];
+        const dim3 gg((unsigned)(std::min(L.R1, nRmax) - L.R0), (unsigned)L.nm);
+        // A panels of the launch's rows: read before the launch overwrites those rows
         if (conv)
-            k_gather_a<T, std::is_same<T, float>::value><<<hi - lo, 256, 0, st>>>(M, N, lo, koff, kcnt, klist, aoff0, A);
+            k_gather_a<T, std::is_same<T, float>::value><<<gg, 256, 0, st>>>(mats, L.mat0, L.R0, L.R1, koff, kcnt,
+                                                                              klist, aoff0, A);
         else
-            k_gather_a<T, false><<<hi - lo, 256, 0, st>>>(M, N, lo, koff, kcnt, klist, aoff0, A);
-        const int64_t m0 = nR - hi, m1 = nR - lo;
-        const int64_t g0 = m0 * (m0 + 1) / 2, nit = m1 * (m1 + 1) / 2 - g0;
+            k_gather_a<T, false><<<gg, 256, 0, st>>>(mats, L.mat0, L.R0, L.R1, koff, kcnt, klist, aoff0, A);
         cudaMemsetAsync(counter, 0, 8, st);
-        if (prof) cudaEventRecord(ev[2 * i], st);
-        kern<<<grid, NTH, psm, st>>>(M, N, nR, g0, nit, koff, kcnt, klist, A, aoff0, fblk, fcnt, tflags, counter, err,
-                                     exact);
-        if (prof) cudaEventRecord(ev[2 * i + 1], st);
+        if (prof) cudaEventRecord(ev[2 * l], st);
+        kern<<<grid, NTH, psm, st>>>(mats, runs + run0[l], (int32_t)(run0[l + 1] - run0[l]), nit[l], koff, kcnt, klist,
+                                     A, aoff0, fblk, fcnt, tflags, counter, err, exact);
+        if (prof) cudaEventRecord(ev[2 * l + 1], st);
         count_launches(2);
         e = cudaGetLastError();
     }
@@ -603,10 +720,21 @@ cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err,
     return done(e);
 }
 
+template <typename T>
+cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
+                       double* updates, FwProfile* prof, cudaStream_t st) {
+    return bg_backsub_many<T>(std::vector<BsInput<T>>{BsInput<T>{M, N, rowflags}}, err, exact, apanel_budget, updates,
+                              prof, st);
+}
+
 template cudaError_t bg_backsub<float>(float*, int64_t, const uint32_t*, uint32_t*, uint32_t*, size_t, double*,
                                        FwProfile*, cudaStream_t);
 template cudaError_t bg_backsub<int32_t>(int32_t*, int64_t, const uint32_t*, uint32_t*, uint32_t*, size_t, double*,
                                          FwProfile*, cudaStream_t);
+template cudaError_t bg_backsub_many<float>(const std::vector<BsInput<float>>&, uint32_t*, uint32_t*, size_t, double*,
+                                            FwProfile*, cudaStream_t);
+template cudaError_t bg_backsub_many<int32_t>(const std::vector<BsInput<int32_t>>&, uint32_t*, uint32_t*, size_t,
+                                              double*, FwProfile*, cudaStream_t);
 
 template cudaError_t launch_fill_marked<float>(float*, int64_t, const uint32_t*, cudaStream_t);
 template cudaError_t launch_fill_marked<int32_t>(int32_t*, int64_t, const uint32_t*, cudaStream_t);

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                    int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite,
-                                                   int32_t flag_stride, const int32_t* __restrict__ sel) {
+                                                   int32_t flag_stride, const int32_t* __restrict__ sel,
+                                                   int32_t trail = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -142,8 +143,9 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
         const MatDesc d = descs[sel ? sel[mi] : mi];
         const int64_t n = d.n;
         const int32_t R = (int32_t)((n + T_ - 1) / T_);
-        if (r >= R || (int32_t)blockIdx.x >= R - 1) continue;
-        const int32_t J = (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
+        // (elimination form: the row tiles right of the pivot only)
+        const int32_t J = trail ? r + 1 + (int32_t)blockIdx.x : (int32_t)blockIdx.x + ((int32_t)blockIdx.x >= r ? 1 : 0);
+        if (r >= R || J >= R) continue;
         T* M = base + d.off;
         const int64_t o = (int64_t)r * T_, cj = (int64_t)J * T_;
         T acc[8][8];
@@ -760,7 +762,7 @@ int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n) {
 
 template <typename T>
 cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
-                         double* updates, cudaStream_t st) {
+                         double* updates, cudaStream_t st, bool trail) {
     if (updates) *updates = 0.0;
     if (nmat <= 0 || max_n <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
@@ -780,8 +782,13 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
         k_phase1<T><<<dim3(1, gy), NTH, T_ * T_ * sizeof(T), st>>>(base, d_descs, nmat, r, nullptr);
         count_launches(1);
-        if (R > 1) {
-            k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr);
+        if (R > 1 && (!trail || r + 1 < R)) {
+            // (elimination form: the flags of the tiles left of r stay clear, so the lists
+            //  and phase 3 hold only tiles right of / below the pivot block)
+            if (trail)
+                k_phase2<T><<<dim3(R - 1 - r, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr, 1);
+            else
+                k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr);
             k_compact_many<<<nmat, 1024, 0, st>>>(flags, R, d_descs, nmat, r, lists, R + 1, offs, tiles);
             launch_scan_excl(offs, nmat + 1, st);
             k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs);
@@ -798,8 +805,9 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
 }
 
 template cudaError_t fw_many_skip<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, uint32_t*, double*,
-                                           cudaStream_t);
-template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_t, uint32_t*, double*, cudaStream_t);
+                                           cudaStream_t, bool);
+template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_t, uint32_t*, double*, cudaStream_t,
+                                         bool);
 
 template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
 template cudaError_t fw_batched<float>(float*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);

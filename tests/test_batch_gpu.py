@@ -81,3 +81,56 @@ def test_batch_rejects_an_invalid_instance():
     with pytest.raises(m.SpqError) as e:
         m.spq_build_many(tup)
     assert e.value.status == m.SPQ_EINVAL
+
+
+def _check_batch(ins, hs, on_device=False):
+    m = spq()
+    outs = m.spq_query_many(hs, [w.pairs for w in ins])
+    for w, h, o in zip(ins, hs, outs):
+        single = build(w.graph, w.part, w.k)
+        assert np.array_equal(o, query(single, w.pairs)), w.name
+        ref = oracle_i32(oracle.pairs_dist(w.graph.row_ptr, w.graph.col, w.graph.w, w.pairs))
+        assert np.array_equal(o.astype(np.int64), ref), w.name
+        assert np.array_equal(single.bg(), h.bg()), w.name
+        single.free()
+
+
+def test_batch_elimination_form_for_every_instance():
+    """bg_method = elimination for the whole batch: every instance's boundary graph by
+    elimination + back-substitution (the forward rounds of all instances in shared
+    launches, one back-substitution over all of them), the same tables and distances as
+    single builds."""
+    m = spq()
+    ins = _instances()
+    o = m.spq_opts_default()
+    o.bg_method = m.SPQ_BG_ELIM
+    hs = m.spq_build_many(_tuples(ins, True), opts=o)
+    for w, h in zip(ins, hs):
+        if h.meta()["nb"].sum() > 0:
+            assert h.profile()["bg_method"] == m.SPQ_BG_ELIM, w.name
+    _check_batch(ins, hs)
+    for h in hs:
+        h.free()
+
+
+def test_batch_takes_elimination_for_large_boundary_graphs():
+    """By default, instances of at least 4,096 boundary vertices take the elimination form
+    (in a vertex nested-dissection order) while the others share the batched
+    Floyd-Warshall rounds on a second stream; both kinds in one batch, also in int32
+    arithmetic and with the back-substitution's A panels split over several launches."""
+    m = spq()
+    big = gen.configs.delaunay_rcb(40000, 8, 2500, seed=79)
+    big.name = "big"
+    ins = [big] + _instances()[:5]
+    for arith, panel_mib in ((m.SPQ_ARITH_AUTO, 0), (m.SPQ_ARITH_I32, 0), (m.SPQ_ARITH_AUTO, 1)):
+        o = m.spq_opts_default()
+        o.arith = arith
+        o.bg_panel_mib = panel_mib
+        hs = m.spq_build_many(_tuples(ins, True), opts=o)
+        nbg = [int(h.meta()["nb"].sum()) for h in hs]
+        assert nbg[0] >= 4096 and max(nbg[1:]) < 4096
+        methods = [h.profile()["bg_method"] for h in hs]
+        assert methods[0] == m.SPQ_BG_ELIM and all(x == m.SPQ_BG_FW for x, n in zip(methods[1:], nbg[1:]) if n > 0)
+        _check_batch(ins, hs)
+        for h in hs:
+            h.free()

@@ -373,6 +373,44 @@ def test_concurrent_elimination_runs_match_floyd_warshall(arith):
     h.free()
 
 
+def _two_islands(weight):
+    """Two far-apart Delaunay triangulations as one graph: a boundary graph in two parts
+    with no path between them."""
+    a = gen.delaunay(9000, seed=47, weight=weight, scale=float(np.sqrt(9000)))
+    u, v, w = gen.edges_from_csr(a)
+    rp, col, ww = gen.csr_from_edges(2 * a.n, np.concatenate([u, u + a.n]), np.concatenate([v, v + a.n]),
+                                     np.concatenate([w, w]))
+    xy = np.concatenate([a.xy, a.xy + np.array([3.0, 0.0])])
+    g = gen.Graph(2 * a.n, rp, col, ww.astype(a.w.dtype), xy)
+    part, k = gen.rcb(g.xy, 5)
+    return g, part, k
+
+
+@pytest.mark.parametrize("weight,arith", [("f32_lognormal", 0), ("int_1e6", 1)])
+def test_elimination_of_a_disconnected_boundary_graph(weight, arith):
+    """Row blocks with no finite entry right of the diagonal (the last blocks of the first
+    island) in the forms that keep float32 values or int32 arithmetic: their tiles to the
+    right must come out infinite, as Floyd-Warshall leaves them."""
+    g, part, k = _two_islands(weight)
+    hf = build(g, part, k, arith=arith, bg=1)
+    he = build(g, part, k, arith=arith, bg=2)
+    assert he.profile()["bg_method"] == 2
+    Bf, Be = hf.bg(), he.bg()
+    fin_f = np.isfinite(Bf) if Bf.dtype == np.float32 else Bf < 0x20000000
+    fin_e = np.isfinite(Be) if Be.dtype == np.float32 else Be < 0x20000000
+    assert np.array_equal(fin_f, fin_e) and not fin_e.all()
+    if Be.dtype == np.float32:
+        np.testing.assert_allclose(Be[fin_e], Bf[fin_f], rtol=1e-5)
+    else:
+        assert np.array_equal(Be, Bf)
+    rng = np.random.default_rng(47)
+    pairs = rng.integers(0, g.n, size=(4000, 2)).astype(np.int32)
+    if Be.dtype != np.float32:
+        assert_pairs_exact(he, g, pairs)
+    hf.free()
+    he.free()
+
+
 def test_elimination_profile_counts():
     m = spq()
     torch, dev = torch_dev()
