@@ -38,9 +38,9 @@ if ROOT not in sys.path:
 
 METRIC = "queries/s + build min-plus Gop/s (1M-vertex planar), vs INT32/HBM roofline, 1xGB300"
 # DRAM bytes (read + write) per min-plus update of k_backsub: ncu on the delaunay1m build
-# (dram__bytes_read.sum 132,176,508,160 + dram__bytes_write.sum 73,134,564,096 for one
+# (dram__bytes_read.sum 132,424,525,056 + dram__bytes_write.sum 73,164,538,368 for one
 # launch of 4.4525e12 updates; profiles/k_backsub_delaunay1m_dram.md)
-BACKSUB_BYTES_PER_UPDATE = (132176508160 + 73134564096) / 4.4525e12
+BACKSUB_BYTES_PER_UPDATE = (132424525056 + 73164538368) / 4.4525e12
 UNIT = "queries/s"
 
 
