@@ -118,6 +118,12 @@ typedef struct spq_opts {
     int32_t bg_panel_mib;   /* SPQ_BG_ELIM: most MiB of device scratch for the gathered
                                back-substitution panels at a time (the row blocks are
                                then done in several launches); 0 (default): 1024 */
+    int32_t comp_method;    /* spq_bg_method for the component tables APSP(C): SPQ_BG_FW
+                               blocked Floyd-Warshall; SPQ_BG_ELIM elimination +
+                               back-substitution in a nested-dissection order of each
+                               component (components of up to 4096 vertices; larger ones
+                               take Floyd-Warshall); SPQ_BG_AUTO (default, and what a
+                               struct_size ending before this field means): elimination */
 } spq_opts;
 
 /* Fill *opts with the defaults (also what opts == NULL means). */
@@ -339,7 +345,9 @@ spq_status spq_query_status(spq_handle* h, void* stream);
 void spq_free(spq_handle* h);
 
 /* Give the memory kept by that pool back to the device (like emptying a caching
- * allocator).  Synchronises the device.  Live handles are not affected. */
+ * allocator): the freed tables and the stream-ordered scratch of every entry point
+ * (build temporaries, query sort buffers), which the pool also serves and keeps.
+ * Synchronises the device.  Live handles are not affected. */
 void spq_release_cached_memory(void);
 
 /* Static English text for a status code. */

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -37,6 +38,7 @@ spq_status read_opts(const spq_opts* in, spq_opts* o) {
     if (o->arith < SPQ_ARITH_AUTO || o->arith > SPQ_ARITH_F32) return SPQ_EINVAL;
     if (o->order < SPQ_ORDER_AUTO || o->order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
     if (o->bg_method < SPQ_BG_AUTO || o->bg_method > SPQ_BG_ELIM || o->bg_panel_mib < 0) return SPQ_EINVAL;
+    if (o->comp_method < SPQ_BG_AUTO || o->comp_method > SPQ_BG_ELIM) return SPQ_EINVAL;
     return SPQ_OK;
 }
 }  // namespace spq
@@ -89,7 +91,7 @@ struct Temps {
     cudaError_t alloc(T** p, size_t count) {
         *p = nullptr;
         if (count == 0) count = 1;
-        cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), st);
+        cudaError_t e = scratch_alloc((void**)p, count * sizeof(T), st);
         if (e == cudaSuccess) ptrs.push_back((void*)*p);
         return e;
     }
@@ -146,6 +148,22 @@ void free_handle_memory(spq_handle* h) {
         if (p) cudaFreeAsync(p, 0);  // back to the pool
     cudaStreamSynchronize(0);
 }
+
+}  // namespace
+
+// Temporaries of every entry point come from the same pool as the tables, so that the
+// memory of one build or query batch is reused by the next instead of being unmapped at
+// each synchronisation and mapped again.
+cudaError_t spq::scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (e == cudaSuccess) e = table_pool(dev, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 4, pool, st);
+}
+
+namespace {
 
 template <typename T>
 cudaError_t dev_alloc(T** p, size_t count, size_t* total, cudaStream_t st) {
@@ -213,8 +231,10 @@ struct BgPlan {
 // boundary-graph assembly and its all-pairs distances.  Sets *inexact if a float32 table
 // holds a finite entry >= 2^24.
 // Component tables APSP(C) in element type T (queued on st; no host wait).
+// With elim, the components that comp_takes_elim selects by elimination in a dissection
+// order (waits on the host), the others by Floyd-Warshall.  Sets h->comp_updates.
 template <typename T>
-cudaError_t build_comp_tables(spq_handle* h, const BuildInputs& in, int32_t max_n, StageEvents& evs,
+cudaError_t build_comp_tables(spq_handle* h, const BuildInputs& in, int32_t max_n, bool elim, StageEvents& evs,
                               cudaStream_t st) {
     evs.mark(2, st);
     T* apsp = (T*)h->apsp;
@@ -223,7 +243,25 @@ cudaError_t build_comp_tables(spq_handle* h, const BuildInputs& in, int32_t max_
     if ((e = launch_scatter_intra<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->descs, apsp, st)) !=
         cudaSuccess)
         return e;
-    if ((e = fw_batched<T>(apsp, h->descs, h->h_descs.data(), h->k, max_n, st)) != cudaSuccess) return e;
+    std::vector<MatDesc> fwd = h->h_descs;  // the Floyd-Warshall set (others: n = 0, skipped)
+    double eu = 0.0;
+    if (elim) {
+        e = comp_tables_elim<T>(apsp, h->descs, h->h_descs, h->h_csize, h->k, in.n, in.rp, in.col, in.w, in.f32w,
+                                in.part, h->local, h->vorder, h->vstart, h->csize, &eu, st);
+        if (e != cudaSuccess) return e;
+        for (int32_t c = 0; c < h->k; ++c)
+            if (comp_takes_elim(h->h_csize[c], fwd[c].n)) fwd[c].n = 0;
+    }
+    int32_t max_fw = 0;
+    double cu = 0.0;
+    for (const MatDesc& d : fwd) {
+        max_fw = std::max(max_fw, d.n);
+        // per round: the diagonal tile, R - 1 row tiles, R(R - 1)/2 upper-triangle tiles
+        const double R = (double)((d.n + kTile - 1) / kTile);
+        cu += R * (1.0 + (R - 1.0) + R * (R - 1.0) / 2.0) * (double)kTile * kTile * kTile;
+    }
+    if (max_fw > 0 && (e = fw_batched<T>(apsp, h->descs, fwd.data(), h->k, max_fw, st)) != cudaSuccess) return e;
+    h->comp_updates = cu + eu;
     evs.mark(3, st);
     return cudaSuccess;
 }
@@ -414,7 +452,9 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const size_t elim_bytes =
         may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(n_max) + apanel_budget + 15 * 4 * (size_t)fw_words_max
                  : 0;
-    size_t need = 4 * (size_t)h->apsp_elems + 4 * (size_t)n_max * (size_t)n_max + 8 * (size_t)n +
+    // (+ the component tables in dissection order, a second copy, for their elimination)
+    const size_t comp_elim_bytes = opts.comp_method != SPQ_BG_FW ? 4 * (size_t)h->apsp_elems + 8 * (size_t)n : 0;
+    size_t need = 4 * (size_t)h->apsp_elems + comp_elim_bytes + 4 * (size_t)n_max * (size_t)n_max + 8 * (size_t)n +
                   (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words_max + hist_words) +
                   8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + (64u << 20);
     size_t free_b = 0, total_b = 0;
@@ -482,15 +522,30 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const bool prof = opts.profile_kernels != 0;
     // float32 arithmetic first (exact below 2^24, checked), int32 if asked or if the check fails
     const bool first_f32 = f32w || opts.arith != SPQ_ARITH_I32;
+    const bool comp_elim = opts.comp_method != SPQ_BG_FW;
+    // the boundary slots' order on a host thread meanwhile (the component elimination
+    // waits on the host for its own bookkeeping)
+    std::vector<int32_t> bgpos;
+    spq_status order_status = SPQ_OK;
+    std::thread order_thread;
+    if (h->nbg > 0)
+        order_thread = std::thread([&]() {
+            order_status = boundary_order_from(k, h->h_nb, bpairs, (spq_order)opts.order, &bgpos, &h->order_method,
+                                               may_elim ? &plan.layout : nullptr);
+        });
+    struct Join {
+        std::thread& t;
+        ~Join() {
+            if (t.joinable()) t.join();
+        }
+    } join_order{order_thread};
     if (first_f32)
-        CK(build_comp_tables<float>(h, in, max_n, evs, st));
+        CK(build_comp_tables<float>(h, in, max_n, comp_elim, evs, st));
     else
-        CK(build_comp_tables<int32_t>(h, in, max_n, evs, st));
+        CK(build_comp_tables<int32_t>(h, in, max_n, comp_elim, evs, st));
+    if (order_thread.joinable()) order_thread.join();
     if (h->nbg > 0) {
-        std::vector<int32_t> bgpos;
-        spq_status s = boundary_order_from(k, h->h_nb, bpairs, (spq_order)opts.order, &bgpos, &h->order_method,
-                                           may_elim ? &plan.layout : nullptr);
-        if (s != SPQ_OK) return s;
+        if (order_status != SPQ_OK) return order_status;
         CK(cudaMemcpyAsync(h->bgpos, bgpos.data(), bgpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));  // bgpos (host) goes out of scope
     }
@@ -529,18 +584,11 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         h->f32store = false;  // converted to int32 by the exactness check
         if (!first_f32 || inexact) {
             h->arith = SPQ_ARITH_I32;
-            if (inexact) CK(build_comp_tables<int32_t>(h, in, max_n, evs, st));
+            if (inexact) CK(build_comp_tables<int32_t>(h, in, max_n, comp_elim, evs, st));
             CK(build_bg_tables<int32_t>(h, in, false, skip, prof, d_flag, fw_scratch, plan, &inexact, evs, st));
             if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
     }
-    double cu = 0.0;
-    for (int32_t c = 0; c < k; ++c) {
-        // per round: the diagonal tile, R - 1 row tiles, R(R - 1)/2 upper-triangle tiles
-        double R = (double)((h->h_descs[c].n + kTile - 1) / kTile);
-        cu += R * (1.0 + (R - 1.0) + R * (R - 1.0) / 2.0) * (double)kTile * kTile * kTile;
-    }
-    h->comp_updates = cu;
     CK(cudaStreamSynchronize(st));
     evs.collect(h->prof_ms);
     return SPQ_OK;
@@ -560,6 +608,7 @@ void spq_opts_default(spq_opts* o) {
     o->query_grouped = 1;
     o->bg_method = SPQ_BG_AUTO;
     o->bg_panel_mib = 0;
+    o->comp_method = SPQ_BG_AUTO;
 }
 
 spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,

@@ -51,16 +51,20 @@ __global__ void k_fill_blocks(T* __restrict__ base, const MatDesc* __restrict__ 
     }
 }
 
-// Intra-component edges: APSP(C)[local u][local v] = min(., w(u, v)).
+// Intra-component edges: APSP(C)[local u][local v] = min(., w(u, v)).  With csize !=
+// NULL only the components of at most max_n vertices and more than min_ld rows, at the
+// positions `local` gives (a dissection order).
 template <typename T>
 __global__ void k_scatter_intra(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const void* __restrict__ w, bool f32w, const int32_t* __restrict__ part,
                                 const int32_t* __restrict__ local, const MatDesc* __restrict__ descs,
-                                T* __restrict__ apsp) {
+                                T* __restrict__ apsp, const int32_t* __restrict__ csize = nullptr, int32_t max_n = 0,
+                                int32_t min_ld = 0) {
     int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
     int32_t c = part[u];
     MatDesc d = descs[c];
+    if (csize && (csize[c] > max_n || d.n <= min_ld)) return;
     T* row = apsp + d.off + (int64_t)local[u] * d.n;
     for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
         int32_t v = col[e];
@@ -187,6 +191,16 @@ cudaError_t launch_scatter_intra(bool f32w, int32_t n, const int64_t* rp, const 
 }
 
 template <typename T>
+cudaError_t launch_scatter_intra_sel(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
+                                     const int32_t* part, const int32_t* pos, const MatDesc* descs,
+                                     const int32_t* csize, int32_t max_n, int32_t min_ld, T* apsp, cudaStream_t st) {
+    k_scatter_intra<T><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, w, f32w, part, pos, descs, apsp, csize, max_n,
+                                                          min_ld);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_bg_fill(T* D, int64_t N, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
     int64_t blocks = N < (int64_t)sm_count() * 16 ? N : (int64_t)sm_count() * 16;
@@ -230,6 +244,9 @@ cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStr
     template cudaError_t launch_fill_blocks<T>(T*, const MatDesc*, int32_t, cudaStream_t);                         \
     template cudaError_t launch_scatter_intra<T>(bool, int32_t, const int64_t*, const int32_t*, const void*,       \
                                                  const int32_t*, const int32_t*, const MatDesc*, T*, cudaStream_t); \
+    template cudaError_t launch_scatter_intra_sel<T>(bool, int32_t, const int64_t*, const int32_t*, const void*,   \
+                                                     const int32_t*, const int32_t*, const MatDesc*, const int32_t*, \
+                                                     int32_t, int32_t, T*, cudaStream_t);                          \
     template cudaError_t launch_bg_fill<T>(T*, int64_t, cudaStream_t);                                             \
     template cudaError_t launch_bg_clique<T>(const T*, const MatDesc*, const int32_t*, const int32_t*,           \
                                              const int32_t*, int32_t, T*, int64_t, cudaStream_t);                 \

@@ -73,7 +73,7 @@ struct TempList {
     template <typename T>
     cudaError_t alloc(T** p, size_t count) {
         *p = nullptr;
-        cudaError_t e = cudaMallocAsync((void**)p, (count ? count : 1) * sizeof(T), st);
+        cudaError_t e = scratch_alloc((void**)p, (count ? count : 1) * sizeof(T), st);
         if (e == cudaSuccess) ptrs.push_back((void*)*p);
         return e;
     }

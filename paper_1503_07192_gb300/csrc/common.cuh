@@ -48,6 +48,10 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Process-wide count of this library's kernel launches (read by spq_kernel_launches).
 void count_launches(int n);
+// Stream-ordered device scratch from the library's memory pool of the current device
+// (kept for reuse across calls; spq_release_cached_memory returns it).  Free with
+// cudaFreeAsync.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
 
 // Record a CUDA error for spq_last_cuda_error (entry points outside api.cu).
 void note_cuda_error(cudaError_t e);
@@ -92,6 +96,12 @@ template <typename T>
 cudaError_t launch_scatter_intra(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
                                  const int32_t* part, const int32_t* local, const MatDesc* descs, T* apsp,
                                  cudaStream_t st);
+// The same for the components of at most max_n vertices and more than min_ld rows only,
+// at the per-vertex positions pos.
+template <typename T>
+cudaError_t launch_scatter_intra_sel(bool f32w, int32_t n, const int64_t* rp, const int32_t* col, const void* w,
+                                     const int32_t* part, const int32_t* pos, const MatDesc* descs,
+                                     const int32_t* csize, int32_t max_n, int32_t min_ld, T* apsp, cudaStream_t st);
 template <typename T>
 cudaError_t launch_bg_fill(T* D, int64_t N, cudaStream_t st);
 template <typename T>
@@ -164,6 +174,21 @@ template <typename T>
 cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
                          double* updates, cudaStream_t st, bool trail = false);
 int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n);
+
+// ---- comp_nd.cu: component tables by elimination in a dissection order ----
+constexpr int32_t kNdMax = 4096;  // largest component ordered (one CTA each)
+// APSP(C) of the components of at most kNdMax vertices and more than one tile row, into
+// apsp (local order), after launch_fill_blocks / launch_scatter_intra of the same tables
+// (their contents there are replaced).  The other components are left to the caller.
+// Waits on the host for the back-substitution's bookkeeping and status.
+template <typename T>
+cudaError_t comp_tables_elim(T* apsp, const MatDesc* d_descs, const std::vector<MatDesc>& h_descs,
+                             const std::vector<int32_t>& h_csize, int32_t k, int32_t n, const int64_t* rp,
+                             const int32_t* col, const void* w, bool f32w, const int32_t* part, const int32_t* local,
+                             const int32_t* vorder, const int32_t* d_vstart, const int32_t* d_csize, double* updates,
+                             cudaStream_t st);
+// Whether component c takes the elimination form in comp_tables_elim.
+inline bool comp_takes_elim(int32_t csize, int32_t ld) { return csize <= kNdMax && ld > kTile; }
 
 // ---- query.cu ----
 template <typename T>

@@ -513,7 +513,7 @@ cudaError_t launch_mark_pairs(const std::vector<int32_t>& blocks, int64_t N, uin
     if (blocks.empty() || N <= 0) return cudaSuccess;
     const int32_t nR = (int32_t)((N + T_ - 1) / T_);
     int32_t* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, blocks.size() * sizeof(int32_t), st);
+    cudaError_t e = scratch_alloc((void**)&d, blocks.size() * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d, blocks.data(), blocks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
@@ -565,7 +565,7 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
     const size_t o_mats = (o_ctr + 8 + 15) & ~(size_t)15;
     const size_t bytes = o_mats + (size_t)nmat * sizeof(BsMat<T>);
     unsigned char* scratch = nullptr;
-    if ((e = cudaMallocAsync(&scratch, bytes, st)) != cudaSuccess) return e;
+    if ((e = scratch_alloc((void**)&scratch, bytes, st)) != cudaSuccess) return e;
     uint4* masks = reinterpret_cast<uint4*>(scratch);
     int32_t* fblk = reinterpret_cast<int32_t*>(scratch + o_fblk);
     uint32_t* tflags = reinterpret_cast<uint32_t*>(scratch + o_tfl);
@@ -615,7 +615,7 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
     const int64_t ktot = hoff[RR];
     if ((e = cudaMemcpyAsync(koff, hoff.data(), (size_t)RR * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return done(e);
-    if ((e = cudaMallocAsync(&klist, (size_t)(ktot > 0 ? ktot : 1) * 4, st)) != cudaSuccess) return done(e);
+    if ((e = scratch_alloc((void**)&klist, (size_t)(ktot > 0 ? ktot : 1) * 4, st)) != cudaSuccess) return done(e);
     k_klist<T><<<dim3(nRmax, nmat), T_, 0, st>>>(mats, masks, fblk, fcnt, kcnt, koff, klist);
     count_launches(1);
     // Launches whose A panels fit the budget: whole matrices side by side, or (a matrix
@@ -680,7 +680,8 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
     if ((e = cudaMemcpyAsync(runs, hruns.data(), hruns.size() * sizeof(BsRun), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return done(e);
-    if ((e = cudaMallocAsync(&A, (size_t)(maxk > 0 ? maxk : 1) * row_bytes, st)) != cudaSuccess) return done(e);
+    if ((e = scratch_alloc((void**)&A, (size_t)(maxk > 0 ? maxk : 1) * row_bytes, st)) != cudaSuccess)
+        return done(e);
     if (prof) {
         ev.assign(2 * launches.size(), nullptr);
         for (auto& x : ev)

@@ -584,7 +584,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
         }
     }
     int32_t* d_buf = nullptr;
-    e = cudaMallocAsync(&d_buf, buf.size() * sizeof(int32_t), st);
+    e = scratch_alloc((void**)&d_buf, buf.size() * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_buf, buf.data(), buf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     const size_t psm = sizeof(PanelSmem<T>);
@@ -628,7 +628,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
     if (e != cudaSuccess) return e;
     MatDesc h{0, (int32_t)N, 0};
     MatDesc* dd = nullptr;
-    e = cudaMallocAsync(&dd, sizeof(MatDesc), st);
+    e = scratch_alloc((void**)&dd, sizeof(MatDesc), st);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(dd, &h, sizeof(MatDesc), cudaMemcpyHostToDevice, st);
     const size_t psm = sizeof(PanelSmem<T>);
@@ -654,7 +654,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
     std::vector<cudaEvent_t> done(nrun, nullptr);
     cudaEvent_t start_ev = nullptr;
     if (nrun > 0) {
-        if (e == cudaSuccess) e = cudaMallocAsync(&run_scratch, nrun * rw * sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = scratch_alloc((void**)&run_scratch, nrun * rw * sizeof(uint32_t), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(run_scratch, 0, nrun * rw * sizeof(uint32_t), st);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(start_ev, st);

@@ -715,7 +715,7 @@ spq_status boundary_pairs(int32_t n, int64_t m, const int64_t* d_rp, const int32
     uint32_t *keys = nullptr, *vals = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr, *cnt = nullptr;
     const int64_t hist_words = radix_hist_words(m);
     auto A = [&](uint32_t** p, size_t c) {
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)p, (c ? c : 1) * sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = scratch_alloc((void**)p, (c ? c : 1) * sizeof(uint32_t), st);
     };
     A(&keys, m);
     A(&vals, m);
@@ -842,7 +842,7 @@ cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t c
     const bool od = dev_ptr(out);
     uint32_t* dst = (uint32_t*)out;
     cudaError_t e = cudaSuccess;
-    if (!od) e = cudaMallocAsync((void**)&dst, (size_t)(rows * cols) * 4, st);
+    if (!od) e = scratch_alloc((void**)&dst, (size_t)(rows * cols) * 4, st);
     if (e != cudaSuccess) return e;
     int64_t blocks = rows < 65535 ? rows : 65535;
     if (pos) {

@@ -290,7 +290,7 @@ extern "C" spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, in
     if (smem > 200 * 1024) return SPQ_EUNSUPPORTED;  // a component with more than ~6,000 boundary vertices
     std::vector<void*> tmp;
     auto alloc = [&](void** p, size_t bytes) {
-        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 4, st);
+        cudaError_t e = scratch_alloc(p, bytes ? bytes : 4, st);
         if (e == cudaSuccess) tmp.push_back(*p);
         return e;
     };

@@ -411,6 +411,74 @@ def test_elimination_of_a_disconnected_boundary_graph(weight, arith):
     he.free()
 
 
+def _mixed_components(weight, seed):
+    """Delaunay kd-tree components of assorted sizes: most of several tiles, one merged
+    from two far-apart leaves (disconnected), a few below one tile, and one merged from
+    many leaves above the 4,096 vertices the dissection kernel orders (Floyd-Warshall)."""
+    g = gen.delaunay(24000, seed=seed, weight=weight, scale=float(np.sqrt(24000)))
+    part, k = gen.kdtree(g.xy, 1400)
+    part = part.copy()
+    part[part == k - 1] = 0                 # two far-apart leaves: a disconnected component
+    part[np.isin(part, [1, 2, 3, 4, 5, 6])] = 1  # one large component
+    rng = np.random.default_rng(seed)
+    small = np.nonzero(part == 7)[0]
+    part[small[:90]] = k - 1                # a component below one tile
+    sizes = np.bincount(part, minlength=k)
+    assert sizes.max() > 4096 and (sizes[sizes > 0] < 128).any() and (sizes > 128).sum() > 5
+    return g, part, k, rng
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_component_elimination_equals_floyd_warshall(arith):
+    """APSP(C) by elimination + back-substitution in a level-structure dissection order
+    of each component equals the blocked Floyd-Warshall tables bit for bit (integer
+    weights, float32 or int32 arithmetic), and the distances are the oracle's."""
+    g, part, k, rng = _mixed_components("int_1e6", 53)
+    hf = build(g, part, k, arith=arith, comp=1)
+    he = build(g, part, k, arith=arith, comp=2)
+    for c in range(k):
+        assert np.array_equal(hf.apsp(c), he.apsp(c)), c
+    assert np.array_equal(hf.bg(), he.bg())
+    # updates: the same Floyd-Warshall count for the component above the ordering limit
+    # in both builds; the others by elimination well below Floyd-Warshall's
+    sizes = np.bincount(part, minlength=k)
+    R = (np.ceil(sizes / 4) * 4 + 127) // 128
+    fw_each = R * (1 + (R - 1) + R * (R - 1) / 2) * 128.0 ** 3
+    big = fw_each[sizes > 4096].sum() + fw_each[(sizes > 0) & (np.ceil(sizes / 4) * 4 <= 128)].sum()
+    su, sf = he.stats()["comp_updates"], hf.stats()["comp_updates"]
+    assert sf == pytest.approx(fw_each.sum())
+    assert 0 < su - big < 0.6 * (sf - big)
+    # rows of the disconnected component and of the one below a tile against Dijkstra
+    # inside the component
+    local = he.meta()["local"]
+    for c in (0, k - 1):
+        ids = np.nonzero(part == c)[0]
+        order = ids[np.argsort(local[ids])]
+        A = he.apsp(c)
+        for li in rng.choice(ids.size, 12, replace=False):
+            ref = oracle_i32(oracle.subgraph_sssp(g.row_ptr, g.col, g.w, part, c, int(order[li])))
+            assert np.array_equal(A[li].astype(np.int64), ref[order]), (c, li)
+    pairs = rng.integers(0, g.n, size=(20000, 2)).astype(np.int32)
+    assert_pairs_exact(he, g, pairs)
+    hf.free()
+    he.free()
+
+
+def test_component_elimination_float_weights():
+    g, part, k, rng = _mixed_components("f32_lognormal", 59)
+    hf = build(g, part, k, comp=1)
+    he = build(g, part, k, comp=2)
+    for c in range(k):
+        a, b = hf.apsp(c), he.apsp(c)
+        assert np.array_equal(np.isinf(a), np.isinf(b)), c
+        np.testing.assert_allclose(b[np.isfinite(b)], a[np.isfinite(a)], rtol=1e-5)
+    pairs = rng.integers(0, g.n, size=(5000, 2)).astype(np.int32)
+    exact = oracle.pairs_dist_f64(g.row_ptr, g.col, g.w.astype(np.float64), pairs)
+    np.testing.assert_allclose(query(he, pairs), exact, rtol=2e-5)
+    hf.free()
+    he.free()
+
+
 def test_elimination_profile_counts():
     m = spq()
     torch, dev = torch_dev()
