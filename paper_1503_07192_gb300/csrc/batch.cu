@@ -151,13 +151,34 @@ struct BatchElim {
     size_t panel_cap = 0;
 };
 
+// The components whose tables take the elimination form (comp_takes_elim) across the
+// batch: their global indices and descriptors, per-component vertex starts (within the
+// instance and in the batch), the sorted vertex array, and the scratch of the dissection
+// order and of the tables in that order.
+struct CompElim {
+    int32_t nsel = 0;
+    std::vector<MatDesc> ed;           // global descriptors of the selected components
+    int32_t* d_sel = nullptr;
+    MatDesc* d_ed = nullptr;
+    int32_t* vstart_local = nullptr;   // [ktot]: start of component c in its instance
+    int32_t* vstart_global = nullptr;  // [ktot]: the same in the batch's sorted order
+    const int32_t* sorted_v = nullptr; // [ntot]: batch vertex ids by (component, local)
+    int32_t* ndpos = nullptr;          // [ntot]
+    int32_t* vpos = nullptr;           // [ntot]
+    void* P = nullptr;                 // the component tables in dissection order
+    NdGraph* d_graphs = nullptr;       // [G]: the instances' CSR and numbering offsets
+    int32_t* d_cgraph = nullptr;       // [ktot]: instance of each component
+    int64_t ktot = 0;
+};
+
 // Tables of every instance in element type T (Algorithm 1 after the reordering).
 template <typename T>
 cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs,
                          const MatDesc* h_cdescs, int64_t ktot,
                          int32_t max_ld, const MatDesc* d_bdescs, int32_t nbmat, int32_t max_N, bool f32w,
                          uint32_t* fw_scratch, uint32_t* d_flag, bool check, bool* inexact, double* bg_updates,
-                         const BatchElim& be, cudaEvent_t* ev, cudaStream_t st) {
+                         const BatchElim& be, const CompElim& ce, double* comp_elim_updates, cudaEvent_t* ev,
+                         cudaStream_t st) {
     *inexact = false;
     T* base = reinterpret_cast<T*>(P.tables);
     cudaError_t e;
@@ -169,7 +190,29 @@ cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc
                                     base + x.apsp_off, st);
         if (e != cudaSuccess) return e;
     }
-    if ((e = fw_batched<T>(base, d_cdescs, h_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess) return e;
+    // component tables: the elimination form for those selected (dissection order per
+    // instance, then the elimination of all of them at once), Floyd-Warshall for the rest
+    // (h_cdescs holds n = 0 for the selected ones)
+    *comp_elim_updates = 0.0;
+    if (ce.nsel > 0) {
+        T* Pc = reinterpret_cast<T*>(ce.P);
+        if ((e = launch_fill_blocks<T>(Pc, ce.d_ed, ce.nsel, st)) != cudaSuccess) return e;
+        e = comp_nd_order(ce.d_graphs, ce.d_cgraph, P.local, ce.sorted_v, ce.vstart_global, P.csize,
+                          (int32_t)ce.ktot, ce.ndpos, st);
+        if (e != cudaSuccess) return e;
+        for (auto& x : I) {
+            if (x.n == 0) continue;
+            e = comp_nd_scatter<T>(Pc + x.apsp_off, P.descs + x.kbase, x.n, x.rp, x.col, x.w, f32w, x.part,
+                                   P.local + x.vbase, ce.vstart_local + x.kbase, P.csize + x.kbase,
+                                   ce.ndpos + x.vbase, ce.vpos + x.vbase, st);
+            if (e != cudaSuccess) return e;
+        }
+        e = comp_elim_finish<T>(base, Pc, d_cdescs, ce.ed, ce.d_sel, ce.d_ed, P.csize, ce.vstart_global, ce.ndpos,
+                                comp_elim_updates, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (max_ld > 0 && (e = fw_batched<T>(base, d_cdescs, h_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess)
+        return e;
     cudaEventRecord(ev[3], st);
     for (auto& x : I) {
         if (x.N == 0) continue;
@@ -397,8 +440,10 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     const size_t o_tables = take(4 * (size_t)table_elems);
     const size_t arena_bytes = off;
     const int64_t fw_words = nbmat > 0 ? fw_many_scratch_words(nbmat, max_N) : 1;
+    const bool comp_elim = o.comp_method != SPQ_BG_FW;
     const size_t temp_bytes = 16 * (size_t)ntot + 4 * (size_t)radix_hist_words(ntot) + 12 * (size_t)mtot +
-                              4 * (size_t)fw_words + (64u << 20);
+                              4 * (size_t)fw_words + (64u << 20) +
+                              (comp_elim ? 4 * (size_t)apsp_tot + 16 * (size_t)ntot : 0);
     size_t free_b = 0, total_b = 0;
     BCK(cudaMemGetInfo(&free_b, &total_b));
     if (arena_bytes + temp_bytes > free_b) return SPQ_ENOMEM;
@@ -444,6 +489,7 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     }
 
     // ---- one stable sort of every instance's vertices by (global component, interior) ----
+    const uint32_t* sorted_v = nullptr;  // (kept for the components' dissection order)
     {
         uint32_t *k0, *v0, *k1, *v1, *hist;
         BCK(tmp.alloc(&k0, (size_t)ntot));
@@ -474,6 +520,7 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         BCK(tmp.alloc(&d_ckbase, (size_t)ktot));
         BCK(cudaMemcpyAsync(d_cstart, cstart.data(), (size_t)ktot * 8, cudaMemcpyHostToDevice, st));
         BCK(cudaMemcpyAsync(d_ckbase, ckbase.data(), (size_t)ktot * 4, cudaMemcpyHostToDevice, st));
+        sorted_v = in_k1 ? v1 : v0;
         k_assign_local_many<<<(unsigned)((ntot + 255) / 256), 256, 0, st>>>(
             ntot, in_k1 ? k1 : k0, in_k1 ? v1 : v0, d_cstart, d_ckbase, P.local, P.comp);
         count_launches(1);
@@ -559,6 +606,62 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     // ---- tables of every instance ----
     std::vector<MatDesc> cd, bd, ed;
     cd.reserve(ktot);
+    // components by elimination (selected), the others by Floyd-Warshall (cd_fw: n = 0
+    // for the selected ones)
+    CompElim ce;
+    std::vector<MatDesc> cd_fw;
+    int32_t max_ld_fw = 0;
+    double comp_fw_updates = 0.0;
+    {
+        std::vector<int32_t> vsl(ktot), vsg(ktot), sel, cgraph(ktot);
+        std::vector<NdGraph> graphs;
+        for (auto& x : I) {
+            graphs.push_back(NdGraph{x.rp, x.col, x.part, (int32_t)x.vbase, (int32_t)x.kbase});
+            for (int32_t c = 0; c < x.k; ++c) cgraph[x.kbase + c] = (int32_t)(&x - I.data());
+            int32_t acc = 0;
+            for (int32_t c = 0; c < x.k; ++c) {
+                const MatDesc d = x.descs[c];
+                vsl[x.kbase + c] = acc;
+                vsg[x.kbase + c] = (int32_t)x.vbase + acc;
+                acc += x.csize[c];
+                const MatDesc g{x.apsp_off + d.off, d.n, 0};
+                if (comp_elim && comp_takes_elim(x.csize[c], d.n)) {
+                    sel.push_back((int32_t)(x.kbase + c));
+                    ce.ed.push_back(g);
+                    cd_fw.push_back(MatDesc{g.off, 0, 0});
+                } else {
+                    cd_fw.push_back(g);
+                    max_ld_fw = std::max(max_ld_fw, d.n);
+                    const double R = (double)((d.n + kTile - 1) / kTile);
+                    comp_fw_updates += R * (1.0 + (R - 1.0) + R * (R - 1.0) / 2.0) * (double)kTile * kTile * kTile;
+                }
+            }
+        }
+        ce.nsel = (int32_t)sel.size();
+        if (ce.nsel > 0) {
+            BCK(tmp.alloc(&ce.d_sel, sel.size()));
+            BCK(tmp.alloc(&ce.d_ed, ce.ed.size()));
+            BCK(tmp.alloc(&ce.vstart_local, (size_t)ktot));
+            BCK(tmp.alloc(&ce.vstart_global, (size_t)ktot));
+            BCK(tmp.alloc(&ce.ndpos, (size_t)ntot));
+            BCK(tmp.alloc(&ce.vpos, (size_t)ntot));
+            uint32_t* pc = nullptr;
+            BCK(tmp.alloc(&pc, (size_t)apsp_tot));
+            ce.P = pc;
+            ce.sorted_v = reinterpret_cast<const int32_t*>(sorted_v);
+            BCK(cudaMemcpyAsync(ce.d_sel, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice, st));
+            BCK(cudaMemcpyAsync(ce.d_ed, ce.ed.data(), ce.ed.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+            BCK(cudaMemcpyAsync(ce.vstart_local, vsl.data(), (size_t)ktot * 4, cudaMemcpyHostToDevice, st));
+            BCK(cudaMemcpyAsync(ce.vstart_global, vsg.data(), (size_t)ktot * 4, cudaMemcpyHostToDevice, st));
+            BCK(tmp.alloc(&ce.d_graphs, graphs.size()));
+            BCK(tmp.alloc(&ce.d_cgraph, (size_t)ktot));
+            BCK(cudaMemcpyAsync(ce.d_graphs, graphs.data(), graphs.size() * sizeof(NdGraph), cudaMemcpyHostToDevice,
+                                st));
+            BCK(cudaMemcpyAsync(ce.d_cgraph, cgraph.data(), (size_t)ktot * 4, cudaMemcpyHostToDevice, st));
+            ce.ktot = ktot;
+            BCK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+        }
+    }
     for (auto& x : I) {
         for (const MatDesc& d : x.descs) cd.push_back(MatDesc{x.apsp_off + d.off, d.n, 0});
         if (x.N > 0) (x.elim ? ed : bd).push_back(MatDesc{x.d_off, (int32_t)x.N, 0});
@@ -586,26 +689,26 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     BCK(tmp.alloc(&d_flag, 1));
     BCK(cudaMemcpyAsync(d_cd, cd.data(), cd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
     if (!bd.empty()) BCK(cudaMemcpyAsync(d_bd, bd.data(), bd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
-    double bg_updates = 0.0;
+    double bg_updates = 0.0, comp_elim_updates = 0.0;
     bool f32store = false;
     int32_t arith = SPQ_ARITH_I32;
     bool inexact = false;
     if (f32w) {
         f32store = true;
         arith = SPQ_ARITH_F32;
-        BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, (int32_t)bd.size(), max_N_fw, true, fw_scratch, d_flag,
-                                false, &inexact, &bg_updates, be, ev, st));
+        BCK(batch_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, d_bd, (int32_t)bd.size(), max_N_fw, true, fw_scratch, d_flag,
+                                false, &inexact, &bg_updates, be, ce, &comp_elim_updates, ev, st));
     } else {
         const bool try_f32 = o.arith != SPQ_ARITH_I32;
         if (try_f32) {
             arith = SPQ_ARITH_F32;
-            BCK(batch_tables<float>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
-                                    d_flag, true, &inexact, &bg_updates, be, ev, st));
+            BCK(batch_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
+                                    d_flag, true, &inexact, &bg_updates, be, ce, &comp_elim_updates, ev, st));
         }
         if (!try_f32 || inexact) {
             arith = SPQ_ARITH_I32;
-            BCK(batch_tables<int32_t>(I, P, d_cd, cd.data(), ktot, max_ld, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
-                                      d_flag, false, &inexact, &bg_updates, be, ev, st));
+            BCK(batch_tables<int32_t>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
+                                      d_flag, false, &inexact, &bg_updates, be, ce, &comp_elim_updates, ev, st));
         }
     }
     BCK(cudaStreamSynchronize(st));
@@ -664,12 +767,7 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         h->nbg = x.nbg;
         h->apsp_elems = x.apsp_elems;
         h->bytes = 4 * (size_t)(x.apsp_elems + x.N * x.N) + 8 * (size_t)x.n + 16 * (size_t)x.k + 4 * (size_t)x.nbg;
-        double cu = 0.0;
-        for (const MatDesc& d : x.descs) {
-            const double R = (double)((d.n + kTile - 1) / kTile);
-            cu += R * (1.0 + (R - 1.0) + R * (R - 1.0) / 2.0) * (double)kTile * kTile * kTile;
-        }
-        h->comp_updates = cu;
+        h->comp_updates = comp_fw_updates + comp_elim_updates;  // the whole batch's component updates
         h->bg_updates = bg_updates;  // the whole batch's boundary-graph updates
         for (int i = 0; i < 6; ++i) h->prof_ms[i] = prof[i];
         h->h_csize = x.csize;

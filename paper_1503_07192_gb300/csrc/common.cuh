@@ -187,6 +187,30 @@ cudaError_t comp_tables_elim(T* apsp, const MatDesc* d_descs, const std::vector<
                              const int32_t* col, const void* w, bool f32w, const int32_t* part, const int32_t* local,
                              const int32_t* vorder, const int32_t* d_vstart, const int32_t* d_csize, double* updates,
                              cudaStream_t st);
+// The parts of comp_tables_elim for several graphs sharing one elimination: the
+// dissection order of every component of every graph (one launch; ndpos at vstart[c] + v
+// in the batch-wide numbering); per graph, each vertex's position and the scatter of its
+// edges into P (the tables in that order, offsets as in d_descs); then, once for all of
+// them, the elimination of the selected tables ed (global descriptors; d_sel their
+// component indices) and their permutation back into apsp.
+struct NdGraph {
+    const int64_t* rp;
+    const int32_t* col;
+    const int32_t* part;
+    int32_t vbase, kbase;  // its first vertex / component in the batch-wide numbering
+};
+cudaError_t comp_nd_order(const NdGraph* d_graphs, const int32_t* d_cgraph, const int32_t* local,
+                          const int32_t* vorder, const int32_t* d_vstart, const int32_t* d_csize, int32_t k,
+                          int32_t* ndpos, cudaStream_t st);
+template <typename T>
+cudaError_t comp_nd_scatter(T* P, const MatDesc* d_descs, int32_t n, const int64_t* rp, const int32_t* col,
+                            const void* w, bool f32w, const int32_t* part, const int32_t* local,
+                            const int32_t* d_vstart, const int32_t* d_csize, const int32_t* ndpos, int32_t* vpos,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t comp_elim_finish(T* apsp, T* P, const MatDesc* d_descs, const std::vector<MatDesc>& ed,
+                             const int32_t* d_sel, const MatDesc* d_ed, const int32_t* d_csize,
+                             const int32_t* d_vstart, const int32_t* ndpos, double* updates, cudaStream_t st);
 // Whether component c takes the elimination form in comp_tables_elim.
 inline bool comp_takes_elim(int32_t csize, int32_t ld) { return csize <= kNdMax && ld > kTile; }
 

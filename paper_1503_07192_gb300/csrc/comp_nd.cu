@@ -45,7 +45,8 @@ __constant__ int8_t c_post[16] = {-1, 14, 6, 13, 2, 5, 9, 12, 0, 1, 3, 4, 7, 8, 
 // have been reached, or (fewer reached: a disconnected piece) its last level.
 __device__ void nd_bfs(int32_t c, int32_t nc, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                        const int32_t* __restrict__ part, const int32_t* __restrict__ local,
-                       const int32_t* __restrict__ verts, const uint8_t* node, uint16_t* lev, const int32_t* src,
+                       const int32_t* __restrict__ verts, int32_t voff, const uint8_t* node, uint16_t* lev,
+                       const int32_t* src,
                        const int32_t* size, int lo, int hi, int32_t* fcnt, int32_t* cum, int32_t* last,
                        int32_t* half) {
     const int tid = threadIdx.x;
@@ -66,7 +67,7 @@ __device__ void nd_bfs(int32_t c, int32_t nc, const int64_t* __restrict__ rp, co
             if (lev[v] != (uint16_t)cur) continue;
             const int x = node[v];
             atomicAdd(&fcnt[x], 1);
-            const int32_t g = verts[v];
+            const int32_t g = verts[v] - voff;
             for (int64_t e = rp[g]; e < rp[g + 1]; ++e) {
                 const int32_t u = col[e];
                 if (part[u] != c) continue;
@@ -93,8 +94,12 @@ __device__ void nd_bfs(int32_t c, int32_t nc, const int64_t* __restrict__ rp, co
 
 // Dissection order of component blockIdx.x (grid-strided): ndpos[vstart[c] + v] = the
 // position of local vertex v.  Components outside [min_n, max_n] keep the local order.
-__global__ void __launch_bounds__(kNdThreads) k_comp_nd(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                        const int32_t* __restrict__ part,
+// The components may belong to several graphs (a batch): component c is component
+// c - kbase of graphs[cgraph[c]] (cgraph null: one graph), whose vertices are numbered
+// from vbase in vorder and local; vorder[vstart[c] + v] - vbase = the vertex (an index
+// into that graph's rp) of local index v.
+__global__ void __launch_bounds__(kNdThreads) k_comp_nd(const NdGraph* __restrict__ graphs,
+                                                        const int32_t* __restrict__ cgraph,
                                                         const int32_t* __restrict__ local,
                                                         const int32_t* __restrict__ vorder,
                                                         const int32_t* __restrict__ vstart,
@@ -106,10 +111,17 @@ __global__ void __launch_bounds__(kNdThreads) k_comp_nd(const int64_t* __restric
     __shared__ int32_t size[16], src[16], fcnt[16], cum[16], last[16], half[16], off[16];
     __shared__ unsigned long long far[16];
     const int tid = threadIdx.x;
-    for (int32_t c = blockIdx.x; c < k; c += gridDim.x) {
-        const int32_t nc = csize[c];
-        const int32_t* verts = vorder + vstart[c];
-        int32_t* out = ndpos + vstart[c];
+    for (int32_t cg = blockIdx.x; cg < k; cg += gridDim.x) {
+        const NdGraph gr = graphs[cgraph ? cgraph[cg] : 0];
+        const int64_t* __restrict__ rp = gr.rp;
+        const int32_t* __restrict__ col = gr.col;
+        const int32_t* __restrict__ part = gr.part;
+        const int32_t voff = gr.vbase;
+        const int32_t c = cg - gr.kbase;  // the component's id in its graph
+        const int32_t* glocal = local + gr.vbase;
+        const int32_t nc = csize[cg];
+        const int32_t* verts = vorder + vstart[cg];
+        int32_t* out = ndpos + vstart[cg];
         if (nc < min_n || nc > max_n) {
             for (int32_t v = tid; v < nc; v += kNdThreads) out[v] = v;
             continue;
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(kNdThreads) k_comp_nd(const int64_t* __restric
             }
             __syncthreads();
             // pseudo-peripheral start: the farthest vertex from the lowest-index one
-            nd_bfs(c, nc, rp, col, part, local, verts, node, lev, src, size, lo, hi, fcnt, cum, last, nullptr);
+            nd_bfs(c, nc, rp, col, part, glocal, verts, voff, node, lev, src, size, lo, hi, fcnt, cum, last, nullptr);
             for (int32_t v = tid; v < nc; v += kNdThreads) {
                 const int x = node[v];
                 if (x >= lo && x < hi && lev[v] != kUnset)
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(kNdThreads) k_comp_nd(const int64_t* __restric
             __syncthreads();
             if (tid >= lo && tid < hi && size[tid] >= kNdMinSplit) src[tid] = (int32_t)(0xffffffffu - (uint32_t)(far[tid] & 0xffffffffull));
             __syncthreads();
-            nd_bfs(c, nc, rp, col, part, local, verts, node, lev, src, size, lo, hi, fcnt, cum, last, half);
+            nd_bfs(c, nc, rp, col, part, glocal, verts, voff, node, lev, src, size, lo, hi, fcnt, cum, last, half);
             // split: separator (level L with a neighbour at L + 1) stays in x, the rest
             // moves to 2x (levels <= L) or 2x + 1 (levels > L, or not reached)
             for (int32_t v = tid; v < nc; v += kNdThreads) {
@@ -155,11 +167,11 @@ __global__ void __launch_bounds__(kNdThreads) k_comp_nd(const int64_t* __restric
                     } else {
                         bool sep = false;
                         if (lv == L) {
-                            const int32_t g = verts[v];
+                            const int32_t g = verts[v] - voff;
                             for (int64_t e = rp[g]; e < rp[g + 1] && !sep; ++e) {
                                 const int32_t u = col[e];
                                 if (part[u] != c) continue;
-                                const int32_t lu = local[u];
+                                const int32_t lu = glocal[u];
                                 sep = node[lu] == x && lev[lu] == (uint16_t)(L + 1);
                             }
                         }
@@ -223,6 +235,67 @@ __global__ void __launch_bounds__(256) k_unpermute(T* __restrict__ A, const T* _
 
 }  // namespace
 
+cudaError_t comp_nd_order(const NdGraph* d_graphs, const int32_t* d_cgraph, const int32_t* local,
+                          const int32_t* vorder, const int32_t* d_vstart, const int32_t* d_csize, int32_t k,
+                          int32_t* ndpos, cudaStream_t st) {
+    if (k <= 0) return cudaSuccess;
+    k_comp_nd<<<std::min<int32_t>(k, 65535), kNdThreads, 0, st>>>(d_graphs, d_cgraph, local, vorder, d_vstart, d_csize,
+                                                                  k, kTile + 1, kNdMax, ndpos);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t comp_nd_scatter(T* P, const MatDesc* d_descs, int32_t n, const int64_t* rp, const int32_t* col,
+                            const void* w, bool f32w, const int32_t* part, const int32_t* local,
+                            const int32_t* d_vstart, const int32_t* d_csize, const int32_t* ndpos, int32_t* vpos,
+                            cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_vertex_ndpos<<<(n + 255) / 256, 256, 0, st>>>(n, part, local, d_vstart, ndpos, vpos);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_scatter_intra_sel<T>(f32w, n, rp, col, w, part, vpos, d_descs, d_csize, kNdMax, kTile, P, st);
+}
+
+template <typename T>
+cudaError_t comp_elim_finish(T* apsp, T* P, const MatDesc* d_descs, const std::vector<MatDesc>& ed,
+                             const int32_t* d_sel, const MatDesc* d_ed, const int32_t* d_csize,
+                             const int32_t* d_vstart, const int32_t* ndpos, double* updates, cudaStream_t st) {
+    if (updates) *updates = 0.0;
+    if (ed.empty()) return cudaSuccess;
+    int32_t max_el = 0;
+    for (const MatDesc& d : ed) max_el = std::max(max_el, d.n);
+    uint32_t *scratch = nullptr, *err = nullptr;
+    cudaError_t e = scratch_alloc((void**)&scratch, (size_t)fw_many_scratch_words((int32_t)ed.size(), max_el) * 4, st);
+    if (e == cudaSuccess) e = scratch_alloc((void**)&err, 4, st);
+    auto done = [&](cudaError_t r) {
+        if (scratch) cudaFreeAsync(scratch, st);
+        if (err) cudaFreeAsync(err, st);
+        return r;
+    };
+    if (e != cudaSuccess) return done(e);
+    if ((e = cudaMemsetAsync(err, 0, 4, st)) != cudaSuccess) return done(e);
+    // forward rounds of all the tables in shared launches, then one back-substitution
+    double fwd = 0.0, bs = 0.0;
+    if ((e = fw_many_skip<T>(P, d_ed, (int32_t)ed.size(), max_el, scratch, &fwd, st, true)) != cudaSuccess)
+        return done(e);
+    std::vector<BsInput<T>> bin;
+    for (const MatDesc& d : ed) bin.push_back(BsInput<T>{P + d.off, (int64_t)d.n, nullptr});
+    if ((e = bg_backsub_many<T>(bin, err, nullptr, (size_t)2 << 30, &bs, nullptr, st)) != cudaSuccess) return done(e);
+    // back to the local order
+    const dim3 g((unsigned)max_el, (unsigned)std::min<size_t>(ed.size(), 65535));
+    k_unpermute<T><<<g, 256, 0, st>>>(apsp, P, d_descs, d_sel, (int32_t)ed.size(), d_csize, d_vstart, ndpos);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
+    uint32_t f = 0;
+    if ((e = cudaMemcpyAsync(&f, err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
+    if (f & kErrWait) return done(cudaErrorLaunchTimeout);
+    if (updates) *updates = fwd + bs;
+    return done(cudaSuccess);
+}
+
 template <typename T>
 cudaError_t comp_tables_elim(T* apsp, const MatDesc* d_descs, const std::vector<MatDesc>& h_descs,
                              const std::vector<int32_t>& h_csize, int32_t k, int32_t n, const int64_t* rp,
@@ -234,30 +307,27 @@ cudaError_t comp_tables_elim(T* apsp, const MatDesc* d_descs, const std::vector<
     // elimination form; the others Floyd-Warshall (after this call, by the caller)
     std::vector<int32_t> sel;
     std::vector<MatDesc> ed;
-    int32_t max_el = 0;
     int64_t pelems = 0;  // the tables in dissection order share the offsets of apsp
     for (int32_t c = 0; c < k; ++c)
         if (comp_takes_elim(h_csize[c], h_descs[c].n)) {
             sel.push_back(c);
             ed.push_back(h_descs[c]);
-            max_el = std::max(max_el, h_descs[c].n);
             pelems = std::max(pelems, h_descs[c].off + (int64_t)h_descs[c].n * h_descs[c].n);
         }
     if (sel.empty()) return cudaSuccess;
     T* P = nullptr;
     int32_t *ndpos = nullptr, *vpos = nullptr, *d_sel = nullptr;
     MatDesc* d_ed = nullptr;
-    uint32_t *scratch = nullptr, *err = nullptr;
-    const int64_t sw = fw_many_scratch_words((int32_t)ed.size(), max_el);
+    NdGraph* d_graph = nullptr;
+    const NdGraph hg{rp, col, part, 0, 0};
     cudaError_t e = scratch_alloc((void**)&P, (size_t)pelems * sizeof(T), st);
+    if (e == cudaSuccess) e = scratch_alloc((void**)&d_graph, sizeof(NdGraph), st);
     if (e == cudaSuccess) e = scratch_alloc((void**)&ndpos, (size_t)n * 4, st);
     if (e == cudaSuccess) e = scratch_alloc((void**)&vpos, (size_t)n * 4, st);
     if (e == cudaSuccess) e = scratch_alloc((void**)&d_sel, sel.size() * 4, st);
     if (e == cudaSuccess) e = scratch_alloc((void**)&d_ed, ed.size() * sizeof(MatDesc), st);
-    if (e == cudaSuccess) e = scratch_alloc((void**)&scratch, (size_t)sw * 4, st);
-    if (e == cudaSuccess) e = scratch_alloc((void**)&err, 4, st);
     auto done = [&](cudaError_t r) {
-        for (void* p : {(void*)P, (void*)ndpos, (void*)vpos, (void*)d_sel, (void*)d_ed, (void*)scratch, (void*)err})
+        for (void* p : {(void*)P, (void*)ndpos, (void*)vpos, (void*)d_sel, (void*)d_ed, (void*)d_graph})
             if (p) cudaFreeAsync(p, st);
         return r;
     };
@@ -267,40 +337,30 @@ cudaError_t comp_tables_elim(T* apsp, const MatDesc* d_descs, const std::vector<
     if ((e = cudaMemcpyAsync(d_ed, ed.data(), ed.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return done(e);
-    if ((e = cudaMemsetAsync(err, 0, 4, st)) != cudaSuccess) return done(e);
-    // dissection order of every selected component; the tables assembled in that order
-    k_comp_nd<<<std::min<int32_t>(k, 65535), kNdThreads, 0, st>>>(rp, col, part, local, vorder, d_vstart, d_csize, k,
-                                                                  kTile + 1, kNdMax, ndpos);
-    k_vertex_ndpos<<<(n + 255) / 256, 256, 0, st>>>(n, part, local, d_vstart, ndpos, vpos);
-    count_launches(2);
+    if ((e = cudaMemcpyAsync(d_graph, &hg, sizeof(NdGraph), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return done(e);
     if ((e = launch_fill_blocks<T>(P, d_ed, (int32_t)ed.size(), st)) != cudaSuccess) return done(e);
-    if ((e = launch_scatter_intra_sel<T>(f32w, n, rp, col, w, part, vpos, d_descs, d_csize, kNdMax, kTile, P,
-                                         st)) != cudaSuccess)
+    if ((e = comp_nd_order(d_graph, nullptr, local, vorder, d_vstart, d_csize, k, ndpos, st)) != cudaSuccess)
         return done(e);
-    // forward rounds of all of them in shared launches, then one back-substitution
-    double fwd = 0.0, bs = 0.0;
-    if ((e = fw_many_skip<T>(P, d_ed, (int32_t)ed.size(), max_el, scratch, &fwd, st, true)) != cudaSuccess)
-        return done(e);
-    std::vector<BsInput<T>> bin;
-    for (const MatDesc& d : ed) bin.push_back(BsInput<T>{P + d.off, (int64_t)d.n, nullptr});
-    if ((e = bg_backsub_many<T>(bin, err, nullptr, (size_t)2 << 30, &bs, nullptr, st)) != cudaSuccess) return done(e);
-    uint32_t f = 0;
-    if ((e = cudaMemcpyAsync(&f, err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(e);
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
-    if (f & kErrWait) return done(cudaErrorLaunchTimeout);
-    // back to the local order
-    const dim3 g((unsigned)max_el, (unsigned)std::min<size_t>(sel.size(), 65535));
-    k_unpermute<T><<<g, 256, 0, st>>>(apsp, P, d_descs, d_sel, (int32_t)sel.size(), d_csize, d_vstart, ndpos);
-    count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
-    if (updates) *updates = fwd + bs;
-    return done(cudaSuccess);
+    e = comp_nd_scatter<T>(P, d_descs, n, rp, col, w, f32w, part, local, d_vstart, d_csize, ndpos, vpos, st);
+    if (e != cudaSuccess) return done(e);
+    return done(comp_elim_finish<T>(apsp, P, d_descs, ed, d_sel, d_ed, d_csize, d_vstart, ndpos, updates, st));
 }
 
 template cudaError_t comp_tables_elim<float>(float*, const MatDesc*, const std::vector<MatDesc>&,
                                              const std::vector<int32_t>&, int32_t, int32_t, const int64_t*,
                                              const int32_t*, const void*, bool, const int32_t*, const int32_t*,
                                              const int32_t*, const int32_t*, const int32_t*, double*, cudaStream_t);
+#define SPQ_COMP_ND_INST(T)                                                                                      \
+    template cudaError_t comp_nd_scatter<T>(T*, const MatDesc*, int32_t, const int64_t*, const int32_t*, const void*, \
+                                            bool, const int32_t*, const int32_t*, const int32_t*, const int32_t*,      \
+                                            const int32_t*, int32_t*, cudaStream_t);                                    \
+    template cudaError_t comp_elim_finish<T>(T*, T*, const MatDesc*, const std::vector<MatDesc>&, const int32_t*,      \
+                                             const MatDesc*, const int32_t*, const int32_t*, const int32_t*, double*,  \
+                                             cudaStream_t);
+SPQ_COMP_ND_INST(float)
+SPQ_COMP_ND_INST(int32_t)
+
 template cudaError_t comp_tables_elim<int32_t>(int32_t*, const MatDesc*, const std::vector<MatDesc>&,
                                                const std::vector<int32_t>&, int32_t, int32_t, const int64_t*,
                                                const int32_t*, const void*, bool, const int32_t*, const int32_t*,
