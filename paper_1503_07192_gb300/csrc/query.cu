@@ -146,15 +146,14 @@ int query_sms() {
 // first position, however far it extends past the tile.  dist is symmetric, so a pair is
 // answered as (v, w) with comp(v) = C1 <= C2 = comp(w).
 //
-// Per batch the 8 warps hold 2 queries each (three CTAs per SM hide the gathers of one
-// another's blocks); lanes own block columns b2 and walk the rows
+// Per batch the 8 warps hold 4 queries each; lanes own block columns b2 and walk the rows
 // b1 with dist_C1(v1, b1) broadcast by shuffle (one fused add-min per update for int32).
 constexpr int GTH = 256;  // 8 warps
 constexpr int GTILE = 64;
 constexpr int GSEGCAP = 1024;         // longest segment (a power of two)
-constexpr int GQPW = 2;               // queries per warp per batch
+constexpr int GQPW = 4;               // queries per warp per batch
 constexpr int GCOLS = 256;            // block columns per pass (two groups of 128)
-constexpr int GSMEM = 16 * 1024;      // staged elements per CTA (64 KB): three CTAs per SM
+constexpr int GSMEM = 24 * 1024;      // staged elements per CTA (96 KB): two CTAs per SM
 
 __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t n, const int32_t* __restrict__ comp,
                              uint32_t k, uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
@@ -275,7 +274,7 @@ __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(GTH, 3) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
+__global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
                                                        const uint32_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ idx, int64_t q, uint32_t k,
                                                        void* __restrict__ out) {
