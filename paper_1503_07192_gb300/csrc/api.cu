@@ -239,10 +239,17 @@ cudaError_t build_comp_tables(spq_handle* h, const BuildInputs& in, int32_t max_
     evs.mark(2, st);
     T* apsp = (T*)h->apsp;
     cudaError_t e;
-    if ((e = launch_fill_blocks<T>(apsp, h->descs, h->k, st)) != cudaSuccess) return e;
-    if ((e = launch_scatter_intra<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->descs, apsp, st)) !=
-        cudaSuccess)
-        return e;
+    // (when every component takes the elimination form, its permutation back writes every
+    //  cell of the tables: no initialisation in the local order)
+    bool all_elim = elim;
+    for (int32_t c = 0; c < h->k && all_elim; ++c)
+        all_elim = h->h_descs[c].n == 0 || comp_takes_elim(h->h_csize[c], h->h_descs[c].n);
+    if (!all_elim) {
+        if ((e = launch_fill_blocks<T>(apsp, h->descs, h->k, st)) != cudaSuccess) return e;
+        if ((e = launch_scatter_intra<T>(in.f32w, in.n, in.rp, in.col, in.w, in.part, h->local, h->descs, apsp,
+                                         st)) != cudaSuccess)
+            return e;
+    }
     std::vector<MatDesc> fwd = h->h_descs;  // the Floyd-Warshall set (others: n = 0, skipped)
     double eu = 0.0;
     if (elim) {

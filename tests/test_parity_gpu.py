@@ -524,8 +524,9 @@ def test_table_memory_is_pooled_and_released():
 
 
 def test_shorter_opts_struct_is_accepted():
-    """A caller compiled against the earlier spq_opts (ending before bg_method) gets the
-    defaults for the newer fields; a struct_size shorter than that is rejected."""
+    """A caller compiled against an earlier spq_opts (ending before bg_method, or before
+    comp_method) gets the defaults for the newer fields; a struct_size shorter than the
+    first version is rejected, and so is an unknown comp_method."""
     m = spq()
     torch, dev = torch_dev()
     w = gen.configs.grid64(q=2000)
@@ -539,5 +540,21 @@ def test_shorter_opts_struct_is_accepted():
     assert_pairs_exact(h, g, w.pairs)
     h.free()
     o.struct_size = m.SpqOpts.bg_method.offset - 4
+    with pytest.raises(m.SpqError):
+        m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+    # a struct ending before comp_method: the component tables take the default form
+    # (elimination), whatever the caller's memory beyond the declared size holds
+    o = m.spq_opts_default()
+    o.comp_method = 1
+    hf = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+    o.struct_size = m.SpqOpts.comp_method.offset
+    he = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+    assert he.stats()["comp_updates"] < hf.stats()["comp_updates"]
+    for c in range(w.k):
+        assert np.array_equal(he.apsp(c), hf.apsp(c))
+    hf.free()
+    he.free()
+    o = m.spq_opts_default()
+    o.comp_method = 3
     with pytest.raises(m.SpqError):
         m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
