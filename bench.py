@@ -109,6 +109,20 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.thread = None
+        self.first = 0  # samples before the timed region (taken during the warm-up)
+
+    def started(self) -> "ClockSampler":
+        """Start before the warm-up and wait for the first sample, so that nvidia-smi's own
+        start-up (driver queries) stays out of the timed region."""
+        self.start()
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < 10:
+            time.sleep(0.05)
+        return self
+
+    def mark(self):
+        """The timed region starts: only samples from here on count."""
+        self.first = len(self.lines)
 
     def start(self):
         try:
@@ -137,7 +151,10 @@ class ClockSampler:
             self.thread.join(timeout=5)
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # samples of the timed region (the last warm-up one too if the region was shorter
+        # than the sampling period)
+        lines = self.lines[max(0, min(self.first, len(self.lines) - 1)):]
+        for ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -289,11 +306,11 @@ def run_batch(args, rank, local_rank):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k, r
 
+    clocks = ClockSampler(local_rank).started()
     for _ in range(args.warmup):
         batched()
     ref = [o.clone() for o in outs]
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    clocks.mark()
     launches0 = spq.spq_kernel_launches()
     ms_b, (st, pf) = timed(batched, args.steps)
     launches = spq.spq_kernel_launches() - launches0
@@ -505,10 +522,10 @@ def run_grad(args, rank, local_rank):
         h.free()
         return [e[i].elapsed_time(e[i + 1]) for i in range(3)]
 
+    clocks = ClockSampler(local_rank).started()
     for _ in range(args.warmup):
         step()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    clocks.mark()
     times = [step() for _ in range(args.steps)]
     clk = clocks.stop()
     build_ms, fwd_ms, bwd_ms = (statistics.mean(t[i] for t in times) for i in range(3))
@@ -604,18 +621,18 @@ def main():
         h.free()  # synchronises the device
         return st, pf, eq0.elapsed_time(eq1)
 
+    clocks = ClockSampler(local_rank).started()
     for i in range(args.warmup):
         st, pf, qms = step()
         log(f"[rank {rank}] warmup {i}: build stages {[round(pf[k], 1) for k in list(pf)[:6]]} ms, query {qms:.1f} ms"
             f", bg updates {st['bg_updates']:.3e}, order {int(pf.get('order_method', -1))}")
 
     # correctness spot check outside the timed region (CUDA path vs the last step's output)
-    clocks = ClockSampler(local_rank)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = spq.spq_kernel_launches()
-    clocks.start()
+    clocks.mark()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     wall0 = time.perf_counter()
