@@ -318,6 +318,18 @@ def run_batch(args, rank, local_rank):
     per_graph()  # warm-up of the per-graph form
     ms_p, _ = timed(per_graph, max(1, args.steps // 2))
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    # the query phase alone on resident handles: spq_query_many (launches issued by the
+    # host) against the same batch captured into a CUDA graph and replayed (spq_query_plan)
+    hs = spq.spq_build_many(graphs)
+    spq.spq_query_many(hs, pairs, outs=outs)
+    ms_qm, _ = timed(lambda: spq.spq_query_many(hs, pairs, outs=outs), max(3, args.steps))
+    plan = spq.spq_query_plan(hs, pairs, outs=outs)
+    plan.run()
+    ms_qp, _ = timed(plan.run, max(3, args.steps))
+    same_plan = all(torch.equal(a, b) for a, b in zip(ref, outs))
+    plan.free()
+    for h in hs:
+        h.free()
     upd = sum(w.graph.n for w in ins)
     line = {
         "metric": METRIC, "value": q_tot / (ms_b * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -327,6 +339,7 @@ def run_batch(args, rank, local_rank):
                    "l2": "tables of all instances (tens of GB) rebuilt every step"},
         "batched_ms": ms_b, "per_graph_ms": ms_p, "speedup_vs_per_graph": ms_p / ms_b,
         "per_graph_qps": q_tot / (ms_p * 1e-3), "results_identical": bool(same),
+        "query_phase_ms": {"query_many": ms_qm, "cuda_graph_plan": ms_qp, "plan_results_identical": bool(same_plan)},
         "batch_stage_ms": {k: round(pf[k], 2) for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw",
                                                          "check")},
         "bg_updates": st["bg_updates"], "gpu_launches": int(launches) // max(1, args.steps), "clocks": clk,

@@ -235,6 +235,24 @@ spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* c
                           void* const* dist_out, void* stream);
 
 /*
+ * Batched query plan (CUDA graph): the launches of spq_query_many for these handles,
+ * DEVICE pair/output buffers and sizes, run once eagerly on `stream` (so the call also
+ * answers the batch) and captured into a CUDA graph; spq_query_plan_run replays the whole
+ * batch with one graph launch on any stream, answering the pairs the buffers hold at that
+ * time (write new pairs in place between replays).  The handles and buffers must outlive
+ * the plan; the plan owns its sort scratch.  Out-of-range pairs are reported as by
+ * spq_query on device buffers (spq_query_status per handle).  SPQ_EINVAL for host buffers
+ * or misaligned ones (pairs 8-byte, outputs 4-byte aligned); SPQ_ECUDA if the capture or
+ * the instantiation fails.  spq_query_plan_free synchronises the device.  A plan is used
+ * by one thread at a time.
+ */
+typedef struct spq_query_plan spq_query_plan;
+spq_status spq_query_plan_create(int32_t count, spq_handle* const* hs, const int32_t* const* pairs, const int64_t* q,
+                                 void* const* dist_out, void* stream, spq_query_plan** out);
+spq_status spq_query_plan_run(spq_query_plan* plan, void* stream);
+void spq_query_plan_free(spq_query_plan* plan);
+
+/*
  * Many-to-many distances: dist_out[i * nt + j] = dist(sources[i], targets[j]) (int32 for
  * SPQ_I32 graphs, SPQ_INF_I32 if unreachable; float for SPQ_F32).  Algorithm 2 split in
  * its two stages: for a source v1 in C1 and a target component C2, t(b2) = min over b1 of

@@ -263,6 +263,63 @@ def spq_query_matrix(h: SpqHandle, sources, targets, out=None, stream=None):
     return o_k
 
 
+class SpqQueryPlan:
+    """A batched query captured into a CUDA graph (spq_query_plan_*): run() answers the
+    pairs the device buffers hold at that time, with one graph launch.  The handles and
+    the tensors (pairs, outs) must outlive the plan."""
+
+    def __init__(self, ptr, handles, pairs, outs):
+        self._p = ptr
+        self.handles, self.pairs, self.outs = list(handles), list(pairs), list(outs)
+
+    def run(self, stream=None):
+        if not self._p:
+            raise ValueError("plan already freed")
+        st = _lib.load().spq_query_plan_run(self._p, _stream(stream, True))
+        if st:
+            raise SpqError(st, "spq_query_plan_run")
+        return self.outs
+
+    def free(self):
+        if self._p:
+            _lib.load().spq_query_plan_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def spq_query_plan(handles, pairs_list, outs=None, stream=None) -> SpqQueryPlan:
+    """Capture spq_query_many for these handles and CUDA pair tensors (int32[q, 2]) into a
+    CUDA graph; the call answers the batch once, and plan.run() answers it again."""
+    lib = _lib.load()
+    n = len(handles)
+    hp = (ctypes.c_void_p * n)()
+    pp = (ctypes.c_void_p * n)()
+    qq = (ctypes.c_int64 * n)()
+    op = (ctypes.c_void_p * n)()
+    keep, outs_k = [], []
+    for i, (h, pairs) in enumerate(zip(handles, pairs_list)):
+        p_p, p_k, p_dev = _ptr(pairs, np.int32)
+        if not p_dev:
+            raise ValueError("a query plan takes device (CUDA) pair tensors")
+        q = int(p_k.shape[0]) if p_k.ndim > 1 else int(p_k.shape[0]) // 2
+        o = outs[i] if outs is not None else torch.empty(
+            q, dtype=torch.float32 if h.wt == SPQ_F32 else torch.int32, device=p_k.device)
+        o_p, o_k, _ = _ptr(o, np.float32 if h.wt == SPQ_F32 else np.int32)
+        keep.append(p_k)
+        outs_k.append(o_k)
+        hp[i], pp[i], qq[i], op[i] = h.ptr, p_p, q, o_p
+    out = ctypes.c_void_p()
+    st = lib.spq_query_plan_create(n, hp, pp, qq, op, _stream(stream, True), ctypes.byref(out))
+    if st:
+        raise SpqError(st, "spq_query_plan_create")
+    return SpqQueryPlan(out, handles, keep, outs_k)
+
+
 def spq_query_noalloc(h: SpqHandle, pairs, out=None, stream=None):
     """spq_query for callers that cannot let the library allocate device memory: pairs
     (int32[q, 2], q <= SPQ_NOALLOC_MAX_PAIRS) and out must be CUDA tensors; the

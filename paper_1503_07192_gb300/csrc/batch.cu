@@ -867,4 +867,94 @@ spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* c
     return SPQ_OK;
 }
 
+// A batched query plan: the launches of spq_query_many for fixed handles, device buffers
+// and sizes, captured once into a CUDA graph and replayed by one graph launch.
+struct spq_query_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t* scratch = nullptr;
+};
+
+namespace {
+
+void plan_destroy(spq_query_plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->scratch) {
+        cudaDeviceSynchronize();  // (replays queued on any stream are done)
+        cudaFreeAsync(p->scratch, 0);
+        cudaStreamSynchronize(0);
+    }
+    delete p;
+}
+
+// The launches of one batch on stream st (device buffers; the grouped form's scratch is
+// shared in stream order).
+cudaError_t issue_queries(int32_t count, spq_handle* const* hs, const int32_t* const* pairs, const int64_t* q,
+                          void* const* dist_out, uint32_t* scratch, cudaStream_t st) {
+    for (int32_t i = 0; i < count; ++i) {
+        if (q[i] == 0) continue;
+        QueryCtx<int32_t> ci;
+        QueryCtx<float> cf;
+        bool f32store = false, out_f32 = false;
+        int32_t k = 0;
+        handle_query_view(hs[i], &ci, &cf, &f32store, &out_f32, &k);
+        uint32_t* sc = hs[i]->query_grouped ? scratch : nullptr;
+        const cudaError_t e = f32store ? launch_query<float>(cf, pairs[i], q[i], dist_out[i], out_f32, (uint32_t)k, sc, st)
+                                       : launch_query<int32_t>(ci, pairs[i], q[i], dist_out[i], out_f32, (uint32_t)k,
+                                                               sc, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+spq_status spq_query_plan_create(int32_t count, spq_handle* const* hs, const int32_t* const* pairs, const int64_t* q,
+                                 void* const* dist_out, void* stream, spq_query_plan** out) {
+    if (!out) return SPQ_EINVAL;
+    *out = nullptr;
+    if (count < 0 || (count > 0 && (!hs || !pairs || !q || !dist_out))) return SPQ_EINVAL;
+    int64_t qmax = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (!hs[i] || q[i] < 0 || (q[i] > 0 && (!pairs[i] || !dist_out[i]))) return SPQ_EINVAL;
+        if (q[i] == 0) continue;
+        if (!dev_pointer(pairs[i]) || !dev_pointer(dist_out[i])) return SPQ_EINVAL;
+        if (((uintptr_t)pairs[i] & 7u) || ((uintptr_t)dist_out[i] & 3u)) return SPQ_EINVAL;
+        qmax = std::max(qmax, q[i]);
+    }
+    spq_query_plan* p = new (std::nothrow) spq_query_plan();
+    if (!p) return SPQ_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = scratch_alloc((void**)&p->scratch, (size_t)query_scratch_words(std::max<int64_t>(qmax, 1)) * 4, st);
+    // one eager pass first (every kernel attribute set, the batch checked), then the capture
+    if (e == cudaSuccess) e = issue_queries(count, hs, pairs, q, dist_out, p->scratch, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t e1 = issue_queries(count, hs, pairs, q, dist_out, p->scratch, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+        e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        plan_destroy(p);
+        return batch_cuda_fail(e);
+    }
+    *out = p;
+    return SPQ_OK;
+}
+
+spq_status spq_query_plan_run(spq_query_plan* p, void* stream) {
+    if (!p || !p->exec) return SPQ_EINVAL;
+    const cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? SPQ_OK : batch_cuda_fail(e);
+}
+
+void spq_query_plan_free(spq_query_plan* p) { plan_destroy(p); }
+
 }  // extern "C"

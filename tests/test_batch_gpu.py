@@ -134,3 +134,39 @@ def test_batch_takes_elimination_for_large_boundary_graphs():
         _check_batch(ins, hs)
         for h in hs:
             h.free()
+
+
+def test_query_plan_replays_the_batch():
+    """spq_query_plan: the batch captured into a CUDA graph answers like spq_query_many,
+    and a replay answers the pairs the buffers hold at that time (pairs rewritten in
+    place, grouped and per-pair query forms, an empty request)."""
+    m = spq()
+    torch, dev = torch_dev()
+    ins = _instances()[:6]
+    hs = m.spq_build_many(_tuples(ins, True))
+    rng = np.random.default_rng(31)
+    sizes = [5000, 100, 0, 9000, 4096, 7]
+    bufs = [torch.from_numpy(rng.integers(0, w.graph.n, size=(q, 2)).astype(np.int32)).to(dev)
+            for w, q in zip(ins, sizes)]
+    plan = m.spq_query_plan(hs, bufs)
+    torch.cuda.synchronize()
+    ref = m.spq_query_many(hs, bufs)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(plan.outs, ref))
+    for rep in range(2):
+        for w, b in zip(ins, bufs):  # new pairs, same buffers
+            b.copy_(torch.from_numpy(rng.integers(0, w.graph.n, size=tuple(b.shape)).astype(np.int32)))
+        outs = plan.run()
+        torch.cuda.synchronize()
+        for h, w, b, o in zip(hs, ins, bufs, outs):
+            if b.shape[0] == 0:
+                continue
+            p = b.cpu().numpy()
+            assert np.array_equal(o.cpu().numpy(), m.spq_query(h, p)), w.name
+            ref = oracle_i32(oracle.pairs_dist(w.graph.row_ptr, w.graph.col, w.graph.w, p[:200]))
+            assert np.array_equal(o.cpu().numpy()[:200].astype(np.int64), ref)
+    with pytest.raises(ValueError):
+        m.spq_query_plan(hs[:1], [bufs[0].cpu().numpy()])
+    plan.free()
+    for h in hs:
+        h.free()
