@@ -172,6 +172,13 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def tuning_summary(spq) -> dict:
+    """The grouped query autotuner's choices: size classes per configuration."""
+    t = spq.spq_query_tuning()
+    return {"classes": len(t), "config1_classes": sorted(c for (_, c), v in t.items() if v == 1),
+            "config0_classes": sorted(c for (_, c), v in t.items() if v == 0)}
+
+
 def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
     """Time the oracle (Dijkstra per pair, all host cores) on a bounded sample of the
     workload's pairs: chunks of uniformly drawn pairs until budget_s has elapsed.
@@ -339,7 +346,9 @@ def run_batch(args, rank, local_rank):
                    "l2": "tables of all instances (tens of GB) rebuilt every step"},
         "batched_ms": ms_b, "per_graph_ms": ms_p, "speedup_vs_per_graph": ms_p / ms_b,
         "per_graph_qps": q_tot / (ms_p * 1e-3), "results_identical": bool(same),
-        "query_phase_ms": {"query_many": ms_qm, "cuda_graph_plan": ms_qp, "plan_results_identical": bool(same_plan)},
+        "query_phase_ms": {"query_many": ms_qm, "cuda_graph_plan": ms_qp,
+                           "plan_results_identical": bool(same_plan)},
+        "query_autotune": tuning_summary(spq),
         "batch_stage_ms": {k: round(pf[k], 2) for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw",
                                                          "check")},
         "bg_updates": st["bg_updates"], "gpu_launches": int(launches) // max(1, args.steps), "clocks": clk,
@@ -746,6 +755,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,
+        "query_autotune": tuning_summary(spq),
     }
 
     # end to end through the public API with host buffers (pinned), H2D/D2H inside

@@ -5,6 +5,8 @@
 #ifndef SPQ_BENCH_H
 #define SPQ_BENCH_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -38,6 +40,14 @@ int spq_component_order_host(int k, const long long* adj_ptr, const int* adj, co
  * Returns 0, or a negative value on bad input.  Needs no GPU. */
 int spq_boundary_order_host(int k, const long long* adj_ptr, const int* adj, const long long* slot_off,
                             const long long* snb_ptr, const int* snb, int rule, int* slot_order_out);
+
+/* The grouped query's autotuner: its choices so far, per (device, size class), as
+ * keys[i] = device * 256 + class and choices[i] = configuration (0: 4 pairs per warp,
+ * two CTAs per SM; 1: 2 pairs per warp, three CTAs per SM).  The class is
+ * 16 * (clamp(floor(log2(pairs per component pair)), -6, 9) + 6)
+ *    + min(floor(log2(boundary slots per component)), 15).
+ * Writes at most cap entries; returns how many there are. */
+int32_t spq_query_tuning(int32_t* keys, int32_t* choices, int32_t cap);
 
 /* Number of kernels this library has launched in this process so far (all entry
  * points, all devices; the micro-benchmark above excluded). */

@@ -435,6 +435,17 @@ def spq_free(h: SpqHandle):
     h.free()
 
 
+def spq_query_tuning() -> dict:
+    """The grouped query's autotuner choices so far: {(device, size class): configuration}
+    (0: 4 pairs per warp, two CTAs per SM; 1: 2 pairs per warp, three CTAs per SM)."""
+    lib = _lib.load()
+    n = int(lib.spq_query_tuning(None, None, 0))
+    keys = (ctypes.c_int32 * max(n, 1))()
+    ch = (ctypes.c_int32 * max(n, 1))()
+    n = min(n, int(lib.spq_query_tuning(keys, ch, n)))
+    return {(keys[i] // 256, keys[i] % 256): int(ch[i]) for i in range(n)}
+
+
 def spq_kernel_launches() -> int:
     return int(_lib.load().spq_kernel_launches())
 

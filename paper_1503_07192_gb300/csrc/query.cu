@@ -14,6 +14,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <atomic>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -151,9 +154,12 @@ int query_sms() {
 constexpr int GTH = 256;  // 8 warps
 constexpr int GTILE = 64;
 constexpr int GSEGCAP = 1024;         // longest segment (a power of two)
-constexpr int GQPW = 4;               // queries per warp per batch
+// Two configurations of the grouped kernel, chosen per size class by measurement (see
+// launch_query): 4 queries per warp, 96 KB of staged block per CTA, two CTAs per SM; or
+// 2 queries per warp, 64 KB, three CTAs per SM (more CTAs to overlap one another's block
+// gathers, fewer queries sharing each staged chunk).  Every answer is computed with the
+// same operations in both.
 constexpr int GCOLS = 256;            // block columns per pass (two groups of 128)
-constexpr int GSMEM = 24 * 1024;      // staged elements per CTA (96 KB): two CTAs per SM
 
 __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t n, const int32_t* __restrict__ comp,
                              uint32_t k, uint32_t* __restrict__ keys, uint32_t* __restrict__ idx) {
@@ -177,19 +183,19 @@ __device__ __forceinline__ bool seg_head(const uint32_t* __restrict__ keys, int6
     return p == 0 || keys[p] != keys[p - 1] || (p & (GSEGCAP - 1)) == 0;
 }
 
-// One pass over up to NG x 128 block columns [jb, jb + cols) for a warp's GQPW queries:
+// One pass over up to NG x 128 block columns [jb, jb + cols) for a warp's QPW queries:
 // r[u] = min(r[u], min over b1, b2 of dist_C1(v1, b1) + D(b1, b2) + dist_C2(b2, v2)).
 // The block rows are staged in chunks into S (row length NG x 128); each lane owns four
 // consecutive columns per 128-column group (one 16-byte shared load per row and group)
 // and dist_C1(v1, b1) is broadcast by shuffle.
-template <typename T, int NG>
+template <typename T, int NG, int QPW, int SMEM>
 __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__ S, const int32_t* __restrict__ pos1,
                                          const int32_t* __restrict__ pos2, int32_t nb1, int32_t jb, int cols,
-                                         const int64_t (&a1off)[GQPW], const int64_t (&a2off)[GQPW],
-                                         const bool (&val)[GQPW], bool active, T (&r)[GQPW], int tid, int lane,
+                                         const int64_t (&a1off)[QPW], const int64_t (&a2off)[QPW],
+                                         const bool (&val)[QPW], bool active, T (&r)[QPW], int tid, int lane,
                                          int warp) {
     constexpr int ld = NG * 128;
-    constexpr int rows_per_chunk = GSMEM / ld;
+    constexpr int rows_per_chunk = SMEM / ld;
     const T inf = Inf<T>::value();
     int32_t colpos[NG * 4];
 #pragma unroll
@@ -197,9 +203,9 @@ __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__
         const int j = jj * 32 + lane;
         colpos[jj] = j < cols ? pos2[jb + j] : -1;
     }
-    T t[GQPW][NG][4];
+    T t[QPW][NG][4];
 #pragma unroll
-    for (int u = 0; u < GQPW; ++u)
+    for (int u = 0; u < QPW; ++u)
 #pragma unroll
         for (int g = 0; g < NG; ++g)
 #pragma unroll
@@ -233,16 +239,16 @@ __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__
         __syncthreads();
         if (!active) continue;
         for (int ib = 0; ib < rows; ib += 32) {
-            T areg[GQPW];
+            T areg[QPW];
 #pragma unroll
-            for (int u = 0; u < GQPW; ++u)
+            for (int u = 0; u < QPW; ++u)
                 areg[u] = (val[u] && ib + lane < rows) ? ctx.apsp[a1off[u] + rc + ib + lane] : inf;
             const int iend = (rows - ib) < 32 ? (rows - ib) : 32;
 #pragma unroll 2
             for (int ii = 0; ii < iend; ++ii) {
-                T ai[GQPW];
+                T ai[QPW];
 #pragma unroll
-                for (int u = 0; u < GQPW; ++u) ai[u] = __shfl_sync(0xffffffffu, areg[u], ii);
+                for (int u = 0; u < QPW; ++u) ai[u] = __shfl_sync(0xffffffffu, areg[u], ii);
                 const T* srow = S + (ib + ii) * ld + lane * 4;
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
@@ -250,7 +256,7 @@ __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__
                     const T s4[4] = {*reinterpret_cast<const T*>(&sv.x), *reinterpret_cast<const T*>(&sv.y),
                                      *reinterpret_cast<const T*>(&sv.z), *reinterpret_cast<const T*>(&sv.w)};
 #pragma unroll
-                    for (int u = 0; u < GQPW; ++u)
+                    for (int u = 0; u < QPW; ++u)
 #pragma unroll
                         for (int e = 0; e < 4; ++e) t[u][g][e] = addmin(ai[u], s4[e], t[u][g][e]);
                 }
@@ -260,7 +266,7 @@ __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__
     if (!active) return;
     // dist_C2(b2, v2) for this pass's columns (a lane's four consecutive columns)
 #pragma unroll
-    for (int u = 0; u < GQPW; ++u)
+    for (int u = 0; u < QPW; ++u)
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
             const int j0 = g * 128 + lane * 4;
@@ -273,13 +279,13 @@ __device__ __forceinline__ void seg_pass(const QueryCtx<T>& ctx, T* __restrict__
         }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
+template <typename T, int MODE, int QPW, int SMEM, int MINB>
+__global__ void __launch_bounds__(GTH, MINB) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
                                                        const uint32_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ idx, int64_t q, uint32_t k,
                                                        void* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* S = reinterpret_cast<T*>(smem_raw);  // GSMEM elements, rows of `ld` = cols rounded up to 32
+    T* S = reinterpret_cast<T*>(smem_raw);  // SMEM elements, rows of `ld` = cols rounded up to 32
     __shared__ int32_t heads[GTILE + 1];
     __shared__ uint32_t hb[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -332,17 +338,17 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
         const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];
         const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
         const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
-        for (int bq = s0; bq < s1; bq += 8 * GQPW) {
-            // this warp's queries: bq + warp * GQPW + u (warps past the segment's end idle
+        for (int bq = s0; bq < s1; bq += 8 * QPW) {
+            // this warp's queries: bq + warp * QPW + u (warps past the segment's end idle
             // through the compute and only help staging)
-            int64_t a1off[GQPW], a2off[GQPW];
-            int32_t l2s[GQPW];
-            uint32_t qis[GQPW];
-            bool val[GQPW], same_v[GQPW];
-            T r[GQPW];
+            int64_t a1off[QPW], a2off[QPW];
+            int32_t l2s[QPW];
+            uint32_t qis[QPW];
+            bool val[QPW], same_v[QPW];
+            T r[QPW];
 #pragma unroll
-            for (int u = 0; u < GQPW; ++u) {
-                const int sp = bq + warp * GQPW + u;
+            for (int u = 0; u < QPW; ++u) {
+                const int sp = bq + warp * QPW + u;
                 val[u] = sp < s1;
                 qis[u] = 0;
                 a1off[u] = a2off[u] = 0;
@@ -367,12 +373,12 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
             for (int32_t jb = 0; jb < nb2; jb += GCOLS) {
                 const int cols = (nb2 - jb) < GCOLS ? (nb2 - jb) : GCOLS;
                 if (cols > 128)
-                    seg_pass<T, 2>(ctx, S, pos1, pos2, nb1, jb, cols, a1off, a2off, val, active, r, tid, lane, warp);
+                    seg_pass<T, 2, QPW, SMEM>(ctx, S, pos1, pos2, nb1, jb, cols, a1off, a2off, val, active, r, tid, lane, warp);
                 else
-                    seg_pass<T, 1>(ctx, S, pos1, pos2, nb1, jb, cols, a1off, a2off, val, active, r, tid, lane, warp);
+                    seg_pass<T, 1, QPW, SMEM>(ctx, S, pos1, pos2, nb1, jb, cols, a1off, a2off, val, active, r, tid, lane, warp);
             }
 #pragma unroll
-            for (int u = 0; u < GQPW; ++u) {
+            for (int u = 0; u < QPW; ++u) {
                 T y = warp_min(r[u]);
                 if (val[u]) {
                     if (c1 == c2) y = tmin(y, ctx.apsp[a1off[u] + l2s[u]]);
@@ -388,6 +394,73 @@ __global__ void __launch_bounds__(GTH, 2) k_query_grouped(const QueryCtx<T> ctx,
         }
     }
 }
+
+namespace {
+
+// One configuration of the grouped kernel (QPW queries per warp, SMEMK x 1024 staged
+// elements per CTA, MINB CTAs per SM).
+template <typename T, int MODE, int QPW, int SMEMK, int MINB>
+cudaError_t launch_grouped_one(unsigned blocks, const QueryCtx<T>& ctx, const int2* p2, const uint32_t* sk,
+                               const uint32_t* sv, int64_t q, uint32_t k, void* out, cudaStream_t st) {
+    constexpr size_t smem = sizeof(T) * SMEMK * 1024;
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        const cudaError_t e = cudaFuncSetAttribute(k_query_grouped<T, MODE, QPW, SMEMK * 1024, MINB>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr.store(true);
+    }
+    k_query_grouped<T, MODE, QPW, SMEMK * 1024, MINB><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_grouped(int cfg, bool mode_f32, unsigned blocks, const QueryCtx<T>& ctx, const int2* p2,
+                           const uint32_t* sk, const uint32_t* sv, int64_t q, uint32_t k, void* out,
+                           cudaStream_t st) {
+    if (cfg == 0)
+        return mode_f32 ? launch_grouped_one<T, kOutF32, 4, 24, 2>(blocks, ctx, p2, sk, sv, q, k, out, st)
+                        : launch_grouped_one<T, kOutI32, 4, 24, 2>(blocks, ctx, p2, sk, sv, q, k, out, st);
+    return mode_f32 ? launch_grouped_one<T, kOutF32, 2, 16, 3>(blocks, ctx, p2, sk, sv, q, k, out, st)
+                    : launch_grouped_one<T, kOutI32, 2, 16, 3>(blocks, ctx, p2, sk, sv, q, k, out, st);
+}
+
+// Size class of a grouped launch: log2 of the pairs per component pair (which decides how
+// many queries share a staged block) and log2 of the mean boundary slots per component
+// (the block's size).
+int grouped_size_class(int64_t q, uint32_t k, int64_t N) {
+    const double cp = (double)k * ((double)k + 1.0) / 2.0;
+    const double ppp = (double)q / (cp > 0.0 ? cp : 1.0);
+    const double nb = (double)N / (k > 0 ? (double)k : 1.0);
+    int a = (int)floor(log2(ppp > 1e-9 ? ppp : 1e-9));
+    a = (a < -6 ? -6 : (a > 9 ? 9 : a)) + 6;
+    int b = (int)floor(log2(nb > 1.0 ? nb : 1.0));
+    b = b > 15 ? 15 : b;
+    return a * 16 + b;
+}
+
+// The autotuner's choices per (device, size class), measured on the first grouped launch
+// of each class in the process.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune;
+
+int tuned_config(int cls) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({dev, cls});
+    return it == g_tune.end() ? -1 : it->second;
+}
+
+void store_tuned(int cls, int cfg) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{dev, cls}] = cfg;
+}
+
+}  // namespace
 
 int64_t query_scratch_words(int64_t q) { return 4 * q + radix_hist_words(q) + 4; }
 
@@ -413,25 +486,31 @@ cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q
         if (e != cudaSuccess) return e;
         const uint32_t* sk = in_k1 ? k1 : keys;
         const uint32_t* sv = in_k1 ? v1 : vals;
-        const size_t smem = sizeof(T) * GSMEM;
-        static bool attr_set[2] = {false, false};
-        if (!attr_set[mode_f32]) {
-            if (mode_f32)
-                e = cudaFuncSetAttribute(k_query_grouped<T, kOutF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-            else
-                e = cudaFuncSetAttribute(k_query_grouped<T, kOutI32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_set[mode_f32] = true;
-        }
         const unsigned blocks = (unsigned)((q + GTILE - 1) / GTILE);
-        if (mode_f32)
-            k_query_grouped<T, kOutF32><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, out);
-        else
-            k_query_grouped<T, kOutI32><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, out);
-        count_launches(1);
-        return cudaGetLastError();
+        const int cls = grouped_size_class(q, k, ctx.N);
+        int cfg = tuned_config(cls);
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        if (cfg < 0 && cap != cudaStreamCaptureStatusNone) cfg = 0;  // no timing inside a graph capture
+        if (cfg >= 0) return launch_grouped<T>(cfg, mode_f32, blocks, ctx, p2, sk, sv, q, k, out, st);
+        // first grouped launch of this size class on this device: time both configurations
+        // on these inputs (the second writes the same answers again) and keep the faster
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        for (auto& x : ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&x);
+        float ms[2] = {0.f, 0.f};
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess) e = launch_grouped<T>(0, mode_f32, blocks, ctx, p2, sk, sv, q, k, out, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = launch_grouped<T>(1, mode_f32, blocks, ctx, p2, sk, sv, q, k, out, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+        if (e == cudaSuccess) store_tuned(cls, ms[1] < ms[0] ? 1 : 0);
+        for (auto& x : ev)
+            if (x) cudaEventDestroy(x);
+        return e;
     }
     int64_t blocks = (q + (QTH / 32) - 1) / (QTH / 32);
     int64_t cap = (int64_t)query_sms() * 16;
@@ -450,3 +529,16 @@ template cudaError_t launch_query<float>(const QueryCtx<float>&, const int32_t*,
                                          uint32_t*, cudaStream_t);
 
 }  // namespace spq
+
+extern "C" int32_t spq_query_tuning(int32_t* keys, int32_t* choices, int32_t cap) {
+    std::lock_guard<std::mutex> lk(spq::g_tune_mu);
+    int32_t n = 0;
+    for (const auto& kv : spq::g_tune) {
+        if (n < cap && keys && choices) {
+            keys[n] = kv.first.first * 256 + kv.first.second;
+            choices[n] = kv.second;
+        }
+        ++n;
+    }
+    return n;
+}

@@ -303,6 +303,31 @@ def test_grouped_and_input_order_queries_agree_float_weights():
     hu.free()
 
 
+def test_grouped_query_autotuner_records_its_choice():
+    """The first grouped launch of a size class times both kernel configurations on its
+    inputs and keeps the faster (the answers are the same operations in both): the class
+    of this launch is in the table afterwards, and a second launch (the chosen
+    configuration) answers the same."""
+    m = spq()
+    torch, dev = torch_dev()
+    w = gen.configs.grid_blocks_workload(48, 48, 12, 12, 60, 30000, seed=29)
+    h = build(w.graph, w.part, w.k)
+    pairs = torch.from_numpy(w.pairs).to(dev)
+    a = m.spq_query(h, pairs)
+    b = m.spq_query(h, pairs)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    q, k, nbg = w.pairs.shape[0], w.k, int(h.meta()["nb"].sum())
+    # (few boundary slots: no alignment padding, the matrix order is nbg rounded up to 4)
+    N = -(-nbg // 4) * 4
+    cls = 16 * (min(max(int(np.floor(np.log2(q / (k * (k + 1) / 2)))), -6), 9) + 6) + min(int(np.log2(N / k)), 15)
+    table = m.spq_query_tuning()
+    assert table and set(table.values()) <= {0, 1}
+    assert (0, cls) in table, (cls, table)
+    assert_pairs_exact(h, w.graph, w.pairs[:3000])
+    h.free()
+
+
 def test_grouped_queries_mark_invalid_pairs():
     m = spq()
     w = gen.configs.grid_blocks_workload(32, 32, 8, 8, 50, 10000, seed=19)
