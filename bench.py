@@ -172,6 +172,24 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The maximum of x over all ranks (every rank gets it); x itself with one rank.  The
+    timed span of a multi-GPU run is the slowest rank's."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units of all ranks per second of the slowest rank (weak scaling: every rank does
+    the same work)."""
+    return world * units_per_rank / seconds
+
+
 def tuning_summary(spq) -> dict:
     """The grouped query autotuner's choices: size classes per configuration."""
     t = spq.spq_query_tuning()
@@ -669,11 +687,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     launches = spq.spq_kernel_launches() - launches0
-    elapsed_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
     K = args.steps
     build_ms = [sum(pf[k] for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check"))
@@ -725,7 +739,7 @@ def main():
 
     line = {
         "metric": METRIC,
-        "value": world * K * q / (elapsed_ms * 1e-3),
+        "value": whole_job_rate(K * q, world, elapsed_ms * 1e-3),
         "unit": UNIT,
         "n_gpus": world,
         "steps": K,
@@ -778,12 +792,9 @@ def main():
             h = spq.spq_build(g.n, h_rp, h_col, h_w, h_part, w.k)
             spq.spq_query(h, h_pairs, out=h_out)
             h.free()
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        line["e2e"] = {"value": world * args.e2e_steps * q / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        te = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        line["e2e"] = {"value": whole_job_rate(args.e2e_steps * q, world, te), "unit": UNIT,
+                       "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
 
     if rank == 0 and world == 1:
