@@ -377,9 +377,21 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     BCK(tmp.alloc(&errs, (size_t)G + 1));
     BCK(cudaMemsetAsync(cnt, 0, 2 * (size_t)ktot * 4, st));
     BCK(cudaMemsetAsync(errs, 0, ((size_t)G + 1) * 4, st));
-    for (auto& x : I)
-        BCK(launch_validate(f32w, x.n, x.m, x.rp, x.col, x.w, x.part, x.k, bflag + x.vbase, cnt + x.kbase,
-                            cnt + ktot + x.kbase, errs + (&x - I.data()), st));
+    // every instance in one launch
+    std::vector<ValGraph> vg;
+    std::vector<int64_t> vb;
+    for (auto& x : I) {
+        vg.push_back(ValGraph{x.n, x.k, x.m, x.rp, x.col, x.w, x.part, x.kbase});
+        vb.push_back(x.vbase);
+    }
+    vb.push_back(ntot);
+    ValGraph* d_vg;
+    int64_t* d_vb;
+    BCK(tmp.alloc(&d_vg, vg.size()));
+    BCK(tmp.alloc(&d_vb, vb.size()));
+    BCK(cudaMemcpyAsync(d_vg, vg.data(), vg.size() * sizeof(ValGraph), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(d_vb, vb.data(), vb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    BCK(launch_validate_many(f32w, d_vg, d_vb, G, ntot, bflag, cnt, cnt + ktot, errs, st));
     std::vector<int32_t> hcnt(2 * (size_t)ktot);
     std::vector<uint32_t> herr(G);
     BCK(cudaMemcpyAsync(hcnt.data(), cnt, hcnt.size() * 4, cudaMemcpyDeviceToHost, st));

@@ -76,6 +76,20 @@ struct FwProfile {
 cudaError_t launch_validate(bool f32, int32_t n, int64_t m, const int64_t* rp, const int32_t* col, const void* w,
                             const int32_t* part, int32_t k, uint8_t* bflag, int32_t* cnt_c, int32_t* cnt_b,
                             uint32_t* err, cudaStream_t st);
+// The same for G graphs at once (one launch): graph g's vertices are the global indices
+// [vbase[g], vbase[g + 1]); its flags at bflag + vbase[g], its counts at kbase, its status
+// word err[g].
+struct ValGraph {
+    int32_t n, k;
+    int64_t m;
+    const int64_t* rp;
+    const int32_t* col;
+    const void* w;
+    const int32_t* part;
+    int64_t kbase;
+};
+cudaError_t launch_validate_many(bool f32, const ValGraph* gs, const int64_t* vbase, int32_t G, int64_t ntot,
+                                 uint8_t* bflag, int32_t* cnt_c, int32_t* cnt_b, uint32_t* err, cudaStream_t st);
 // Stable LSD radix sort of (key, val) by the low key_bits bits.  Buffers: k0/v0 hold
 // the input, k1/v1 are scratch of the same size; hist needs radix_hist_words(n) words.
 // Returns (via *in_k1) whether the sorted result ended in k1/v1.

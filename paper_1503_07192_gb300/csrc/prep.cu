@@ -21,12 +21,11 @@ __device__ __forceinline__ bool weight_ok(float w) { return isfinite(w) && w >= 
 // neighbour u (smallest weight of the slots v->u equals that of u->v).  Cost is
 // O(sum over v of deg(v)^2).
 template <typename W>
-__global__ void k_validate(int32_t n, int64_t m, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           const W* __restrict__ w, const int32_t* __restrict__ part, int32_t k,
-                           uint8_t* __restrict__ bflag, int32_t* __restrict__ cnt_c, int32_t* __restrict__ cnt_b,
-                           uint32_t* __restrict__ err) {
-    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
+__device__ __forceinline__ void validate_vertex(int32_t v, int32_t n, int64_t m, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const W* __restrict__ w,
+                                                const int32_t* __restrict__ part, int32_t k,
+                                                uint8_t* __restrict__ bflag, int32_t* __restrict__ cnt_c,
+                                                int32_t* __restrict__ cnt_b, uint32_t* __restrict__ err) {
     uint32_t bits = 0;
     int64_t a = rp[v], b = rp[v + 1];
     int32_t p = part[v];
@@ -79,6 +78,36 @@ __global__ void k_validate(int32_t n, int64_t m, const int64_t* __restrict__ rp,
         atomicAdd(&cnt_c[p], 1);
         if (bnd) atomicAdd(&cnt_b[p], 1);
     }
+}
+
+template <typename W>
+__global__ void k_validate(int32_t n, int64_t m, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const W* __restrict__ w, const int32_t* __restrict__ part, int32_t k,
+                           uint8_t* __restrict__ bflag, int32_t* __restrict__ cnt_c, int32_t* __restrict__ cnt_b,
+                           uint32_t* __restrict__ err) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) validate_vertex<W>(v, n, m, rp, col, w, part, k, bflag, cnt_c, cnt_b, err);
+}
+
+// Every vertex of several graphs in one launch: global vertex gv belongs to the graph g
+// with vbase[g] <= gv < vbase[g + 1] (found by binary search), whose flags and counts
+// start at its vbase and kbase and whose status word is err[g].
+template <typename W>
+__global__ void k_validate_many(const ValGraph* __restrict__ gs, const int64_t* __restrict__ vbase, int32_t G,
+                                uint8_t* __restrict__ bflag, int32_t* __restrict__ cnt_c, int32_t* __restrict__ cnt_b,
+                                uint32_t* __restrict__ err) {
+    const int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gv >= vbase[G]) return;
+    int32_t lo = 0, hi = G;  // the last graph starting at or before gv
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (vbase[mid] <= gv) lo = mid; else hi = mid;
+    }
+    while (lo + 1 < G && vbase[lo + 1] <= gv) ++lo;  // (empty graphs share a start)
+    const ValGraph g = gs[lo];
+    const int32_t v = (int32_t)(gv - vbase[lo]);
+    validate_vertex<W>(v, g.n, g.m, g.rp, g.col, reinterpret_cast<const W*>(g.w), g.part, g.k, bflag + vbase[lo],
+                       cnt_c + g.kbase, cnt_b + g.kbase, err + lo);
 }
 
 __global__ void k_make_keys(int32_t n, const int32_t* __restrict__ part, const uint8_t* __restrict__ bflag,
@@ -203,6 +232,18 @@ cudaError_t launch_validate(bool f32, int32_t n, int64_t m, const int64_t* rp, c
     else
         k_validate<int32_t>
             <<<blocks, 256, 0, st>>>(n, m, rp, col, (const int32_t*)w, part, k, bflag, cnt_c, cnt_b, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_many(bool f32, const ValGraph* gs, const int64_t* vbase, int32_t G, int64_t ntot,
+                                 uint8_t* bflag, int32_t* cnt_c, int32_t* cnt_b, uint32_t* err, cudaStream_t st) {
+    if (ntot <= 0 || G <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((ntot + 255) / 256);
+    if (f32)
+        k_validate_many<float><<<blocks, 256, 0, st>>>(gs, vbase, G, bflag, cnt_c, cnt_b, err);
+    else
+        k_validate_many<int32_t><<<blocks, 256, 0, st>>>(gs, vbase, G, bflag, cnt_c, cnt_b, err);
     count_launches(1);
     return cudaGetLastError();
 }
