@@ -149,7 +149,7 @@ int query_sms() {
 // first position, however far it extends past the tile.  dist is symmetric, so a pair is
 // answered as (v, w) with comp(v) = C1 <= C2 = comp(w).
 //
-// Per batch the 8 warps hold 4 queries each; lanes own block columns b2 and walk the rows
+// Per batch the 8 warps hold QPW queries each; lanes own block columns b2 and walk the rows
 // b1 with dist_C1(v1, b1) broadcast by shuffle (one fused add-min per update for int32).
 constexpr int GTH = 256;  // 8 warps
 constexpr int GTILE = 64;
