@@ -37,9 +37,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "queries/s + build min-plus Gop/s (1M-vertex planar), vs INT32/HBM roofline, 1xGB300"
-# DRAM bytes (read + write) per min-plus update of k_backsub: ncu on the delaunay1m build
-# (dram__bytes_read.sum 132,424,525,056 + dram__bytes_write.sum 73,164,538,368 for one
-# launch of 4.4525e12 updates; profiles/k_backsub_delaunay1m_dram.md)
+# DRAM bytes (read + write) per min-plus update of k_backsub, from one ncu capture of its
+# launch on the delaunay1m build: dram__bytes_read.sum 132,424,525,056 +
+# dram__bytes_write.sum 73,164,538,368 over 4.4525e12 updates.  The bench scales it by
+# each launch's update count, so its "traffic" is scaled from that capture, not measured
+# in the run.
 BACKSUB_BYTES_PER_UPDATE = (132424525056 + 73164538368) / 4.4525e12
 UNIT = "queries/s"
 
@@ -62,11 +64,9 @@ def parse():
     p.add_argument("--instances", type=int, default=512, help="batch512: number of instances")
     p.add_argument("--queries", type=int, default=None, help="override the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
-    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--arith", type=int, default=0, help="spq_arith of the build (0 auto, 1 int32, 2 float32)")
     p.add_argument("--bg", type=int, default=0, help="spq_bg_method of the build (0 auto, 1 FW, 2 elimination)")
-    p.add_argument("--server", choices=["native", "python"], default="native",
-                   help="serve: the library's scheduler thread (spq_server_*) or the Python one")
     return p.parse_args()
 
 
@@ -190,6 +190,16 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+def measured_hbm_gbs() -> dict:
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json, written by the pool's
+    driver), else the fallback of one earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return {"value": float(json.load(f)["hbm_gbs"]), "basis": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    except Exception:
+        return {"value": 6800.0, "basis": "of fallback (6.8 TB/s)"}
+
+
 def tuning_summary(spq) -> dict:
     """The grouped query autotuner's choices: size classes per configuration."""
     t = spq.spq_query_tuning()
@@ -200,7 +210,8 @@ def tuning_summary(spq) -> dict:
 def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
     """Time the oracle (Dijkstra per pair, all host cores) on a bounded sample of the
     workload's pairs: chunks of uniformly drawn pairs until budget_s has elapsed.
-    Returns (queries/s, sample size, seconds, cores)."""
+    Returns (queries/s, sample size, seconds, cores, sampled pair indices, their oracle
+    distances as int64)."""
     import numpy as np
 
     import oracle
@@ -211,12 +222,14 @@ def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
     rng = np.random.default_rng(seed)
     oracle.pairs_dist(g.row_ptr, g.col, g.w, w.pairs[:cores], nthreads=cores)  # load, spin up threads
     n, t0 = 0, time.perf_counter()
+    idx, res = [], []
     while time.perf_counter() - t0 < budget_s and n < w.pairs.shape[0]:
-        chunk = w.pairs[rng.integers(0, w.pairs.shape[0], size=8 * cores)]
-        oracle.pairs_dist(g.row_ptr, g.col, g.w, chunk, nthreads=cores)
-        n += chunk.shape[0]
+        ci = rng.integers(0, w.pairs.shape[0], size=8 * cores)
+        res.append(oracle.pairs_dist(g.row_ptr, g.col, g.w, w.pairs[ci], nthreads=cores))
+        idx.append(ci)
+        n += ci.shape[0]
     dt = time.perf_counter() - t0
-    return n / dt, n, dt, cores
+    return n / dt, n, dt, cores, np.concatenate(idx), np.concatenate(res).astype(np.int64)
 
 
 def run_reference(args, rank):
@@ -387,16 +400,13 @@ def run_serve(args, rank, local_rank):
 
     import gen
     import paper_1503_07192_gb300 as spq
-    from paper_1503_07192_gb300.serve import NativeQueryServer, QueryServer
+    from paper_1503_07192_gb300.serve import NativeQueryServer
 
     torch.cuda.set_device(local_rank)
     spq.build()
-    native = args.server == "native"
-    if not native:
-        sys.setswitchinterval(1e-4)  # the scheduler thread shares the interpreter with the producer
     t0 = time.time()
     ws = [gen.configs.grid1024diag()] + gen.configs.batch_instances(count=8, q_per=10)
-    srv = (NativeQueryServer if native else QueryServer)(device=local_rank, slots=4, max_pairs=1 << 20)
+    srv = NativeQueryServer(device=local_rank, slots=4, max_pairs=1 << 20)
     gopts = spq.spq_opts_default()
     gopts.bg_method = args.bg
     for gid, w in enumerate(ws):
@@ -414,25 +424,19 @@ def run_serve(args, rank, local_rank):
         # warm-up: one request per graph
         for gid in range(len(ws)):
             srv.query(gid, reqs[0][1][:1] % ws[gid].graph.n)
-        if native:
-            srv.latency_stats(reset=True)
-        else:
-            srv.completed.clear()
+        srv.latency_stats(reset=True)
         start = time.perf_counter() + 0.05
         t_arr = start + np.cumsum(gaps)
         futs = []
         lag = np.zeros(n_req)
         for i, ((gid, p), ta) in enumerate(zip(reqs, t_arr)):
-            # sleep until just before the arrival (a Python spin would hold the
-            # interpreter lock the Python scheduler thread needs), then submit
+            # sleep until just before the arrival, then submit (latency is counted from
+            # submission: the producer's lag behind the arrival time is reported)
             dt = ta - time.perf_counter()
             if dt > 2e-4:
                 time.sleep(dt - 1e-4)
-            if native:  # (latency counted from submission: the lag behind the arrival is reported)
-                lag[i] = max(0.0, time.perf_counter() - ta)
-                futs.append(srv.submit(gid, p))
-            else:
-                futs.append(srv.submit(gid, p, t_arrival=float(ta)))
+            lag[i] = max(0.0, time.perf_counter() - ta)
+            futs.append(srv.submit(gid, p))
         outs = [f.result(timeout=600) for f in futs]
         t_end = time.perf_counter()
         st = srv.latency_stats()
@@ -443,10 +447,7 @@ def run_serve(args, rank, local_rank):
                       "offered_pairs_s": pairs / (t_arr[-1] - start + 1e-9),
                       "achieved_pairs_s": pairs / (t_end - start), "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                       "same_alone_and_in_mix": bool(same)})
-        if "mean_ms" in st:
-            sweep[-1]["mean_ms"] = st["mean_ms"]
-        if native:
-            sweep[-1]["submit_lag_p99_ms"] = float(np.percentile(lag, 99) * 1e3)
+        sweep[-1]["submit_lag_p99_ms"] = float(np.percentile(lag, 99) * 1e3)
         log(f"[rank {rank}] rate {rate}: {sweep[-1]}")
     srv.close()
     best = sweep[-1]
@@ -454,7 +455,7 @@ def run_serve(args, rank, local_rank):
             "warmup": 1, "ms_per_step": args.duration * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve", "graphs": ["grid1024diag"] + [f"batch{i}" for i in range(8)],
-                       "request_pairs": "U{1..4096}", "arrivals": "Poisson", "slots": 4, "server": args.server},
+                       "request_pairs": "U{1..4096}", "arrivals": "Poisson", "slots": 4, "server": "native"},
             "sweep": sweep}
     print(json.dumps(line), flush=True)
     return 0
@@ -658,6 +659,7 @@ def main():
         spq.spq_query(h, d_pairs, out=d_out)
         eq1.record(stream)
         st, pf = h.stats(), h.profile()
+        pf["query_kernel"] = spq.spq_query_profile(h)
         h.free()  # synchronises the device
         return st, pf, eq0.elapsed_time(eq1)
 
@@ -667,7 +669,6 @@ def main():
         log(f"[rank {rank}] warmup {i}: build stages {[round(pf[k], 1) for k in list(pf)[:6]]} ms, query {qms:.1f} ms"
             f", bg updates {st['bg_updates']:.3e}, order {int(pf.get('order_method', -1))}")
 
-    # correctness spot check outside the timed region (CUDA path vs the last step's output)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -711,8 +712,8 @@ def main():
         "k_phase3_list": {"what": "k_phase3_list (boundary-graph elimination / Floyd-Warshall, phase 3)",
                           "ms": p3_ms, "launches": p3_launches, "updates": p3_updates,
                           "traffic": 6.5329e9 / 32131 * p3_updates / max(p3_launches, 1) / 128 ** 3},
-        # DRAM bytes per min-plus update of the back-substitution, from an ncu capture of
-        # its launch on delaunay1m itself (see profiles/), times this launch's updates
+        # DRAM bytes per min-plus update of the back-substitution (BACKSUB_BYTES_PER_UPDATE),
+        # times this launch's updates
         "k_backsub": {"what": "k_backsub (boundary-graph back-substitution, persistent)",
                       "ms": bs_ms, "launches": bs_launches, "updates": bs_updates,
                       "traffic": BACKSUB_BYTES_PER_UPDATE * bs_updates / max(bs_launches, 1)
@@ -726,9 +727,28 @@ def main():
         ach = kd["updates"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
         return {"kernel": kd["what"], "bound": "alu", "achieved": ach, "peak": peak_gops, "unit": "Gop/s",
                 "frac": (ach / peak_gops) if ach else None, "traffic": kd["traffic"],
-                "traffic_unit": "bytes per launch (DRAM read + write)", "launches": int(kd["launches"]),
+                "traffic_unit": "bytes per launch (DRAM read + write), scaled from one ncu capture",
+                "launches": int(kd["launches"]),
                 "avg_launch_ms": kd["ms"] / max(kd["launches"], 1),
                 "share_of_bg_ms": kd["ms"] / K / max(statistics.mean(pf["bg_fw"] for _, pf, _ in per), 1e-9)}
+
+    # the grouped query kernel (block copy): ALU and DRAM fractions of its own launches
+    qk = [pf.get("query_kernel") for _, pf, _ in per]
+    roof_query = None
+    if all(qk):
+        qms = statistics.mean(x["kernel_ms"] for x in qk)
+        q_upd, q_bytes = qk[0]["updates"], qk[0]["bytes"]
+        hbm_peak = measured_hbm_gbs()
+        roof_query = {
+            "kernel": "k_qb_blocks (grouped queries over the component-blocked copy)", "bound": "alu",
+            "achieved": q_upd / (qms * 1e-3) / 1e9, "peak": peak_gops, "unit": "Gop/s",
+            "frac": q_upd / (qms * 1e-3) / 1e9 / peak_gops, "launches": len(qk), "avg_launch_ms": qms,
+            "updates": q_upd, "hbm": {"achieved": q_bytes / (qms * 1e-3) / 1e9, "peak": hbm_peak["value"],
+                                      "unit": "GB/s", "frac": q_bytes / (qms * 1e-3) / 1e9 / hbm_peak["value"],
+                                      "peak_basis": hbm_peak["basis"], "bytes": q_bytes,
+                                      "bytes_formula": "per item 4*|B1|*ld2 (its block, once) + per pair "
+                                                       "4*(roundup4(|B1|) + ld2) + 16; ld2 = roundup4(|B2|)"},
+            "traffic": None}
 
     # measured issue peak of the update (same process, after the timed region)
     ups, pms = ctypes.c_double(), ctypes.c_double()
@@ -748,7 +768,8 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if st0["arith"] == spq.SPQ_ARITH_F32 else "int32",
+        "dtype": ("int32 results, exact float32 arithmetic (checked)" if st0["arith"] == spq.SPQ_ARITH_F32
+                  else "int32"),
         "data": "synthetic",
         "config": dict(desc, l2="inputs larger than L2 (the 71 GB boundary-graph matrix is rebuilt every step)",
                        parallelism="replicas" if world > 1 else "single GPU"),
@@ -765,12 +786,14 @@ def main():
                            for k in ("validate", "reorder", "comp_fw", "bg_assemble", "bg_fw", "check")},
         "roofline": dict(roof(top), peak_basis=f"{sms} SMs x 128 lanes x 2070 MHz / 2 lane-ops per min-plus "
                                                  "update (derived)", microbench_gops=micro),
-        "roofline_other": [roof(x) for x in other],
+        "roofline_other": [roof(x) for x in other] + ([roof_query] if roof_query else []),
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,
         "query_autotune": tuning_summary(spq),
     }
+
+    last_out = d_out.cpu().numpy()  # answers of the last timed step (outside the timed region)
 
     # end to end through the public API with host buffers (pinned), H2D/D2H inside
     if args.e2e_steps > 0:
@@ -787,21 +810,31 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        spq.spq_free(spq.spq_build(g.n, h_rp, h_col, h_w, h_part, w.k))  # host-buffer path warm
+        torch.cuda.synchronize()
+        e2e_s = []
         for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
             h = spq.spq_build(g.n, h_rp, h_col, h_w, h_part, w.k)
             spq.spq_query(h, h_pairs, out=h_out)
             h.free()
-        te = max_over_ranks(time.perf_counter() - t0, dist, dev)
+            e2e_s.append(time.perf_counter() - t0)
+        te = max_over_ranks(sum(e2e_s), dist, dev)
         line["e2e"] = {"value": whole_job_rate(args.e2e_steps * q, world, te), "unit": UNIT,
                        "h2d_bytes_per_step": int(h2d),
-                       "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+                       "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                       "step_s": [round(x, 4) for x in e2e_s],
+                       "same_answers_as_device_step": bool(np.array_equal(h_out.numpy(), last_out))}
 
     if rank == 0 and world == 1:
-        qps, n, dt, cores = cpu_oracle_sample(w, args.cpu_seconds)
+        qps, n, dt, cores, idx, ref = cpu_oracle_sample(w, args.cpu_seconds)
+        # the oracle's answers on its sample against the GPU's answers of the last timed step
+        ref = np.where(ref >= (1 << 62), spq.SPQ_INF_I32, ref)
+        agree = int((last_out[idx].astype(np.int64) == ref).sum())
         line["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n} uniformly drawn pairs of the workload ({dt:.1f} s), binary-heap "
-                                          f"Dijkstra with early exit per pair, OpenMP over pairs, no preprocessing"}
+                                          f"Dijkstra with early exit per pair, OpenMP over pairs, no preprocessing",
+                                "gpu_answers_equal_on_sample": f"{agree}/{n}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

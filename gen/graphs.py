@@ -142,14 +142,15 @@ def delaunay(npts: int, seed: int = 0, weight: str = "int_1e6", lognormal_sigma:
     """Delaunay triangulation of npts uniform points in the unit square.
 
     weight = "int_1e6": w = round(1e6 * Euclidean length) as int32, clamped to >= 1.
+    weight = "int": w = round(scale * Euclidean length) as int32, clamped to >= 1.
     weight = "f32_lognormal": w = scale * length * exp(N(0, sigma^2)) as float32
     (the lognormal factor is drawn once per undirected edge)."""
     xy = delaunay_points(npts, seed)
     u, v = delaunay_edges(xy)
     length = np.sqrt(((xy[u] - xy[v]) ** 2).sum(axis=1))
     meta = {"kind": "delaunay", "npts": npts}
-    if weight == "int_1e6":
-        w = np.rint(1e6 * length)
+    if weight in ("int_1e6", "int"):
+        w = np.rint((1e6 if weight == "int_1e6" else scale) * length)
         meta["clamped_to_1"] = int((w < 1).sum())
         w = np.maximum(w, 1).astype(np.int32)
     elif weight == "f32_lognormal":

@@ -22,6 +22,9 @@
  *   - Pointer arguments may point to host memory or to device memory of the current
  *     device; the library tells them apart with cudaPointerGetAttributes.  Inputs are
  *     borrowed for the duration of the call only; outputs are owned by the caller.
+ *   - A handle lives on the device that was current when it was built; every call that
+ *     takes a handle must be made with that device current (SPQ_EINVAL otherwise, before
+ *     any work is queued).
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is queued on
  *     it.  spq_build returns after its work has completed.  spq_query with host output
  *     returns after the results are in host memory; with device output it returns once
@@ -124,6 +127,13 @@ typedef struct spq_opts {
                                component (components of up to 4096 vertices; larger ones
                                take Floyd-Warshall); SPQ_BG_AUTO (default, and what a
                                struct_size ending before this field means): elimination */
+    int32_t block_copy;     /* 1 (default, and what a struct_size ending before this field
+                               means): the build also keeps a copy of the boundary matrix's
+                               upper block-triangle grouped by component (block (C1, C2),
+                               C1 <= C2, contiguous: the paper's Fig. 1 layout), about half
+                               the matrix's memory, from which the grouped queries stage each
+                               block with 16-byte copies; 0: no copy, the grouped queries
+                               gather their blocks from the matrix */
 } spq_opts;
 
 /* Fill *opts with the defaults (also what opts == NULL means). */
@@ -147,8 +157,8 @@ void spq_opts_default(spq_opts* opts);
  * G must be symmetric: for every slot u -> v (u != v) there is a slot v -> u, and the
  * smallest weight over the parallel slots u -> v equals that over v -> u.  Parallel
  * slots are allowed (the smallest weight is the edge's weight, as a path takes the
- * lightest) and self-loops are ignored.  Weights must be >= 0 (and finite for SPQ_F32).
- * For SPQ_I32 every finite distance must be < SPQ_INF_I32.
+ * lightest) and self-loops are ignored.  Weights must be >= 0 (and finite for SPQ_F32);
+ * SPQ_I32 weights must be below SPQ_INF_I32, and every finite distance must be too.
  *
  * Arithmetic: with SPQ_ARITH_AUTO or _F32 the Floyd-Warshall updates of an SPQ_I32
  * graph run in float32 and the library then checks that every finite table entry is
@@ -158,7 +168,7 @@ void spq_opts_default(spq_opts* opts);
  * build is redone with int32 arithmetic.
  *
  * Errors: SPQ_EINVAL for n < 1, k < 1, a bad row_ptr, col or part entry, a negative or
- * non-finite weight, or an asymmetric graph; SPQ_ENOMEM if the tables (about
+ * non-finite weight, an SPQ_I32 weight >= SPQ_INF_I32, or an asymmetric graph; SPQ_ENOMEM if the tables (about
  * 4 * (sum over C of |C|^2 + |BG|^2) bytes, rows padded to 4 entries) exceed free device
  * memory; SPQ_ECUDA on a CUDA failure.  On error nothing is leaked and *out is NULL.
  */
@@ -177,6 +187,11 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
  * A pair with an id outside [0, n) yields -1 (SPQ_I32) or NaN (SPQ_F32) in its slot and
  * marks the handle: with host buffers the call then returns SPQ_EINVAL; with device
  * buffers, spq_query_status reports it.
+ *
+ * Kernel choice: the first grouped launch of a size class (see spq_query_tuning) in the
+ * process runs both kernel configurations on its inputs, timed with CUDA events (the
+ * answers are the same), so that call costs about twice the device time; the host does
+ * not wait for the timing, which a later launch of the class reads once it is complete.
  */
 spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream);
 
@@ -190,7 +205,7 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
  *   - q <= SPQ_NOALLOC_MAX_PAIRS (a larger q returns SPQ_EINVAL and queues nothing);
  *   - pairs and dist_out must be device memory (else SPQ_EINVAL); the call returns once
  *     the work is queued, and spq_query_status reports out-of-range pairs;
- *   - its scratch is one fixed array of about 4.3 MB in the library's device memory,
+ *   - its scratch is one fixed array of about 13.7 MB in the library's device memory,
  *     present on every GPU that loads the library until the process exits.  The first
  *     call on a device looks up that array's address (cudaGetSymbolAddress, once per
  *     device); make that first call before any stream capture.  All calls share the

@@ -7,6 +7,8 @@
 
 #include <stdint.h>
 
+#include "spq.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -43,11 +45,35 @@ int spq_boundary_order_host(int k, const long long* adj_ptr, const int* adj, con
 
 /* The grouped query's autotuner: its choices so far, per (device, size class), as
  * keys[i] = device * 256 + class and choices[i] = configuration (0: 4 pairs per warp,
- * two CTAs per SM; 1: 2 pairs per warp, three CTAs per SM).  The class is
+ * two CTAs per SM; 1: 2 pairs per warp, three CTAs per SM; -1: measured, not read yet).  The class is
  * 16 * (clamp(floor(log2(pairs per component pair)), -6, 9) + 6)
  *    + min(floor(log2(boundary slots per component)), 15).
  * Writes at most cap entries; returns how many there are. */
 int32_t spq_query_tuning(int32_t* keys, int32_t* choices, int32_t cap);
+
+/* Test hook of the back-substitution's bounded dependency waits (a CTA waits on a flag that
+ * another CTA of the same launch sets when it finishes a tile the first one reads; each
+ * wait gives up after a bound, the launch stops and the build returns SPQ_ETIMEOUT).
+ *   limit_ns  the bound of one wait in nanoseconds; 0 restores the default (2 s)
+ *   withhold  nonzero: the launches compute every tile but set none of those flags, so the
+ *             first tile that depends on another waits until the bound runs out
+ * Applies to the launches queued after the call, process-wide.  No wait is unbounded
+ * either way, and nothing faults: the launch returns and the device stays usable. */
+void spq_test_backsub_wait(unsigned long long limit_ns, int32_t withhold);
+
+/* The last grouped query launch on h with the block copy (h built with
+ * opts.profile_kernels = 1): the block-copy kernel's device time (CUDA events on the
+ * query's stream), its min-plus updates (sum over pairs of |B1| x |B2|) and the bytes it
+ * must move: each item's block once (|B1| x ld2 x 4, ld2 = |B2| rounded up to 4), per pair
+ * its two table rows (4 x (|B1| rounded up to 4 + ld2)) plus 16 bytes (the pair, its
+ * position, its answer).  Waits for that launch.  SPQ_EUNSUPPORTED if h was not built for
+ * profiling or has run no such launch. */
+spq_status spq_query_profile(const spq_handle* h, double* kernel_ms, double* updates, double* bytes);
+
+/* Bytes of the library's device memory pool on `device` (the tables and the
+ * stream-ordered scratch of every entry point come from it): in use by live allocations,
+ * and reserved from the device.  Returns 0, or a cudaError_t code. */
+int spq_pool_usage(int device, unsigned long long* used, unsigned long long* reserved);
 
 /* Number of kernels this library has launched in this process so far (all entry
  * points, all devices; the micro-benchmark above excluded). */

@@ -22,6 +22,8 @@ from ._lib import (  # noqa: F401
     SPQ_ECUDA,
     SPQ_EINVAL,
     SPQ_ENOMEM,
+    SPQ_ETIMEOUT,
+    SPQ_EUNSUPPORTED,
     SPQ_OK,
     SPQ_ARITH_AUTO,
     SPQ_ARITH_F32,
@@ -444,6 +446,17 @@ def spq_query_tuning() -> dict:
     ch = (ctypes.c_int32 * max(n, 1))()
     n = min(n, int(lib.spq_query_tuning(keys, ch, n)))
     return {(keys[i] // 256, keys[i] % 256): int(ch[i]) for i in range(n)}
+
+
+def spq_query_profile(h) -> dict | None:
+    """The last grouped query launch on h (built with opts.profile_kernels = 1): the
+    block-copy kernel's device ms, its min-plus updates and algorithmic bytes; None if
+    there is none."""
+    ms, upd, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = _lib.load().spq_query_profile(h.ptr, ctypes.byref(ms), ctypes.byref(upd), ctypes.byref(by))
+    if st:
+        return None
+    return {"kernel_ms": ms.value, "updates": upd.value, "bytes": by.value}
 
 
 def spq_kernel_launches() -> int:

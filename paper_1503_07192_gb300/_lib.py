@@ -24,7 +24,7 @@ i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 class SpqOpts(ctypes.Structure):
     _fields_ = [("struct_size", i32), ("arith", i32), ("order", i32), ("skip_inf_tiles", i32),
                 ("profile_kernels", i32), ("query_grouped", i32), ("bg_method", i32),
-                ("bg_panel_mib", i32), ("comp_method", i32)]
+                ("bg_panel_mib", i32), ("comp_method", i32), ("block_copy", i32)]
 
 
 class SpqGraph(ctypes.Structure):
@@ -68,6 +68,10 @@ SIGNATURES = {
     "spq_peak_minplus": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(f64),
                                         ctypes.POINTER(f64)]),
     "spq_kernel_launches": (ctypes.c_ulonglong, []),
+    "spq_test_backsub_wait": (None, [ctypes.c_ulonglong, i32]),
+    "spq_query_profile": (ctypes.c_int, [P, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(f64)]),
+    "spq_pool_usage": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong),
+                                      ctypes.POINTER(ctypes.c_ulonglong)]),
     "spq_component_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, ctypes.c_int, P, P]),
     "spq_boundary_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.c_int, P]),
     "spq_get_meta": (ctypes.c_int, [P, P, P, P, P, P, P]),

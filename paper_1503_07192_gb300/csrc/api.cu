@@ -39,6 +39,7 @@ spq_status read_opts(const spq_opts* in, spq_opts* o) {
     if (o->order < SPQ_ORDER_AUTO || o->order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
     if (o->bg_method < SPQ_BG_AUTO || o->bg_method > SPQ_BG_ELIM || o->bg_panel_mib < 0) return SPQ_EINVAL;
     if (o->comp_method < SPQ_BG_AUTO || o->comp_method > SPQ_BG_ELIM) return SPQ_EINVAL;
+    if (o->block_copy != 0 && o->block_copy != 1) return SPQ_EINVAL;
     return SPQ_OK;
 }
 }  // namespace spq
@@ -58,6 +59,7 @@ namespace {
 constexpr int64_t kGroupedMinQueries = 4096;
 
 spq_status cuda_fail(cudaError_t e) {
+    if (e == kWaitGaveUp) return SPQ_ETIMEOUT;
     g_last_cuda = (int)e;
     return SPQ_ECUDA;
 }
@@ -143,10 +145,13 @@ void free_handle_memory(spq_handle* h) {
         return;
     }
     void* ps[] = {h->comp,   h->local,   h->descs,   h->nb,  h->bg_off, h->bgpos,  h->csize, h->apsp,
-                  h->D,      h->err,     h->csr_rp,  h->csr_col, h->csr_w, h->vorder, h->vstart};
+                  h->D,      h->err,     h->csr_rp,  h->csr_col, h->csr_w, h->vorder, h->vstart,
+                  h->Dc,     h->dcS,     h->dcP,   h->qstats};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);  // back to the pool
     cudaStreamSynchronize(0);
+    for (cudaEvent_t& e : h->qev)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -185,7 +190,7 @@ int bits_for(uint64_t x) {
 
 // CUDA events bracketing the build stages (see spq_build_profile).
 struct StageEvents {
-    cudaEvent_t ev[7] = {};
+    cudaEvent_t ev[8] = {};
     bool ok = true;
     StageEvents() {
         for (auto& e : ev)
@@ -199,7 +204,7 @@ struct StageEvents {
         if (ok) cudaEventRecord(ev[i], st);
     }
     void collect(double* ms) {
-        for (int i = 0; i < 6; ++i) {
+        for (int i = 0; i < 7; ++i) {
             float t = 0.f;
             ms[i] = (ok && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ? (double)t : 0.0;
         }
@@ -443,6 +448,12 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         bo += h->h_nb[c];
     }
     h->nbg = bo;
+    // the component-blocked copy of the boundary matrix for the grouped queries
+    std::vector<int64_t> dcS, dcP;
+    int64_t dc_elems = 0;
+    int32_t dc_max = 0;
+    const bool want_dc = opts.query_grouped != 0 && opts.block_copy != 0 && bo > 0;
+    if (want_dc) dc_layout(h->h_nb, &dcS, &dcP, &dc_elems, &dc_max);
     // matrix order: the slots, plus (elimination form) up to 15 alignment gaps of < 128
     const bool may_elim = opts.bg_method != SPQ_BG_FW && bo > 0;
     const int64_t n_max = round_up(bo + (may_elim ? 15 * (kTile - 1) : 0), 4);
@@ -463,7 +474,8 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const size_t comp_elim_bytes = opts.comp_method != SPQ_BG_FW ? 4 * (size_t)h->apsp_elems + 8 * (size_t)n : 0;
     size_t need = 4 * (size_t)h->apsp_elems + comp_elim_bytes + 4 * (size_t)n_max * (size_t)n_max + 8 * (size_t)n +
                   (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words_max + hist_words) +
-                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + (64u << 20);
+                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + 4 * (size_t)dc_elems +
+                  16 * ((size_t)k + 1) + (64u << 20);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     free_b += pool_cached_bytes(h->device);
@@ -596,6 +608,28 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
             if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
     }
+    if (want_dc) {
+        CK(dev_alloc((uint32_t**)&h->Dc, (size_t)dc_elems, &bytes, st));
+        CK(dev_alloc(&h->dcS, (size_t)k, &bytes, st));
+        CK(dev_alloc(&h->dcP, (size_t)k + 1, &bytes, st));
+        h->bytes = bytes;
+        h->dc_elems = dc_elems;
+        h->dc_max_ld = dc_max;
+        if (opts.profile_kernels) {
+            CK(dev_alloc(&h->qstats, 2, &bytes, st));
+            CK(cudaEventCreate(&h->qev[0]));
+            CK(cudaEventCreate(&h->qev[1]));
+        }
+        CK(cudaMemcpyAsync(h->dcS, dcS.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->dcP, dcP.data(), ((size_t)k + 1) * 8, cudaMemcpyHostToDevice, st));
+        if (h->f32store)
+            CK(launch_build_dc<float>((const float*)h->D, h->N, h->bgpos, h->bg_off, h->nb, h->dcS, h->dcP, k, h->nbg,
+                                      dcP[k], (float*)h->Dc, st));
+        else
+            CK(launch_build_dc<int32_t>((const int32_t*)h->D, h->N, h->bgpos, h->bg_off, h->nb, h->dcS, h->dcP, k,
+                                        h->nbg, dcP[k], (int32_t*)h->Dc, st));
+    }
+    evs.mark(7, st);
     CK(cudaStreamSynchronize(st));
     evs.collect(h->prof_ms);
     return SPQ_OK;
@@ -616,6 +650,7 @@ void spq_opts_default(spq_opts* o) {
     o->bg_method = SPQ_BG_AUTO;
     o->bg_panel_mib = 0;
     o->comp_method = SPQ_BG_AUTO;
+    o->block_copy = 1;
 }
 
 spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
@@ -651,7 +686,7 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
 spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream) {
     if (!h || q < 0) return SPQ_EINVAL;
     if (q == 0) return SPQ_OK;
-    if (!pairs || !dist_out) return SPQ_EINVAL;
+    if (!pairs || !dist_out || !on_handle_device(h)) return SPQ_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool pd = is_device_ptr(pairs), od = is_device_ptr(dist_out);
     if (pd != od) return SPQ_EINVAL;
@@ -662,14 +697,13 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
     if (h->query_grouped && q >= kGroupedMinQueries && h->k <= 65535)
         CK(tmp.alloc(&scratch, (size_t)query_scratch_words(q)));
     auto launch = [&](const int32_t* p, void* o) -> cudaError_t {
-        if (h->f32store) {
-            QueryCtx<float> c{h->n,   h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
-                              (const float*)h->D, h->N, h->err};
-            return launch_query<float>(c, p, q, o, out_f32, (uint32_t)h->k, scratch, st);
-        }
-        QueryCtx<int32_t> c{h->n,     h->comp,   h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
-                            (const int32_t*)h->D, h->N, h->err};
-        return launch_query<int32_t>(c, p, q, o, out_f32, (uint32_t)h->k, scratch, st);
+        QueryCtx<int32_t> ci;
+        QueryCtx<float> cf;
+        bool f32store = false, of32 = false;
+        int32_t k = 0;
+        handle_query_view(h, &ci, &cf, &f32store, &of32, &k);
+        return f32store ? launch_query<float>(cf, p, q, o, out_f32, (uint32_t)k, scratch, st)
+                        : launch_query<int32_t>(ci, p, q, o, out_f32, (uint32_t)k, scratch, st);
     };
     if (pd) {
         if (((uintptr_t)pairs & 7u) || ((uintptr_t)dist_out & 3u)) return SPQ_EINVAL;
@@ -695,7 +729,7 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
 }
 
 spq_status spq_query_status(spq_handle* h, void* stream) {
-    if (!h) return SPQ_EINVAL;
+    if (!h || !on_handle_device(h)) return SPQ_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t f = 0;
     CK(cudaMemcpyAsync(&f, h->err, sizeof(f), cudaMemcpyDeviceToHost, st));
@@ -748,7 +782,7 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
 
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     if (!h || !ms || count <= 0) return 0;
-    double v[15];
+    double v[16];
     for (int i = 0; i < 6; ++i) v[i] = h->prof_ms[i];
     v[6] = h->fwprof.p3_ms;
     v[7] = (double)h->fwprof.p3_launches;
@@ -759,16 +793,41 @@ int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     v[12] = h->fwprof.bs_updates;
     v[13] = h->fwprof.bs_items;
     v[14] = (double)h->fwprof.bs_launches;
-    int32_t c = count < 15 ? count : 15;
+    v[15] = h->prof_ms[6];
+    int32_t c = count < 16 ? count : 16;
     for (int32_t i = 0; i < c; ++i) ms[i] = v[i];
     return c;
 }
 
 unsigned long long spq_kernel_launches(void) { return spq::g_kernel_launches.load(); }
 
+spq_status spq_query_profile(const spq_handle* h, double* kernel_ms, double* updates, double* bytes) {
+    if (!h || !h->qstats || !h->qprof_ran) return SPQ_EUNSUPPORTED;
+    unsigned long long st[2] = {0, 0};
+    float ms = 0.f;
+    CK(cudaEventSynchronize(h->qev[1]));
+    CK(cudaEventElapsedTime(&ms, h->qev[0], h->qev[1]));
+    CK(cudaMemcpy(st, h->qstats, sizeof(st), cudaMemcpyDeviceToHost));
+    if (kernel_ms) *kernel_ms = ms;
+    if (updates) *updates = (double)st[0];
+    if (bytes) *bytes = (double)st[1];
+    return SPQ_OK;
+}
+
+int spq_pool_usage(int device, unsigned long long* used, unsigned long long* reserved) {
+    cudaMemPool_t pool;
+    cudaError_t e = table_pool(device, &pool);
+    uint64_t u = 0, r = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+    if (used) *used = u;
+    if (reserved) *reserved = r;
+    return (int)e;
+}
+
 spq_status spq_get_meta(const spq_handle* h, int32_t* comp, int32_t* local, int32_t* csize, int32_t* nb,
                         int32_t* bg_off, void* stream) {
-    if (!h) return SPQ_EINVAL;
+    if (!h || !on_handle_device(h)) return SPQ_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     struct Item {
         int32_t* dst;
@@ -789,7 +848,7 @@ spq_status spq_get_meta(const spq_handle* h, int32_t* comp, int32_t* local, int3
 }
 
 spq_status spq_get_apsp(const spq_handle* h, int32_t c, void* out, void* stream) {
-    if (!h || c < 0 || c >= h->k || !out) return SPQ_EINVAL;
+    if (!h || c < 0 || c >= h->k || !out || !on_handle_device(h)) return SPQ_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t sz = h->h_csize[c];
     if (sz == 0) return SPQ_OK;
@@ -801,7 +860,7 @@ spq_status spq_get_apsp(const spq_handle* h, int32_t c, void* out, void* stream)
 }
 
 spq_status spq_get_bg(const spq_handle* h, void* out, void* stream) {
-    if (!h || !out) return SPQ_EINVAL;
+    if (!h || !out || !on_handle_device(h)) return SPQ_EINVAL;
     if (h->nbg == 0) return SPQ_OK;
     cudaStream_t st = (cudaStream_t)stream;
     return copy_table_out(h->f32store && h->wt == SPQ_I32, h->D, h->nbg, h->nbg, h->N, h->bgpos, out, st) == cudaSuccess
@@ -813,13 +872,28 @@ spq_status spq_get_bg(const spq_handle* h, void* out, void* stream) {
 
 namespace spq {
 
+bool on_handle_device(const spq_handle* h) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return dev == h->device;
+}
+
 // Read-only view of a handle's device tables for entry points defined in other files.
 void handle_query_view(const spq_handle* h, QueryCtx<int32_t>* ci, QueryCtx<float>* cf, bool* f32store, bool* out_f32,
                        int32_t* k) {
-    *ci = QueryCtx<int32_t>{h->n,     h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
-                            (const int32_t*)h->D, h->N, h->err};
-    *cf = QueryCtx<float>{h->n,   h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
-                          (const float*)h->D, h->N, h->err};
+    *ci = QueryCtx<int32_t>{h->n,      h->comp,   h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
+                            (const int32_t*)h->D, h->N, h->err, (const int32_t*)h->Dc, h->dcS, h->dcP, h->dc_max_ld};
+    *cf = QueryCtx<float>{h->n,    h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
+                          (const float*)h->D, h->N, h->err, (const float*)h->Dc, h->dcS, h->dcP, h->dc_max_ld};
+    if (h->qstats) {
+        spq_handle* m = const_cast<spq_handle*>(h);
+        m->qprof_ran = true;
+        ci->qev = cf->qev = m->qev;
+        ci->qstats = cf->qstats = m->qstats;
+    }
     *f32store = h->f32store;
     *out_f32 = h->wt == SPQ_F32;
     *k = h->k;

@@ -43,7 +43,9 @@ thread_local int g_batch_cuda_error = 0;
 constexpr int64_t kBatchElimMin = 4096;
 
 spq_status batch_cuda_fail(cudaError_t e) {
+    if (e == kWaitGaveUp) return SPQ_ETIMEOUT;
     g_batch_cuda_error = (int)e;
+    note_cuda_error(e);  // (spq_last_cuda_error)
     return SPQ_ECUDA;
 }
 
@@ -820,6 +822,7 @@ spq_status spq_query_many(int32_t count, spq_handle* const* hs, const int32_t* c
     bool any_dev = false, any_host = false;
     for (int32_t i = 0; i < count; ++i) {
         if (!hs[i] || q[i] < 0 || (q[i] > 0 && (!pairs[i] || !dist_out[i]))) return SPQ_EINVAL;
+        if (!on_handle_device(hs[i])) return SPQ_EINVAL;
         if (q[i] == 0) continue;
         const bool pd = dev_pointer(pairs[i]), od = dev_pointer(dist_out[i]);
         if (pd != od) return SPQ_EINVAL;
@@ -931,6 +934,7 @@ spq_status spq_query_plan_create(int32_t count, spq_handle* const* hs, const int
     int64_t qmax = 0;
     for (int32_t i = 0; i < count; ++i) {
         if (!hs[i] || q[i] < 0 || (q[i] > 0 && (!pairs[i] || !dist_out[i]))) return SPQ_EINVAL;
+        if (!on_handle_device(hs[i])) return SPQ_EINVAL;
         if (q[i] == 0) continue;
         if (!dev_pointer(pairs[i]) || !dev_pointer(dist_out[i])) return SPQ_EINVAL;
         if (((uintptr_t)pairs[i] & 7u) || ((uintptr_t)dist_out[i] & 3u)) return SPQ_EINVAL;
@@ -955,6 +959,7 @@ spq_status spq_query_plan_create(int32_t count, spq_handle* const* hs, const int
     if (cs) cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
         plan_destroy(p);
+        cudaGetLastError();  // a failed capture leaves no error behind for later calls
         return batch_cuda_fail(e);
     }
     *out = p;

@@ -22,6 +22,10 @@ enum : uint32_t {
     kErrWait = 128u,  // a bounded device-side wait gave up (back-substitution dependencies)
 };
 
+// Internal return code of the host helpers when a bounded device-side wait gave up (the
+// back-substitution's kErrWait); the entry points turn it into SPQ_ETIMEOUT.
+constexpr cudaError_t kWaitGaveUp = cudaErrorLaunchTimeout;
+
 constexpr int kTile = 128;  // Floyd-Warshall tile edge (rows = columns = pivot block)
 
 // +infinity / the int32 sentinel, per table element type.
@@ -242,6 +246,17 @@ struct QueryCtx {
     const T* D;
     int64_t N;
     uint32_t* err;
+    // the component-blocked copy of the matrix's upper block-triangle (query_blocks.cu), or
+    // null: block (c1 <= c2) at dcS[c1] + nb[c1] * (dcP[c2] - dcP[c1]), rows of
+    // dcP[c2 + 1] - dcP[c2] elements; dc_max_ld its widest row
+    const T* Dc = nullptr;
+    const int64_t* dcS = nullptr;
+    const int64_t* dcP = nullptr;
+    int32_t dc_max_ld = 0;
+    // profiling (built with opts.profile_kernels): events around the block-copy kernel
+    // and its algorithmic counts (min-plus updates, bytes), or null
+    cudaEvent_t* qev = nullptr;
+    unsigned long long* qstats = nullptr;
 };
 // Queries; with scratch (query_scratch_words(q) words) and k <= 65535 the grouped form
 // (sorted by component pair), else one warp per query in input order.
@@ -249,6 +264,33 @@ int64_t query_scratch_words(int64_t q);
 template <typename T>
 cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
                          uint32_t k, uint32_t* scratch, cudaStream_t st);
+
+// ---- query_blocks.cu ----
+// Layout of the block copy for the boundary counts nb: dcS (k), dcP (k + 1), its
+// elements and its widest padded row.
+void dc_layout(const std::vector<int32_t>& nb, std::vector<int64_t>* S, std::vector<int64_t>* P, int64_t* elems,
+               int32_t* max_ld);
+// The copy from the boundary-graph matrix D (N x N, slot s at row / column bgpos[s]).
+template <typename T>
+cudaError_t launch_build_dc(const T* D, int64_t N, const int32_t* bgpos, const int32_t* bg_off, const int32_t* nb,
+                            const int64_t* S, const int64_t* P, int32_t k, int64_t nbg, int64_t Pk, T* Dc,
+                            cudaStream_t st);
+// Widest block (padded columns) the block-copy query handles; wider blocks take the
+// gathering form of query.cu.
+int32_t query_blocks_max_ld();
+// Scratch words of launch_query_blocks beyond the sort's.
+int64_t query_blocks_scratch_words(int64_t q);
+// The grouped queries over the block copy, given the pairs' sorted keys and positions.
+template <typename T>
+cudaError_t launch_query_blocks(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
+                                uint32_t k, const uint32_t* keys, const uint32_t* idx, uint32_t* scratch,
+                                cudaStream_t st);
+
+// True if the current device is the one h was built on (api.cu).  Every entry point that
+// queues work on a handle's tables checks this first: the tables and the library's scratch
+// pool are per device, so work queued with another device current would read another
+// GPU's memory.
+bool on_handle_device(const spq_handle* h);
 
 // Read-only view of a handle's device tables (api.cu), for other entry points.
 void handle_query_view(const spq_handle* h, QueryCtx<int32_t>* ci, QueryCtx<float>* cf, bool* f32store, bool* out_f32,

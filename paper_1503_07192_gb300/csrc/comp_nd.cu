@@ -291,7 +291,7 @@ cudaError_t comp_elim_finish(T* apsp, T* P, const MatDesc* d_descs, const std::v
     uint32_t f = 0;
     if ((e = cudaMemcpyAsync(&f, err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
-    if (f & kErrWait) return done(cudaErrorLaunchTimeout);
+    if (f & kErrWait) return done(kWaitGaveUp);
     if (updates) *updates = fwd + bs;
     return done(cudaSuccess);
 }

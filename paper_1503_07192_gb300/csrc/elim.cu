@@ -30,6 +30,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <vector>
 
@@ -41,6 +42,11 @@ namespace spq {
 namespace {
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of one dependency wait
+
+// Test hook (spq_test_backsub_wait): a shorter bound, and launches that release none of
+// their tiles, so that a dependency wait runs out without any fault or hang.
+std::atomic<unsigned long long> g_wait_ns{kWaitNs};
+std::atomic<int> g_withhold{0};
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -342,7 +348,8 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
               const int64_t* __restrict__ koff, const int32_t* __restrict__ kcnt, const int32_t* __restrict__ klist,
               const T* __restrict__ A, int64_t aoff0, const int32_t* __restrict__ fblk,
               const int32_t* __restrict__ fcnt, uint32_t* __restrict__ tflags,
-              unsigned long long* __restrict__ counter, uint32_t* __restrict__ err, uint32_t* __restrict__ exact) {
+              unsigned long long* __restrict__ counter, uint32_t* __restrict__ err, uint32_t* __restrict__ exact,
+              unsigned long long wait_ns, int withhold) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     __shared__ int64_t s_item;
@@ -393,7 +400,12 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
                         const unsigned long long t0 = global_ns();
                         while (ld_acquire(f) == 0u) {
                             __nanosleep(256);
-                            if (global_ns() - t0 > kWaitNs) {
+                            // another CTA gave up (the launch is abandoned), or the bound ran out
+                            if (*reinterpret_cast<volatile uint32_t*>(err) & kErrWait) {
+                                s_fail = 1;
+                                break;
+                            }
+                            if (global_ns() - t0 > wait_ns) {
                                 atomicOr(err, kErrWait);
                                 s_fail = 1;
                                 break;
@@ -469,7 +481,7 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS)
             if (J != R) store_c_transposed<T>(acc, M, N, r0, c0, tx, ty);
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !withhold) {
             __threadfence();
             st_release(tflags + m.pair0 + (int64_t)R * nR + J, 1u);
         }
@@ -702,7 +714,8 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
         cudaMemsetAsync(counter, 0, 8, st);
         if (prof) cudaEventRecord(ev[2 * l], st);
         kern<<<grid, NTH, psm, st>>>(mats, runs + run0[l], (int32_t)(run0[l + 1] - run0[l]), nit[l], koff, kcnt, klist,
-                                     A, aoff0, fblk, fcnt, tflags, counter, err, exact);
+                                     A, aoff0, fblk, fcnt, tflags, counter, err, exact, g_wait_ns.load(),
+                                     g_withhold.load());
         if (prof) cudaEventRecord(ev[2 * l + 1], st);
         count_launches(2);
         e = cudaGetLastError();
@@ -741,3 +754,8 @@ template cudaError_t launch_fill_marked<float>(float*, int64_t, const uint32_t*,
 template cudaError_t launch_fill_marked<int32_t>(int32_t*, int64_t, const uint32_t*, cudaStream_t);
 
 }  // namespace spq
+
+extern "C" void spq_test_backsub_wait(unsigned long long limit_ns, int32_t withhold) {
+    spq::g_wait_ns.store(limit_ns > 0 ? limit_ns : spq::kWaitNs);
+    spq::g_withhold.store(withhold != 0 ? 1 : 0);
+}

@@ -329,7 +329,7 @@ extern "C" {
 spq_status spq_query_saved(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, int32_t* saved,
                            void* stream) {
     using namespace spq;
-    if (!h || q < 0) return SPQ_EINVAL;
+    if (!h || q < 0 || !on_handle_device(h)) return SPQ_EINVAL;
     if (q == 0) return SPQ_OK;
     if (!h->vorder || !h->csr_rp) return SPQ_EUNSUPPORTED;
     if (!on_device(pairs) || !on_device(dist_out) || !on_device(saved)) return SPQ_EINVAL;
@@ -351,7 +351,7 @@ spq_status spq_query_saved(spq_handle* h, const int32_t* pairs, int64_t q, void*
 spq_status spq_query_backward(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved,
                               const float* grad_dist, float* grad_w, void* stream) {
     using namespace spq;
-    if (!h || q < 0) return SPQ_EINVAL;
+    if (!h || q < 0 || !on_handle_device(h)) return SPQ_EINVAL;
     if (q == 0) return SPQ_OK;
     if (!h->vorder || !h->csr_rp) return SPQ_EUNSUPPORTED;
     if (!on_device(pairs) || !on_device(saved) || !on_device(grad_dist) || !on_device(grad_w)) return SPQ_EINVAL;
@@ -374,7 +374,7 @@ spq_status spq_query_backward(spq_handle* h, const int32_t* pairs, int64_t q, co
 spq_status spq_query_paths(spq_handle* h, const int32_t* pairs, int64_t q, const int32_t* saved, int32_t max_len,
                            int32_t* verts, int32_t* lens, void* stream) {
     using namespace spq;
-    if (!h || q < 0 || max_len < 0) return SPQ_EINVAL;
+    if (!h || q < 0 || max_len < 0 || !on_handle_device(h)) return SPQ_EINVAL;
     if (q == 0) return SPQ_OK;
     if (!h->vorder || !h->csr_rp) return SPQ_EUNSUPPORTED;
     if (!on_device(pairs) || !on_device(saved) || !on_device(lens) || (max_len > 0 && !on_device(verts)))

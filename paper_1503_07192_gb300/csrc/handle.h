@@ -38,12 +38,22 @@ struct spq_handle {
     int32_t* csize = nullptr;
     void* apsp = nullptr;
     void* D = nullptr;
+    // component-blocked copy of D's upper block-triangle, for the grouped queries
+    void* Dc = nullptr;
+    int64_t* dcS = nullptr;
+    int64_t* dcP = nullptr;
+    int32_t dc_max_ld = 0;
+    int64_t dc_elems = 0;
+    // profiling of the grouped query kernel (opts.profile_kernels)
+    cudaEvent_t qev[2] = {nullptr, nullptr};
+    unsigned long long* qstats = nullptr;  // device: updates, bytes of the last profiled launch
+    bool qprof_ran = false;
     uint32_t* err = nullptr;
     int64_t N = 0, nbg = 0;
     int64_t apsp_elems = 0;
     size_t bytes = 0;
     double comp_updates = 0.0, bg_updates = 0.0;
-    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    double prof_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     spq::FwProfile fwprof;
     std::vector<int32_t> h_csize, h_nb, h_bgoff;
     std::vector<spq::MatDesc> h_descs;

@@ -13,7 +13,9 @@ namespace spq {
 
 namespace {
 
-__device__ __forceinline__ bool weight_ok(int32_t w) { return w >= 0; }
+// int32 weights: below SPQ_INF_I32, the sentinel of an unreachable pair (a weight at or
+// above it would read as infinity, and sums of such weights could overflow)
+__device__ __forceinline__ bool weight_ok(int32_t w) { return w >= 0 && w < SPQ_INF_I32; }
 __device__ __forceinline__ bool weight_ok(float w) { return isfinite(w) && w >= 0.0f; }
 
 // One thread per vertex v: range checks of its CSR row, its weights and its part, the

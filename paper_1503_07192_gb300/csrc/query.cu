@@ -179,6 +179,8 @@ __global__ void k_query_keys(const int2* __restrict__ pairs, int64_t q, int32_t 
 __device__ __forceinline__ int32_t addmin(int32_t a, int32_t b, int32_t t) { return __viaddmin_s32(a, b, t); }
 __device__ __forceinline__ float addmin(float a, float b, float t) { return fminf(t, a + b); }
 
+__device__ __forceinline__ int32_t round_up4(int32_t x) { return (x + 3) & ~3; }
+
 __device__ __forceinline__ bool seg_head(const uint32_t* __restrict__ keys, int64_t p) {
     return p == 0 || keys[p] != keys[p - 1] || (p & (GSEGCAP - 1)) == 0;
 }
@@ -283,7 +285,7 @@ template <typename T, int MODE, int QPW, int SMEM, int MINB>
 __global__ void __launch_bounds__(GTH, MINB) k_query_grouped(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
                                                        const uint32_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ idx, int64_t q, uint32_t k,
-                                                       void* __restrict__ out) {
+                                                       int32_t min_ld, void* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);  // SMEM elements, rows of `ld` = cols rounded up to 32
     __shared__ int32_t heads[GTILE + 1];
@@ -322,6 +324,9 @@ __global__ void __launch_bounds__(GTH, MINB) k_query_grouped(const QueryCtx<T> c
     for (int sg = 0; sg < nh; ++sg) {
         const int s0 = heads[sg], s1 = heads[sg + 1];
         const uint32_t key = keys[t0 + s0];
+        // (with the block copy, only the blocks wider than min_ld come here: the others,
+        //  the empty blocks and the out-of-range pairs are answered by query_blocks.cu)
+        if (min_ld >= 0 && (key >= k * k || ctx.nb[key / k] == 0 || round_up4(ctx.nb[key % k]) <= min_ld)) continue;
         if (key >= k * k) {  // out-of-range pairs
             for (int u = tid; u < s1 - s0; u += GTH) {
                 const uint32_t qi = idx[t0 + s0 + u];
@@ -401,7 +406,7 @@ namespace {
 // elements per CTA, MINB CTAs per SM).
 template <typename T, int MODE, int QPW, int SMEMK, int MINB>
 cudaError_t launch_grouped_one(unsigned blocks, const QueryCtx<T>& ctx, const int2* p2, const uint32_t* sk,
-                               const uint32_t* sv, int64_t q, uint32_t k, void* out, cudaStream_t st) {
+                               const uint32_t* sv, int64_t q, uint32_t k, int32_t min_ld, void* out, cudaStream_t st) {
     constexpr size_t smem = sizeof(T) * SMEMK * 1024;
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
@@ -410,20 +415,20 @@ cudaError_t launch_grouped_one(unsigned blocks, const QueryCtx<T>& ctx, const in
         if (e != cudaSuccess) return e;
         attr.store(true);
     }
-    k_query_grouped<T, MODE, QPW, SMEMK * 1024, MINB><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, out);
+    k_query_grouped<T, MODE, QPW, SMEMK * 1024, MINB><<<blocks, GTH, smem, st>>>(ctx, p2, sk, sv, q, k, min_ld, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_grouped(int cfg, bool mode_f32, unsigned blocks, const QueryCtx<T>& ctx, const int2* p2,
-                           const uint32_t* sk, const uint32_t* sv, int64_t q, uint32_t k, void* out,
+                           const uint32_t* sk, const uint32_t* sv, int64_t q, uint32_t k, int32_t min_ld, void* out,
                            cudaStream_t st) {
     if (cfg == 0)
-        return mode_f32 ? launch_grouped_one<T, kOutF32, 4, 24, 2>(blocks, ctx, p2, sk, sv, q, k, out, st)
-                        : launch_grouped_one<T, kOutI32, 4, 24, 2>(blocks, ctx, p2, sk, sv, q, k, out, st);
-    return mode_f32 ? launch_grouped_one<T, kOutF32, 2, 16, 3>(blocks, ctx, p2, sk, sv, q, k, out, st)
-                    : launch_grouped_one<T, kOutI32, 2, 16, 3>(blocks, ctx, p2, sk, sv, q, k, out, st);
+        return mode_f32 ? launch_grouped_one<T, kOutF32, 4, 24, 2>(blocks, ctx, p2, sk, sv, q, k, min_ld, out, st)
+                        : launch_grouped_one<T, kOutI32, 4, 24, 2>(blocks, ctx, p2, sk, sv, q, k, min_ld, out, st);
+    return mode_f32 ? launch_grouped_one<T, kOutF32, 2, 16, 3>(blocks, ctx, p2, sk, sv, q, k, min_ld, out, st)
+                    : launch_grouped_one<T, kOutI32, 2, 16, 3>(blocks, ctx, p2, sk, sv, q, k, min_ld, out, st);
 }
 
 // Size class of a grouped launch: log2 of the pairs per component pair (which decides how
@@ -441,11 +446,42 @@ int grouped_size_class(int64_t q, uint32_t k, int64_t N) {
 }
 
 // The autotuner's choices per (device, size class), measured on the first grouped launch
-// of each class in the process.
+// of each class in the process.  The measurement is never waited for: the events of the
+// two timed launches are kept as pending, and a later launch of the class reads them once
+// they have completed (cudaEventQuery); until then the class takes the first configuration.
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tune;
+struct PendingTune {
+    cudaEvent_t ev[3];
+};
+std::map<std::pair<int, int>, PendingTune> g_pending;
 
+// -1: never measured (the caller measures now); -2: measured, result not ready yet;
+// else the chosen configuration.
 int tuned_config(int cls) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({dev, cls});
+    if (it != g_tune.end()) return it->second;
+    auto pt = g_pending.find({dev, cls});
+    if (pt == g_pending.end()) return -1;
+    const cudaError_t q = cudaEventQuery(pt->second.ev[2]);
+    if (q == cudaErrorNotReady) return -2;
+    int cfg = 0;
+    float ms0 = 0.f, ms1 = 0.f;
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms0, pt->second.ev[0], pt->second.ev[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms1, pt->second.ev[1], pt->second.ev[2]) == cudaSuccess)
+        cfg = ms1 < ms0 ? 1 : 0;
+    cudaGetLastError();
+    for (cudaEvent_t x : pt->second.ev) cudaEventDestroy(x);
+    g_pending.erase(pt);
+    g_tune[{dev, cls}] = cfg;
+    return cfg;
+}
+
+// The stored choice of a class without reading pending measurements (-1 if none).
+int tuned_choice(int cls) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -453,16 +489,20 @@ int tuned_config(int cls) {
     return it == g_tune.end() ? -1 : it->second;
 }
 
-void store_tuned(int cls, int cfg) {
+// Keeps the events of a measurement; false if the class is already pending or tuned
+// (another thread measured it meanwhile: the caller destroys its events).
+bool store_pending(int cls, const cudaEvent_t (&ev)[3]) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[{dev, cls}] = cfg;
+    if (g_tune.count({dev, cls}) || g_pending.count({dev, cls})) return false;
+    g_pending[{dev, cls}] = PendingTune{{ev[0], ev[1], ev[2]}};
+    return true;
 }
 
 }  // namespace
 
-int64_t query_scratch_words(int64_t q) { return 4 * q + radix_hist_words(q) + 4; }
+int64_t query_scratch_words(int64_t q) { return 4 * q + radix_hist_words(q) + 4 + query_blocks_scratch_words(q); }
 
 template <typename T>
 cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
@@ -487,29 +527,38 @@ cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q
         const uint32_t* sk = in_k1 ? k1 : keys;
         const uint32_t* sv = in_k1 ? v1 : vals;
         const unsigned blocks = (unsigned)((q + GTILE - 1) / GTILE);
+        int32_t min_ld = -1;  // -1: every block by the gathering kernel below
+        if (ctx.Dc) {
+            // blocks up to query_blocks_max_ld() columns from the block copy; wider ones (if
+            // any component has that many boundary vertices) gathered below
+            if ((e = launch_query_blocks<T>(ctx, pairs, q, out, out_f32, k, sk, sv, hist + radix_hist_words(q) + 4,
+                                            st)) != cudaSuccess)
+                return e;
+            if (ctx.dc_max_ld <= query_blocks_max_ld()) return cudaSuccess;
+            min_ld = query_blocks_max_ld();
+        }
         const int cls = grouped_size_class(q, k, ctx.N);
-        int cfg = tuned_config(cls);
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cap);
-        if (cfg < 0 && cap != cudaStreamCaptureStatusNone) cfg = 0;  // no timing inside a graph capture
-        if (cfg >= 0) return launch_grouped<T>(cfg, mode_f32, blocks, ctx, p2, sk, sv, q, k, out, st);
+        // inside a graph capture: the stored choice or the first configuration, no timing
+        // and no event query (the capture would be invalidated)
+        int cfg = cap != cudaStreamCaptureStatusNone ? tuned_choice(cls) : tuned_config(cls);
+        if (cfg == -2 || (cfg == -1 && cap != cudaStreamCaptureStatusNone)) cfg = 0;  // not read yet / no timing
+        if (cfg >= 0) return launch_grouped<T>(cfg, mode_f32, blocks, ctx, p2, sk, sv, q, k, min_ld, out, st);
         // first grouped launch of this size class on this device: time both configurations
-        // on these inputs (the second writes the same answers again) and keep the faster
+        // on these inputs (the second writes the same answers again) with events that a
+        // later launch reads; nothing here waits for the device
         cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
         for (auto& x : ev)
             if (e == cudaSuccess) e = cudaEventCreate(&x);
-        float ms[2] = {0.f, 0.f};
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        if (e == cudaSuccess) e = launch_grouped<T>(0, mode_f32, blocks, ctx, p2, sk, sv, q, k, out, st);
+        if (e == cudaSuccess) e = launch_grouped<T>(0, mode_f32, blocks, ctx, p2, sk, sv, q, k, min_ld, out, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = launch_grouped<T>(1, mode_f32, blocks, ctx, p2, sk, sv, q, k, out, st);
+        if (e == cudaSuccess) e = launch_grouped<T>(1, mode_f32, blocks, ctx, p2, sk, sv, q, k, min_ld, out, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
-        if (e == cudaSuccess) store_tuned(cls, ms[1] < ms[0] ? 1 : 0);
-        for (auto& x : ev)
-            if (x) cudaEventDestroy(x);
+        if (e != cudaSuccess || !store_pending(cls, ev))
+            for (auto& x : ev)
+                if (x) cudaEventDestroy(x);
         return e;
     }
     int64_t blocks = (q + (QTH / 32) - 1) / (QTH / 32);
@@ -537,6 +586,13 @@ extern "C" int32_t spq_query_tuning(int32_t* keys, int32_t* choices, int32_t cap
         if (n < cap && keys && choices) {
             keys[n] = kv.first.first * 256 + kv.first.second;
             choices[n] = kv.second;
+        }
+        ++n;
+    }
+    for (const auto& kv : spq::g_pending) {  // measured, not read yet
+        if (n < cap && keys && choices) {
+            keys[n] = kv.first.first * 256 + kv.first.second;
+            choices[n] = -1;
         }
         ++n;
     }

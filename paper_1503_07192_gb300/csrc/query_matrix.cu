@@ -261,7 +261,7 @@ int64_t runs_words(int64_t n) { return 4 * n + 3 * (n + 1) + radix_hist_words(n)
 extern "C" spq_status spq_query_matrix(spq_handle* h, const int32_t* sources, int64_t ns, const int32_t* targets,
                                        int64_t nt, void* dist_out, void* stream) {
     using namespace spq;
-    if (!h || ns < 0 || nt < 0) return SPQ_EINVAL;
+    if (!h || ns < 0 || nt < 0 || !on_handle_device(h)) return SPQ_EINVAL;
     if (ns == 0 || nt == 0) return SPQ_OK;
     if (!sources || !targets || !dist_out) return SPQ_EINVAL;
     if (ns > INT32_MAX || nt > INT32_MAX) return SPQ_EINVAL;

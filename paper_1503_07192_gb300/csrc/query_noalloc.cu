@@ -30,8 +30,10 @@ namespace {
 
 constexpr int64_t kMaxPairs = SPQ_NOALLOC_MAX_PAIRS;
 // 4 words per pair (keys, values and their sort copies) + one radix histogram of 256
-// words per 4,096-pair tile + 4 spare words: query_scratch_words(kMaxPairs).
-constexpr int64_t kWords = 4 * kMaxPairs + 256 * ((kMaxPairs + 4095) / 4096) + 4;
+// words per 4,096-pair tile + 4 spare words, then the grouped kernel's records (9 words per
+// pair: table rows, starting values, items; + 8): query_scratch_words(kMaxPairs), about
+// 13.7 MB.
+constexpr int64_t kWords = 4 * kMaxPairs + 256 * ((kMaxPairs + 4095) / 4096) + 4 + 9 * kMaxPairs + 8;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kWords];
 
@@ -73,6 +75,9 @@ extern "C" spq_status spq_query_noalloc(spq_handle* h, const int32_t* pairs, int
     if (!h || q < 0) return SPQ_EINVAL;
     if (q == 0) return SPQ_OK;
     if (!pairs || !dist_out || q > kMaxPairs) return SPQ_EINVAL;
+    // the handle's tables and this device's copy of the scratch array must be on the
+    // current device
+    if (!on_handle_device(h)) return SPQ_EINVAL;
     if (query_scratch_words(q) > kWords) return SPQ_EINVAL;
     if (!device_pointer(pairs) || !device_pointer(dist_out)) return SPQ_EINVAL;
     if (((uintptr_t)pairs & 7u) || ((uintptr_t)dist_out & 3u)) return SPQ_EINVAL;

@@ -248,6 +248,7 @@ spq_status spq_server_create(int device, int32_t slots, int64_t max_pairs, size_
 
 spq_status spq_server_add_graph(spq_server* s, int32_t gid, spq_handle* h) {
     if (!s || !h) return SPQ_EINVAL;
+    if (h->device != s->device) return SPQ_EINVAL;  // the server's slots run on its own device
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->graphs.count(gid)) return SPQ_EINVAL;
     const size_t fp = h->bytes;

@@ -254,8 +254,8 @@ def test_delaunay16k_sampled_and_full_rows():
     h.free()
 
 
-def _build_with(w, grouped):
-    return build(w.graph, w.part, w.k, query_grouped=grouped)
+def _build_with(w, grouped, block_copy=1):
+    return build(w.graph, w.part, w.k, query_grouped=grouped, block_copy=block_copy)
 
 
 def test_grouped_and_input_order_queries_agree():
@@ -274,13 +274,17 @@ def test_grouped_and_input_order_queries_agree():
                             np.repeat(np.arange(0, g.n, 97)[:, None], 2, 1).astype(np.int32)])
     pairs = pairs[rng.permutation(pairs.shape[0])]
     hg = _build_with(w, 1)
+    hc = _build_with(w, 1, block_copy=0)  # grouped, blocks gathered from the matrix
     hu = _build_with(w, 0)
     a = query(hg, pairs)
     b = query(hu, pairs)
-    assert np.array_equal(a, b)
+    c = query(hc, pairs)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert hg.stats()["footprint_bytes"] > hc.stats()["footprint_bytes"]
     assert_pairs_exact(hg, g, pairs[:20000])
     hg.free()
     hu.free()
+    hc.free()
 
 
 def test_grouped_and_input_order_queries_agree_float_weights():
@@ -294,9 +298,11 @@ def test_grouped_and_input_order_queries_agree_float_weights():
     pairs = np.concatenate([pairs, pairs[:, ::-1]])
     hg = build(g, part, k, query_grouped=1)
     hu = build(g, part, k, query_grouped=0)
+    hc = build(g, part, k, query_grouped=1, block_copy=0)
     a = query(hg, pairs)
     b = query(hu, pairs)
-    assert a.dtype == np.float32 and np.array_equal(a, b)
+    assert a.dtype == np.float32 and np.array_equal(a, b) and np.array_equal(a, query(hc, pairs))
+    hc.free()
     diff = part[pairs[:30000, 0]] != part[pairs[:30000, 1]]  # (same-component pairs keep their own order)
     assert np.array_equal(a[:30000][diff], a[30000:][diff])
     hg.free()
@@ -305,26 +311,69 @@ def test_grouped_and_input_order_queries_agree_float_weights():
 
 def test_grouped_query_autotuner_records_its_choice():
     """The first grouped launch of a size class times both kernel configurations on its
-    inputs and keeps the faster (the answers are the same operations in both): the class
-    of this launch is in the table afterwards, and a second launch (the chosen
-    configuration) answers the same."""
+    inputs (the answers are the same operations in both) without waiting for them; a
+    later launch of the class, once the timing is complete, reads it and keeps the
+    faster.  After that the class is in the table, and the chosen configuration answers
+    the same."""
     m = spq()
     torch, dev = torch_dev()
     w = gen.configs.grid_blocks_workload(48, 48, 12, 12, 60, 30000, seed=29)
-    h = build(w.graph, w.part, w.k)
+    h = build(w.graph, w.part, w.k, block_copy=0)  # the gathering kernel is the tuned one
     pairs = torch.from_numpy(w.pairs).to(dev)
     a = m.spq_query(h, pairs)
-    b = m.spq_query(h, pairs)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    b = m.spq_query(h, pairs)  # reads the completed measurement
+    c = m.spq_query(h, pairs)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(a, c)
     q, k, nbg = w.pairs.shape[0], w.k, int(h.meta()["nb"].sum())
     # (few boundary slots: no alignment padding, the matrix order is nbg rounded up to 4)
     N = -(-nbg // 4) * 4
     cls = 16 * (min(max(int(np.floor(np.log2(q / (k * (k + 1) / 2)))), -6), 9) + 6) + min(int(np.log2(N / k)), 15)
     table = m.spq_query_tuning()
-    assert table and set(table.values()) <= {0, 1}
-    assert (0, cls) in table, (cls, table)
+    assert table and set(table.values()) <= {-1, 0, 1}
+    assert table.get((0, cls)) in (0, 1), (cls, table)
     assert_pairs_exact(h, w.graph, w.pairs[:3000])
+    h.free()
+
+
+def test_first_query_of_a_size_class_does_not_wait_for_the_device():
+    """The autotuner's measurement on the first launch of a size class is queued, not
+    waited for: the call returns while its kernels still run (its host time is well
+    below their device time)."""
+    import time
+
+    m = spq()
+    torch, dev = torch_dev()
+    # 4 components of 8,192 vertices (about 330 boundary slots each) and 1M pairs: a size
+    # class no other test uses, and tens of milliseconds of device work; no block copy
+    # (the gathering kernel is the tuned one)
+    w = gen.configs.delaunay_rcb(1 << 15, 2, 1_000_000, seed=31)
+    h = build(w.graph, w.part, w.k, block_copy=0)
+    pairs = torch.from_numpy(w.pairs).to(dev)
+    m.spq_query(h, pairs[:5000])  # another size class: loads both kernel configurations
+    torch.cuda.synchronize()
+    before = m.spq_query_tuning()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    t0 = time.perf_counter()
+    out = m.spq_query(h, pairs)
+    host_ms = (time.perf_counter() - t0) * 1e3
+    e1.record(s)
+    torch.cuda.synchronize()
+    dev_ms = e0.elapsed_time(e1)
+    after = m.spq_query_tuning()
+    mine = {key: v for key, v in after.items() if key not in before}
+    if not mine:
+        pytest.skip("this size class was measured earlier in the process")
+    assert list(mine.values()) == [-1], mine  # measured, not read yet
+    assert host_ms < 0.5 * dev_ms, (host_ms, dev_ms)
+    again = m.spq_query(h, pairs)
+    torch.cuda.synchronize()
+    assert torch.equal(out, again)
+    assert m.spq_query_tuning()[next(iter(mine))] in (0, 1)  # read by the second launch
+    assert_pairs_exact(h, w.graph, w.pairs[:2000])
     h.free()
 
 
@@ -581,5 +630,72 @@ def test_shorter_opts_struct_is_accepted():
     he.free()
     o = m.spq_opts_default()
     o.comp_method = 3
+    with pytest.raises(m.SpqError):
+        m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+
+
+def test_wide_blocks_take_the_gathering_kernel_in_the_same_launch():
+    """Grouped queries read component blocks from the block copy up to 2,048 padded
+    columns; wider blocks (components with more boundary vertices) are gathered from the
+    boundary matrix by the other kernel of the same launch.  A 2,200 x 3 grid cut into
+    its three rows (every vertex a boundary vertex: 2,200-wide blocks) plus a narrow
+    4 x 40 strip of two components joined to it: all answers against the oracle."""
+    W = 2200
+    u, v = [], []
+    for y in range(3):
+        for x in range(W):
+            i = y * W + x
+            if x + 1 < W:
+                u.append(i), v.append(i + 1)
+            if y + 1 < 3:
+                u.append(i), v.append(i + W)
+    base = 3 * W
+    for y in range(40):
+        for x in range(4):
+            i = base + y * 4 + x
+            if x + 1 < 4:
+                u.append(i), v.append(i + 1)
+            if y + 1 < 40:
+                u.append(i), v.append(i + 4)
+    u.append(base), v.append(0)  # the strip hangs off the grid's corner
+    n = base + 160
+    rng = np.random.default_rng(101)
+    w = rng.integers(1, 50, size=len(u)).astype(np.int32)
+    rp, col, ww = gen.csr_from_edges(n, np.array(u), np.array(v), w)
+    g = gen.Graph(n, rp, col, ww.astype(np.int32))
+    part = np.empty(n, np.int32)
+    part[:base] = np.arange(base) // W
+    part[base:] = 3 + (np.arange(160) // 80)
+    h = build(g, part, 5)
+    assert h.meta()["nb"].max() > 2048
+    pairs = rng.integers(0, n, size=(30000, 2)).astype(np.int32)
+    assert_pairs_exact(h, g, pairs)
+    hu = build(g, part, 5, query_grouped=0)
+    assert np.array_equal(query(h, pairs), query(hu, pairs))
+    h.free()
+    hu.free()
+
+
+def test_block_copy_option_and_shorter_struct():
+    """A caller's spq_opts that ends before block_copy gets the block copy (the default);
+    block_copy = 0 builds without it (a smaller footprint) and answers the same; values
+    other than 0 and 1 are rejected."""
+    m = spq()
+    torch, dev = torch_dev()
+    w = gen.configs.grid64(q=8000)
+    g = w.graph
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    o = m.spq_opts_default()
+    o.block_copy = 0
+    h0 = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+    o.struct_size = m.SpqOpts.block_copy.offset  # (the 0 above lies outside the declared size)
+    h1 = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
+    assert h1.stats()["footprint_bytes"] > h0.stats()["footprint_bytes"]
+    assert np.array_equal(query(h0, w.pairs), query(h1, w.pairs))
+    assert_pairs_exact(h1, g, w.pairs)
+    h0.free()
+    h1.free()
+    o = m.spq_opts_default()
+    o.block_copy = 2
     with pytest.raises(m.SpqError):
         m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)

@@ -27,6 +27,12 @@ def _call(lib, h, pairs, out, torch):
                                  ctypes.c_void_p(out.data_ptr()), stream)
 
 
+def _pool_used(lib, torch):
+    used, reserved = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    assert lib.spq_pool_usage(torch.cuda.current_device(), ctypes.byref(used), ctypes.byref(reserved)) == 0
+    return used.value, reserved.value
+
+
 def test_noalloc_matches_spq_query_on_two_calls_in_a_row():
     m = spq()
     torch, dev = torch_dev()
@@ -35,12 +41,23 @@ def test_noalloc_matches_spq_query_on_two_calls_in_a_row():
     h = build(w.graph, w.part, w.k)
     rng = np.random.default_rng(23)
     batches = [w.pairs, np.ascontiguousarray(w.pairs[rng.permutation(w.pairs.shape[0])[:41000], ::-1])]
-    for b in batches:
+    for i, b in enumerate(batches):
         pairs = torch.from_numpy(np.ascontiguousarray(b)).to(dev)
         ref = m.spq_query(h, pairs)
         out = torch.full((pairs.shape[0],), -7, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        # the call must take no memory from the library's pool, from torch's caching
+        # allocator or (after the first call, which may load the array's module under
+        # CUDA's lazy module loading) from the device: its scratch is the fixed array
+        pool0 = _pool_used(lib, torch)
+        torch0 = torch.cuda.memory_allocated(dev)
+        free0 = torch.cuda.mem_get_info(dev)[0]
         assert _call(lib, h, pairs, out, torch) == 0
         torch.cuda.synchronize()
+        assert _pool_used(lib, torch) == pool0
+        assert torch.cuda.memory_allocated(dev) == torch0
+        if i > 0:
+            assert torch.cuda.mem_get_info(dev)[0] == free0
         m.spq_query_status(h)
         assert torch.equal(out, ref)
     h.free()
