@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="delaunay1m",
-                   choices=["delaunay1m", "grid64", "delaunay65k", "delaunay262k", "grid1024diag", "batch512",
+                   choices=["delaunay1m", "grid64", "delaunay65k", "delaunay131k", "delaunay262k", "grid1024diag",
+                            "batch512",
                             "serve", "grad256k", "matrix1m"])
     p.add_argument("--rates", default="500,2000,8000", help="serve: request arrival rates (1/s) to sweep")
     p.add_argument("--duration", type=float, default=3.0, help="serve: seconds of arrivals per rate")
@@ -67,6 +68,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--arith", type=int, default=0, help="spq_arith of the build (0 auto, 1 int32, 2 float32)")
     p.add_argument("--bg", type=int, default=0, help="spq_bg_method of the build (0 auto, 1 FW, 2 elimination)")
+    p.add_argument("--query-kernel", type=int, default=0, choices=[0, 1],
+                   help="opts.query_kernel of the build (0: staged grouped kernel, 1: the gathering one)")
     return p.parse_args()
 
 
@@ -86,6 +89,12 @@ def make_workload(name, q):
         w = gen.configs.grid1024diag(q=q or 10_000_000)
         desc = {"workload": "grid1024diag", "vertices": w.graph.n, "components": w.k,
                 "partition": "32x32-vertex blocks", "queries_per_step": int(w.pairs.shape[0])}
+    elif name == "delaunay131k":
+        # the delaunay1m regime at 1/8 size (components of 1,024 vertices, about 19 pairs
+        # per component pair), a few GB on the device: the case for kernel captures
+        w = gen.configs.delaunay_rcb(1 << 17, 7, q or 157_000, seed=1242)
+        desc = {"workload": "delaunay131k", "vertices": w.graph.n, "components": w.k,
+                "queries_per_step": int(w.pairs.shape[0])}
     elif name == "delaunay65k":
         w = gen.configs.delaunay_rcb(1 << 16, 6, q or 1_000_000, seed=1240)
         desc = {"workload": "delaunay65k", "vertices": w.graph.n, "components": w.k,
@@ -647,7 +656,7 @@ def main():
     d_out = torch.empty(q, dtype=torch.int32, device=dev)
     opts = spq.spq_opts_default()
     opts.profile_kernels = 1
-    opts.arith, opts.bg_method = args.arith, args.bg
+    opts.arith, opts.bg_method, opts.query_kernel = args.arith, args.bg, args.query_kernel
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -740,14 +749,14 @@ def main():
         q_upd, q_bytes = qk[0]["updates"], qk[0]["bytes"]
         hbm_peak = measured_hbm_gbs()
         roof_query = {
-            "kernel": "k_qb_blocks (grouped queries over the component-blocked copy)", "bound": "alu",
+            "kernel": "k_qb_blocks (staged grouped queries)", "bound": "alu",
             "achieved": q_upd / (qms * 1e-3) / 1e9, "peak": peak_gops, "unit": "Gop/s",
             "frac": q_upd / (qms * 1e-3) / 1e9 / peak_gops, "launches": len(qk), "avg_launch_ms": qms,
             "updates": q_upd, "hbm": {"achieved": q_bytes / (qms * 1e-3) / 1e9, "peak": hbm_peak["value"],
                                       "unit": "GB/s", "frac": q_bytes / (qms * 1e-3) / 1e9 / hbm_peak["value"],
                                       "peak_basis": hbm_peak["basis"], "bytes": q_bytes,
-                                      "bytes_formula": "per item 4*|B1|*ld2 (its block, once) + per pair "
-                                                       "4*(roundup4(|B1|) + ld2) + 16; ld2 = roundup4(|B2|)"},
+                                      "bytes_formula": "per item 4*|B1|*|B2| (its block, once) + per pair "
+                                                       "4*(roundup4(|B1|) + roundup4(|B2|)) + 16"},
             "traffic": None}
 
     # measured issue peak of the update (same process, after the timed region)

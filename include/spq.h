@@ -127,13 +127,13 @@ typedef struct spq_opts {
                                component (components of up to 4096 vertices; larger ones
                                take Floyd-Warshall); SPQ_BG_AUTO (default, and what a
                                struct_size ending before this field means): elimination */
-    int32_t block_copy;     /* 1 (default, and what a struct_size ending before this field
-                               means): the build also keeps a copy of the boundary matrix's
-                               upper block-triangle grouped by component (block (C1, C2),
-                               C1 <= C2, contiguous: the paper's Fig. 1 layout), about half
-                               the matrix's memory, from which the grouped queries stage each
-                               block with 16-byte copies; 0: no copy, the grouped queries
-                               gather their blocks from the matrix */
+    int32_t query_kernel;   /* kernel of the grouped queries.  0 (default, and what a
+                               struct_size ending before this field means): a persistent
+                               kernel stages each boundary-graph block in shared memory with
+                               asynchronous copies, pipelined across blocks (blocks with up
+                               to 512 rows and columns; larger ones as with 1); 1: every block
+                               gathered by the earlier kernel (autotuned between two
+                               configurations, see spq_query_tuning) */
 } spq_opts;
 
 /* Fill *opts with the defaults (also what opts == NULL means). */
@@ -205,7 +205,7 @@ spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_
  *   - q <= SPQ_NOALLOC_MAX_PAIRS (a larger q returns SPQ_EINVAL and queues nothing);
  *   - pairs and dist_out must be device memory (else SPQ_EINVAL); the call returns once
  *     the work is queued, and spq_query_status reports out-of-range pairs;
- *   - its scratch is one fixed array of about 13.7 MB in the library's device memory,
+ *   - its scratch is one fixed array of about 23.1 MB in the library's device memory,
  *     present on every GPU that loads the library until the process exits.  The first
  *     call on a device looks up that array's address (cudaGetSymbolAddress, once per
  *     device); make that first call before any stream capture.  All calls share the

@@ -61,13 +61,12 @@ int32_t spq_query_tuning(int32_t* keys, int32_t* choices, int32_t cap);
  * either way, and nothing faults: the launch returns and the device stays usable. */
 void spq_test_backsub_wait(unsigned long long limit_ns, int32_t withhold);
 
-/* The last grouped query launch on h with the block copy (h built with
- * opts.profile_kernels = 1): the block-copy kernel's device time (CUDA events on the
- * query's stream), its min-plus updates (sum over pairs of |B1| x |B2|) and the bytes it
- * must move: each item's block once (|B1| x ld2 x 4, ld2 = |B2| rounded up to 4), per pair
- * its two table rows (4 x (|B1| rounded up to 4 + ld2)) plus 16 bytes (the pair, its
- * position, its answer).  Waits for that launch.  SPQ_EUNSUPPORTED if h was not built for
- * profiling or has run no such launch. */
+/* The last launch of the staged grouped query kernel on h (h built with
+ * opts.profile_kernels = 1): its device time (CUDA events on the query's stream), its
+ * min-plus updates (sum over pairs of |B1| x |B2|) and the bytes it must move: each item's
+ * block once (|B1| x |B2| x 4), per pair its two table rows (4 x (|B1| + |B2|), each rounded
+ * up to 4) plus 16 bytes (the pair, its position, its answer).  Waits for that launch.
+ * SPQ_EUNSUPPORTED if h was not built for profiling or has run no such launch. */
 spq_status spq_query_profile(const spq_handle* h, double* kernel_ms, double* updates, double* bytes);
 
 /* Bytes of the library's device memory pool on `device` (the tables and the

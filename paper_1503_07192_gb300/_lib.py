@@ -24,7 +24,7 @@ i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 class SpqOpts(ctypes.Structure):
     _fields_ = [("struct_size", i32), ("arith", i32), ("order", i32), ("skip_inf_tiles", i32),
                 ("profile_kernels", i32), ("query_grouped", i32), ("bg_method", i32),
-                ("bg_panel_mib", i32), ("comp_method", i32), ("block_copy", i32)]
+                ("bg_panel_mib", i32), ("comp_method", i32), ("query_kernel", i32)]
 
 
 class SpqGraph(ctypes.Structure):

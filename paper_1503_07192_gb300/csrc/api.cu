@@ -39,7 +39,7 @@ spq_status read_opts(const spq_opts* in, spq_opts* o) {
     if (o->order < SPQ_ORDER_AUTO || o->order > SPQ_ORDER_VERTEX_DISSECTION) return SPQ_EINVAL;
     if (o->bg_method < SPQ_BG_AUTO || o->bg_method > SPQ_BG_ELIM || o->bg_panel_mib < 0) return SPQ_EINVAL;
     if (o->comp_method < SPQ_BG_AUTO || o->comp_method > SPQ_BG_ELIM) return SPQ_EINVAL;
-    if (o->block_copy != 0 && o->block_copy != 1) return SPQ_EINVAL;
+    if (o->query_kernel != 0 && o->query_kernel != 1) return SPQ_EINVAL;
     return SPQ_OK;
 }
 }  // namespace spq
@@ -146,7 +146,7 @@ void free_handle_memory(spq_handle* h) {
     }
     void* ps[] = {h->comp,   h->local,   h->descs,   h->nb,  h->bg_off, h->bgpos,  h->csize, h->apsp,
                   h->D,      h->err,     h->csr_rp,  h->csr_col, h->csr_w, h->vorder, h->vstart,
-                  h->Dc,     h->dcS,     h->dcP,   h->qstats};
+                  h->qstats};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);  // back to the pool
     cudaStreamSynchronize(0);
@@ -448,12 +448,7 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
         bo += h->h_nb[c];
     }
     h->nbg = bo;
-    // the component-blocked copy of the boundary matrix for the grouped queries
-    std::vector<int64_t> dcS, dcP;
-    int64_t dc_elems = 0;
-    int32_t dc_max = 0;
-    const bool want_dc = opts.query_grouped != 0 && opts.block_copy != 0 && bo > 0;
-    if (want_dc) dc_layout(h->h_nb, &dcS, &dcP, &dc_elems, &dc_max);
+    h->max_nb = k > 0 ? *std::max_element(h->h_nb.begin(), h->h_nb.end()) : 0;
     // matrix order: the slots, plus (elimination form) up to 15 alignment gaps of < 128
     const bool may_elim = opts.bg_method != SPQ_BG_FW && bo > 0;
     const int64_t n_max = round_up(bo + (may_elim ? 15 * (kTile - 1) : 0), 4);
@@ -474,8 +469,7 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const size_t comp_elim_bytes = opts.comp_method != SPQ_BG_FW ? 4 * (size_t)h->apsp_elems + 8 * (size_t)n : 0;
     size_t need = 4 * (size_t)h->apsp_elems + comp_elim_bytes + 4 * (size_t)n_max * (size_t)n_max + 8 * (size_t)n +
                   (size_t)k * (sizeof(MatDesc) + 16) + 16 * (size_t)n + 4 * (size_t)(fw_words_max + hist_words) +
-                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + 4 * (size_t)dc_elems +
-                  16 * ((size_t)k + 1) + (64u << 20);
+                  8 * ((size_t)n + 1) + 8 * (size_t)m + 4 * (size_t)n + elim_bytes + (64u << 20);
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     free_b += pool_cached_bytes(h->device);
@@ -608,26 +602,11 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
             if (plan.wait_failed) return SPQ_ETIMEOUT;
         }
     }
-    if (want_dc) {
-        CK(dev_alloc((uint32_t**)&h->Dc, (size_t)dc_elems, &bytes, st));
-        CK(dev_alloc(&h->dcS, (size_t)k, &bytes, st));
-        CK(dev_alloc(&h->dcP, (size_t)k + 1, &bytes, st));
+    if (opts.profile_kernels && h->nbg > 0) {  // timing of the staged grouped query kernel
+        CK(dev_alloc(&h->qstats, 2, &bytes, st));
+        CK(cudaEventCreate(&h->qev[0]));
+        CK(cudaEventCreate(&h->qev[1]));
         h->bytes = bytes;
-        h->dc_elems = dc_elems;
-        h->dc_max_ld = dc_max;
-        if (opts.profile_kernels) {
-            CK(dev_alloc(&h->qstats, 2, &bytes, st));
-            CK(cudaEventCreate(&h->qev[0]));
-            CK(cudaEventCreate(&h->qev[1]));
-        }
-        CK(cudaMemcpyAsync(h->dcS, dcS.data(), (size_t)k * 8, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(h->dcP, dcP.data(), ((size_t)k + 1) * 8, cudaMemcpyHostToDevice, st));
-        if (h->f32store)
-            CK(launch_build_dc<float>((const float*)h->D, h->N, h->bgpos, h->bg_off, h->nb, h->dcS, h->dcP, k, h->nbg,
-                                      dcP[k], (float*)h->Dc, st));
-        else
-            CK(launch_build_dc<int32_t>((const int32_t*)h->D, h->N, h->bgpos, h->bg_off, h->nb, h->dcS, h->dcP, k,
-                                        h->nbg, dcP[k], (int32_t*)h->Dc, st));
     }
     evs.mark(7, st);
     CK(cudaStreamSynchronize(st));
@@ -650,7 +629,7 @@ void spq_opts_default(spq_opts* o) {
     o->bg_method = SPQ_BG_AUTO;
     o->bg_panel_mib = 0;
     o->comp_method = SPQ_BG_AUTO;
-    o->block_copy = 1;
+    o->query_kernel = 0;
 }
 
 spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, const void* w, spq_dtype wt,
@@ -672,6 +651,7 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
     h->k = k;
     h->wt = wt;
     h->query_grouped = o.query_grouped;
+    h->query_kernel = o.query_kernel;
     spq_status s = build_impl(n, row_ptr, col, w, wt, part, k, o, (cudaStream_t)stream, h);
     if (s != SPQ_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -782,7 +762,7 @@ void spq_stats(const spq_handle* h, int64_t* n_bg, double* comp_updates, double*
 
 int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     if (!h || !ms || count <= 0) return 0;
-    double v[16];
+    double v[15];
     for (int i = 0; i < 6; ++i) v[i] = h->prof_ms[i];
     v[6] = h->fwprof.p3_ms;
     v[7] = (double)h->fwprof.p3_launches;
@@ -793,8 +773,7 @@ int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
     v[12] = h->fwprof.bs_updates;
     v[13] = h->fwprof.bs_items;
     v[14] = (double)h->fwprof.bs_launches;
-    v[15] = h->prof_ms[6];
-    int32_t c = count < 16 ? count : 16;
+    int32_t c = count < 15 ? count : 15;
     for (int32_t i = 0; i < c; ++i) ms[i] = v[i];
     return c;
 }
@@ -885,9 +864,12 @@ bool on_handle_device(const spq_handle* h) {
 void handle_query_view(const spq_handle* h, QueryCtx<int32_t>* ci, QueryCtx<float>* cf, bool* f32store, bool* out_f32,
                        int32_t* k) {
     *ci = QueryCtx<int32_t>{h->n,      h->comp,   h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const int32_t*)h->apsp,
-                            (const int32_t*)h->D, h->N, h->err, (const int32_t*)h->Dc, h->dcS, h->dcP, h->dc_max_ld};
+                            (const int32_t*)h->D, h->N, h->err, h->query_kernel == 0 ? 1 : 0, h->max_nb};
     *cf = QueryCtx<float>{h->n,    h->comp, h->local, h->descs, h->nb, h->bg_off, h->bgpos, (const float*)h->apsp,
-                          (const float*)h->D, h->N, h->err, (const float*)h->Dc, h->dcS, h->dcP, h->dc_max_ld};
+                          (const float*)h->D, h->N, h->err, h->query_kernel == 0 ? 1 : 0, h->max_nb};
+    // float32 arithmetic of an int32 graph passed the exactness check: every finite entry
+    // of the (converted) int32 tables is below 2^24
+    ci->exact24 = (h->wt == SPQ_I32 && !h->f32store && h->arith == SPQ_ARITH_F32) ? 1 : 0;
     if (h->qstats) {
         spq_handle* m = const_cast<spq_handle*>(h);
         m->qprof_ran = true;

@@ -246,17 +246,18 @@ struct QueryCtx {
     const T* D;
     int64_t N;
     uint32_t* err;
-    // the component-blocked copy of the matrix's upper block-triangle (query_blocks.cu), or
-    // null: block (c1 <= c2) at dcS[c1] + nb[c1] * (dcP[c2] - dcP[c1]), rows of
-    // dcP[c2 + 1] - dcP[c2] elements; dc_max_ld its widest row
-    const T* Dc = nullptr;
-    const int64_t* dcS = nullptr;
-    const int64_t* dcP = nullptr;
-    int32_t dc_max_ld = 0;
+    // grouped queries: 1 by the staged kernel of query_blocks.cu (blocks of up to
+    // query_blocks_max_nb() rows and columns; the rest gathered), 0 all gathered; max_nb:
+    // the largest |B(C)|
+    int32_t staged = 0;
+    int32_t max_nb = 0;
     // profiling (built with opts.profile_kernels): events around the block-copy kernel
     // and its algorithmic counts (min-plus updates, bytes), or null
     cudaEvent_t* qev = nullptr;
     unsigned long long* qstats = nullptr;
+    // 1: int32 tables whose finite entries are all below 2^24 (the build's exactness
+    // check passed), so the queries may use the float encoding of query_blocks.cu
+    int32_t exact24 = 0;
 };
 // Queries; with scratch (query_scratch_words(q) words) and k <= 65535 the grouped form
 // (sorted by component pair), else one warp per query in input order.
@@ -266,21 +267,12 @@ cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q
                          uint32_t k, uint32_t* scratch, cudaStream_t st);
 
 // ---- query_blocks.cu ----
-// Layout of the block copy for the boundary counts nb: dcS (k), dcP (k + 1), its
-// elements and its widest padded row.
-void dc_layout(const std::vector<int32_t>& nb, std::vector<int64_t>* S, std::vector<int64_t>* P, int64_t* elems,
-               int32_t* max_ld);
-// The copy from the boundary-graph matrix D (N x N, slot s at row / column bgpos[s]).
-template <typename T>
-cudaError_t launch_build_dc(const T* D, int64_t N, const int32_t* bgpos, const int32_t* bg_off, const int32_t* nb,
-                            const int64_t* S, const int64_t* P, int32_t k, int64_t nbg, int64_t Pk, T* Dc,
-                            cudaStream_t st);
-// Widest block (padded columns) the block-copy query handles; wider blocks take the
-// gathering form of query.cu.
-int32_t query_blocks_max_ld();
+// Largest block side (|B1| or |B2|) the staged grouped kernel handles; larger blocks take
+// the gathering kernel of query.cu.
+int32_t query_blocks_max_nb();
 // Scratch words of launch_query_blocks beyond the sort's.
 int64_t query_blocks_scratch_words(int64_t q);
-// The grouped queries over the block copy, given the pairs' sorted keys and positions.
+// The staged grouped queries, given the pairs' sorted keys and positions.
 template <typename T>
 cudaError_t launch_query_blocks(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
                                 uint32_t k, const uint32_t* keys, const uint32_t* idx, uint32_t* scratch,

@@ -38,12 +38,8 @@ struct spq_handle {
     int32_t* csize = nullptr;
     void* apsp = nullptr;
     void* D = nullptr;
-    // component-blocked copy of D's upper block-triangle, for the grouped queries
-    void* Dc = nullptr;
-    int64_t* dcS = nullptr;
-    int64_t* dcP = nullptr;
-    int32_t dc_max_ld = 0;
-    int64_t dc_elems = 0;
+    int32_t query_kernel = 0;  // opts.query_kernel
+    int32_t max_nb = 0;        // the largest |B(C)|
     // profiling of the grouped query kernel (opts.profile_kernels)
     cudaEvent_t qev[2] = {nullptr, nullptr};
     unsigned long long* qstats = nullptr;  // device: updates, bytes of the last profiled launch

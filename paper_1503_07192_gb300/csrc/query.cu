@@ -324,9 +324,13 @@ __global__ void __launch_bounds__(GTH, MINB) k_query_grouped(const QueryCtx<T> c
     for (int sg = 0; sg < nh; ++sg) {
         const int s0 = heads[sg], s1 = heads[sg + 1];
         const uint32_t key = keys[t0 + s0];
-        // (with the block copy, only the blocks wider than min_ld come here: the others,
-        //  the empty blocks and the out-of-range pairs are answered by query_blocks.cu)
-        if (min_ld >= 0 && (key >= k * k || ctx.nb[key / k] == 0 || round_up4(ctx.nb[key % k]) <= min_ld)) continue;
+        // (with min_ld >= 0 only the blocks with a side longer than min_ld come here: the
+        //  others, the empty blocks and the out-of-range pairs are answered by the staged
+        //  kernel of query_blocks.cu)
+        if (min_ld >= 0 &&
+            (key >= k * k || ctx.nb[key / k] == 0 || ctx.nb[key % k] == 0 ||
+             (ctx.nb[key / k] <= min_ld && ctx.nb[key % k] <= min_ld)))
+            continue;
         if (key >= k * k) {  // out-of-range pairs
             for (int u = tid; u < s1 - s0; u += GTH) {
                 const uint32_t qi = idx[t0 + s0 + u];
@@ -528,14 +532,14 @@ cudaError_t launch_query(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q
         const uint32_t* sv = in_k1 ? v1 : vals;
         const unsigned blocks = (unsigned)((q + GTILE - 1) / GTILE);
         int32_t min_ld = -1;  // -1: every block by the gathering kernel below
-        if (ctx.Dc) {
-            // blocks up to query_blocks_max_ld() columns from the block copy; wider ones (if
-            // any component has that many boundary vertices) gathered below
+        if (ctx.staged) {
+            // blocks with at most query_blocks_max_nb() rows and columns by the staged kernel;
+            // larger ones (if a component has that many boundary vertices) gathered below
             if ((e = launch_query_blocks<T>(ctx, pairs, q, out, out_f32, k, sk, sv, hist + radix_hist_words(q) + 4,
                                             st)) != cudaSuccess)
                 return e;
-            if (ctx.dc_max_ld <= query_blocks_max_ld()) return cudaSuccess;
-            min_ld = query_blocks_max_ld();
+            if (ctx.max_nb <= query_blocks_max_nb()) return cudaSuccess;
+            min_ld = query_blocks_max_nb();
         }
         const int cls = grouped_size_class(q, k, ctx.N);
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

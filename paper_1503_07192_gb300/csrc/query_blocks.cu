@@ -1,30 +1,24 @@
-// Grouped distance queries over the component-blocked copy of the boundary-graph matrix
-// (Algorithm 2 for batches of pairs sorted by component pair).
+// Grouped distance queries (Algorithm 2 for batches of pairs sorted by component pair),
+// staging each boundary-graph block in shared memory with asynchronous copies.
 //
-// The block copy.  For components C1 <= C2 the |B(C1)| x |B(C2)| block dist_BG(B(C1),
-// B(C2)) of the paper's Fig. 2 is stored contiguously, row-major, its rows padded to
-// ld(C2) = |B(C2)| rounded up to 4 (padding columns infinite); the blocks are laid out row
-// of blocks by row of blocks (C1 ascending, then C2 >= C1 ascending):
-//   P[c]  = sum over c' < c of ld(c')                 (padded column start of c)
-//   S[c1] = sum over c < c1 of |B(c)| * (P[k] - P[c]) (start of c1's row of blocks)
-//   block (c1, c2) starts at S[c1] + |B(c1)| * (P[c2] - P[c1]).
-// Every block start and row is a multiple of 16 bytes, so a block's rows are staged with
-// 16-byte asynchronous copies.  This is the upper block-triangle of the matrix in the
-// component order of the paper's Fig. 1: half the matrix.
-//
-// The queries.  Pairs are sorted by their unordered component pair (query.cu) and cut
-// into items of at most 64 pairs sharing one block.  A persistent kernel (two CTAs of 256
-// threads per SM) walks its items in a fixed stride; each item's block is staged in row
-// chunks together with the chunk's piece of dist_C1(v1, .) for every pair, double
-// buffered across chunk and item boundaries, so the copy of the next chunk (or of the
-// next item's first chunk) overlaps the current one's arithmetic.  For an item of s pairs
-// and a block of ld columns a thread owns 4 pairs x 4 columns of t(b2) = min over b1 of
-// dist_C1(v1, b1) + D(b1, b2) in registers, for a share of the chunk's rows (the rows are
-// split so that the (pairs/4) x (ld/4) tiles times the splits fill the 256 threads); at
-// the item's end, min over its columns of t(b2) + dist_C2(b2, v2) is folded into a
-// per-pair minimum in shared memory.  The minimum over row splits commutes with adding
-// dist_C2(b2, v2) (x -> x + c is monotone, also in float arithmetic), so each answer is
-// the same value the one-warp-per-pair form computes.
+// Pairs are sorted by their unordered component pair (query.cu) and cut into items of at
+// most 64 pairs sharing one block dist_BG(B(C1), B(C2)) (the paper's Fig. 2: the block of
+// the boundary matrix whose rows are C1's boundary slots and columns C2's).  A persistent
+// kernel (two CTAs of 256 threads per SM) walks its items in a fixed stride; each item's
+// block is staged in row chunks, gathered from the matrix through the slots' positions with
+// 4-byte asynchronous copies (a component's slots form a few long runs in the matrix
+// order, so a warp's consecutive columns mostly read consecutive addresses), together with
+// the chunk's piece of dist_C1(v1, .) for every pair (16-byte copies), double buffered
+// across chunk and item boundaries: the copy of the next chunk (or of the next item's first
+// chunk) overlaps the current one's arithmetic.  For an item of s pairs and a block of ld
+// columns (|B2| rounded up to 4) a thread owns 4 pairs x 4 columns of
+// t(b2) = min over b1 of dist_C1(v1, b1) + D(b1, b2) in registers, for a share of the
+// chunk's rows (the rows are split so that the (pairs/4) x (ld/4) tiles times the splits
+// fill the 256 threads); at the item's end, min over its columns of t(b2) + dist_C2(b2, v2)
+// is folded into a per-pair minimum in shared memory.  The minimum over row splits
+// commutes with adding dist_C2(b2, v2) (x -> x + c is monotone, also in float arithmetic),
+// so each answer is the same value the one-warp-per-pair form computes.  Blocks with more
+// than 512 rows or columns are left to the gathering kernel of query.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,21 +37,31 @@ constexpr int QB_S = 8192;     // staged block elements per buffer (32 KB)
 constexpr int QB_A = 4096;     // staged dist_C1 elements per buffer (pairs x chunk rows)
 constexpr int QB_MAXP = 64;    // pairs per item
 constexpr int QB_UMAX = 3;     // 4 x 4 tiles per thread
+constexpr int QB_PMAX = 512;   // widest block side (rows or columns) staged here
+constexpr int QB_PREG = (2 * QB_PMAX) / (2 * QB_TH);  // prefetched positions per thread and side
 
+// One item: its pairs (a run of sorted positions) and the shape of its staged work, set
+// once by the item builder.
 struct QItem {
-    uint32_t start;  // first position in the sorted pairs
-    int32_t count;   // pairs
-    int32_t c1, c2;  // component pair, c1 <= c2
+    uint32_t start;          // first position in the sorted pairs
+    int32_t count;           // pairs (at most QB_MAXP)
+    int32_t c1, c2;          // component pair, c1 <= c2
+    int32_t nb1, ld2, nb2;   // block rows, padded columns, columns
+    int32_t chr, nch;        // rows per chunk (a multiple of 4), chunks
+    int32_t G, H, Rs;        // pair groups (of 4), column groups (of 4), row splits
 };
+static_assert(sizeof(QItem) == 48, "item records are 12 words");
 
 template <typename T>
 struct QbSmem {
     T s[2][QB_S];                // block rows of the chunk, row-major, ld columns
     T a[2][QB_A];                // dist_C1(v1, rows of the chunk), one row of `chr` per pair
-    int64_t a2off[2][QB_MAXP];   // per item parity: row of dist_C2(., v2) in the tables
-    uint32_t qidx[2][QB_MAXP];   // the pair's position in the caller's arrays
-    T init[2][QB_MAXP];          // the answer's starting value (same component, v == w)
-    int32_t res[2][QB_MAXP];     // running minimum over the item's tiles (bit pattern)
+    int32_t pos1[2][QB_PMAX];    // per item parity: matrix rows of C1's slots
+    int32_t pos2[2][QB_PMAX];    //                  matrix columns of C2's slots
+    int64_t a2off[2][QB_MAXP];   //                  row of dist_C2(., v2) in the tables
+    uint32_t qidx[2][QB_MAXP];   //                  the pair's position in the caller's arrays
+    T init[2][QB_MAXP];          //                  the answer's starting value
+    int32_t res[2][QB_MAXP];     //                  running minimum (bit pattern)
 };
 
 // Largest pair count of an item on a block of ld columns: (pairs / 4) x (ld / 4) tiles
@@ -69,21 +73,20 @@ __host__ __device__ __forceinline__ int32_t qb_pair_cap(int32_t ld) {
     return cap < QB_MAXP ? cap : QB_MAXP;
 }
 
-struct QbParams {
-    int64_t off;             // block start in the copy
-    int32_t nb1, ld2;        // block rows, padded columns
-    int32_t chr, nch;        // rows per chunk (a multiple of 4), chunks
-    int32_t G, H, Rs;        // pair groups, column groups, row splits
-};
-
-__device__ __forceinline__ QbParams qb_params(const QItem& it, const int32_t* __restrict__ nb,
-                                              const int64_t* __restrict__ S, const int64_t* __restrict__ P) {
-    QbParams p;
-    p.nb1 = nb[it.c1];
-    const int64_t P1 = P[it.c1], P2 = P[it.c2];
-    p.ld2 = (int32_t)(P[it.c2 + 1] - P2);
-    p.off = S[it.c1] + (int64_t)p.nb1 * (P2 - P1);
-    const int32_t spad = (it.count + 3) & ~3;
+// The item of `count` pairs from `start` on block (c1, c2): rows staged in balanced chunks
+// of at most 64 rows (a multiple of 4) that fit the buffers, and the row splits that keep
+// the most threads busy with at most QB_UMAX tiles of 4 pairs x 4 columns each.
+__device__ __forceinline__ QItem qb_make_item(uint32_t start, int32_t count, int32_t c1, int32_t c2,
+                                              const int32_t* __restrict__ nb) {
+    QItem p;
+    p.start = start;
+    p.count = count;
+    p.c1 = c1;
+    p.c2 = c2;
+    p.nb1 = nb[c1];
+    p.nb2 = nb[c2];
+    p.ld2 = (p.nb2 + 3) & ~3;
+    const int32_t spad = (count + 3) & ~3;
     int32_t chr = QB_S / p.ld2;
     chr = min(chr, QB_A / spad);
     chr = min(chr, 64) & ~3;
@@ -93,7 +96,6 @@ __device__ __forceinline__ QbParams qb_params(const QItem& it, const int32_t* __
     p.G = spad / 4;
     p.H = p.ld2 / 4;
     const int32_t U = p.G * p.H;
-    // row splits: the most threads busy, at most QB_UMAX tiles each
     int32_t best = 1, bneed = U, bnu = (U + QB_TH - 1) / QB_TH;
     for (int32_t r = 2; r <= 8 && 4 * r <= p.chr; ++r) {
         const int32_t need = U * r, nu = (need + QB_TH - 1) / QB_TH;
@@ -108,14 +110,65 @@ __device__ __forceinline__ QbParams qb_params(const QItem& it, const int32_t* __
     return p;
 }
 
+// A thread's tiles of an item: tile k is x = tid + k * QB_TH of the (row split, pair group,
+// column group) space, packed as r << 28 | g << 20 | h (h < 2^20), or -1 past its end.
+__device__ __forceinline__ void qb_units(const QItem& p, int tid, int32_t (&u)[QB_UMAX]) {
+    const int32_t U = p.G * p.H, need = U * p.Rs;
+#pragma unroll
+    for (int k = 0; k < QB_UMAX; ++k) {
+        const int32_t x = tid + k * QB_TH;
+        if (x < need) {
+            const int32_t r = x / U, rest = x - r * U, g = rest / p.H, h = rest - g * p.H;
+            u[k] = (r << 28) | (g << 20) | h;
+        } else {
+            u[k] = -1;
+        }
+    }
+}
+
 template <typename T>
 struct QbCtx {
     const T* apsp;
-    const T* Dc;
-    const int32_t* nb;
-    const int64_t* S;
-    const int64_t* P;
+    const T* D;
+    int64_t N;
+    const int32_t* bgpos;
+    const int32_t* bg_off;
 };
+
+// An item's slot positions (matrix rows of C1's slots, columns of C2's) into parity pp.
+template <typename T>
+__device__ __forceinline__ void qb_load_pos(QbSmem<T>& sm, int pp, const QbCtx<T>& c, const QItem& p, int tid) {
+    if (p.count == 0) return;
+    for (int32_t i = tid; i < p.nb1; i += QB_TH) sm.pos1[pp][i] = c.bgpos[c.bg_off[p.c1] + i];
+    for (int32_t i = tid; i < p.nb2; i += QB_TH) sm.pos2[pp][i] = c.bgpos[c.bg_off[p.c2] + i];
+}
+// The same in two steps: loads into registers (issued an item ahead of their use) ...
+template <typename T>
+__device__ __forceinline__ void qb_fetch_pos(const QbCtx<T>& c, const QItem& p, int tid, int32_t (&r1)[QB_PREG],
+                                             int32_t (&r2)[QB_PREG]) {
+#pragma unroll
+    for (int u = 0; u < QB_PREG; ++u) {
+        const int32_t i = tid + u * QB_TH;
+        r1[u] = (p.count > 0 && i < p.nb1) ? c.bgpos[c.bg_off[p.c1] + i] : 0;
+        r2[u] = (p.count > 0 && i < p.nb2) ? c.bgpos[c.bg_off[p.c2] + i] : 0;
+    }
+}
+// ... and the stores into parity pp.
+template <typename T>
+__device__ __forceinline__ void qb_store_pos(QbSmem<T>& sm, int pp, const QItem& p, int tid,
+                                             const int32_t (&r1)[QB_PREG], const int32_t (&r2)[QB_PREG]) {
+#pragma unroll
+    for (int u = 0; u < QB_PREG; ++u) {
+        const int32_t i = tid + u * QB_TH;
+        if (p.count > 0 && i < p.nb1) sm.pos1[pp][i] = r1[u];
+        if (p.count > 0 && i < p.nb2) sm.pos2[pp][i] = r2[u];
+    }
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
 
 template <typename T>
 __device__ __forceinline__ int32_t enc_min(T v);
@@ -145,34 +198,51 @@ __device__ __forceinline__ int32_t res_reset() {
 __device__ __forceinline__ int32_t qb_addmin(int32_t a, int32_t b, int32_t t) { return __viaddmin_s32(a, b, t); }
 __device__ __forceinline__ float qb_addmin(float a, float b, float t) { return fminf(t, a + b); }
 
-// Queue the asynchronous copies of chunk ch of item it into buffer b: the block rows (all
-// threads) and dist_C1(v1, rows) of pair tid (thread tid < count).  Rows of the last
-// chunk past the block's end are set to infinity.
+// Queue the asynchronous copies of chunk ch of item p (positions in parity pp) into buffer
+// b: the block rows gathered from the matrix (warps over rows, lanes over columns) and
+// dist_C1(v1, rows) of pair tid (thread tid < count).  Padding columns past |B2| and rows
+// of the last chunk past the block's end are set to infinity.
 template <typename T>
-__device__ __forceinline__ void qb_issue(QbSmem<T>& sm, int b, const QbCtx<T>& c, const QItem& it,
-                                         const QbParams& p, int ch, int64_t a1off, int tid) {
+__device__ __forceinline__ void qb_issue(QbSmem<T>& sm, int b, int pp, const QbCtx<T>& c, const QItem& p, int ch,
+                                         int64_t a1off, int tid) {
     const int32_t r0 = ch * p.chr;
     const int32_t nrows = min(p.chr, p.nb1 - r0);
     const int32_t nr4 = (nrows + 3) & ~3;
-    const T* src = c.Dc + p.off + (int64_t)r0 * p.ld2;
-    const int32_t n16 = nrows * p.ld2 / 4;
+    const int warp = tid >> 5, lane = tid & 31;
     T* dst = sm.s[b];
-    for (int32_t x = tid; x < n16; x += QB_TH) cp_async16(dst + 4 * x, src + 4 * x);
-    const int32_t nfill = (nr4 - nrows) * p.ld2;
     const T inf = Inf<T>::value();
-    for (int32_t x = tid; x < nfill; x += QB_TH) dst[nrows * p.ld2 + x] = inf;
-    if (tid < it.count) {
+    for (int32_t ii = warp; ii < nr4; ii += QB_TH / 32) {
+        T* d = dst + ii * p.ld2;
+        if (ii < nrows) {
+            const T* row = c.D + (int64_t)sm.pos1[pp][r0 + ii] * c.N;
+            for (int32_t jj = lane; jj < p.nb2; jj += 32) cp_async4(d + jj, row + sm.pos2[pp][jj]);
+            if (p.nb2 + lane < p.ld2) d[p.nb2 + lane] = inf;
+        } else {
+            for (int32_t jj = lane; jj < p.ld2; jj += 32) d[jj] = inf;
+        }
+    }
+    if (tid < p.count) {
         const T* a = c.apsp + a1off + r0;
         T* d = sm.a[b] + tid * p.chr;
         for (int32_t x = 0; x < nr4; x += 4) cp_async16(d + x, a + x);
     }
 }
 
-template <typename T, int MODE>
+// ENC (int32 tables whose finite entries are all below 2^24): the int32 values are read
+// as the bit patterns of floats (m -> m x 2^-149, subnormal or in the lowest normal
+// binade): float addition of two of them is exact integer addition of the patterns while
+// the sum stays below 2^24, float order is integer order, and a sum at or above 2^24 never
+// rounds below it; SPQ_INF_I32 (2^29) reads as 2^-63, far above.  Packed f32x2 adds and
+// three-input mins then do the updates.  An answer below 2^24 is exact (its minimising
+// sum has no term at or above 2^24); an answer at or above it (a long or an unreachable
+// pair) is listed in fb and recomputed exactly in int32 by k_qb_fallback.  No subnormal
+// is flushed: the kernel is built without fast math or .ftz.
+template <typename T, int MODE, bool ENC>
 __global__ void __launch_bounds__(QB_TH, 2)
     k_qb_blocks(const QbCtx<T> c, const QItem* __restrict__ items, const uint32_t* __restrict__ nitems_p,
                 const longlong2* __restrict__ rows, const T* __restrict__ init, const uint32_t* __restrict__ idx,
-                void* __restrict__ out) {
+                void* __restrict__ out, uint32_t* __restrict__ fb, uint32_t* __restrict__ nfb) {
+    using CT = typename std::conditional<ENC, float, T>::type;  // the arithmetic's type
     extern __shared__ __align__(16) unsigned char qb_raw[];
     QbSmem<T>& sm = *reinterpret_cast<QbSmem<T>*>(qb_raw);
     const int tid = threadIdx.x;
@@ -180,8 +250,8 @@ __global__ void __launch_bounds__(QB_TH, 2)
     const uint32_t G = gridDim.x;
     uint32_t it = blockIdx.x;
     if (it >= nitems) return;
-    if (tid < 2 * QB_MAXP) sm.res[tid / QB_MAXP][tid % QB_MAXP] = res_reset<T>();
-    const T inf = Inf<T>::value();
+    if (tid < 2 * QB_MAXP) sm.res[tid / QB_MAXP][tid % QB_MAXP] = res_reset<CT>();
+    const CT inf = ENC ? __int_as_float(SPQ_INF_I32) : (CT)Inf<T>::value();
     // the current item, the next one (with its per-pair records) and the one after that
     // (its record only): loads are issued an item ahead of their use
     QItem cur = items[it];
@@ -192,22 +262,30 @@ __global__ void __launch_bounds__(QB_TH, 2)
         sm.qidx[0][tid] = idx[cur.start + tid];
     }
     uint32_t itn = it + G;
-    QItem nxt = itn < nitems ? items[itn] : QItem{0, 0, 0, 0};
+    QItem nxt = itn < nitems ? items[itn] : QItem{};
     longlong2 nrow = tid < nxt.count ? rows[nxt.start + tid] : make_longlong2(0, 0);
     T ninit = tid < nxt.count ? init[nxt.start + tid] : T(0);
     uint32_t nidx = tid < nxt.count ? idx[nxt.start + tid] : 0u;
-    QItem nn = itn + G < nitems ? items[itn + G] : QItem{0, 0, 0, 0};
+    QItem nn = itn + G < nitems ? items[itn + G] : QItem{};
+    // slot positions: of the first two items into shared memory now, of the third into
+    // registers (stored when the first item is done)
+    qb_load_pos(sm, 0, c, cur, tid);
+    qb_load_pos(sm, 1, c, nxt, tid);
+    int32_t pr1[QB_PREG], pr2[QB_PREG];
+    qb_fetch_pos(c, nn, tid, pr1, pr2);
+    __syncthreads();
 
-    QbParams p = qb_params(cur, c.nb, c.S, c.P);
+    int32_t unit[QB_UMAX];
+    qb_units(cur, tid, unit);
     int ch = 0, b = 0, par = 0;
-    qb_issue<T>(sm, 0, c, cur, p, 0, crow.x, tid);
+    qb_issue<T>(sm, 0, 0, c, cur, 0, crow.x, tid);
     cp_async_commit();
-    T acc[QB_UMAX][4][4];
+    CT acc[QB_UMAX][4][4];
     for (;;) {
-        const bool next_same = ch + 1 < p.nch;
+        const bool next_same = ch + 1 < cur.nch;
         const bool has_next = next_same || itn < nitems;
         if (next_same) {
-            qb_issue<T>(sm, b ^ 1, c, cur, p, ch + 1, crow.x, tid);
+            qb_issue<T>(sm, b ^ 1, par, c, cur, ch + 1, crow.x, tid);
         } else if (has_next) {
             // the next item's first chunk; its epilogue records go to the other parity
             // (last read by the item before this one, behind a barrier since)
@@ -216,7 +294,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
                 sm.init[par ^ 1][tid] = ninit;
                 sm.qidx[par ^ 1][tid] = nidx;
             }
-            qb_issue<T>(sm, b ^ 1, c, nxt, qb_params(nxt, c.nb, c.S, c.P), 0, nrow.x, tid);
+            qb_issue<T>(sm, b ^ 1, par ^ 1, c, nxt, 0, nrow.x, tid);
         }
         if (has_next) {
             cp_async_commit();
@@ -225,10 +303,8 @@ __global__ void __launch_bounds__(QB_TH, 2)
             cp_async_wait<0>();
         }
         __syncthreads();
-        // ---- the chunk's arithmetic ----
-        const int32_t r0 = ch * p.chr;
-        const int32_t nq = (min(p.chr, p.nb1 - r0) + 3) >> 2;
-        const int32_t U = p.G * p.H, need = U * p.Rs;
+        // ---- the chunk's arithmetic: row split r takes the quads r, r + Rs, ... ----
+        const int32_t nq = (min(cur.chr, cur.nb1 - ch * cur.chr) + 3) >> 2;
         if (ch == 0) {
 #pragma unroll
             for (int k = 0; k < QB_UMAX; ++k)
@@ -239,38 +315,63 @@ __global__ void __launch_bounds__(QB_TH, 2)
         }
 #pragma unroll
         for (int k = 0; k < QB_UMAX; ++k) {
-            const int32_t x = tid + k * QB_TH;
-            if (x < need) {
-                const int32_t r = x / U, rest = x - r * U;
-                const int32_t g = rest / p.H, h = rest - g * p.H;
-                const int32_t q0 = r * nq / p.Rs, q1 = (r + 1) * nq / p.Rs;
-                const T* ap = sm.a[b] + 4 * g * p.chr;
+            if (unit[k] >= 0) {
+                const int32_t r = unit[k] >> 28, g = (unit[k] >> 20) & 0xff, h = unit[k] & 0xfffff;
+                const T* ap = sm.a[b] + 4 * g * cur.chr;
                 const T* sp = sm.s[b] + 4 * h;
 #pragma unroll 1
-                for (int32_t qq = q0; qq < q1; ++qq) {
-                    T av[4][4], sv[4][4];
+                for (int32_t qq = r; qq < nq; qq += cur.Rs) {
+                    if constexpr (ENC) {
+                        float4 av[4], sv[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int4 v = *reinterpret_cast<const int4*>(ap + i * p.chr + 4 * qq);
-                        av[i][0] = *reinterpret_cast<const T*>(&v.x);
-                        av[i][1] = *reinterpret_cast<const T*>(&v.y);
-                        av[i][2] = *reinterpret_cast<const T*>(&v.z);
-                        av[i][3] = *reinterpret_cast<const T*>(&v.w);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int4 v = *reinterpret_cast<const int4*>(sp + (4 * qq + j) * p.ld2);
-                        sv[j][0] = *reinterpret_cast<const T*>(&v.x);
-                        sv[j][1] = *reinterpret_cast<const T*>(&v.y);
-                        sv[j][2] = *reinterpret_cast<const T*>(&v.z);
-                        sv[j][3] = *reinterpret_cast<const T*>(&v.w);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                        for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(ap + i * cur.chr + 4 * qq);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
+                            sv[j] = *reinterpret_cast<const float4*>(sp + (4 * qq + j) * cur.ld2);
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[k][i][e] = qb_addmin(av[i][j], sv[j][e], acc[k][i][e]);
+                        for (int i = 0; i < 4; ++i) {
+                            const float a[4] = {av[i].x, av[i].y, av[i].z, av[i].w};  // rows 4qq..4qq+3
+#pragma unroll
+                            for (int jp = 0; jp < 2; ++jp) {
+                                const float2 p0 = make_float2(a[2 * jp], a[2 * jp]);
+                                const float2 p1 = make_float2(a[2 * jp + 1], a[2 * jp + 1]);
+                                const float4 s0 = sv[2 * jp], s1 = sv[2 * jp + 1];
+                                const float2 t0 = __fadd2_rn(p0, make_float2(s0.x, s0.y));
+                                const float2 u0 = __fadd2_rn(p1, make_float2(s1.x, s1.y));
+                                const float2 t1 = __fadd2_rn(p0, make_float2(s0.z, s0.w));
+                                const float2 u1 = __fadd2_rn(p1, make_float2(s1.z, s1.w));
+                                acc[k][i][0] = fmin3(acc[k][i][0], t0.x, u0.x);
+                                acc[k][i][1] = fmin3(acc[k][i][1], t0.y, u0.y);
+                                acc[k][i][2] = fmin3(acc[k][i][2], t1.x, u1.x);
+                                acc[k][i][3] = fmin3(acc[k][i][3], t1.y, u1.y);
+                            }
+                        }
+                    } else {
+                        T av[4][4], sv[4][4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int4 v = *reinterpret_cast<const int4*>(ap + i * cur.chr + 4 * qq);
+                            av[i][0] = *reinterpret_cast<const T*>(&v.x);
+                            av[i][1] = *reinterpret_cast<const T*>(&v.y);
+                            av[i][2] = *reinterpret_cast<const T*>(&v.z);
+                            av[i][3] = *reinterpret_cast<const T*>(&v.w);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int4 v = *reinterpret_cast<const int4*>(sp + (4 * qq + j) * cur.ld2);
+                            sv[j][0] = *reinterpret_cast<const T*>(&v.x);
+                            sv[j][1] = *reinterpret_cast<const T*>(&v.y);
+                            sv[j][2] = *reinterpret_cast<const T*>(&v.z);
+                            sv[j][3] = *reinterpret_cast<const T*>(&v.w);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    acc[k][i][e] = qb_addmin(av[i][j], sv[j][e], acc[k][i][e]);
+                    }
                 }
             }
         }
@@ -278,39 +379,48 @@ __global__ void __launch_bounds__(QB_TH, 2)
             // ---- the item's end: + dist_C2(b2, v2), min over the columns, per pair ----
 #pragma unroll
             for (int k = 0; k < QB_UMAX; ++k) {
-                const int32_t x = tid + k * QB_TH;
-                if (x < need) {
-                    const int32_t rest = x % U;
-                    const int32_t g = rest / p.H, h = rest - g * p.H;
+                if (unit[k] >= 0) {
+                    const int32_t g = (unit[k] >> 20) & 0xff, h = unit[k] & 0xfffff;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int32_t u = 4 * g + i;
                         if (u < cur.count) {
                             const int4 cv = __ldg(reinterpret_cast<const int4*>(c.apsp + sm.a2off[par][u] + 4 * h));
-                            const T c4[4] = {*reinterpret_cast<const T*>(&cv.x), *reinterpret_cast<const T*>(&cv.y),
-                                             *reinterpret_cast<const T*>(&cv.z), *reinterpret_cast<const T*>(&cv.w)};
-                            T v = acc[k][i][0] + c4[0];
+                            const CT c4[4] = {*reinterpret_cast<const CT*>(&cv.x), *reinterpret_cast<const CT*>(&cv.y),
+                                              *reinterpret_cast<const CT*>(&cv.z), *reinterpret_cast<const CT*>(&cv.w)};
+                            // (padding columns past |B2| hold no distance: skipped)
+                            CT v = acc[k][i][0] + c4[0];
 #pragma unroll
                             for (int e = 1; e < 4; ++e) {
-                                const T y = acc[k][i][e] + c4[e];
-                                v = y < v ? y : v;
+                                const CT y = acc[k][i][e] + c4[e];
+                                v = (y < v && 4 * h + e < cur.nb2) ? y : v;
                             }
-                            atomicMin(&sm.res[par][u], enc_min<T>(v));
+                            atomicMin(&sm.res[par][u], enc_min<CT>(v));
                         }
                     }
                 }
             }
             __syncthreads();
             if (tid < cur.count) {
-                T y = dec_min<T>(sm.res[par][tid]);
-                const T z = sm.init[par][tid];
-                y = z < y ? z : y;
-                sm.res[par][tid] = res_reset<T>();
                 const uint32_t qi = sm.qidx[par][tid];
-                if (MODE == 2)
-                    ((float*)out)[qi] = (float)y;
-                else
-                    ((int32_t*)out)[qi] = (int32_t)min((int32_t)y, (int32_t)SPQ_INF_I32);
+                const T z = sm.init[par][tid];
+                if constexpr (ENC) {
+                    // the bit pattern is the exact integer below 2^24
+                    const int32_t y = sm.res[par][tid];
+                    const int32_t zi = *reinterpret_cast<const int32_t*>(&z);
+                    if (y < (1 << 24) || zi < (1 << 24))
+                        ((int32_t*)out)[qi] = zi < y ? zi : y;
+                    else
+                        fb[atomicAdd(nfb, 1u)] = qi;  // recomputed exactly in int32
+                } else {
+                    T y = dec_min<T>(sm.res[par][tid]);
+                    y = z < y ? z : y;
+                    if (MODE == 2)
+                        ((float*)out)[qi] = (float)y;
+                    else
+                        ((int32_t*)out)[qi] = (int32_t)min((int32_t)y, (int32_t)SPQ_INF_I32);
+                }
+                sm.res[par][tid] = res_reset<CT>();
             }
         }
         __syncthreads();  // buffer b is free for the next issue
@@ -322,16 +432,61 @@ __global__ void __launch_bounds__(QB_TH, 2)
             itn = it + G;
             cur = nxt;
             crow = nrow;
-            p = qb_params(cur, c.nb, c.S, c.P);
+            qb_units(cur, tid, unit);
             ch = 0;
             par ^= 1;
             nxt = nn;
             nrow = tid < nxt.count ? rows[nxt.start + tid] : make_longlong2(0, 0);
             ninit = tid < nxt.count ? init[nxt.start + tid] : T(0);
             nidx = tid < nxt.count ? idx[nxt.start + tid] : 0u;
-            nn = itn + G < nitems ? items[itn + G] : QItem{0, 0, 0, 0};
+            // the finished item's positions make room for the one after next
+            qb_store_pos(sm, par ^ 1, nxt, tid, pr1, pr2);
+            nn = itn + G < nitems ? items[itn + G] : QItem{};
+            qb_fetch_pos(c, nn, tid, pr1, pr2);
+            __syncthreads();
         }
         b ^= 1;
+    }
+}
+
+// The listed pairs (positions in the caller's arrays) in exact int32 arithmetic, one warp
+// per pair, reading the block through the slot positions: the answers of the encoded form
+// at or above 2^24.
+__global__ void __launch_bounds__(256) k_qb_fallback(const QueryCtx<int32_t> ctx, const int2* __restrict__ pairs,
+                                                     const uint32_t* __restrict__ fb, const uint32_t* __restrict__ nfb,
+                                                     int32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *nfb;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t qi = fb[w];
+        int2 pr = pairs[qi];
+        int32_t c1 = ctx.comp[pr.x], c2 = ctx.comp[pr.y];
+        if (c1 > c2) {
+            pr = make_int2(pr.y, pr.x);
+            const int32_t t = c1;
+            c1 = c2;
+            c2 = t;
+        }
+        const MatDesc d1 = ctx.descs[c1], d2 = ctx.descs[c2];
+        const int32_t* A1 = ctx.apsp + d1.off + (int64_t)ctx.local[pr.x] * d1.n;
+        const int32_t* A2 = ctx.apsp + d2.off + (int64_t)ctx.local[pr.y] * d2.n;
+        const int32_t nb1 = ctx.nb[c1], nb2 = ctx.nb[c2];
+        const int32_t* pos1 = ctx.bgpos + ctx.bg_off[c1];
+        const int32_t* pos2 = ctx.bgpos + ctx.bg_off[c2];
+        int32_t r = SPQ_INF_I32;
+        for (int32_t jb = 0; jb < nb2; jb += 32) {
+            const int32_t j = jb + lane;
+            const int32_t col = j < nb2 ? pos2[j] : 0;
+            int32_t t = SPQ_INF_I32;
+            for (int32_t b1 = 0; b1 < nb1; ++b1)
+                if (j < nb2) t = __viaddmin_s32(A1[b1], ctx.D[(int64_t)pos1[b1] * ctx.N + col], t);
+            if (j < nb2) r = min(r, t + A2[j]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = min(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (c1 == c2) r = min(r, A1[ctx.local[pr.y]]);
+        if (pr.x == pr.y) r = 0;
+        if (lane == 0) out[qi] = min(r, (int32_t)SPQ_INF_I32);
     }
 }
 
@@ -377,19 +532,19 @@ __global__ void k_qb_prep(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
     }
 }
 
-// Items: every run of one component pair (a nonempty block no wider than the copy's
-// limit) cut into nearly equal pieces of at most qb_pair_cap(ld) pairs; the order of the
+// Items: every run of one component pair (a nonempty block with at most QB_PMAX rows and
+// columns) cut into nearly equal pieces of at most qb_pair_cap(ld) pairs; the order of the
 // item list is arbitrary.
 __global__ void k_qb_items(const uint32_t* __restrict__ keys, int64_t q, uint32_t k, const int32_t* __restrict__ nb,
-                           const int64_t* __restrict__ P, int32_t max_ld, QItem* __restrict__ items,
-                           uint32_t* __restrict__ nitems, unsigned long long* __restrict__ stats) {
+                           QItem* __restrict__ items, uint32_t* __restrict__ nitems,
+                           unsigned long long* __restrict__ stats) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= q) return;
     const uint32_t key = keys[p];
     if (key >= k * k || (p > 0 && keys[p - 1] == key)) return;
     const int32_t c1 = (int32_t)(key / k), c2 = (int32_t)(key % k);
-    const int32_t ld2 = (int32_t)(P[c2 + 1] - P[c2]);
-    if (nb[c1] == 0 || nb[c2] == 0 || ld2 > max_ld) return;
+    const int32_t nb1 = nb[c1], nb2 = nb[c2];
+    if (nb1 == 0 || nb2 == 0 || nb1 > QB_PMAX || nb2 > QB_PMAX) return;
     int64_t lo = p + 1, hi = q;  // the run's end: first position with a larger key
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -399,58 +554,21 @@ __global__ void k_qb_items(const uint32_t* __restrict__ keys, int64_t q, uint32_
             hi = mid;
     }
     const int64_t n = lo - p;
+    const int32_t ld2 = (nb2 + 3) & ~3;
     const int64_t cap = qb_pair_cap(ld2);
     const int64_t pieces = (n + cap - 1) / cap;
     const uint32_t base = atomicAdd(nitems, (uint32_t)pieces);
     if (stats) {
         // algorithmic work of the run: |B1| x |B2| updates per pair; bytes: each item's
         // block once, per pair its two table rows, the pair, its position and its answer
-        const int64_t nb1 = nb[c1], nb2 = nb[c2];
         atomicAdd(&stats[0], (unsigned long long)(n * nb1 * nb2));
-        atomicAdd(&stats[1], (unsigned long long)(4 * pieces * nb1 * ld2 + n * (4 * (((nb1 + 3) & ~3) + ld2) + 16)));
+        atomicAdd(&stats[1], (unsigned long long)(4 * pieces * (int64_t)nb1 * nb2 +
+                                                  n * (4 * (((nb1 + 3) & ~3) + ld2) + 16)));
     }
     for (int64_t i = 0; i < pieces; ++i) {
         const int64_t s0 = p + i * n / pieces, s1 = p + (i + 1) * n / pieces;
-        items[base + i] = QItem{(uint32_t)s0, (int32_t)(s1 - s0), c1, c2};
+        items[base + i] = qb_make_item((uint32_t)s0, (int32_t)(s1 - s0), c1, c2, nb);
     }
-}
-
-// The block copy from the boundary-graph matrix (any order of its rows, reached through
-// bgpos): one CTA per boundary slot s of component c1, writing row s - bg_off[c1] of every
-// block (c1, c2 >= c1); pcomp[u] is the component of padded column u.
-template <typename T>
-__global__ void __launch_bounds__(256) k_build_dc(const T* __restrict__ D, int64_t N, const int32_t* __restrict__ bgpos,
-                                                  const int32_t* __restrict__ bg_off, const int32_t* __restrict__ nb,
-                                                  const int64_t* __restrict__ S, const int64_t* __restrict__ P,
-                                                  const int32_t* __restrict__ pcomp, int32_t k, int64_t nbg,
-                                                  T* __restrict__ Dc) {
-    const T inf = Inf<T>::value();
-    const int64_t Pk = P[k];
-    for (int64_t s = blockIdx.x; s < nbg; s += gridDim.x) {
-        int32_t lo = 0, hi = k;  // the last component whose first slot is <= s
-        while (hi - lo > 1) {
-            const int32_t mid = (lo + hi) >> 1;
-            if (bg_off[mid] <= s) lo = mid; else hi = mid;
-        }
-        const int32_t c1 = lo;
-        const int64_t b1 = s - bg_off[c1];
-        const int64_t nb1 = nb[c1], P1 = P[c1];
-        const T* drow = D + (int64_t)bgpos[s] * N;
-        const int64_t base = S[c1];
-        for (int64_t u = P1 + threadIdx.x; u < Pk; u += blockDim.x) {
-            const int32_t c2 = pcomp[u];
-            const int64_t P2 = P[c2];
-            const int64_t j = u - P2, ld2 = P[c2 + 1] - P2;
-            const T v = j < nb[c2] ? drow[bgpos[bg_off[c2] + j]] : inf;
-            Dc[base + nb1 * (P2 - P1) + b1 * ld2 + j] = v;
-        }
-    }
-}
-
-__global__ void k_pcomp(const int64_t* __restrict__ P, int32_t k, int32_t* __restrict__ pcomp) {
-    const int32_t c = blockIdx.x * blockDim.y + threadIdx.y;
-    if (c >= k) return;
-    for (int64_t u = P[c] + threadIdx.x; u < P[c + 1]; u += blockDim.x) pcomp[u] = c;
 }
 
 int qb_sms() {
@@ -464,84 +582,53 @@ int qb_sms() {
     return n;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool ENC>
 cudaError_t launch_blocks_kernel(const QbCtx<T>& c, const QItem* items, const uint32_t* nitems, const longlong2* rows,
-                                 const T* init, const uint32_t* idx, void* out, int64_t q, cudaStream_t st) {
+                                 const T* init, const uint32_t* idx, void* out, uint32_t* fb, uint32_t* nfb, int64_t q,
+                                 cudaStream_t st) {
     static std::atomic<bool> attr{false};
     const size_t smem = sizeof(QbSmem<T>);
     if (!attr.load()) {
         const cudaError_t e =
-            cudaFuncSetAttribute(k_qb_blocks<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_qb_blocks<T, MODE, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr.store(true);
     }
     int64_t grid = (int64_t)qb_sms() * 2;
     if (grid > q) grid = q;  // at most q items
-    k_qb_blocks<T, MODE><<<(unsigned)grid, QB_TH, smem, st>>>(c, items, nitems, rows, init, idx, out);
+    k_qb_blocks<T, MODE, ENC><<<(unsigned)grid, QB_TH, smem, st>>>(c, items, nitems, rows, init, idx, out, fb, nfb);
     count_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int32_t query_blocks_max_ld() { return 2048; }
+int32_t query_blocks_max_nb() { return QB_PMAX; }
 
 int64_t query_blocks_scratch_words(int64_t q) {
-    // rows (4 words per pair), starting values (1), items (4), the item counter (+ 4 for
-    // 16-byte alignment of what follows a word count that is not a multiple of 4)
-    return 9 * q + 8;
-}
-
-void dc_layout(const std::vector<int32_t>& nb, std::vector<int64_t>* S, std::vector<int64_t>* P, int64_t* elems,
-               int32_t* max_ld) {
-    const int32_t k = (int32_t)nb.size();
-    P->assign((size_t)k + 1, 0);
-    S->assign((size_t)k, 0);
-    int32_t mx = 0;
-    for (int32_t c = 0; c < k; ++c) {
-        const int32_t ld = (int32_t)round_up(nb[c], 4);
-        (*P)[c + 1] = (*P)[c] + ld;
-        mx = std::max(mx, ld);
-    }
-    int64_t acc = 0;
-    for (int32_t c = 0; c < k; ++c) {
-        (*S)[c] = acc;
-        acc += (int64_t)nb[c] * ((*P)[k] - (*P)[c]);
-    }
-    *elems = acc;
-    *max_ld = mx;
-}
-
-template <typename T>
-cudaError_t launch_build_dc(const T* D, int64_t N, const int32_t* bgpos, const int32_t* bg_off, const int32_t* nb,
-                            const int64_t* S, const int64_t* P, int32_t k, int64_t nbg, int64_t Pk, T* Dc,
-                            cudaStream_t st) {
-    if (nbg <= 0) return cudaSuccess;
-    int32_t* pcomp = nullptr;
-    cudaError_t e = scratch_alloc((void**)&pcomp, (size_t)(Pk > 0 ? Pk : 1) * 4, st);
-    if (e != cudaSuccess) return e;
-    k_pcomp<<<(unsigned)((k + 7) / 8), dim3(32, 8), 0, st>>>(P, k, pcomp);
-    const int64_t grid = std::min<int64_t>(nbg, (int64_t)qb_sms() * 16);
-    k_build_dc<T><<<(unsigned)grid, 256, 0, st>>>(D, N, bgpos, bg_off, nb, S, P, pcomp, k, nbg, Dc);
-    count_launches(2);
-    e = cudaGetLastError();
-    cudaFreeAsync(pcomp, st);
-    return e;
+    // rows (4 words per pair), starting values (1), items (12), the fallback list (1), two
+    // counters, and up to 6 words of 16-byte alignment
+    return 18 * q + 8;
 }
 
 template <typename T>
 cudaError_t launch_query_blocks(const QueryCtx<T>& ctx, const int32_t* pairs, int64_t q, void* out, bool out_f32,
                                 uint32_t k, const uint32_t* keys, const uint32_t* idx, uint32_t* scratch,
                                 cudaStream_t st) {
-    // scratch: rows (16-byte aligned) | starting values | items | counter
+    // scratch: rows (16-byte aligned) | starting values | items | fallback list | counters
     uint32_t* base = (uint32_t*)(((uintptr_t)scratch + 15) & ~(uintptr_t)15);
     longlong2* rows = reinterpret_cast<longlong2*>(base);
     T* init = reinterpret_cast<T*>(base + 4 * q);
-    QItem* items = reinterpret_cast<QItem*>(base + ((5 * q + 3) & ~(int64_t)3));
-    uint32_t* nitems = base + ((5 * q + 3) & ~(int64_t)3) + 4 * q;
+    const int64_t o_items = (5 * q + 3) & ~(int64_t)3;
+    QItem* items = reinterpret_cast<QItem*>(base + o_items);
+    uint32_t* fb = base + o_items + 12 * q;
+    uint32_t* nitems = fb + q;
+    uint32_t* nfb = nitems + 1;
     const int2* p2 = reinterpret_cast<const int2*>(pairs);
     const bool mode_f32 = out_f32 || !std::is_same<T, int32_t>::value;
-    cudaError_t e = cudaMemsetAsync(nitems, 0, 4, st);
+    // int32 tables with every finite entry below 2^24: the float-encoded arithmetic
+    const bool enc = std::is_same<T, int32_t>::value && !mode_f32 && ctx.exact24;
+    cudaError_t e = cudaMemsetAsync(nitems, 0, 8, st);
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)((q + 255) / 256);
     if (mode_f32)
@@ -553,24 +640,28 @@ cudaError_t launch_query_blocks(const QueryCtx<T>& ctx, const int32_t* pairs, in
     cudaStreamIsCapturing(st, &cap);
     const bool prof = ctx.qev && ctx.qstats && cap == cudaStreamCaptureStatusNone;
     if (prof && (e = cudaMemsetAsync(ctx.qstats, 0, 16, st)) != cudaSuccess) return e;
-    k_qb_items<<<g, 256, 0, st>>>(keys, q, k, ctx.nb, ctx.dcP, query_blocks_max_ld(), items, nitems,
-                                  prof ? ctx.qstats : nullptr);
+    k_qb_items<<<g, 256, 0, st>>>(keys, q, k, ctx.nb, items, nitems, prof ? ctx.qstats : nullptr);
     count_launches(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const QbCtx<T> c{ctx.apsp, ctx.Dc, ctx.nb, ctx.dcS, ctx.dcP};
+    const QbCtx<T> c{ctx.apsp, ctx.D, ctx.N, ctx.bgpos, ctx.bg_off};
     if (prof && (e = cudaEventRecord(ctx.qev[0], st)) != cudaSuccess) return e;
-    e = mode_f32 ? launch_blocks_kernel<T, 2>(c, items, nitems, rows, init, idx, out, q, st)
-                 : launch_blocks_kernel<T, 0>(c, items, nitems, rows, init, idx, out, q, st);
+    if (mode_f32)
+        e = launch_blocks_kernel<T, 2, false>(c, items, nitems, rows, init, idx, out, fb, nfb, q, st);
+    else if (enc)
+        e = launch_blocks_kernel<T, 0, true>(c, items, nitems, rows, init, idx, out, fb, nfb, q, st);
+    else
+        e = launch_blocks_kernel<T, 0, false>(c, items, nitems, rows, init, idx, out, fb, nfb, q, st);
     if (e == cudaSuccess && prof) e = cudaEventRecord(ctx.qev[1], st);
+    if constexpr (std::is_same<T, int32_t>::value) {
+        if (e == cudaSuccess && enc) {
+            k_qb_fallback<<<(unsigned)(qb_sms() * 4), 256, 0, st>>>(ctx, p2, fb, nfb, (int32_t*)out);
+            count_launches(1);
+            e = cudaGetLastError();
+        }
+    }
     return e;
 }
 
-template cudaError_t launch_build_dc<int32_t>(const int32_t*, int64_t, const int32_t*, const int32_t*, const int32_t*,
-                                              const int64_t*, const int64_t*, int32_t, int64_t, int64_t, int32_t*,
-                                              cudaStream_t);
-template cudaError_t launch_build_dc<float>(const float*, int64_t, const int32_t*, const int32_t*, const int32_t*,
-                                            const int64_t*, const int64_t*, int32_t, int64_t, int64_t, float*,
-                                            cudaStream_t);
 template cudaError_t launch_query_blocks<int32_t>(const QueryCtx<int32_t>&, const int32_t*, int64_t, void*, bool,
                                                   uint32_t, const uint32_t*, const uint32_t*, uint32_t*, cudaStream_t);
 template cudaError_t launch_query_blocks<float>(const QueryCtx<float>&, const int32_t*, int64_t, void*, bool, uint32_t,

@@ -26,11 +26,11 @@ def torch_dev():
     return torch, torch.device("cuda:0")
 
 
-def opts(arith=0, order=0, skip=1, query_grouped=1, bg=0, panel_mib=0, comp=0, block_copy=1):
+def opts(arith=0, order=0, skip=1, query_grouped=1, bg=0, panel_mib=0, comp=0, query_kernel=0):
     m = spq()
     o = m.spq_opts_default()
     o.arith, o.order, o.skip_inf_tiles, o.query_grouped = arith, order, skip, query_grouped
-    o.bg_method, o.bg_panel_mib, o.comp_method, o.block_copy = bg, panel_mib, comp, block_copy
+    o.bg_method, o.bg_panel_mib, o.comp_method, o.query_kernel = bg, panel_mib, comp, query_kernel
     return o
 
 

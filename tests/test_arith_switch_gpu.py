@@ -138,3 +138,28 @@ def test_int32_weight_at_the_sentinel_is_rejected():
     got = h.meta()
     assert got["comp"].shape == (64,)
     h.free()
+
+
+def test_answers_above_2_24_from_tables_below_it():
+    """Every table entry below 2^24 (the build keeps float32-exact arithmetic) while some
+    answers exceed it: two chains of 80 vertices (one component each, odd weights of
+    200,001, so that a float sum rounded in the binade above 2^24 would be off by one)
+    joined end to end, plus an isolated third chain (unreachable pairs).  The grouped
+    queries compute in the float encoding and recompute the answers at or above 2^24 in
+    int32: all must be the oracle's."""
+    L, W = 80, 200_001
+    u, v = [], []
+    for c in range(3):
+        for i in range(L - 1):
+            u.append(c * L + i), v.append(c * L + i + 1)
+    u.append(L - 1), v.append(L)  # chains 0 and 1 joined; chain 2 isolated
+    n = 3 * L
+    rp, col, ww = gen.csr_from_edges(n, np.array(u), np.array(v), np.full(len(u), W, np.int32))
+    g = gen.Graph(n, rp, col, ww.astype(np.int32))
+    part = (np.arange(n) // L).astype(np.int32)
+    assert (L - 1) * W < TWO24 < (2 * L - 1) * W
+    h = build(g, part, 3)
+    assert h.stats()["arith"] == ARITH_F32
+    pairs = np.stack(np.meshgrid(np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 2).astype(np.int32)
+    assert_pairs_exact(h, g, pairs)
+    h.free()

@@ -254,8 +254,8 @@ def test_delaunay16k_sampled_and_full_rows():
     h.free()
 
 
-def _build_with(w, grouped, block_copy=1):
-    return build(w.graph, w.part, w.k, query_grouped=grouped, block_copy=block_copy)
+def _build_with(w, grouped, query_kernel=0):
+    return build(w.graph, w.part, w.k, query_grouped=grouped, query_kernel=query_kernel)
 
 
 def test_grouped_and_input_order_queries_agree():
@@ -274,13 +274,12 @@ def test_grouped_and_input_order_queries_agree():
                             np.repeat(np.arange(0, g.n, 97)[:, None], 2, 1).astype(np.int32)])
     pairs = pairs[rng.permutation(pairs.shape[0])]
     hg = _build_with(w, 1)
-    hc = _build_with(w, 1, block_copy=0)  # grouped, blocks gathered from the matrix
+    hc = _build_with(w, 1, query_kernel=1)  # grouped, every block by the gathering kernel
     hu = _build_with(w, 0)
     a = query(hg, pairs)
     b = query(hu, pairs)
     c = query(hc, pairs)
     assert np.array_equal(a, b) and np.array_equal(a, c)
-    assert hg.stats()["footprint_bytes"] > hc.stats()["footprint_bytes"]
     assert_pairs_exact(hg, g, pairs[:20000])
     hg.free()
     hu.free()
@@ -298,7 +297,7 @@ def test_grouped_and_input_order_queries_agree_float_weights():
     pairs = np.concatenate([pairs, pairs[:, ::-1]])
     hg = build(g, part, k, query_grouped=1)
     hu = build(g, part, k, query_grouped=0)
-    hc = build(g, part, k, query_grouped=1, block_copy=0)
+    hc = build(g, part, k, query_grouped=1, query_kernel=1)
     a = query(hg, pairs)
     b = query(hu, pairs)
     assert a.dtype == np.float32 and np.array_equal(a, b) and np.array_equal(a, query(hc, pairs))
@@ -318,7 +317,7 @@ def test_grouped_query_autotuner_records_its_choice():
     m = spq()
     torch, dev = torch_dev()
     w = gen.configs.grid_blocks_workload(48, 48, 12, 12, 60, 30000, seed=29)
-    h = build(w.graph, w.part, w.k, block_copy=0)  # the gathering kernel is the tuned one
+    h = build(w.graph, w.part, w.k, query_kernel=1)  # the gathering kernel is the tuned one
     pairs = torch.from_numpy(w.pairs).to(dev)
     a = m.spq_query(h, pairs)
     torch.cuda.synchronize()
@@ -346,10 +345,10 @@ def test_first_query_of_a_size_class_does_not_wait_for_the_device():
     m = spq()
     torch, dev = torch_dev()
     # 4 components of 8,192 vertices (about 330 boundary slots each) and 1M pairs: a size
-    # class no other test uses, and tens of milliseconds of device work; no block copy
-    # (the gathering kernel is the tuned one)
+    # class no other test uses, and tens of milliseconds of device work; the gathering
+    # kernel (the tuned one)
     w = gen.configs.delaunay_rcb(1 << 15, 2, 1_000_000, seed=31)
-    h = build(w.graph, w.part, w.k, block_copy=0)
+    h = build(w.graph, w.part, w.k, query_kernel=1)
     pairs = torch.from_numpy(w.pairs).to(dev)
     m.spq_query(h, pairs[:5000])  # another size class: loads both kernel configurations
     torch.cuda.synchronize()
@@ -676,26 +675,25 @@ def test_wide_blocks_take_the_gathering_kernel_in_the_same_launch():
     hu.free()
 
 
-def test_block_copy_option_and_shorter_struct():
-    """A caller's spq_opts that ends before block_copy gets the block copy (the default);
-    block_copy = 0 builds without it (a smaller footprint) and answers the same; values
-    other than 0 and 1 are rejected."""
+def test_query_kernel_option_and_shorter_struct():
+    """A caller's spq_opts that ends before query_kernel gets the default (the staged
+    grouped kernel); query_kernel = 1 gathers every block with the earlier kernel and
+    answers the same; values other than 0 and 1 are rejected."""
     m = spq()
     torch, dev = torch_dev()
     w = gen.configs.grid64(q=8000)
     g = w.graph
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     o = m.spq_opts_default()
-    o.block_copy = 0
-    h0 = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
-    o.struct_size = m.SpqOpts.block_copy.offset  # (the 0 above lies outside the declared size)
+    o.query_kernel = 1
     h1 = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
-    assert h1.stats()["footprint_bytes"] > h0.stats()["footprint_bytes"]
+    o.struct_size = m.SpqOpts.query_kernel.offset  # (the 1 above lies outside the declared size)
+    h0 = m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
     assert np.array_equal(query(h0, w.pairs), query(h1, w.pairs))
-    assert_pairs_exact(h1, g, w.pairs)
+    assert_pairs_exact(h0, g, w.pairs)
     h0.free()
     h1.free()
     o = m.spq_opts_default()
-    o.block_copy = 2
+    o.query_kernel = 2
     with pytest.raises(m.SpqError):
         m.spq_build(g.n, t(g.row_ptr), t(g.col), t(g.w), t(w.part), w.k, opts=o)
