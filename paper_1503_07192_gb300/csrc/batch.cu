@@ -765,6 +765,8 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         h->f32store = f32store;
         h->arith = arith;
         h->query_grouped = o.query_grouped;
+        h->query_kernel = o.query_kernel;
+        h->max_nb = x.k > 0 ? *std::max_element(x.nb.begin(), x.nb.end()) : 0;
         h->order_method = methods[g];
         h->bg_method = x.elim ? SPQ_BG_ELIM : SPQ_BG_FW;
         h->comp = P.comp + x.vbase;

@@ -4,7 +4,7 @@
 // Pairs are sorted by their unordered component pair (query.cu) and cut into items of at
 // most 64 pairs sharing one block dist_BG(B(C1), B(C2)) (the paper's Fig. 2: the block of
 // the boundary matrix whose rows are C1's boundary slots and columns C2's).  A persistent
-// kernel (two CTAs of 256 threads per SM) walks its items in a fixed stride; each item's
+// kernel (three CTAs of 256 threads per SM) walks its items in a fixed stride; each item's
 // block is staged in row chunks, gathered from the matrix through the slots' positions with
 // 4-byte asynchronous copies (a component's slots form a few long runs in the matrix
 // order, so a warp's consecutive columns mostly read consecutive addresses), together with
@@ -33,10 +33,11 @@ namespace spq {
 namespace {
 
 constexpr int QB_TH = 256;
-constexpr int QB_S = 8192;     // staged block elements per buffer (32 KB)
-constexpr int QB_A = 4096;     // staged dist_C1 elements per buffer (pairs x chunk rows)
+constexpr int QB_S = 4096;     // staged block elements per buffer (16 KB)
+constexpr int QB_A = 2048;     // staged dist_C1 elements per buffer (pairs x chunk rows)
 constexpr int QB_MAXP = 64;    // pairs per item
-constexpr int QB_UMAX = 3;     // 4 x 4 tiles per thread
+constexpr int QB_UMAX = 2;     // 4 x 4 tiles per thread
+constexpr int QB_CTAS = 3;     // CTAs per SM
 constexpr int QB_PMAX = 512;   // widest block side (rows or columns) staged here
 constexpr int QB_PREG = (2 * QB_PMAX) / (2 * QB_TH);  // prefetched positions per thread and side
 
@@ -58,10 +59,12 @@ struct QbSmem {
     T a[2][QB_A];                // dist_C1(v1, rows of the chunk), one row of `chr` per pair
     int32_t pos1[2][QB_PMAX];    // per item parity: matrix rows of C1's slots
     int32_t pos2[2][QB_PMAX];    //                  matrix columns of C2's slots
-    int64_t a2off[2][QB_MAXP];   //                  row of dist_C2(., v2) in the tables
+    int64_t a1off[2][QB_MAXP];   //                  row of dist_C1(v1, .) in the tables
+    int64_t a2off[2][QB_MAXP];   //                  row of dist_C2(., v2)
     uint32_t qidx[2][QB_MAXP];   //                  the pair's position in the caller's arrays
     T init[2][QB_MAXP];          //                  the answer's starting value
     int32_t res[2][QB_MAXP];     //                  running minimum (bit pattern)
+    QItem item[4];               // the records of items m .. m + 3 (item m in slot m & 3)
 };
 
 // Largest pair count of an item on a block of ld columns: (pairs / 4) x (ld / 4) tiles
@@ -198,33 +201,52 @@ __device__ __forceinline__ int32_t res_reset() {
 __device__ __forceinline__ int32_t qb_addmin(int32_t a, int32_t b, int32_t t) { return __viaddmin_s32(a, b, t); }
 __device__ __forceinline__ float qb_addmin(float a, float b, float t) { return fminf(t, a + b); }
 
-// Queue the asynchronous copies of chunk ch of item p (positions in parity pp) into buffer
-// b: the block rows gathered from the matrix (warps over rows, lanes over columns) and
-// dist_C1(v1, rows) of pair tid (thread tid < count).  Padding columns past |B2| and rows
-// of the last chunk past the block's end are set to infinity.
+// Queue the asynchronous copies of chunk ch of item p (per-item records in parity pp)
+// into buffer b: the block rows gathered from the matrix (warps over rows, lanes over
+// columns) and the pieces dist_C1(v1, rows) of every pair, spread over all threads.
+// Padding columns past |B2| and rows of the last chunk past the block's end are set to
+// infinity.
 template <typename T>
 __device__ __forceinline__ void qb_issue(QbSmem<T>& sm, int b, int pp, const QbCtx<T>& c, const QItem& p, int ch,
-                                         int64_t a1off, int tid) {
+                                         int tid) {
     const int32_t r0 = ch * p.chr;
     const int32_t nrows = min(p.chr, p.nb1 - r0);
     const int32_t nr4 = (nrows + 3) & ~3;
     const int warp = tid >> 5, lane = tid & 31;
     T* dst = sm.s[b];
     const T inf = Inf<T>::value();
-    for (int32_t ii = warp; ii < nr4; ii += QB_TH / 32) {
-        T* d = dst + ii * p.ld2;
-        if (ii < nrows) {
-            const T* row = c.D + (int64_t)sm.pos1[pp][r0 + ii] * c.N;
-            for (int32_t jj = lane; jj < p.nb2; jj += 32) cp_async4(d + jj, row + sm.pos2[pp][jj]);
-            if (p.nb2 + lane < p.ld2) d[p.nb2 + lane] = inf;
-        } else {
-            for (int32_t jj = lane; jj < p.ld2; jj += 32) d[jj] = inf;
+    if (p.nb2 <= 128) {  // (the usual case: a lane's columns in registers)
+        int32_t col[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) col[k] = lane + 32 * k < p.nb2 ? sm.pos2[pp][lane + 32 * k] : 0;
+        for (int32_t ii = warp; ii < nr4; ii += QB_TH / 32) {
+            T* d = dst + ii * p.ld2;
+            if (ii < nrows) {
+                const T* row = c.D + (int64_t)sm.pos1[pp][r0 + ii] * c.N;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (lane + 32 * k < p.nb2) cp_async4(d + lane + 32 * k, row + col[k]);
+                if (p.nb2 + lane < p.ld2) d[p.nb2 + lane] = inf;
+            } else {
+                for (int32_t jj = lane; jj < p.ld2; jj += 32) d[jj] = inf;
+            }
+        }
+    } else {
+        for (int32_t ii = warp; ii < nr4; ii += QB_TH / 32) {
+            T* d = dst + ii * p.ld2;
+            if (ii < nrows) {
+                const T* row = c.D + (int64_t)sm.pos1[pp][r0 + ii] * c.N;
+                for (int32_t jj = lane; jj < p.nb2; jj += 32) cp_async4(d + jj, row + sm.pos2[pp][jj]);
+                if (p.nb2 + lane < p.ld2) d[p.nb2 + lane] = inf;
+            } else {
+                for (int32_t jj = lane; jj < p.ld2; jj += 32) d[jj] = inf;
+            }
         }
     }
-    if (tid < p.count) {
-        const T* a = c.apsp + a1off + r0;
-        T* d = sm.a[b] + tid * p.chr;
-        for (int32_t x = 0; x < nr4; x += 4) cp_async16(d + x, a + x);
+    const int32_t nq4 = nr4 >> 2;
+    for (int32_t x = tid; x < p.count * nq4; x += QB_TH) {
+        const int32_t u = x / nq4, q4 = x - u * nq4;
+        cp_async16(sm.a[b] + u * p.chr + 4 * q4, c.apsp + sm.a1off[pp][u] + r0 + 4 * q4);
     }
 }
 
@@ -238,7 +260,7 @@ __device__ __forceinline__ void qb_issue(QbSmem<T>& sm, int b, int pp, const QbC
 // pair) is listed in fb and recomputed exactly in int32 by k_qb_fallback.  No subnormal
 // is flushed: the kernel is built without fast math or .ftz.
 template <typename T, int MODE, bool ENC>
-__global__ void __launch_bounds__(QB_TH, 2)
+__global__ void __launch_bounds__(QB_TH, QB_CTAS)
     k_qb_blocks(const QbCtx<T> c, const QItem* __restrict__ items, const uint32_t* __restrict__ nitems_p,
                 const longlong2* __restrict__ rows, const T* __restrict__ init, const uint32_t* __restrict__ idx,
                 void* __restrict__ out, uint32_t* __restrict__ fb, uint32_t* __restrict__ nfb) {
@@ -248,54 +270,57 @@ __global__ void __launch_bounds__(QB_TH, 2)
     const int tid = threadIdx.x;
     const uint32_t nitems = *nitems_p;
     const uint32_t G = gridDim.x;
-    uint32_t it = blockIdx.x;
-    if (it >= nitems) return;
+    if (blockIdx.x >= nitems) return;
+    // the CTA's items are m = 0, 1, ...: item id blockIdx.x + m * G, record in slot m & 3,
+    // per-pair records and slot positions in parity m & 1.  After the switch to item m,
+    // shared memory holds the records of items m .. m + 3 and the per-pair records and
+    // positions of m and m + 1; registers hold those of m + 2 (loaded an item ahead).
+    auto item_at = [&](uint32_t m) { const uint32_t i = blockIdx.x + m * G; return i < nitems ? items[i] : QItem{}; };
+    if (tid < 4) sm.item[tid] = item_at(tid);
     if (tid < 2 * QB_MAXP) sm.res[tid / QB_MAXP][tid % QB_MAXP] = res_reset<CT>();
-    const CT inf = ENC ? __int_as_float(SPQ_INF_I32) : (CT)Inf<T>::value();
-    // the current item, the next one (with its per-pair records) and the one after that
-    // (its record only): loads are issued an item ahead of their use
-    QItem cur = items[it];
-    longlong2 crow = tid < cur.count ? rows[cur.start + tid] : make_longlong2(0, 0);
-    if (tid < cur.count) {
-        sm.a2off[0][tid] = crow.y;
-        sm.init[0][tid] = init[cur.start + tid];
-        sm.qidx[0][tid] = idx[cur.start + tid];
-    }
-    uint32_t itn = it + G;
-    QItem nxt = itn < nitems ? items[itn] : QItem{};
-    longlong2 nrow = tid < nxt.count ? rows[nxt.start + tid] : make_longlong2(0, 0);
-    T ninit = tid < nxt.count ? init[nxt.start + tid] : T(0);
-    uint32_t nidx = tid < nxt.count ? idx[nxt.start + tid] : 0u;
-    QItem nn = itn + G < nitems ? items[itn + G] : QItem{};
-    // slot positions: of the first two items into shared memory now, of the third into
-    // registers (stored when the first item is done)
-    qb_load_pos(sm, 0, c, cur, tid);
-    qb_load_pos(sm, 1, c, nxt, tid);
-    int32_t pr1[QB_PREG], pr2[QB_PREG];
-    qb_fetch_pos(c, nn, tid, pr1, pr2);
     __syncthreads();
+    for (int pp = 0; pp < 2; ++pp) {
+        const QItem& p = sm.item[pp];
+        if (tid < p.count) {
+            const longlong2 r = rows[p.start + tid];
+            sm.a1off[pp][tid] = r.x;
+            sm.a2off[pp][tid] = r.y;
+            sm.init[pp][tid] = init[p.start + tid];
+            sm.qidx[pp][tid] = idx[p.start + tid];
+        }
+        qb_load_pos(sm, pp, c, p, tid);
+    }
+    longlong2 nrow;
+    T ninit;
+    uint32_t nidx;
+    int32_t pr1[QB_PREG], pr2[QB_PREG];
+    {
+        const QItem& p = sm.item[2];
+        nrow = tid < p.count ? rows[p.start + tid] : make_longlong2(0, 0);
+        ninit = tid < p.count ? init[p.start + tid] : T(0);
+        nidx = tid < p.count ? idx[p.start + tid] : 0u;
+        qb_fetch_pos(c, p, tid, pr1, pr2);
+    }
+    __syncthreads();
+    const CT inf = ENC ? __int_as_float(SPQ_INF_I32) : (CT)Inf<T>::value();
 
+    uint32_t m = 0;
     int32_t unit[QB_UMAX];
-    qb_units(cur, tid, unit);
-    int ch = 0, b = 0, par = 0;
-    qb_issue<T>(sm, 0, 0, c, cur, 0, crow.x, tid);
+    qb_units(sm.item[0], tid, unit);
+    int ch = 0, b = 0;
+    qb_issue<T>(sm, 0, 0, c, sm.item[0], 0, tid);
     cp_async_commit();
     CT acc[QB_UMAX][4][4];
     for (;;) {
-        const bool next_same = ch + 1 < cur.nch;
-        const bool has_next = next_same || itn < nitems;
-        if (next_same) {
-            qb_issue<T>(sm, b ^ 1, par, c, cur, ch + 1, crow.x, tid);
-        } else if (has_next) {
-            // the next item's first chunk; its epilogue records go to the other parity
-            // (last read by the item before this one, behind a barrier since)
-            if (tid < nxt.count) {
-                sm.a2off[par ^ 1][tid] = nrow.y;
-                sm.init[par ^ 1][tid] = ninit;
-                sm.qidx[par ^ 1][tid] = nidx;
-            }
-            qb_issue<T>(sm, b ^ 1, par ^ 1, c, nxt, 0, nrow.x, tid);
-        }
+        const QItem& cur = sm.item[m & 3];
+        const int par = m & 1;
+        const int32_t nch = cur.nch, chr = cur.chr, ld2 = cur.ld2, Rs = cur.Rs;
+        const bool next_same = ch + 1 < nch;
+        const bool has_next = next_same || sm.item[(m + 1) & 3].count > 0;
+        if (next_same)
+            qb_issue<T>(sm, b ^ 1, par, c, cur, ch + 1, tid);
+        else if (has_next)
+            qb_issue<T>(sm, b ^ 1, par ^ 1, c, sm.item[(m + 1) & 3], 0, tid);
         if (has_next) {
             cp_async_commit();
             cp_async_wait<1>();
@@ -304,7 +329,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
         }
         __syncthreads();
         // ---- the chunk's arithmetic: row split r takes the quads r, r + Rs, ... ----
-        const int32_t nq = (min(cur.chr, cur.nb1 - ch * cur.chr) + 3) >> 2;
+        const int32_t nq = (min(chr, cur.nb1 - ch * chr) + 3) >> 2;
         if (ch == 0) {
 #pragma unroll
             for (int k = 0; k < QB_UMAX; ++k)
@@ -317,17 +342,16 @@ __global__ void __launch_bounds__(QB_TH, 2)
         for (int k = 0; k < QB_UMAX; ++k) {
             if (unit[k] >= 0) {
                 const int32_t r = unit[k] >> 28, g = (unit[k] >> 20) & 0xff, h = unit[k] & 0xfffff;
-                const T* ap = sm.a[b] + 4 * g * cur.chr;
+                const T* ap = sm.a[b] + 4 * g * chr;
                 const T* sp = sm.s[b] + 4 * h;
 #pragma unroll 1
-                for (int32_t qq = r; qq < nq; qq += cur.Rs) {
+                for (int32_t qq = r; qq < nq; qq += Rs) {
                     if constexpr (ENC) {
                         float4 av[4], sv[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(ap + i * cur.chr + 4 * qq);
+                        for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(ap + i * chr + 4 * qq);
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            sv[j] = *reinterpret_cast<const float4*>(sp + (4 * qq + j) * cur.ld2);
+                        for (int j = 0; j < 4; ++j) sv[j] = *reinterpret_cast<const float4*>(sp + (4 * qq + j) * ld2);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const float a[4] = {av[i].x, av[i].y, av[i].z, av[i].w};  // rows 4qq..4qq+3
@@ -350,7 +374,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
                         T av[4][4], sv[4][4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const int4 v = *reinterpret_cast<const int4*>(ap + i * cur.chr + 4 * qq);
+                            const int4 v = *reinterpret_cast<const int4*>(ap + i * chr + 4 * qq);
                             av[i][0] = *reinterpret_cast<const T*>(&v.x);
                             av[i][1] = *reinterpret_cast<const T*>(&v.y);
                             av[i][2] = *reinterpret_cast<const T*>(&v.z);
@@ -358,7 +382,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
                         }
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const int4 v = *reinterpret_cast<const int4*>(sp + (4 * qq + j) * cur.ld2);
+                            const int4 v = *reinterpret_cast<const int4*>(sp + (4 * qq + j) * ld2);
                             sv[j][0] = *reinterpret_cast<const T*>(&v.x);
                             sv[j][1] = *reinterpret_cast<const T*>(&v.y);
                             sv[j][2] = *reinterpret_cast<const T*>(&v.z);
@@ -377,6 +401,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
         }
         if (!next_same) {
             // ---- the item's end: + dist_C2(b2, v2), min over the columns, per pair ----
+            const int32_t count = cur.count, nb2 = cur.nb2;
 #pragma unroll
             for (int k = 0; k < QB_UMAX; ++k) {
                 if (unit[k] >= 0) {
@@ -384,7 +409,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int32_t u = 4 * g + i;
-                        if (u < cur.count) {
+                        if (u < count) {
                             const int4 cv = __ldg(reinterpret_cast<const int4*>(c.apsp + sm.a2off[par][u] + 4 * h));
                             const CT c4[4] = {*reinterpret_cast<const CT*>(&cv.x), *reinterpret_cast<const CT*>(&cv.y),
                                               *reinterpret_cast<const CT*>(&cv.z), *reinterpret_cast<const CT*>(&cv.w)};
@@ -393,7 +418,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
 #pragma unroll
                             for (int e = 1; e < 4; ++e) {
                                 const CT y = acc[k][i][e] + c4[e];
-                                v = (y < v && 4 * h + e < cur.nb2) ? y : v;
+                                v = (y < v && 4 * h + e < nb2) ? y : v;
                             }
                             atomicMin(&sm.res[par][u], enc_min<CT>(v));
                         }
@@ -401,7 +426,7 @@ __global__ void __launch_bounds__(QB_TH, 2)
                 }
             }
             __syncthreads();
-            if (tid < cur.count) {
+            if (tid < count) {
                 const uint32_t qi = sm.qidx[par][tid];
                 const T z = sm.init[par][tid];
                 if constexpr (ENC) {
@@ -428,22 +453,29 @@ __global__ void __launch_bounds__(QB_TH, 2)
         if (next_same) {
             ++ch;
         } else {
-            it = itn;
-            itn = it + G;
-            cur = nxt;
-            crow = nrow;
-            qb_units(cur, tid, unit);
+            // the switch to item m + 1: item m's records make room for m + 2 (from the
+            // registers) and m + 4 (its record, by one thread)
+            ++m;
             ch = 0;
-            par ^= 1;
-            nxt = nn;
-            nrow = tid < nxt.count ? rows[nxt.start + tid] : make_longlong2(0, 0);
-            ninit = tid < nxt.count ? init[nxt.start + tid] : T(0);
-            nidx = tid < nxt.count ? idx[nxt.start + tid] : 0u;
-            // the finished item's positions make room for the one after next
-            qb_store_pos(sm, par ^ 1, nxt, tid, pr1, pr2);
-            nn = itn + G < nitems ? items[itn + G] : QItem{};
-            qb_fetch_pos(c, nn, tid, pr1, pr2);
+            {
+                const QItem& p2 = sm.item[(m + 1) & 3];
+                const int pp = (m + 1) & 1;
+                if (tid < p2.count) {
+                    sm.a1off[pp][tid] = nrow.x;
+                    sm.a2off[pp][tid] = nrow.y;
+                    sm.init[pp][tid] = ninit;
+                    sm.qidx[pp][tid] = nidx;
+                }
+                qb_store_pos(sm, pp, p2, tid, pr1, pr2);
+            }
+            if (tid == 0) sm.item[(m + 3) & 3] = item_at(m + 3);
+            qb_units(sm.item[m & 3], tid, unit);
             __syncthreads();
+            const QItem& p3 = sm.item[(m + 2) & 3];
+            nrow = tid < p3.count ? rows[p3.start + tid] : make_longlong2(0, 0);
+            ninit = tid < p3.count ? init[p3.start + tid] : T(0);
+            nidx = tid < p3.count ? idx[p3.start + tid] : 0u;
+            qb_fetch_pos(c, p3, tid, pr1, pr2);
         }
         b ^= 1;
     }
@@ -594,7 +626,7 @@ cudaError_t launch_blocks_kernel(const QbCtx<T>& c, const QItem* items, const ui
         if (e != cudaSuccess) return e;
         attr.store(true);
     }
-    int64_t grid = (int64_t)qb_sms() * 2;
+    int64_t grid = (int64_t)qb_sms() * QB_CTAS;
     if (grid > q) grid = q;  // at most q items
     k_qb_blocks<T, MODE, ENC><<<(unsigned)grid, QB_TH, smem, st>>>(c, items, nitems, rows, init, idx, out, fb, nfb);
     count_launches(1);
