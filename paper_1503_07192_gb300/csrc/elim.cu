@@ -36,6 +36,7 @@
 
 #include "common.cuh"
 #include "fw_tile.cuh"
+#include "sync.cuh"
 
 namespace spq {
 
@@ -48,19 +49,6 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of one dependenc
 std::atomic<unsigned long long> g_wait_ns{kWaitNs};
 std::atomic<int> g_withhold{0};
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Integer encoding of the converted (CONV) back-substitution.  An int32 table value m
 // with 0 <= m < 2^24, read as the bits of a float, is the float m * 2^-149 (a subnormal
@@ -753,6 +741,11 @@ template cudaError_t bg_backsub_many<int32_t>(const std::vector<BsInput<int32_t>
 template cudaError_t launch_fill_marked<float>(float*, int64_t, const uint32_t*, cudaStream_t);
 template cudaError_t launch_fill_marked<int32_t>(int32_t*, int64_t, const uint32_t*, cudaStream_t);
 
+}  // namespace spq
+
+namespace spq {
+unsigned long long wait_bound_ns() { return g_wait_ns.load(); }
+int wait_withhold() { return g_withhold.load(); }
 }  // namespace spq
 
 extern "C" void spq_test_backsub_wait(unsigned long long limit_ns, int32_t withhold) {
