@@ -138,7 +138,8 @@ size_t pool_cached_bytes(int dev) {
 void free_handle_memory(spq_handle* h) {
     if (h->arena) {
         if (h->arena->refs.fetch_sub(1) == 1) {
-            cudaFree(h->arena->base);
+            cudaFreeAsync(h->arena->base, 0);  // back to the pool
+            cudaStreamSynchronize(0);
             delete h->arena;
         }
         h->arena = nullptr;
@@ -155,6 +156,15 @@ void free_handle_memory(spq_handle* h) {
 }
 
 }  // namespace
+
+size_t spq::pool_cached_bytes_current() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return pool_cached_bytes(dev);
+}
 
 // Temporaries of every entry point come from the same pool as the tables, so that the
 // memory of one build or query batch is reused by the next instead of being unmapped at

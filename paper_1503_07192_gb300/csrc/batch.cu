@@ -173,15 +173,12 @@ struct CompElim {
     int64_t ktot = 0;
 };
 
-// Tables of every instance in element type T (Algorithm 1 after the reordering).
+// Component tables of every instance in element type T (Algorithm 1 after the
+// reordering; independent of the boundary slots' order).
 template <typename T>
-cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs,
-                         const MatDesc* h_cdescs, int64_t ktot,
-                         int32_t max_ld, const MatDesc* d_bdescs, int32_t nbmat, int32_t max_N, bool f32w,
-                         uint32_t* fw_scratch, uint32_t* d_flag, bool check, bool* inexact, double* bg_updates,
-                         const BatchElim& be, const CompElim& ce, double* comp_elim_updates, cudaEvent_t* ev,
-                         cudaStream_t st) {
-    *inexact = false;
+cudaError_t batch_comp_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs,
+                              const MatDesc* h_cdescs, int64_t ktot, int32_t max_ld, bool f32w, const CompElim& ce,
+                              double* comp_elim_updates, cudaEvent_t* ev, cudaStream_t st) {
     T* base = reinterpret_cast<T*>(P.tables);
     cudaError_t e;
     cudaEventRecord(ev[2], st);
@@ -216,6 +213,18 @@ cudaError_t batch_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc
     if (max_ld > 0 && (e = fw_batched<T>(base, d_cdescs, h_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess)
         return e;
     cudaEventRecord(ev[3], st);
+    return cudaSuccess;
+}
+
+// Boundary graphs of every instance in element type T (after batch_comp_tables<T>):
+// assembly, all-pairs distances, and (check) the exactness check of every float32 table.
+template <typename T>
+cudaError_t batch_bg_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_bdescs, int32_t nbmat,
+                            int32_t max_N, bool f32w, uint32_t* fw_scratch, uint32_t* d_flag, bool check,
+                            bool* inexact, double* bg_updates, const BatchElim& be, cudaEvent_t* ev, cudaStream_t st) {
+    *inexact = false;
+    T* base = reinterpret_cast<T*>(P.tables);
+    cudaError_t e;
     for (auto& x : I) {
         if (x.N == 0) continue;
         T* D = base + x.d_off;
@@ -460,16 +469,22 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
                               (comp_elim ? 4 * (size_t)apsp_tot + 16 * (size_t)ntot : 0);
     size_t free_b = 0, total_b = 0;
     BCK(cudaMemGetInfo(&free_b, &total_b));
+    free_b += pool_cached_bytes_current();
     if (arena_bytes + temp_bytes > free_b) return SPQ_ENOMEM;
     void* arena_base = nullptr;
     {
-        cudaError_t e = cudaMalloc(&arena_base, arena_bytes);
+        // (from the library's pool: a batch's tens of gigabytes are kept mapped for the next)
+        cudaError_t e = scratch_alloc(&arena_base, arena_bytes, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SPQ_ENOMEM : batch_cuda_fail(e);
     }
     struct ArenaGuard {
         void* p;
         ~ArenaGuard() {
-            if (p) cudaFree(p);
+            if (p) {
+                cudaFreeAsync(p, 0);
+                cudaStreamSynchronize(0);
+            }
         }
     } aguard{arena_base};
     char* ab = static_cast<char*>(arena_base);
@@ -542,9 +557,22 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         BCK(cudaStreamSynchronize(st));  // cstart / ckbase go out of scope
     }
 
-    // ---- boundary-slot order of every instance: one gather, host ordering in threads ----
+    // ---- boundary-slot order of every instance: one gather, host ordering in threads (on
+    // a background thread, while the GPU computes the component tables) ----
     std::vector<int32_t> bgpos(slot_tot);
     std::vector<int32_t> methods(G, 0);
+    std::vector<std::vector<uint32_t>> hk(G);
+    std::vector<std::vector<int32_t>> hs(G), hcm(G);
+    std::atomic<int32_t> next{0};
+    std::atomic<int> bad{0};
+    std::thread order_thread;
+    bool order_pending = false;
+    struct Join {
+        std::thread& t;
+        ~Join() {
+            if (t.joinable()) t.join();
+        }
+    } join_order{order_thread};
     for (auto& x : I)
         for (int64_t i = 0; i < x.nbg; ++i) bgpos[x.slotbase + i] = (int32_t)i;
     if ((spq_order)o.order != SPQ_ORDER_ID && mtot > 0) {
@@ -565,8 +593,6 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         std::vector<uint32_t> hc(2 * (size_t)G);
         BCK(cudaMemcpyAsync(hc.data(), counters, hc.size() * 4, cudaMemcpyDeviceToHost, st));
         BCK(cudaStreamSynchronize(st));
-        std::vector<std::vector<uint32_t>> hk(G);
-        std::vector<std::vector<int32_t>> hs(G), hcm(G);
         for (int32_t g = 0; g < G; ++g) {
             const Inst& x = I[g];
             hk[g].resize(hc[2 * g]);
@@ -580,8 +606,8 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
             }
         }
         BCK(cudaStreamSynchronize(st));
-        std::atomic<int32_t> next{0};
-        std::atomic<int> bad{0};
+        order_pending = true;
+        order_thread = std::thread([&, order = (spq_order)o.order]() {
         auto worker = [&]() {
             for (;;) {
                 const int32_t g = next.fetch_add(1);
@@ -590,8 +616,7 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
                 if (hk[g].empty()) continue;
                 std::vector<int32_t> bp;
                 int32_t meth = 0;
-                if (boundary_order_host(x.k, x.nb, std::move(hk[g]), hs[g], hcm[g], (spq_order)o.order, &bp,
-                                        &meth) != SPQ_OK ||
+                if (boundary_order_host(x.k, x.nb, std::move(hk[g]), hs[g], hcm[g], order, &bp, &meth) != SPQ_OK ||
                     (int64_t)bp.size() != x.nbg) {
                     bad = 1;
                     continue;
@@ -605,19 +630,10 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         for (int t = 1; t < nth; ++t) pool.emplace_back(worker);
         worker();
         for (auto& t : pool) t.join();
-        if (bad) return SPQ_EINVAL;
-    }
-    if (slot_tot > 0) BCK(cudaMemcpyAsync(P.bgpos, bgpos.data(), (size_t)slot_tot * 4, cudaMemcpyHostToDevice, st));
-
-    // ---- the form of each boundary graph: elimination + back-substitution when asked
-    // for, or by default from kBatchElimMin slots on in a dissection order ----
-    for (int32_t g = 0; g < G; ++g) {
-        Inst& x = I[g];
-        x.elim = x.nbg > 0 && (o.bg_method == SPQ_BG_ELIM ||
-                               (o.bg_method == SPQ_BG_AUTO && x.nbg >= kBatchElimMin && methods[g] != 0));
+        });
     }
 
-    // ---- tables of every instance ----
+    // ---- component tables of every instance (while the host orders the slots) ----
     std::vector<MatDesc> cd, bd, ed;
     cd.reserve(ktot);
     // components by elimination (selected), the others by Floyd-Warshall (cd_fw: n = 0
@@ -676,10 +692,38 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
             BCK(cudaStreamSynchronize(st));  // the host vectors go out of scope
         }
     }
-    for (auto& x : I) {
+    for (auto& x : I)
         for (const MatDesc& d : x.descs) cd.push_back(MatDesc{x.apsp_off + d.off, d.n, 0});
-        if (x.N > 0) (x.elim ? ed : bd).push_back(MatDesc{x.d_off, (int32_t)x.N, 0});
+    MatDesc *d_cd, *d_bd;
+    uint32_t *fw_scratch, *d_flag;
+    BCK(tmp.alloc(&d_cd, cd.size()));
+    BCK(tmp.alloc(&d_flag, 1));
+    BCK(cudaMemcpyAsync(d_cd, cd.data(), cd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
+    double bg_updates = 0.0, comp_elim_updates = 0.0;
+    bool f32store = false;
+    int32_t arith = SPQ_ARITH_I32;
+    bool inexact = false;
+    // float32 first (exact below 2^24, checked), int32 if asked or if the check fails
+    const bool first_f32 = f32w || o.arith != SPQ_ARITH_I32;
+    if (first_f32)
+        BCK(batch_comp_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, f32w, ce, &comp_elim_updates, ev, st));
+    else
+        BCK(batch_comp_tables<int32_t>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, f32w, ce, &comp_elim_updates, ev,
+                                       st));
+
+    // ---- the slots' order, and the form of each boundary graph: elimination +
+    // back-substitution when asked for, or by default from kBatchElimMin slots on in a
+    // dissection order ----
+    if (order_thread.joinable()) order_thread.join();
+    if (order_pending && bad) return SPQ_EINVAL;
+    if (slot_tot > 0) BCK(cudaMemcpyAsync(P.bgpos, bgpos.data(), (size_t)slot_tot * 4, cudaMemcpyHostToDevice, st));
+    for (int32_t g = 0; g < G; ++g) {
+        Inst& x = I[g];
+        x.elim = x.nbg > 0 && (o.bg_method == SPQ_BG_ELIM ||
+                               (o.bg_method == SPQ_BG_AUTO && x.nbg >= kBatchElimMin && methods[g] != 0));
     }
+    for (auto& x : I)
+        if (x.N > 0) (x.elim ? ed : bd).push_back(MatDesc{x.d_off, (int32_t)x.N, 0});
     int32_t max_N_fw = 0, max_N_el = 0;
     for (const MatDesc& d : bd) max_N_fw = std::max(max_N_fw, d.n);
     for (const MatDesc& d : ed) max_N_el = std::max(max_N_el, d.n);
@@ -695,34 +739,27 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         BCK(cudaMemcpyAsync(be.descs, ed.data(), ed.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
         BCK(cudaMemsetAsync(be.err, 0, 4, st));
     }
-    MatDesc *d_cd, *d_bd;
-    uint32_t *fw_scratch, *d_flag;
-    BCK(tmp.alloc(&d_cd, cd.size()));
     BCK(tmp.alloc(&d_bd, bd.size()));
     BCK(tmp.alloc(&fw_scratch, (size_t)fw_words));
-    BCK(tmp.alloc(&d_flag, 1));
-    BCK(cudaMemcpyAsync(d_cd, cd.data(), cd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
     if (!bd.empty()) BCK(cudaMemcpyAsync(d_bd, bd.data(), bd.size() * sizeof(MatDesc), cudaMemcpyHostToDevice, st));
-    double bg_updates = 0.0, comp_elim_updates = 0.0;
-    bool f32store = false;
-    int32_t arith = SPQ_ARITH_I32;
-    bool inexact = false;
     if (f32w) {
         f32store = true;
         arith = SPQ_ARITH_F32;
-        BCK(batch_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, d_bd, (int32_t)bd.size(), max_N_fw, true, fw_scratch, d_flag,
-                                false, &inexact, &bg_updates, be, ce, &comp_elim_updates, ev, st));
+        BCK(batch_bg_tables<float>(I, P, d_bd, (int32_t)bd.size(), max_N_fw, true, fw_scratch, d_flag, false, &inexact,
+                                   &bg_updates, be, ev, st));
     } else {
-        const bool try_f32 = o.arith != SPQ_ARITH_I32;
-        if (try_f32) {
+        if (first_f32) {
             arith = SPQ_ARITH_F32;
-            BCK(batch_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
-                                    d_flag, true, &inexact, &bg_updates, be, ce, &comp_elim_updates, ev, st));
+            BCK(batch_bg_tables<float>(I, P, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch, d_flag, true,
+                                       &inexact, &bg_updates, be, ev, st));
         }
-        if (!try_f32 || inexact) {
+        if (!first_f32 || inexact) {
             arith = SPQ_ARITH_I32;
-            BCK(batch_tables<int32_t>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch,
-                                      d_flag, false, &inexact, &bg_updates, be, ce, &comp_elim_updates, ev, st));
+            if (inexact)
+                BCK(batch_comp_tables<int32_t>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, false, ce,
+                                               &comp_elim_updates, ev, st));
+            BCK(batch_bg_tables<int32_t>(I, P, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch, d_flag, false,
+                                         &inexact, &bg_updates, be, ev, st));
         }
     }
     BCK(cudaStreamSynchronize(st));
@@ -753,7 +790,8 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         spq_handle* h = new (std::nothrow) spq_handle();
         if (!h) {  // nothing was handed out yet: release everything
             for (int32_t j = 0; j < g; ++j) delete (*out)[j];
-            cudaFree(ar->base);
+            cudaFreeAsync(ar->base, 0);
+            cudaStreamSynchronize(0);
             delete ar;
             out->clear();
             return SPQ_ENOMEM;

@@ -57,6 +57,10 @@ void count_launches(int n);
 // cudaFreeAsync.
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
 
+// Bytes the library's pool on the current device holds but no allocation uses (free for
+// the next build; api.cu).
+size_t pool_cached_bytes_current();
+
 // Record a CUDA error for spq_last_cuda_error (entry points outside api.cu).
 void note_cuda_error(cudaError_t e);
 
