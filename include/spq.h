@@ -241,6 +241,35 @@ spq_status spq_build_many(int32_t count, const spq_graph* graphs, const spq_opts
                           spq_handle** outs);
 
 /*
+ * Build plan (CUDA graph) for re-weighting: Algorithm 1 on the same `count` graphs and
+ * partitions, again and again, with new edge weights.  spq_build_plan_create takes the
+ * arguments of spq_build_many (host or device arrays; the plan copies them, so they may be
+ * freed on return), builds once, and captures the weight-dependent launches (component
+ * tables, boundary-graph assembly and all-pairs distances, exactness check) into one CUDA
+ * graph; the steps that depend on the structure alone (numbering, boundary-slot order,
+ * elimination forms and their frontier bookkeeping) are not repeated.
+ *   handles[count] receives the instances' handles.  They belong to the plan: query them as
+ *   any handle, but do not pass them to spq_free (it ignores them); spq_build_plan_free
+ *   releases them with the plan.
+ * spq_build_plan_run(plan, weights, stream): weights[i] holds instance i's m_i weights in
+ * its CSR slot order and the plan's dtype (host or device memory).  They are copied and
+ * checked as spq_build checks them (SPQ_EINVAL before any table changes), then the graph
+ * replays on `stream` and the call returns when the tables are final (it synchronises the
+ * stream).  The handles' tables then hold the new distances, bit-identical to a fresh
+ * spq_build_many of the same graphs.  If the float32 tables of an SPQ_I32 plan fail the
+ * exactness check, that run is redone in int32 (spq_stats reports the arithmetic of the
+ * last run; a spq_query_plan made on these handles keeps the arithmetic it was made with,
+ * so remake it when that changes).  Queries on the handles must not overlap a run.
+ * SPQ_ETIMEOUT as spq_build; SPQ_ECUDA if the capture or a replay fails.  A plan is used by
+ * one thread at a time; spq_build_plan_free synchronises the device.
+ */
+typedef struct spq_build_plan spq_build_plan;
+spq_status spq_build_plan_create(int32_t count, const spq_graph* graphs, const spq_opts* opts, void* stream,
+                                 spq_build_plan** out, spq_handle** handles);
+spq_status spq_build_plan_run(spq_build_plan* plan, const void* const* weights, void* stream);
+void spq_build_plan_free(spq_build_plan* plan);
+
+/*
  * spq_query for `count` handles at once: pairs[i] (int32[q[i]][2]) against hs[i], answers
  * in dist_out[i].  All buffers host memory (synchronous; SPQ_EINVAL if any pair was out of
  * range) or all device memory (queued; spq_query_status per handle).  One scratch

@@ -137,7 +137,7 @@ class SpqHandle:
         return out
 
     def free(self):
-        if self._h:
+        if self._h and not getattr(self, "plan_owned", False):  # (a build plan's: freed with it)
             _lib.load().spq_free(self._h)
             self._h = None
 
@@ -194,6 +194,86 @@ def spq_build_many(graphs, opts: SpqOpts | None = None, stream=None) -> list:
         raise SpqError(st, "spq_build_many")
     return [SpqHandle(ctypes.c_void_p(outs[i]), int(graphs[i][0]), int(graphs[i][5]), arr[i].wt)
             for i in range(len(graphs))]
+
+
+class SpqBuildPlan:
+    """A batched build kept for re-weighting (spq_build_plan_*): run(weights) rebuilds
+    every instance's tables from new edge weights by one CUDA graph launch.  .handles
+    belong to the plan and stop working when it is freed."""
+
+    def __init__(self, ptr, handles, m, wt):
+        self._p = ptr
+        self.handles, self.m, self.wt = handles, m, wt
+
+    def run(self, weights, stream=None):
+        """weights: one array / tensor per instance (m_i values, CSR slot order)."""
+        if not self._p:
+            raise ValueError("plan already freed")
+        if len(weights) != len(self.handles):
+            raise ValueError("one weight array per instance")
+        arr = (ctypes.c_void_p * len(weights))()
+        keep = []
+        dev = False
+        for i, w in enumerate(weights):
+            w_p, w_k, w_d = _ptr(w, np.float32 if self.wt == SPQ_F32 else np.int32)
+            if int(w_k.numel() if _is_torch(w_k) else w_k.size) != self.m[i]:
+                raise ValueError(f"instance {i}: {self.m[i]} weights expected")
+            dev = dev or w_d
+            keep.append(w_k)
+            arr[i] = w_p
+        st = _lib.load().spq_build_plan_run(self._p, arr, _stream(stream, dev))
+        del keep
+        if st:
+            raise SpqError(st, "spq_build_plan_run")
+        return self.handles
+
+    def free(self):
+        if self._p:
+            for h in self.handles:
+                h._h = None  # (released with the plan)
+            _lib.load().spq_build_plan_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def spq_build_plan(graphs, opts: SpqOpts | None = None, stream=None) -> SpqBuildPlan:
+    """spq_build_many kept as a build plan: graphs as for spq_build_many; the plan copies
+    them.  Returns the plan; its .handles are the instances' handles, already built."""
+    lib = _lib.load()
+    keep = []
+    arr = (_lib.SpqGraph * len(graphs))()
+    wt0 = None
+    dev = False
+    ms = []
+    for i, (n, row_ptr, col, w, part, k) in enumerate(graphs):
+        wt = SPQ_F32 if (getattr(w, "dtype", None) in (np.float32, np.float64) or
+                         (_is_torch(w) and w.is_floating_point())) else SPQ_I32
+        wt0 = wt if wt0 is None else wt0
+        rp_p, rp_k, rp_d = _ptr(row_ptr, np.int64)
+        col_p, col_k, _ = _ptr(col, np.int32)
+        w_p, w_k, _ = _ptr(w, np.float32 if wt == SPQ_F32 else np.int32)
+        pt_p, pt_k, _ = _ptr(part, np.int32)
+        dev = dev or rp_d
+        keep += [rp_k, col_k, w_k, pt_k]
+        ms.append(int(w_k.numel() if _is_torch(w_k) else w_k.size))
+        arr[i] = _lib.SpqGraph(int(n), rp_p, col_p, w_p, wt, pt_p, int(k))
+    outs = (ctypes.c_void_p * len(graphs))()
+    plan = ctypes.c_void_p()
+    st = lib.spq_build_plan_create(len(graphs), arr, ctypes.byref(opts) if opts is not None else None,
+                                   _stream(stream, dev), ctypes.byref(plan), outs)
+    del keep
+    if st:
+        raise SpqError(st, "spq_build_plan_create")
+    hs = [SpqHandle(ctypes.c_void_p(outs[i]), int(graphs[i][0]), int(graphs[i][5]), arr[i].wt)
+          for i in range(len(graphs))]
+    for h in hs:
+        h.plan_owned = True
+    return SpqBuildPlan(plan, hs, ms, wt0)
 
 
 def spq_query_many(handles, pairs_list, outs=None, stream=None) -> list:

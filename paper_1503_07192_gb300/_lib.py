@@ -49,6 +49,10 @@ SIGNATURES = {
     "spq_query_plan_create": (ctypes.c_int, [i32, P, P, P, P, P, ctypes.POINTER(P)]),
     "spq_query_plan_run": (ctypes.c_int, [P, P]),
     "spq_query_plan_free": (None, [P]),
+    "spq_build_plan_create": (ctypes.c_int, [i32, ctypes.POINTER(SpqGraph), ctypes.POINTER(SpqOpts), P,
+                                             ctypes.POINTER(P), ctypes.POINTER(P)]),
+    "spq_build_plan_run": (ctypes.c_int, [P, ctypes.POINTER(P), P]),
+    "spq_build_plan_free": (None, [P]),
     "spq_server_create": (ctypes.c_int, [ctypes.c_int, i32, i64, ctypes.c_size_t, ctypes.POINTER(P)]),
     "spq_server_add_graph": (ctypes.c_int, [P, i32, P]),
     "spq_server_remove_graph": (ctypes.c_int, [P, i32]),

@@ -733,7 +733,7 @@ spq_status spq_query_status(spq_handle* h, void* stream) {
 }
 
 void spq_free(spq_handle* h) {
-    if (!h) return;
+    if (!h || h->plan_owned) return;
     cudaDeviceSynchronize();
     free_handle_memory(h);
     delete h;

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "handle.h"
+#include "spq_bench.h"
 #include "order.h"
 
 using namespace spq;
@@ -173,15 +174,47 @@ struct CompElim {
     int64_t ktot = 0;
 };
 
+// The weight-dependent launches of a batched build in element type T, kept for replay
+// (build plans): the components' elimination, the Floyd-Warshall round lists, the
+// boundary graphs' back-substitution, and the second stream of the boundary graphs'
+// Floyd-Warshall with its fork / join events.  Recorded by the first build (ready = false
+// on entry), replayed by a stream capture (ready = true: no host step, no allocation).
+template <typename T>
+struct StageKeep {
+    bool ready = false;
+    CompElimPlan<T> ce;
+    int32_t* fwb = nullptr;
+    BsPlan<T> bg;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    void release(cudaStream_t st) {
+        ce.release(st);
+        bg.release(st);
+        if (fwb) cudaFreeAsync(fwb, st);
+        fwb = nullptr;
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s2) {
+            cudaStreamSynchronize(s2);
+            cudaStreamDestroy(s2);
+        }
+        fork = join = nullptr;
+        s2 = nullptr;
+        ready = false;
+    }
+};
+
 // Component tables of every instance in element type T (Algorithm 1 after the
-// reordering; independent of the boundary slots' order).
+// reordering; independent of the boundary slots' order).  ev: stage events (may be null);
+// keep: record / replay (may be null).
 template <typename T>
 cudaError_t batch_comp_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_cdescs,
                               const MatDesc* h_cdescs, int64_t ktot, int32_t max_ld, bool f32w, const CompElim& ce,
-                              double* comp_elim_updates, cudaEvent_t* ev, cudaStream_t st) {
+                              double* comp_elim_updates, cudaEvent_t* ev, cudaStream_t st,
+                              StageKeep<T>* keep = nullptr) {
     T* base = reinterpret_cast<T*>(P.tables);
     cudaError_t e;
-    cudaEventRecord(ev[2], st);
+    if (ev) cudaEventRecord(ev[2], st);
     if ((e = launch_fill_blocks<T>(base, d_cdescs, (int32_t)ktot, st)) != cudaSuccess) return e;
     for (auto& x : I) {
         if (x.n == 0) continue;
@@ -207,22 +240,28 @@ cudaError_t batch_comp_tables(std::vector<Inst>& I, const BatchPtrs& P, const Ma
             if (e != cudaSuccess) return e;
         }
         e = comp_elim_finish<T>(base, Pc, d_cdescs, ce.ed, ce.d_sel, ce.d_ed, P.csize, ce.vstart_global, ce.ndpos,
-                                comp_elim_updates, st);
+                                comp_elim_updates, st, keep ? &keep->ce : nullptr);
         if (e != cudaSuccess) return e;
     }
-    if (max_ld > 0 && (e = fw_batched<T>(base, d_cdescs, h_cdescs, (int32_t)ktot, max_ld, st)) != cudaSuccess)
+    if (max_ld > 0 &&
+        (e = fw_batched<T>(base, d_cdescs, h_cdescs, (int32_t)ktot, max_ld, st, keep ? &keep->fwb : nullptr)) !=
+            cudaSuccess)
         return e;
-    cudaEventRecord(ev[3], st);
+    if (ev) cudaEventRecord(ev[3], st);
     return cudaSuccess;
 }
 
 // Boundary graphs of every instance in element type T (after batch_comp_tables<T>):
 // assembly, all-pairs distances, and (check) the exactness check of every float32 table.
+// ev: stage events (may be null).  keep: record / replay (may be null); a replay leaves
+// the check's flag in d_flag and the status in be.err for the caller to read.
 template <typename T>
 cudaError_t batch_bg_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatDesc* d_bdescs, int32_t nbmat,
                             int32_t max_N, bool f32w, uint32_t* fw_scratch, uint32_t* d_flag, bool check,
-                            bool* inexact, double* bg_updates, const BatchElim& be, cudaEvent_t* ev, cudaStream_t st) {
+                            bool* inexact, double* bg_updates, const BatchElim& be, cudaEvent_t* ev, cudaStream_t st,
+                            StageKeep<T>* keep = nullptr) {
     *inexact = false;
+    const bool replay = keep && keep->ready;
     T* base = reinterpret_cast<T*>(P.tables);
     cudaError_t e;
     for (auto& x : I) {
@@ -236,22 +275,36 @@ cudaError_t batch_bg_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatD
                                P.bgpos + x.slotbase, D, x.N, st);
         if (e != cudaSuccess) return e;
     }
-    cudaEventRecord(ev[4], st);
-    // The Floyd-Warshall instances' rounds on a second stream (their host waits on a
-    // helper thread), the elimination instances' forward rounds and back-substitution
-    // here: both sets of launches side by side.
+    if (ev) cudaEventRecord(ev[4], st);
+    // The Floyd-Warshall instances' rounds on a second stream, the elimination instances'
+    // forward rounds and back-substitution here: both sets of launches side by side.  A
+    // build waits on the host for the first set on a helper thread; a replay forks and
+    // joins the second stream with events (branches of the captured graph).
     double fw_upd = 0.0;
     cudaError_t fw_err = cudaSuccess;
     cudaStream_t s2 = nullptr;
     cudaEvent_t fw_done = nullptr;
     std::thread fw_thread;
-    if (nbmat > 0) {
+    if (nbmat > 0 && replay) {
+        if ((e = cudaEventRecord(keep->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(keep->s2, keep->fork, 0)) != cudaSuccess) return e;
+        if ((e = fw_many_skip<T>(base, d_bdescs, nbmat, max_N, fw_scratch, nullptr, keep->s2, false, false)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(keep->join, keep->s2)) != cudaSuccess) return e;
+    } else if (nbmat > 0) {
         if ((e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&fw_done, cudaEventDisableTiming)) != cudaSuccess) {
             cudaStreamDestroy(s2);
             return e;
         }
-        cudaStreamWaitEvent(s2, ev[4], 0);
+        if (ev) {
+            cudaStreamWaitEvent(s2, ev[4], 0);
+        } else {
+            // (no stage events: order s2 after the assembly with fw_done itself)
+            cudaEventRecord(fw_done, st);
+            cudaStreamWaitEvent(s2, fw_done, 0);
+        }
         fw_thread = std::thread([&, dev = be.dev]() {
             fw_err = cudaSetDevice(dev);
             if (fw_err == cudaSuccess) fw_err = fw_many_skip<T>(base, d_bdescs, nbmat, max_N, fw_scratch, &fw_upd, s2);
@@ -261,38 +314,45 @@ cudaError_t batch_bg_tables(std::vector<Inst>& I, const BatchPtrs& P, const MatD
     double el_upd = 0.0;
     if (be.n > 0) {
         double fwd = 0.0, bs = 0.0;
-        e = fw_many_skip<T>(base, be.descs, be.n, be.max_N, be.scratch, &fwd, st, true);
+        e = fw_many_skip<T>(base, be.descs, be.n, be.max_N, be.scratch, &fwd, st, true, !replay);
         if (e == cudaSuccess) {
             std::vector<BsInput<T>> bin;
             for (auto& x : I)
                 if (x.elim) bin.push_back(BsInput<T>{base + x.d_off, x.N, nullptr});
-            e = bg_backsub_many<T>(bin, be.err, nullptr, be.panel_cap, &bs, nullptr, st);
+            e = bg_backsub_many<T>(bin, be.err, nullptr, be.panel_cap, &bs, nullptr, st, keep ? &keep->bg : nullptr);
         }
         el_upd = fwd + bs;
     }
-    if (fw_thread.joinable()) fw_thread.join();
-    if (fw_done) {
-        if (fw_err == cudaSuccess) cudaStreamWaitEvent(st, fw_done, 0);
-        cudaEventDestroy(fw_done);
+    if (replay) {
+        if (nbmat > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(st, keep->join, 0);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (fw_thread.joinable()) fw_thread.join();
+        if (fw_done) {
+            if (fw_err == cudaSuccess) cudaStreamWaitEvent(st, fw_done, 0);
+            cudaEventDestroy(fw_done);
+        }
+        if (s2) {
+            if (fw_err != cudaSuccess) cudaStreamSynchronize(s2);
+            cudaStreamDestroy(s2);
+        }
+        if (e != cudaSuccess) return e;
+        if (fw_err != cudaSuccess) return fw_err;
+        *bg_updates = fw_upd + el_upd;
     }
-    if (s2) {
-        if (fw_err != cudaSuccess) cudaStreamSynchronize(s2);
-        cudaStreamDestroy(s2);
-    }
-    if (e != cudaSuccess) return e;
-    if (fw_err != cudaSuccess) return fw_err;
-    *bg_updates = fw_upd + el_upd;
-    cudaEventRecord(ev[5], st);
+    if (ev) cudaEventRecord(ev[5], st);
     if (check) {
         if ((e = cudaMemsetAsync(d_flag, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
         if ((e = launch_check_convert(reinterpret_cast<float*>(P.tables), P.table_elems, d_flag, st)) != cudaSuccess)
             return e;
-        uint32_t f = 0;
-        if ((e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-        *inexact = (f & kErrExact) != 0;
+        if (!replay) {
+            uint32_t f = 0;
+            if ((e = cudaMemcpyAsync(&f, d_flag, sizeof(f), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+            *inexact = (f & kErrExact) != 0;
+        }
     }
-    cudaEventRecord(ev[6], st);
+    if (ev) cudaEventRecord(ev[6], st);
     return cudaSuccess;
 }
 
@@ -306,8 +366,43 @@ int bits_of(uint64_t x) {
 
 namespace {
 
+// What a build plan keeps of its first build: the batch's layout and device temporaries,
+// and the recorded weight-dependent launches of both element types.
+struct BuildKeep {
+    std::vector<void*> temps;  // device temporaries of the first build
+    std::vector<Inst> I;
+    BatchPtrs P;
+    MatDesc* d_cd = nullptr;
+    std::vector<MatDesc> cd_fw;
+    int64_t ktot = 0, mtot = 0;
+    int32_t max_ld_fw = 0;
+    bool f32w = false;
+    CompElim ce;
+    MatDesc* d_bd = nullptr;
+    int32_t nbmat = 0, max_N_fw = 0;
+    uint32_t* fw_scratch = nullptr;
+    uint32_t* d_flag = nullptr;
+    BatchElim be;
+    int32_t arith = SPQ_ARITH_I32;
+    // the validation launch of every instance (its records and outputs)
+    ValGraph* d_vg = nullptr;
+    int64_t* d_vb = nullptr;
+    uint8_t* bflag = nullptr;
+    int32_t* cnt = nullptr;
+    uint32_t* errs = nullptr;
+    int64_t ntot = 0;
+    StageKeep<float> kf;
+    StageKeep<int32_t> ki;
+    void release(cudaStream_t st) {
+        kf.release(st);
+        ki.release(st);
+        for (void* p : temps) cudaFreeAsync(p, st);
+        temps.clear();
+    }
+};
+
 spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cudaStream_t st,
-                           std::vector<spq_handle*>* out) {
+                           std::vector<spq_handle*>* out, BuildKeep* keep = nullptr) {
     TempList tmp(st);
     const spq_dtype wt = gs[0].wt;
     const bool f32w = wt == SPQ_F32;
@@ -705,11 +800,14 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
     bool inexact = false;
     // float32 first (exact below 2^24, checked), int32 if asked or if the check fails
     const bool first_f32 = f32w || o.arith != SPQ_ARITH_I32;
+    StageKeep<float>* kf = keep ? &keep->kf : nullptr;
+    StageKeep<int32_t>* ki = keep ? &keep->ki : nullptr;
     if (first_f32)
-        BCK(batch_comp_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, f32w, ce, &comp_elim_updates, ev, st));
+        BCK(batch_comp_tables<float>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, f32w, ce, &comp_elim_updates, ev, st,
+                                     kf));
     else
         BCK(batch_comp_tables<int32_t>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, f32w, ce, &comp_elim_updates, ev,
-                                       st));
+                                       st, ki));
 
     // ---- the slots' order, and the form of each boundary graph: elimination +
     // back-substitution when asked for, or by default from kBatchElimMin slots on in a
@@ -746,20 +844,20 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         f32store = true;
         arith = SPQ_ARITH_F32;
         BCK(batch_bg_tables<float>(I, P, d_bd, (int32_t)bd.size(), max_N_fw, true, fw_scratch, d_flag, false, &inexact,
-                                   &bg_updates, be, ev, st));
+                                   &bg_updates, be, ev, st, kf));
     } else {
         if (first_f32) {
             arith = SPQ_ARITH_F32;
             BCK(batch_bg_tables<float>(I, P, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch, d_flag, true,
-                                       &inexact, &bg_updates, be, ev, st));
+                                       &inexact, &bg_updates, be, ev, st, kf));
         }
         if (!first_f32 || inexact) {
             arith = SPQ_ARITH_I32;
             if (inexact)
                 BCK(batch_comp_tables<int32_t>(I, P, d_cd, cd_fw.data(), ktot, max_ld_fw, false, ce,
-                                               &comp_elim_updates, ev, st));
+                                               &comp_elim_updates, ev, st, ki));
             BCK(batch_bg_tables<int32_t>(I, P, d_bd, (int32_t)bd.size(), max_N_fw, false, fw_scratch, d_flag, false,
-                                         &inexact, &bg_updates, be, ev, st));
+                                         &inexact, &bg_updates, be, ev, st, ki));
         }
     }
     BCK(cudaStreamSynchronize(st));
@@ -768,6 +866,32 @@ spq_status build_many_impl(int32_t G, const spq_graph* gs, const spq_opts& o, cu
         uint32_t f = 0;
         BCK(cudaMemcpy(&f, be.err, 4, cudaMemcpyDeviceToHost));
         if (f & kErrWait) return SPQ_ETIMEOUT;
+    }
+    if (keep) {
+        keep->I = I;
+        keep->P = P;
+        keep->d_cd = d_cd;
+        keep->cd_fw = cd_fw;
+        keep->ktot = ktot;
+        keep->mtot = mtot;
+        keep->max_ld_fw = max_ld_fw;
+        keep->f32w = f32w;
+        keep->ce = ce;
+        keep->d_bd = d_bd;
+        keep->nbmat = (int32_t)bd.size();
+        keep->max_N_fw = max_N_fw;
+        keep->fw_scratch = fw_scratch;
+        keep->d_flag = d_flag;
+        keep->be = be;
+        keep->arith = arith;
+        keep->d_vg = d_vg;
+        keep->d_vb = d_vb;
+        keep->bflag = bflag;
+        keep->cnt = cnt;
+        keep->errs = errs;
+        keep->ntot = ntot;
+        keep->temps = std::move(tmp.ptrs);
+        tmp.ptrs.clear();
     }
     double prof[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < 6; ++i) {
@@ -1013,5 +1137,251 @@ spq_status spq_query_plan_run(spq_query_plan* p, void* stream) {
 }
 
 void spq_query_plan_free(spq_query_plan* p) { plan_destroy(p); }
+
+}  // extern "C"
+
+// ---- build plans: fixed topologies, changing weights ----
+
+namespace {
+
+// The weight-dependent launches of a plan in element type T, with the recorded plans of
+// sk: replayed (sk.ready: the stream capture) or run afresh (sk = null).  ev-less.
+template <typename T>
+cudaError_t plan_stage(BuildKeep& K, StageKeep<T>* sk, bool check, bool* inexact, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (K.be.n > 0) e = cudaMemsetAsync(K.be.err, 0, 4, st);
+    double cu = 0.0, bu = 0.0;
+    *inexact = false;
+    if (e == cudaSuccess)
+        e = batch_comp_tables<T>(K.I, K.P, K.d_cd, K.cd_fw.data(), K.ktot, K.max_ld_fw, K.f32w, K.ce, &cu, nullptr,
+                                 st, sk);
+    if (e == cudaSuccess)
+        e = batch_bg_tables<T>(K.I, K.P, K.d_bd, K.nbmat, K.max_N_fw, K.f32w, K.fw_scratch, K.d_flag, check, inexact,
+                               &bu, K.be, nullptr, st, sk);
+    return e;
+}
+
+// An uncaptured pass (fresh bookkeeping): float32 first when asked, int32 after it if
+// the float32 tables fail the exactness check (check: int32 weights in float32).
+cudaError_t plan_rebuild(BuildKeep& K, bool f32, bool check, int32_t* arith, cudaStream_t st) {
+    bool inexact = false;
+    cudaError_t e = cudaSuccess;
+    if (f32) {
+        e = plan_stage<float>(K, nullptr, check, &inexact, st);
+        *arith = SPQ_ARITH_F32;
+    }
+    if (e == cudaSuccess && (!f32 || inexact)) {
+        e = plan_stage<int32_t>(K, nullptr, false, &inexact, st);
+        *arith = SPQ_ARITH_I32;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && K.be.n > 0) {
+        uint32_t f = 0;
+        e = cudaMemcpy(&f, K.be.err, 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && (f & kErrWait)) e = kWaitGaveUp;
+    }
+    return e;
+}
+
+}  // namespace
+
+// A batched build kept for re-weighting (Algorithm 1 again on the same graphs and
+// partitions with new edge weights).  The steps that depend on the structure only
+// (numbering, boundary-slot order, elimination forms, the back-substitution's frontier
+// bookkeeping) are done once; the weight-dependent launches are captured once into a
+// CUDA graph, replayed by every run.
+struct spq_build_plan {
+    int dev = 0;
+    int32_t G = 0;
+    spq_dtype wt = SPQ_I32;
+    BuildKeep keep;
+    std::vector<spq_handle*> hs;
+    std::vector<int64_t> m, woff;  // per instance: edges, offset of its weights in wbuf
+    uint32_t* wbuf = nullptr;      // every instance's weights (the graph reads them here)
+    std::vector<void*> own;        // the plan's copies of the CSR arrays and partitions
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool f32_path = false;  // the captured launches compute in float32
+    bool check = false;     // ... and end with the exactness check (int32 weights)
+    unsigned long long launches = 0;  // kernels per replay
+};
+
+namespace {
+
+void build_plan_destroy(spq_build_plan* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->keep.release(0);
+    for (void* x : p->own) cudaFreeAsync(x, 0);
+    if (p->wbuf) cudaFreeAsync(p->wbuf, 0);
+    cudaStreamSynchronize(0);
+    for (spq_handle* h : p->hs)
+        if (h) {
+            h->plan_owned = false;
+            spq_free(h);
+        }
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+spq_status spq_build_plan_create(int32_t count, const spq_graph* graphs, const spq_opts* opts, void* stream,
+                                 spq_build_plan** out, spq_handle** handles) {
+    if (!out) return SPQ_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !graphs || !handles) return SPQ_EINVAL;
+    for (int32_t g = 0; g < count; ++g) handles[g] = nullptr;
+    spq_opts o;
+    if (spq_status so = read_opts(opts, &o)) return so;
+    const spq_dtype wt = graphs[0].wt;
+    for (int32_t g = 0; g < count; ++g) {
+        const spq_graph& a = graphs[g];
+        if (a.n < 1 || a.k < 1 || !a.row_ptr || !a.part || a.wt != wt) return SPQ_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    spq_build_plan* p = new (std::nothrow) spq_build_plan();
+    if (!p) return SPQ_ENOMEM;
+    struct Guard {
+        spq_build_plan*& p;
+        ~Guard() { build_plan_destroy(p); }
+    } guard{p};
+    p->G = count;
+    p->wt = wt;
+    BCK(cudaGetDevice(&p->dev));
+    // the plan's own copies of every instance's arrays (the caller's may go away), the
+    // weights of all instances in one buffer
+    int64_t mtot = 0;
+    std::vector<spq_graph> gs(count);
+    for (int32_t g = 0; g < count; ++g) {
+        const spq_graph& a = graphs[g];
+        int64_t m = 0;
+        if (dev_pointer(a.row_ptr)) {
+            BCK(cudaMemcpy(&m, a.row_ptr + a.n, 8, cudaMemcpyDeviceToHost));
+        } else {
+            m = a.row_ptr[a.n];
+        }
+        if (m < 0 || m > INT32_MAX || (m > 0 && (!a.col || !a.w))) return SPQ_EINVAL;
+        p->m.push_back(m);
+        p->woff.push_back(mtot);
+        mtot += m;
+        int64_t* rp;
+        int32_t *col = nullptr, *part;
+        BCK(scratch_alloc((void**)&rp, ((size_t)a.n + 1) * 8, st));
+        p->own.push_back(rp);
+        BCK(scratch_alloc((void**)&part, (size_t)a.n * 4, st));
+        p->own.push_back(part);
+        BCK(cudaMemcpyAsync(rp, a.row_ptr, ((size_t)a.n + 1) * 8, cudaMemcpyDefault, st));
+        BCK(cudaMemcpyAsync(part, a.part, (size_t)a.n * 4, cudaMemcpyDefault, st));
+        if (m > 0) {
+            BCK(scratch_alloc((void**)&col, (size_t)m * 4, st));
+            p->own.push_back(col);
+            BCK(cudaMemcpyAsync(col, a.col, (size_t)m * 4, cudaMemcpyDefault, st));
+        }
+        gs[g] = spq_graph{a.n, rp, col, nullptr, wt, part, a.k};
+    }
+    BCK(scratch_alloc((void**)&p->wbuf, (size_t)(mtot > 0 ? mtot : 1) * 4, st));
+    for (int32_t g = 0; g < count; ++g) {
+        if (p->m[g] > 0)
+            BCK(cudaMemcpyAsync(p->wbuf + p->woff[g], graphs[g].w, (size_t)p->m[g] * 4, cudaMemcpyDefault, st));
+        gs[g].w = p->wbuf + p->woff[g];
+    }
+    BCK(cudaStreamSynchronize(st));
+    // the first build, recording the launches' bookkeeping
+    if (spq_status s = build_many_impl(count, gs.data(), o, st, &p->hs, &p->keep)) {
+        cudaStreamSynchronize(st);
+        return s;
+    }
+    for (spq_handle* h : p->hs) h->plan_owned = true;
+    BuildKeep& K = p->keep;
+    p->f32_path = K.arith == SPQ_ARITH_F32;
+    p->check = p->f32_path && !K.f32w;
+    // the capture: the recorded launches of the arithmetic the first build ended in
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    auto prep = [&](auto& sk) {
+        cudaError_t r = cudaStreamCreateWithFlags(&sk.s2, cudaStreamNonBlocking);
+        if (r == cudaSuccess) r = cudaEventCreateWithFlags(&sk.fork, cudaEventDisableTiming);
+        if (r == cudaSuccess) r = cudaEventCreateWithFlags(&sk.join, cudaEventDisableTiming);
+        sk.ready = true;
+        return r;
+    };
+    if (e == cudaSuccess) e = p->f32_path ? prep(K.kf) : prep(K.ki);
+    // (the bookkeeping of the other element type is not needed)
+    if (p->f32_path)
+        K.ki.release(st);
+    else
+        K.kf.release(st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const unsigned long long n0 = spq_kernel_launches();
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        bool inexact = false;
+        const cudaError_t e1 = p->f32_path ? plan_stage<float>(K, &K.kf, p->check, &inexact, cs)
+                                           : plan_stage<int32_t>(K, &K.ki, false, &inexact, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+        e = e1 != cudaSuccess ? e1 : e2;
+    }
+    p->launches = spq_kernel_launches() - n0;
+    count_launches(-(int)p->launches);  // (captured, not launched)
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // a failed capture leaves no error behind for later calls
+        return batch_cuda_fail(e);
+    }
+    for (int32_t g = 0; g < count; ++g) handles[g] = p->hs[g];
+    *out = p;
+    p = nullptr;  // (kept)
+    return SPQ_OK;
+}
+
+spq_status spq_build_plan_run(spq_build_plan* p, const void* const* weights, void* stream) {
+    if (!p || !p->exec || !weights) return SPQ_EINVAL;
+    for (int32_t g = 0; g < p->G; ++g)
+        if (p->m[g] > 0 && !weights[g]) return SPQ_EINVAL;
+    int dev = 0;
+    BCK(cudaGetDevice(&dev));
+    if (dev != p->dev) return SPQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    BuildKeep& K = p->keep;
+    for (int32_t g = 0; g < p->G; ++g)
+        if (p->m[g] > 0)
+            BCK(cudaMemcpyAsync(p->wbuf + p->woff[g], weights[g], (size_t)p->m[g] * 4, cudaMemcpyDefault, st));
+    // the new weights checked as a build checks them, before any table is touched
+    BCK(cudaMemsetAsync(K.cnt, 0, 2 * (size_t)K.ktot * 4, st));
+    BCK(cudaMemsetAsync(K.errs, 0, ((size_t)p->G + 1) * 4, st));
+    BCK(launch_validate_many(K.f32w, K.d_vg, K.d_vb, p->G, K.ntot, K.bflag, K.cnt, K.cnt + K.ktot, K.errs, st));
+    std::vector<uint32_t> herr(p->G);
+    BCK(cudaMemcpyAsync(herr.data(), K.errs, (size_t)p->G * 4, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    for (uint32_t f : herr)
+        if (f) return SPQ_EINVAL;
+    // the recorded launches; then their status words
+    BCK(cudaGraphLaunch(p->exec, st));
+    count_launches((int)p->launches);
+    uint32_t flag = 0, cerr = 0, berr = 0;
+    const uint32_t* ce_err = p->f32_path ? K.kf.ce.err : K.ki.ce.err;
+    if (p->check) BCK(cudaMemcpyAsync(&flag, K.d_flag, 4, cudaMemcpyDeviceToHost, st));
+    if (ce_err) BCK(cudaMemcpyAsync(&cerr, ce_err, 4, cudaMemcpyDeviceToHost, st));
+    if (K.be.n > 0) BCK(cudaMemcpyAsync(&berr, K.be.err, 4, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    if ((cerr | berr) & kErrWait) return SPQ_ETIMEOUT;
+    int32_t arith = p->f32_path ? SPQ_ARITH_F32 : SPQ_ARITH_I32;
+    if ((cerr | berr) & kErrPlan) {
+        // another finite-tile structure than recorded (distances at the int32 limit): the
+        // launches again with fresh bookkeeping
+        BCK(plan_rebuild(K, p->f32_path, p->check, &arith, st));
+    } else if (p->check && (flag & kErrExact)) {
+        BCK(plan_rebuild(K, false, false, &arith, st));
+    }
+    for (spq_handle* h : p->hs) h->arith = arith;
+    return SPQ_OK;
+}
+
+void spq_build_plan_free(spq_build_plan* p) { build_plan_destroy(p); }
 
 }  // extern "C"

@@ -20,6 +20,7 @@ enum : uint32_t {
     kErrExact = 32u,  // float32 tables hold a finite entry >= 2^24 (not provably exact)
     kErrWalk = 64u,   // a gradient path walk did not reach its target (ties of zero length)
     kErrWait = 128u,  // a bounded device-side wait gave up (back-substitution dependencies)
+    kErrPlan = 256u,  // a replayed build met a finite-tile structure other than the recorded one
 };
 
 // Internal return code of the host helpers when a bounded device-side wait gave up (the
@@ -140,9 +141,11 @@ cudaError_t launch_check_convert(float* a, int64_t count, uint32_t* err, cudaStr
 // ---- fw.cu: blocked Floyd-Warshall (Venkataraman, Sahni & Mukhopadhyaya 2003) ----
 // Many matrices (descs on the device and on the host); each round touches only the
 // matrices that still have tiles left.
+// keep_buf (build plans): if *keep_buf is null, the per-round lists are uploaded into a
+// buffer left in *keep_buf; if not, that buffer is used again (no upload).
 template <typename T>
 cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, int32_t nmat, int32_t max_n,
-                       cudaStream_t st);
+                       cudaStream_t st, int32_t** keep_buf = nullptr);
 // One matrix of size N, optionally skipping tiles whose pivot panel is all infinite.
 // *updates receives the number of min-plus updates issued (host-side count).
 // rowflags == NULL: the full Floyd-Warshall.  rowflags = R x R words (R = ceil(N/128)),
@@ -174,9 +177,46 @@ struct BsInput {
     int64_t N;
     const uint32_t* rowflags;
 };
+// A back-substitution kept for replay (build plans): its bookkeeping, which depends on
+// the matrices' finite-tile structure only, and its device buffers.  bg_backsub_many with
+// keep != NULL records into *keep (if not ready) or replays it (if ready): the same
+// launches with no host step and no allocation, the frontier marks taken afresh and
+// checked against the recorded ones (a row block with more finite columns than recorded
+// is left out and kErrPlan set in err).
+template <typename T>
+struct BsPlan {
+    struct Launch {
+        int32_t mat0, nm, R0, R1;  // matrices [mat0, mat0 + nm), row blocks [R0, R1)
+        int64_t aoff0, nit;        // first A-panel row; work items
+        size_t run0, run1;         // its runs of the work order
+    };
+    bool ready = false;
+    int32_t nmat = 0, nRmax = 0;
+    int64_t P2 = 0, RR = 0;
+    unsigned char* scratch = nullptr;  // the records below, one allocation
+    void *masks = nullptr, *runs = nullptr, *mats = nullptr;
+    int32_t *fblk = nullptr, *fcnt = nullptr, *kcnt = nullptr, *kplan = nullptr;
+    uint32_t* tflags = nullptr;
+    int64_t* koff = nullptr;
+    unsigned long long* counter = nullptr;
+    int32_t* klist = nullptr;
+    T* A = nullptr;
+    std::vector<Launch> launches;
+    double updates = 0.0;
+    void release(cudaStream_t st) {
+        if (klist) cudaFreeAsync(klist, st);
+        if (A) cudaFreeAsync(A, st);
+        if (scratch) cudaFreeAsync(scratch, st);
+        klist = nullptr;
+        A = nullptr;
+        scratch = nullptr;
+        ready = false;
+        launches.clear();
+    }
+};
 template <typename T>
 cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, uint32_t* exact, size_t apanel_budget,
-                            double* updates, FwProfile* prof, cudaStream_t st);
+                            double* updates, FwProfile* prof, cudaStream_t st, BsPlan<T>* keep = nullptr);
 // Marks of every pair of the given tiles (host list).
 cudaError_t launch_mark_pairs(const std::vector<int32_t>& blocks, int64_t N, uint32_t* flags, cudaStream_t st);
 // Infinity (0 on the diagonal) in the marked tiles, their mirrors and the diagonal tiles.
@@ -191,10 +231,11 @@ cudaError_t launch_mark_bg_tiles(int32_t n, const int64_t* rp, const int32_t* co
 // Many matrices (sizes up to max_n) at once, with infinite-panel skipping per matrix;
 // *updates receives the phase-2 and phase-3 min-plus updates issued.  trail: the
 // elimination form's forward pass instead (each round's phases 2 and 3 restricted to the
-// tiles right of / below the pivot block), for bg_backsub_many to complete.
+// tiles right of / below the pivot block), for bg_backsub_many to complete.  stats = false:
+// no host read of the update count (*updates untouched; for stream capture).
 template <typename T>
 cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
-                         double* updates, cudaStream_t st, bool trail = false);
+                         double* updates, cudaStream_t st, bool trail = false, bool stats = true);
 int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n);
 
 // ---- comp_nd.cu: component tables by elimination in a dissection order ----
@@ -229,10 +270,31 @@ cudaError_t comp_nd_scatter(T* P, const MatDesc* d_descs, int32_t n, const int64
                             const void* w, bool f32w, const int32_t* part, const int32_t* local,
                             const int32_t* d_vstart, const int32_t* d_csize, const int32_t* ndpos, int32_t* vpos,
                             cudaStream_t st);
+// keep (build plans): as for bg_backsub_many.  Recording keeps the scratch, the status
+// word and the back-substitution; a replay enqueues the same launches and leaves the
+// status word (kErrWait, kErrPlan) in keep->err for the caller to read.
+template <typename T>
+struct CompElimPlan {
+    bool ready = false;
+    uint32_t* scratch = nullptr;
+    uint32_t* err = nullptr;
+    int32_t max_el = 0;
+    double updates = 0.0;
+    BsPlan<T> bs;
+    void release(cudaStream_t st) {
+        bs.release(st);
+        if (scratch) cudaFreeAsync(scratch, st);
+        if (err) cudaFreeAsync(err, st);
+        scratch = nullptr;
+        err = nullptr;
+        ready = false;
+    }
+};
 template <typename T>
 cudaError_t comp_elim_finish(T* apsp, T* P, const MatDesc* d_descs, const std::vector<MatDesc>& ed,
                              const int32_t* d_sel, const MatDesc* d_ed, const int32_t* d_csize,
-                             const int32_t* d_vstart, const int32_t* ndpos, double* updates, cudaStream_t st);
+                             const int32_t* d_vstart, const int32_t* ndpos, double* updates, cudaStream_t st,
+                             CompElimPlan<T>* keep = nullptr);
 // Whether component c takes the elimination form in comp_tables_elim.
 inline bool comp_takes_elim(int32_t csize, int32_t ld) { return csize <= kNdMax && ld > kTile; }
 

@@ -261,15 +261,32 @@ cudaError_t comp_nd_scatter(T* P, const MatDesc* d_descs, int32_t n, const int64
 template <typename T>
 cudaError_t comp_elim_finish(T* apsp, T* P, const MatDesc* d_descs, const std::vector<MatDesc>& ed,
                              const int32_t* d_sel, const MatDesc* d_ed, const int32_t* d_csize,
-                             const int32_t* d_vstart, const int32_t* ndpos, double* updates, cudaStream_t st) {
+                             const int32_t* d_vstart, const int32_t* ndpos, double* updates, cudaStream_t st,
+                             CompElimPlan<T>* keep) {
     if (updates) *updates = 0.0;
-    if (ed.empty()) return cudaSuccess;
+    if (ed.empty()) {
+        if (keep) keep->ready = true;
+        return cudaSuccess;
+    }
+    const bool replay = keep && keep->ready;
     int32_t max_el = 0;
     for (const MatDesc& d : ed) max_el = std::max(max_el, d.n);
-    uint32_t *scratch = nullptr, *err = nullptr;
-    cudaError_t e = scratch_alloc((void**)&scratch, (size_t)fw_many_scratch_words((int32_t)ed.size(), max_el) * 4, st);
-    if (e == cudaSuccess) e = scratch_alloc((void**)&err, 4, st);
+    uint32_t *scratch = replay ? keep->scratch : nullptr, *err = replay ? keep->err : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!replay) {
+        e = scratch_alloc((void**)&scratch, (size_t)fw_many_scratch_words((int32_t)ed.size(), max_el) * 4, st);
+        if (e == cudaSuccess) e = scratch_alloc((void**)&err, 4, st);
+    }
     auto done = [&](cudaError_t r) {
+        if (keep && !replay && r == cudaSuccess) {
+            keep->scratch = scratch;
+            keep->err = err;
+            keep->max_el = max_el;
+            keep->ready = true;
+            return r;
+        }
+        if (replay) return r;
+        if (keep) keep->bs.release(st);
         if (scratch) cudaFreeAsync(scratch, st);
         if (err) cudaFreeAsync(err, st);
         return r;
@@ -278,21 +295,29 @@ cudaError_t comp_elim_finish(T* apsp, T* P, const MatDesc* d_descs, const std::v
     if ((e = cudaMemsetAsync(err, 0, 4, st)) != cudaSuccess) return done(e);
     // forward rounds of all the tables in shared launches, then one back-substitution
     double fwd = 0.0, bs = 0.0;
-    if ((e = fw_many_skip<T>(P, d_ed, (int32_t)ed.size(), max_el, scratch, &fwd, st, true)) != cudaSuccess)
+    if ((e = fw_many_skip<T>(P, d_ed, (int32_t)ed.size(), max_el, scratch, &fwd, st, true, !replay)) != cudaSuccess)
         return done(e);
     std::vector<BsInput<T>> bin;
     for (const MatDesc& d : ed) bin.push_back(BsInput<T>{P + d.off, (int64_t)d.n, nullptr});
-    if ((e = bg_backsub_many<T>(bin, err, nullptr, (size_t)2 << 30, &bs, nullptr, st)) != cudaSuccess) return done(e);
+    if ((e = bg_backsub_many<T>(bin, err, nullptr, (size_t)2 << 30, &bs, nullptr, st, keep ? &keep->bs : nullptr)) !=
+        cudaSuccess)
+        return done(e);
     // back to the local order
     const dim3 g((unsigned)max_el, (unsigned)std::min<size_t>(ed.size(), 65535));
     k_unpermute<T><<<g, 256, 0, st>>>(apsp, P, d_descs, d_sel, (int32_t)ed.size(), d_csize, d_vstart, ndpos);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
+    if (replay) {
+        // (the caller reads keep->err after the replay)
+        if (updates) *updates = keep->updates;
+        return done(cudaSuccess);
+    }
     uint32_t f = 0;
     if ((e = cudaMemcpyAsync(&f, err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
     if (f & kErrWait) return done(kWaitGaveUp);
     if (updates) *updates = fwd + bs;
+    if (keep) keep->updates = fwd + bs;
     return done(cudaSuccess);
 }
 
@@ -357,7 +382,7 @@ template cudaError_t comp_tables_elim<float>(float*, const MatDesc*, const std::
                                             const int32_t*, int32_t*, cudaStream_t);                                    \
     template cudaError_t comp_elim_finish<T>(T*, T*, const MatDesc*, const std::vector<MatDesc>&, const int32_t*,      \
                                              const MatDesc*, const int32_t*, const int32_t*, const int32_t*, double*,  \
-                                             cudaStream_t);
+                                             cudaStream_t, CompElimPlan<T>*);
 SPQ_COMP_ND_INST(float)
 SPQ_COMP_ND_INST(int32_t)
 

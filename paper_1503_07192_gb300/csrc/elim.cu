@@ -192,7 +192,8 @@ struct BsRun {
 template <typename T>
 __global__ void __launch_bounds__(256) k_colmask(const BsMat<T>* __restrict__ mats, uint4* __restrict__ masks,
                                                  int32_t* __restrict__ fblk, int32_t* __restrict__ fcnt,
-                                                 int32_t* __restrict__ kcnt) {
+                                                 int32_t* __restrict__ kcnt, const int32_t* __restrict__ kplan,
+                                                 uint32_t* __restrict__ err) {
     __shared__ uint32_t colf[2][T_];
     __shared__ uint32_t wm[4];
     const BsMat<T> m = mats[blockIdx.y];
@@ -230,6 +231,13 @@ __global__ void __launch_bounds__(256) k_colmask(const BsMat<T>* __restrict__ ma
         __syncthreads();
     }
     if (tid == 0) {
+        // (a replay: more finite columns than recorded would overrun the recorded lists;
+        //  the row block is left out and the caller told to rebuild)
+        if (kplan && kc > kplan[m.row0 + R]) {
+            cnt = 0;
+            kc = 0;
+            atomicOr(err, kErrPlan);
+        }
         fcnt[m.row0 + R] = cnt;
         kcnt[m.row0 + R] = kc;
     }
@@ -534,69 +542,132 @@ size_t bg_backsub_scratch_bytes(int64_t N) {
     return (size_t)(nR * nR) * 24 + (size_t)nR * 32 + 256;
 }
 
+// The launches of a back-substitution after its bookkeeping (klist, A panels, work
+// order): the k lists, then per launch its A panels and the persistent kernel.
+template <typename T>
+cudaError_t bs_enqueue(const BsPlan<T>& p, uint32_t* err, uint32_t* exact, std::vector<cudaEvent_t>* ev,
+                       cudaStream_t st) {
+    const bool conv = std::is_same<T, float>::value && exact != nullptr;
+    auto kern = conv ? k_backsub<T, std::is_same<T, float>::value> : k_backsub<T, false>;
+    const BsMat<T>* mats = static_cast<const BsMat<T>*>(p.mats);
+    const uint4* masks = static_cast<const uint4*>(p.masks);
+    const BsRun* runs = static_cast<const BsRun*>(p.runs);
+    k_klist<T><<<dim3(p.nRmax, p.nmat), T_, 0, st>>>(mats, masks, p.fblk, p.fcnt, p.kcnt, p.koff, p.klist);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    const size_t psm = sizeof(PanelSmem<T>);
+    const int grid = sms_e() * SPQ_FW_MIN_CTAS;
+    for (size_t l = 0; l < p.launches.size() && e == cudaSuccess; ++l) {
+        const typename BsPlan<T>::Launch& L = p.launches[l];
+        const dim3 gg((unsigned)(std::min(L.R1, p.nRmax) - L.R0), (unsigned)L.nm);
+        // A panels of the launch's rows: read before the launch overwrites those rows
+        if (conv)
+            k_gather_a<T, std::is_same<T, float>::value><<<gg, 256, 0, st>>>(mats, L.mat0, L.R0, L.R1, p.koff, p.kcnt,
+                                                                              p.klist, L.aoff0, p.A);
+        else
+            k_gather_a<T, false><<<gg, 256, 0, st>>>(mats, L.mat0, L.R0, L.R1, p.koff, p.kcnt, p.klist, L.aoff0, p.A);
+        cudaMemsetAsync(p.counter, 0, 8, st);
+        if (ev) cudaEventRecord((*ev)[2 * l], st);
+        kern<<<grid, NTH, psm, st>>>(mats, runs + L.run0, (int32_t)(L.run1 - L.run0), L.nit, p.koff, p.kcnt, p.klist,
+                                     p.A, L.aoff0, p.fblk, p.fcnt, p.tflags, p.counter, err, exact, g_wait_ns.load(),
+                                     g_withhold.load());
+        if (ev) cudaEventRecord((*ev)[2 * l + 1], st);
+        count_launches(2);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// A recorded back-substitution again (the matrices' contents may differ, their structure
+// not): frontier marks afresh, checked against the recorded |K(R)|, then the same
+// launches; no host step, no allocation.
+template <typename T>
+cudaError_t bs_replay(const BsPlan<T>& p, uint32_t* err, uint32_t* exact, cudaStream_t st) {
+    if (p.nmat == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p.tflags, 0, (size_t)p.P2 * 4, st);
+    if (e != cudaSuccess) return e;
+    k_colmask<T><<<dim3(p.nRmax, p.nmat), 256, 0, st>>>(static_cast<const BsMat<T>*>(p.mats),
+                                                        static_cast<uint4*>(p.masks), p.fblk, p.fcnt, p.kcnt, p.kplan,
+                                                        err);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return bs_enqueue<T>(p, err, exact, nullptr, st);
+}
+
 template <typename T>
 cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, uint32_t* exact, size_t apanel_budget,
-                            double* updates, FwProfile* prof, cudaStream_t st) {
+                            double* updates, FwProfile* prof, cudaStream_t st, BsPlan<T>* keep) {
+    if (keep && keep->ready) {
+        if (updates) *updates = keep->updates;
+        return bs_replay<T>(*keep, err, exact, st);
+    }
     if (updates) *updates = 0.0;
+    BsPlan<T> p;
     std::vector<BsMat<T>> hm;
-    int64_t P2 = 0, RR = 0;
-    int32_t nRmax = 0;
     for (const BsInput<T>& x : in) {
         if (x.N <= 0) continue;
         const int32_t nR = (int32_t)((x.N + T_ - 1) / T_);
-        hm.push_back(BsMat<T>{x.M, x.N, nR, x.rowflags, P2, RR});
-        P2 += (int64_t)nR * nR;
-        RR += nR;
-        nRmax = std::max(nRmax, nR);
+        hm.push_back(BsMat<T>{x.M, x.N, nR, x.rowflags, p.P2, p.RR});
+        p.P2 += (int64_t)nR * nR;
+        p.RR += nR;
+        p.nRmax = std::max(p.nRmax, nR);
     }
-    const int32_t nmat = (int32_t)hm.size();
-    if (nmat == 0) return cudaSuccess;
-    if (nmat > 65535) return cudaErrorInvalidValue;
+    p.nmat = (int32_t)hm.size();
+    if (p.nmat == 0) {
+        if (keep) keep->ready = true;  // nothing to replay
+        return cudaSuccess;
+    }
+    if (p.nmat > 65535) return cudaErrorInvalidValue;
+    const int64_t P2 = p.P2, RR = p.RR;
+    const int32_t nmat = p.nmat, nRmax = p.nRmax;
     // exact != NULL (float tables only): store int32 tables, checking exactness
     const bool conv = std::is_same<T, float>::value && exact != nullptr;
     auto kern = conv ? k_backsub<T, std::is_same<T, float>::value> : k_backsub<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
-    // one scratch block: masks | fblk | tflags | koff | fcnt | kcnt | runs | counter | mats
+    // one scratch block: masks | fblk | tflags | koff | fcnt | kcnt | kplan | runs | counter | mats
     const size_t o_fblk = (size_t)P2 * 16, o_tfl = o_fblk + (size_t)P2 * 4, o_koff = o_tfl + (size_t)P2 * 4;
-    const size_t o_fcnt = o_koff + (size_t)RR * 8, o_kcnt = o_fcnt + (size_t)RR * 4;
-    const size_t o_runs = (o_kcnt + (size_t)RR * 4 + 15) & ~(size_t)15;
+    const size_t o_fcnt = o_koff + (size_t)RR * 8, o_kcnt = o_fcnt + (size_t)RR * 4, o_kpl = o_kcnt + (size_t)RR * 4;
+    const size_t o_runs = (o_kpl + (size_t)RR * 4 + 15) & ~(size_t)15;
     const size_t o_ctr = o_runs + (size_t)RR * sizeof(BsRun);
     const size_t o_mats = (o_ctr + 8 + 15) & ~(size_t)15;
     const size_t bytes = o_mats + (size_t)nmat * sizeof(BsMat<T>);
-    unsigned char* scratch = nullptr;
-    if ((e = scratch_alloc((void**)&scratch, bytes, st)) != cudaSuccess) return e;
-    uint4* masks = reinterpret_cast<uint4*>(scratch);
-    int32_t* fblk = reinterpret_cast<int32_t*>(scratch + o_fblk);
-    uint32_t* tflags = reinterpret_cast<uint32_t*>(scratch + o_tfl);
-    int64_t* koff = reinterpret_cast<int64_t*>(scratch + o_koff);
-    int32_t* fcnt = reinterpret_cast<int32_t*>(scratch + o_fcnt);
-    int32_t* kcnt = reinterpret_cast<int32_t*>(scratch + o_kcnt);
-    BsRun* runs = reinterpret_cast<BsRun*>(scratch + o_runs);
-    unsigned long long* counter = reinterpret_cast<unsigned long long*>(scratch + o_ctr);
-    BsMat<T>* mats = reinterpret_cast<BsMat<T>*>(scratch + o_mats);
-    int32_t* klist = nullptr;
-    T* A = nullptr;
+    if ((e = scratch_alloc((void**)&p.scratch, bytes, st)) != cudaSuccess) return e;
+    unsigned char* scratch = p.scratch;
+    p.masks = scratch;
+    p.fblk = reinterpret_cast<int32_t*>(scratch + o_fblk);
+    p.tflags = reinterpret_cast<uint32_t*>(scratch + o_tfl);
+    p.koff = reinterpret_cast<int64_t*>(scratch + o_koff);
+    p.fcnt = reinterpret_cast<int32_t*>(scratch + o_fcnt);
+    p.kcnt = reinterpret_cast<int32_t*>(scratch + o_kcnt);
+    p.kplan = reinterpret_cast<int32_t*>(scratch + o_kpl);
+    p.runs = scratch + o_runs;
+    p.counter = reinterpret_cast<unsigned long long*>(scratch + o_ctr);
+    p.mats = scratch + o_mats;
     std::vector<cudaEvent_t> ev;  // per launch of k_backsub: start, end (profiling only)
     std::vector<int32_t> hk(RR);
     std::vector<int64_t> hoff(RR + 1, 0);
     std::vector<BsRun> hruns;
     auto done = [&](cudaError_t r) {
-        if (klist) cudaFreeAsync(klist, st);
-        if (A) cudaFreeAsync(A, st);
-        cudaFreeAsync(scratch, st);
         for (auto& x : ev)
             if (x) cudaEventDestroy(x);
+        if (keep && r == cudaSuccess) {
+            p.ready = true;
+            *keep = std::move(p);
+        } else {
+            p.release(st);
+        }
         return r;
     };
-    if ((e = cudaMemcpyAsync(mats, hm.data(), hm.size() * sizeof(BsMat<T>), cudaMemcpyHostToDevice, st)) !=
+    if ((e = cudaMemcpyAsync(p.mats, hm.data(), hm.size() * sizeof(BsMat<T>), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return done(e);
-    if ((e = cudaMemsetAsync(tflags, 0, (size_t)P2 * 4, st)) != cudaSuccess) return done(e);
-    k_colmask<T><<<dim3(nRmax, nmat), 256, 0, st>>>(mats, masks, fblk, fcnt, kcnt);
+    if ((e = cudaMemsetAsync(p.tflags, 0, (size_t)P2 * 4, st)) != cudaSuccess) return done(e);
+    k_colmask<T><<<dim3(nRmax, nmat), 256, 0, st>>>(static_cast<const BsMat<T>*>(p.mats), static_cast<uint4*>(p.masks),
+                                                    p.fblk, p.fcnt, p.kcnt, nullptr, nullptr);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return done(e);
-    if ((e = cudaMemcpyAsync(hk.data(), kcnt, (size_t)RR * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(hk.data(), p.kcnt, (size_t)RR * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return done(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(e);
     double upd = 0.0, items = 0.0;
@@ -607,25 +678,25 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
             upd += (double)hk[i] * T_ * T_ * (double)(m.nR - R);
             items += (double)(m.nR - R);
         }
+    p.updates = upd;
     if (updates) *updates = upd;
     if (prof) {
         prof->bs_updates = upd;
         prof->bs_items = items;
     }
     const int64_t ktot = hoff[RR];
-    if ((e = cudaMemcpyAsync(koff, hoff.data(), (size_t)RR * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(p.koff, hoff.data(), (size_t)RR * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return done(e);
-    if ((e = scratch_alloc((void**)&klist, (size_t)(ktot > 0 ? ktot : 1) * 4, st)) != cudaSuccess) return done(e);
-    k_klist<T><<<dim3(nRmax, nmat), T_, 0, st>>>(mats, masks, fblk, fcnt, kcnt, koff, klist);
-    count_launches(1);
+    if ((e = cudaMemcpyAsync(p.kplan, hk.data(), (size_t)RR * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return done(e);
+    if ((e = scratch_alloc((void**)&p.klist, (size_t)(ktot > 0 ? ktot : 1) * 4, st)) != cudaSuccess) return done(e);
     // Launches whose A panels fit the budget: whole matrices side by side, or (a matrix
     // whose panels alone exceed it) ranges of its row blocks from the last rows down.
     // Each launch's panels are contiguous in the koff order.
-    struct Launch {
-        int32_t mat0, nm, R0, R1;  // matrices [mat0, mat0 + nm), row blocks [R0, R1)
-    };
-    std::vector<Launch> launches;
+    using Launch = typename BsPlan<T>::Launch;
+    std::vector<Launch>& launches = p.launches;
     const int64_t row_bytes = (int64_t)T_ * sizeof(T);
+    auto whole = [&](int32_t g0, int32_t g1) { launches.push_back(Launch{g0, g1 - g0, 0, nRmax, 0, 0, 0, 0}); };
     {
         int32_t g0 = 0;
         int64_t gk = 0;
@@ -634,33 +705,32 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
             const int64_t mk = hoff[m.row0 + m.nR] - hoff[m.row0];
             if (mk * row_bytes <= (int64_t)apanel_budget) {
                 if (i > g0 && (gk + mk) * row_bytes > (int64_t)apanel_budget) {
-                    launches.push_back(Launch{g0, i - g0, 0, nRmax});
+                    whole(g0, i);
                     g0 = i;
                     gk = 0;
                 }
                 gk += mk;
                 continue;
             }
-            if (i > g0) launches.push_back(Launch{g0, i - g0, 0, nRmax});
+            if (i > g0) whole(g0, i);
             std::vector<int32_t> cuts{m.nR};
             for (int32_t R = m.nR - 1; R >= 0; --R) {
                 const int64_t lo_k = hoff[m.row0 + R], hi_k = hoff[m.row0 + cuts.back()];
                 if (R < cuts.back() - 1 && (hi_k - lo_k) * row_bytes > (int64_t)apanel_budget) cuts.push_back(R + 1);
             }
             cuts.push_back(0);
-            for (size_t c = 0; c + 1 < cuts.size(); ++c) launches.push_back(Launch{i, 1, cuts[c + 1], cuts[c]});
+            for (size_t c = 0; c + 1 < cuts.size(); ++c)
+                launches.push_back(Launch{i, 1, cuts[c + 1], cuts[c], 0, 0, 0, 0});
             g0 = i + 1;
             gk = 0;
         }
-        if (g0 < nmat) launches.push_back(Launch{g0, nmat - g0, 0, nRmax});
+        if (g0 < nmat) whole(g0, nmat);
     }
     // the runs of every launch: row blocks from the last down, the matrices of a launch
     // interleaved (their q-th rows from the end side by side)
-    std::vector<size_t> run0(launches.size() + 1, 0);
-    std::vector<int64_t> nit(launches.size(), 0);
     int64_t maxk = 0;
-    for (size_t l = 0; l < launches.size(); ++l) {
-        const Launch& L = launches[l];
+    for (Launch& L : launches) {
+        L.run0 = hruns.size();
         int64_t start = 0;
         int32_t depth = 0;
         for (int32_t i = L.mat0; i < L.mat0 + L.nm; ++i) depth = std::max(depth, std::min(hm[i].nR, L.R1) - L.R0);
@@ -671,43 +741,23 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
                 hruns.push_back(BsRun{start, i, R});
                 start += hm[i].nR - R;
             }
-        run0[l + 1] = hruns.size();
-        nit[l] = start;
-        const BsMat<T>& a = hm[L.mat0];
+        L.run1 = hruns.size();
+        L.nit = start;
+        L.aoff0 = hoff[hm[L.mat0].row0 + L.R0];
         const BsMat<T>& z = hm[L.mat0 + L.nm - 1];
-        maxk = std::max(maxk, hoff[z.row0 + std::min(z.nR, L.R1)] - hoff[a.row0 + L.R0]);
+        maxk = std::max(maxk, hoff[z.row0 + std::min(z.nR, L.R1)] - L.aoff0);
     }
-    if ((e = cudaMemcpyAsync(runs, hruns.data(), hruns.size() * sizeof(BsRun), cudaMemcpyHostToDevice, st)) !=
+    if ((e = cudaMemcpyAsync(p.runs, hruns.data(), hruns.size() * sizeof(BsRun), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return done(e);
-    if ((e = scratch_alloc((void**)&A, (size_t)(maxk > 0 ? maxk : 1) * row_bytes, st)) != cudaSuccess)
+    if ((e = scratch_alloc((void**)&p.A, (size_t)(maxk > 0 ? maxk : 1) * row_bytes, st)) != cudaSuccess)
         return done(e);
     if (prof) {
         ev.assign(2 * launches.size(), nullptr);
         for (auto& x : ev)
             if ((e = cudaEventCreate(&x)) != cudaSuccess) return done(e);
     }
-    const size_t psm = sizeof(PanelSmem<T>);
-    const int grid = sms_e() * SPQ_FW_MIN_CTAS;
-    for (size_t l = 0; l < launches.size() && e == cudaSuccess; ++l) {
-        const Launch& L = launches[l];
-        const int64_t aoff0 = hoff[hm[L.mat0].row0 + L.R0];
-        const dim3 gg((unsigned)(std::min(L.R1, nRmax) - L.R0), (unsigned)L.nm);
-        // A panels of the launch's rows: read before the launch overwrites those rows
-        if (conv)
-            k_gather_a<T, std::is_same<T, float>::value><<<gg, 256, 0, st>>>(mats, L.mat0, L.R0, L.R1, koff, kcnt,
-                                                                              klist, aoff0, A);
-        else
-            k_gather_a<T, false><<<gg, 256, 0, st>>>(mats, L.mat0, L.R0, L.R1, koff, kcnt, klist, aoff0, A);
-        cudaMemsetAsync(counter, 0, 8, st);
-        if (prof) cudaEventRecord(ev[2 * l], st);
-        kern<<<grid, NTH, psm, st>>>(mats, runs + run0[l], (int32_t)(run0[l + 1] - run0[l]), nit[l], koff, kcnt, klist,
-                                     A, aoff0, fblk, fcnt, tflags, counter, err, exact, g_wait_ns.load(),
-                                     g_withhold.load());
-        if (prof) cudaEventRecord(ev[2 * l + 1], st);
-        count_launches(2);
-        e = cudaGetLastError();
-    }
+    e = bs_enqueue<T>(p, err, exact, prof ? &ev : nullptr, st);
     if (prof && e == cudaSuccess && !ev.empty() && (e = cudaEventSynchronize(ev.back())) == cudaSuccess) {
         prof->bs_ms = 0.0;
         prof->bs_launches = 0;
@@ -719,6 +769,7 @@ cudaError_t bg_backsub_many(const std::vector<BsInput<T>>& in, uint32_t* err, ui
             }
         }
     }
+    // (the host lists above are uploaded from pageable memory: staged before return)
     return done(e);
 }
 
@@ -726,7 +777,7 @@ template <typename T>
 cudaError_t bg_backsub(T* M, int64_t N, const uint32_t* rowflags, uint32_t* err, uint32_t* exact, size_t apanel_budget,
                        double* updates, FwProfile* prof, cudaStream_t st) {
     return bg_backsub_many<T>(std::vector<BsInput<T>>{BsInput<T>{M, N, rowflags}}, err, exact, apanel_budget, updates,
-                              prof, st);
+                              prof, st, nullptr);
 }
 
 template cudaError_t bg_backsub<float>(float*, int64_t, const uint32_t*, uint32_t*, uint32_t*, size_t, double*,
@@ -734,9 +785,9 @@ template cudaError_t bg_backsub<float>(float*, int64_t, const uint32_t*, uint32_
 template cudaError_t bg_backsub<int32_t>(int32_t*, int64_t, const uint32_t*, uint32_t*, uint32_t*, size_t, double*,
                                          FwProfile*, cudaStream_t);
 template cudaError_t bg_backsub_many<float>(const std::vector<BsInput<float>>&, uint32_t*, uint32_t*, size_t, double*,
-                                            FwProfile*, cudaStream_t);
+                                            FwProfile*, cudaStream_t, BsPlan<float>*);
 template cudaError_t bg_backsub_many<int32_t>(const std::vector<BsInput<int32_t>>&, uint32_t*, uint32_t*, size_t,
-                                              double*, FwProfile*, cudaStream_t);
+                                              double*, FwProfile*, cudaStream_t, BsPlan<int32_t>*);
 
 template cudaError_t launch_fill_marked<float>(float*, int64_t, const uint32_t*, cudaStream_t);
 template cudaError_t launch_fill_marked<int32_t>(int32_t*, int64_t, const uint32_t*, cudaStream_t);

@@ -553,7 +553,7 @@ cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R,
 
 template <typename T>
 cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, int32_t nmat, int32_t max_n,
-                       cudaStream_t st) {
+                       cudaStream_t st, int32_t** keep_buf) {
     if (nmat <= 0 || max_n <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
     if (e != cudaSuccess) return e;
@@ -583,10 +583,13 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
             }
         }
     }
-    int32_t* d_buf = nullptr;
-    e = scratch_alloc((void**)&d_buf, buf.size() * sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(d_buf, buf.data(), buf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    int32_t* d_buf = keep_buf ? *keep_buf : nullptr;
+    if (!d_buf) {
+        e = scratch_alloc((void**)&d_buf, buf.size() * sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(d_buf, buf.data(), buf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (keep_buf) *keep_buf = d_buf;
+    }
     const size_t psm = sizeof(PanelSmem<T>);
     const int p3_grid = sms() * 2;
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
@@ -604,7 +607,7 @@ cudaError_t fw_batched(T* base, const MatDesc* d_descs, const MatDesc* h_descs, 
         }
         e = cudaGetLastError();
     }
-    cudaFreeAsync(d_buf, st);  // (the pageable upload above completed before it returned)
+    if (!keep_buf) cudaFreeAsync(d_buf, st);  // (the pageable upload above completed before it returned)
     return e;
 }
 
@@ -762,8 +765,8 @@ int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n) {
 
 template <typename T>
 cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t max_n, uint32_t* scratch,
-                         double* updates, cudaStream_t st, bool trail) {
-    if (updates) *updates = 0.0;
+                         double* updates, cudaStream_t st, bool trail, bool stats) {
+    if (updates && stats) *updates = 0.0;
     if (nmat <= 0 || max_n <= 0) return cudaSuccess;
     cudaError_t e = set_smem_attrs<T>();
     if (e != cudaSuccess) return e;
@@ -796,6 +799,7 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
         }
         e = cudaGetLastError();
     }
+    if (!stats) return e;
     unsigned long long htv[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(htv, tiles, sizeof(htv), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -805,12 +809,14 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
 }
 
 template cudaError_t fw_many_skip<int32_t>(int32_t*, const MatDesc*, int32_t, int32_t, uint32_t*, double*,
-                                           cudaStream_t, bool);
+                                           cudaStream_t, bool, bool);
 template cudaError_t fw_many_skip<float>(float*, const MatDesc*, int32_t, int32_t, uint32_t*, double*, cudaStream_t,
-                                         bool);
+                                         bool, bool);
 
-template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
-template cudaError_t fw_batched<float>(float*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t);
+template cudaError_t fw_batched<int32_t>(int32_t*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t,
+                                         int32_t**);
+template cudaError_t fw_batched<float>(float*, const MatDesc*, const MatDesc*, int32_t, int32_t, cudaStream_t,
+                                       int32_t**);
 template cudaError_t fw_single<int32_t>(int32_t*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*,
                                         cudaStream_t, const std::vector<ElimTask>*);
 template cudaError_t fw_single<float>(float*, int64_t, bool, uint32_t*, uint32_t*, double*, FwProfile*, cudaStream_t,

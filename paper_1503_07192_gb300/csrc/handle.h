@@ -54,6 +54,7 @@ struct spq_handle {
     std::vector<int32_t> h_csize, h_nb, h_bgoff;
     std::vector<spq::MatDesc> h_descs;
     spq::Arena* arena = nullptr;  // set: every device pointer above lies in the arena
+    bool plan_owned = false;      // belongs to a build plan (spq_free leaves it alone)
     // kept for path walks (gradients): the graph's CSR and, per component, the vertices
     // in local order (vorder[vstart[c] + i] = vertex with local index i in component c)
     int64_t m = 0;
