@@ -177,6 +177,44 @@ __global__ void __launch_bounds__(1024) k_scan_excl(uint32_t* __restrict__ a, in
     }
 }
 
+// The radix sort's histogram: block d turns the counts of digit d over the tiles,
+// hist[d * ntiles ..), into their exclusive prefix sums in place (1,024 coalesced counts at
+// a time, the carry kept in a register) and writes the digit's total to tot[d].
+__global__ void __launch_bounds__(1024) k_scan_digits(uint32_t* __restrict__ hist, int64_t ntiles,
+                                                      uint32_t* __restrict__ tot) {
+    __shared__ uint32_t ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* h = hist + (int64_t)blockIdx.x * ntiles;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < ntiles; base += 1024) {
+        const int64_t i = base + tid;
+        const uint32_t x = i < ntiles ? h[i] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) ws[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            ws[lane] = w;  // inclusive over the warps
+        }
+        __syncthreads();
+        const uint32_t before = (warp > 0 ? ws[warp - 1] : 0u) + incl - x;
+        if (i < ntiles) h[i] = carry + before;
+        carry += ws[31];
+        __syncthreads();
+    }
+    if (tid == 0) tot[blockIdx.x] = carry;
+}
+
 // Stable scatter of one tile: element it*256 + tid of the tile goes after every earlier
 // element of the tile with the same digit (earlier rounds, then lower warps, then lower
 // lanes of the same warp).
@@ -189,7 +227,23 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint32_t* __res
     __shared__ uint32_t run[256];
     __shared__ uint32_t wcnt[kRsWarps][256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    gofs[tid] = hist[(int64_t)tid * ntiles + blockIdx.x];
+    // the digit's start: the totals of the smaller digits (hist + 256 * ntiles, exclusive
+    // scan over the 256 digits here), plus the earlier tiles' counts of the digit
+    {
+        const uint32_t t = hist[256 * ntiles + tid];
+        uint32_t incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) run[warp] = incl;
+        __syncthreads();
+        uint32_t before = incl - t;
+        for (int w = 0; w < warp; ++w) before += run[w];
+        gofs[tid] = before + hist[(int64_t)tid * ntiles + blockIdx.x];
+        __syncthreads();
+    }
     run[tid] = 0;
     for (int w = 0; w < kRsWarps; ++w) wcnt[w][tid] = 0;
     __syncthreads();
@@ -272,7 +326,7 @@ cudaError_t launch_scan_excl(uint32_t* a, int64_t len, cudaStream_t st) {
 
 int64_t radix_hist_words(int64_t n) {
     int64_t ntiles = (n + kRsTile - 1) / kRsTile;
-    return 256 * (ntiles > 0 ? ntiles : 1);
+    return 256 * (ntiles > 0 ? ntiles : 1) + 256;  // per digit and tile, then per digit
 }
 
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist, int64_t n,
@@ -287,7 +341,7 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
         uint32_t* ko = flip ? k0 : k1;
         uint32_t* vo = flip ? v0 : v1;
         k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, st>>>(ki, n, shift, hist, ntiles);
-        k_scan_excl<<<1, 1024, 0, st>>>(hist, 256 * ntiles);
+        k_scan_digits<<<256, 1024, 0, st>>>(hist, ntiles, hist + 256 * ntiles);
         k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, st>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
         count_launches(3);
         flip = !flip;

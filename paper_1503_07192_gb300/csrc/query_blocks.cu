@@ -566,38 +566,78 @@ __global__ void k_qb_prep(const QueryCtx<T> ctx, const int2* __restrict__ pairs,
 
 // Items: every run of one component pair (a nonempty block with at most QB_PMAX rows and
 // columns) cut into nearly equal pieces of at most qb_pair_cap(ld) pairs; the order of the
-// item list is arbitrary.
+// item list is arbitrary.  A run's first position finds the run's end by a galloping
+// search (runs are short), and a warp takes the slots of all its runs' items with one
+// atomic (as it adds its runs' profiling counts).
 __global__ void k_qb_items(const uint32_t* __restrict__ keys, int64_t q, uint32_t k, const int32_t* __restrict__ nb,
                            QItem* __restrict__ items, uint32_t* __restrict__ nitems,
                            unsigned long long* __restrict__ stats) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= q) return;
-    const uint32_t key = keys[p];
-    if (key >= k * k || (p > 0 && keys[p - 1] == key)) return;
-    const int32_t c1 = (int32_t)(key / k), c2 = (int32_t)(key % k);
-    const int32_t nb1 = nb[c1], nb2 = nb[c2];
-    if (nb1 == 0 || nb2 == 0 || nb1 > QB_PMAX || nb2 > QB_PMAX) return;
-    int64_t lo = p + 1, hi = q;  // the run's end: first position with a larger key
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (keys[mid] == key)
-            lo = mid + 1;
-        else
-            hi = mid;
+    const int lane = threadIdx.x & 31;
+    uint32_t key = 0, pieces = 0;
+    int32_t c1 = 0, c2 = 0, nb1 = 0, nb2 = 0;
+    int64_t n = 0;
+    if (p < q) {
+        key = keys[p];
+        if (key < k * k && (p == 0 || keys[p - 1] != key)) {
+            c1 = (int32_t)(key / k);
+            c2 = (int32_t)(key % k);
+            nb1 = nb[c1];
+            nb2 = nb[c2];
+            if (nb1 > 0 && nb2 > 0 && nb1 <= QB_PMAX && nb2 <= QB_PMAX) {
+                // keys[lo] == key; hi = q or keys[hi] != key (a larger key)
+                int64_t lo = p, hi = q, step = 1;
+                for (;;) {
+                    const int64_t nx = lo + step;
+                    if (nx >= q || keys[nx] != key) {
+                        hi = nx < q ? nx : q;
+                        break;
+                    }
+                    lo = nx;
+                    step <<= 1;
+                }
+                while (hi - lo > 1) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (keys[mid] == key)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                n = hi - p;
+                const int64_t cap = qb_pair_cap((nb2 + 3) & ~3);
+                pieces = (uint32_t)((n + cap - 1) / cap);
+            }
+        }
     }
-    const int64_t n = lo - p;
-    const int32_t ld2 = (nb2 + 3) & ~3;
-    const int64_t cap = qb_pair_cap(ld2);
-    const int64_t pieces = (n + cap - 1) / cap;
-    const uint32_t base = atomicAdd(nitems, (uint32_t)pieces);
+    // the warp's item slots: an inclusive scan of the piece counts, one atomic
+    uint32_t incl = pieces;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t wbase = 0;
+    if (lane == 31 && incl > 0) wbase = atomicAdd(nitems, incl);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
     if (stats) {
         // algorithmic work of the run: |B1| x |B2| updates per pair; bytes: each item's
         // block once, per pair its two table rows, the pair, its position and its answer
-        atomicAdd(&stats[0], (unsigned long long)(n * nb1 * nb2));
-        atomicAdd(&stats[1], (unsigned long long)(4 * pieces * (int64_t)nb1 * nb2 +
-                                                  n * (4 * (((nb1 + 3) & ~3) + ld2) + 16)));
+        unsigned long long w = pieces ? (unsigned long long)(n * nb1 * nb2) : 0ull;
+        unsigned long long by = pieces ? (unsigned long long)(4 * (int64_t)pieces * nb1 * nb2 +
+                                                              n * (4 * (((nb1 + 3) & ~3) + ((nb2 + 3) & ~3)) + 16))
+                                       : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w += __shfl_down_sync(0xffffffffu, w, o);
+            by += __shfl_down_sync(0xffffffffu, by, o);
+        }
+        if (lane == 0 && w > 0) {
+            atomicAdd(&stats[0], w);
+            atomicAdd(&stats[1], by);
+        }
     }
-    for (int64_t i = 0; i < pieces; ++i) {
+    const uint32_t base = wbase + incl - pieces;
+    for (int64_t i = 0; i < (int64_t)pieces; ++i) {
         const int64_t s0 = p + i * n / pieces, s1 = p + (i + 1) * n / pieces;
         items[base + i] = qb_make_item((uint32_t)s0, (int32_t)(s1 - s0), c1, c2, nb);
     }

@@ -33,7 +33,7 @@ constexpr int64_t kMaxPairs = SPQ_NOALLOC_MAX_PAIRS;
 // words per 4,096-pair tile + 4 spare words, then the grouped kernel's records (18 words
 // per pair: table rows, starting values, item records, fallback list; + 8):
 // query_scratch_words(kMaxPairs), about 23.1 MB.
-constexpr int64_t kWords = 4 * kMaxPairs + 256 * ((kMaxPairs + 4095) / 4096) + 4 + 18 * kMaxPairs + 8;
+constexpr int64_t kWords = 4 * kMaxPairs + (256 * ((kMaxPairs + 4095) / 4096) + 256) + 4 + 18 * kMaxPairs + 8;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kWords];
 
