@@ -32,6 +32,10 @@ import sys
 import threading
 import time
 
+# up to 32 chains of elimination rounds run on their own streams: give the CUDA context
+# as many hardware work queues (before anything creates it)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

@@ -9,11 +9,19 @@ Python or CPU fallback, and a missing library raises.
     h = spq_build(n, row_ptr, col, w, part, k)     # -> SpqHandle
     d = spq_query(h, pairs)                        # int32[q] (or float32[q])
     spq_free(h)
+
+Importing the binding sets CUDA_DEVICE_MAX_CONNECTIONS to 32 unless the environment
+already sets it: the build runs up to 32 independent chains of elimination rounds on
+their own streams, and a CUDA context created with the default 8 hardware work queues
+serialises them.  It only takes effect if no CUDA context exists yet in the process.
 """
 
 from __future__ import annotations
 
 import ctypes
+import os
+
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np
 
