@@ -130,6 +130,90 @@ __global__ void __launch_bounds__(NTH) k_phase1(T* __restrict__ base, const MatD
     }
 }
 
+// Phase 1 of round r of one matrix with 1,024 threads, each owning a 4 x 4 block (rows
+// 4ty.., columns 4tx..): the same two pivot steps per barrier as k_phase1, with four
+// times the warps to hide each step's latency, and the sums formed two at a time by
+// packed f32x2 adds.  For the elimination rounds of one boundary graph, where the closure
+// of the diagonal tile lies on the critical path of every round.  Every step is the
+// same rounded float operation as in k_phase1, so the results are identical.
+__global__ void __launch_bounds__(1024, 1) k_phase1_wide(float* __restrict__ M, int64_t n, int32_t r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float(*S)[T_] = reinterpret_cast<float(*)[T_]>(smem_raw);
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int64_t o = (int64_t)r * T_;
+    for (int idx = tid; idx < T_ * T_ / 4; idx += 1024) {
+        const int i = idx >> 5, c4 = idx & 31;
+        const int64_t gr = o + i, gc = o + c4 * 4;
+        int4 v = (gr < n && gc < n) ? *reinterpret_cast<const int4*>(M + gr * n + gc) : inf4<float>();
+        *reinterpret_cast<int4*>(&S[i][c4 * 4]) = v;
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = *reinterpret_cast<const float4*>(&S[4 * ty + i][4 * tx]);
+        acc[i][0] = v.x;
+        acc[i][1] = v.y;
+        acc[i][2] = v.z;
+        acc[i][3] = v.w;
+    }
+    const int K = (int)((n - o) < T_ ? (n - o) : T_);
+    int k = 0;
+    // rows k and k + 1 are current (by symmetry also columns k and k + 1); row k + 1
+    // after step k is min(D(k+1, x), D(k+1, k) + D(k, x)), formed on the fly
+    for (; k + 1 < K; k += 2) {
+        const float4 p = *reinterpret_cast<const float4*>(&S[k][4 * ty]);
+        const float4 q = *reinterpret_cast<const float4*>(&S[k][4 * tx]);
+        const float4 u = *reinterpret_cast<const float4*>(&S[k + 1][4 * ty]);
+        const float4 v = *reinterpret_cast<const float4*>(&S[k + 1][4 * tx]);
+        const float skk = S[k][k + 1];
+        const float a0[4] = {p.x, p.y, p.z, p.w};
+        const float a1[4] = {fminf(u.x, skk + p.x), fminf(u.y, skk + p.y), fminf(u.z, skk + p.z),
+                             fminf(u.w, skk + p.w)};
+        const float2 b0l = make_float2(q.x, q.y), b0h = make_float2(q.z, q.w);
+        const float2 b1l = make_float2(fminf(v.x, skk + q.x), fminf(v.y, skk + q.y));
+        const float2 b1h = make_float2(fminf(v.z, skk + q.z), fminf(v.w, skk + q.w));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 x0 = make_float2(a0[i], a0[i]), x1 = make_float2(a1[i], a1[i]);
+            const float2 s0l = __fadd2_rn(x0, b0l), s0h = __fadd2_rn(x0, b0h);
+            const float2 s1l = __fadd2_rn(x1, b1l), s1h = __fadd2_rn(x1, b1h);
+            acc[i][0] = fmin3(acc[i][0], s0l.x, s1l.x);
+            acc[i][1] = fmin3(acc[i][1], s0l.y, s1l.y);
+            acc[i][2] = fmin3(acc[i][2], s0h.x, s1h.x);
+            acc[i][3] = fmin3(acc[i][3], s0h.y, s1h.y);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = 4 * ty + i;
+            if (row == k + 2 || row == k + 3)
+                *reinterpret_cast<float4*>(&S[row][4 * tx]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+        __syncthreads();
+    }
+    for (; k < K; ++k) {
+        const float4 p = *reinterpret_cast<const float4*>(&S[k][4 * ty]);
+        const float4 q = *reinterpret_cast<const float4*>(&S[k][4 * tx]);
+        const float a[4] = {p.x, p.y, p.z, p.w}, b[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fminf(acc[i][j], a[i] + b[j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * ty + i == k + 1)
+                *reinterpret_cast<float4*>(&S[k + 1][4 * tx]) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gr = o + 4 * ty + i, gc = o + 4 * tx;
+        if (gr < n && gc < n)
+            *reinterpret_cast<float4*>(M + gr * n + gc) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    }
+}
+
 // ---------------- phase 2: pivot row tiles (and their transposes) ----------------
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
@@ -166,14 +250,83 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
     }
 }
 
+// Ordered list of the marked tiles J in [lo, hi) of one flag row: out[0] = count,
+// out[1..] = J ascending.  Whole block; ends with a barrier.
+__device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t hi, uint32_t* __restrict__ out) {
+    __shared__ uint32_t cnt;
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int32_t base = lo; base < hi; base += blockDim.x) {
+        const int32_t J = base + threadIdx.x;
+        const bool take = J < hi && __ldcg(f + J) != 0u;
+        const unsigned ballot = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) wsum[warp] = __popc(ballot);
+        __syncthreads();
+        uint32_t off = cnt;
+        for (int w = 0; w < warp; ++w) off += wsum[w];
+        if (take) out[1 + off + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)J;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+            cnt += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = cnt;
+    __syncthreads();
+}
+
+// Elimination form, after phase 2 of round r (r = -1: before round 0):
+//   list = the finite row tiles J > r of round r (phase 3 updates list x list);
+//   marks every pair of the list as a tile that may hold a finite entry from now on
+//   (2 where it was unmarked: only the marked tiles were initialised);
+//   cand = the marked tiles J > r + 1 of row r + 1 (phase 2 of the next round).
+__device__ void compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int32_t r, uint32_t* __restrict__ list,
+                              uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles, int32_t do_list) {
+    if (r >= 0 && do_list) {
+        compact_row(rowflags + (int64_t)r * R, r + 1, R, list);
+        const uint32_t c = list[0];
+        for (uint32_t t = threadIdx.x; t < c * c; t += blockDim.x) {
+            const uint32_t x = t / c, y = t % c;
+            if (y > x) {
+                // 2: newly marked, its cells are not initialised yet (phase 3 starts it
+                // from infinity and then marks it 1)
+                uint32_t* f = rowflags + (int64_t)list[1 + x] * R + list[1 + y];
+                if (__ldcg(f) == 0u) *f = 2u;
+            }
+        }
+        if (threadIdx.x == 0) {
+            tiles[0] += (unsigned long long)c * (c + 1) / 2;  // phase-3 tiles of this round
+            tiles[1] += (unsigned long long)c;                // phase-2 tiles computed (finite)
+        }
+        __syncthreads();
+    }
+    if (r + 1 < R) compact_row(rowflags + (int64_t)(r + 1) * R, r + 2, R, cand);
+}
+
+__global__ void k_compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int32_t r, uint32_t* __restrict__ list,
+                                uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles, int32_t do_list) {
+    compact_trail(rowflags, R, r, list, cand, tiles, do_list);
+}
+
 // ---------------- phase 2, elimination form: candidate row tiles only ----------------
 // cand[0] = count, cand[1..] = the tiles J > r of row r that may hold a finite entry (the
 // assembly's and earlier rounds' marks).  A candidate that is all-infinite is unmarked
 // (it stays infinite); the others are updated, with their transposes.
+// With counter != NULL the last CTA to finish (counted there; the counter is left at 0)
+// also does the round's compaction (compact_trail; with mark_all, after marking every
+// tile J > r of row r): no separate launch on the round's critical path.
 template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restrict__ M, int64_t n, int32_t r,
-                                                                      int32_t R, const uint32_t* __restrict__ cand,
-                                                                      uint32_t* __restrict__ rowflags) {
+                                                                      int32_t R, uint32_t* __restrict__ cand,
+                                                                      uint32_t* __restrict__ rowflags,
+                                                                      uint32_t* __restrict__ list,
+                                                                      unsigned long long* __restrict__ tiles,
+                                                                      uint32_t* __restrict__ counter,
+                                                                      int32_t mark_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -198,67 +351,23 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restr
         store_c<T>(acc, M, n, o, cj, tx, ty);
         store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
     }
-}
-
-// Ordered list of the marked tiles J in [lo, hi) of one flag row: out[0] = count,
-// out[1..] = J ascending.  Whole block; ends with a barrier.
-__device__ void compact_row(const uint32_t* __restrict__ f, int32_t lo, int32_t hi, uint32_t* __restrict__ out) {
-    __shared__ uint32_t cnt;
-    __shared__ uint32_t wsum[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) cnt = 0;
+    if (counter == nullptr) return;
+    __shared__ uint32_t last;
+    __threadfence();  // (this CTA's tiles and flags, before its ticket)
     __syncthreads();
-    for (int32_t base = lo; base < hi; base += blockDim.x) {
-        const int32_t J = base + threadIdx.x;
-        const bool take = J < hi && f[J] != 0u;
-        const unsigned ballot = __ballot_sync(0xffffffffu, take);
-        if (lane == 0) wsum[warp] = __popc(ballot);
-        __syncthreads();
-        uint32_t off = cnt;
-        for (int w = 0; w < warp; ++w) off += wsum[w];
-        if (take) out[1 + off + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)J;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
-            cnt += tot;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = cnt;
+    if (tid == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1u ? 1u : 0u;
     __syncthreads();
+    if (!last) return;
+    __threadfence();  // (every other CTA's writes, after their tickets)
+    if (mark_all)
+        for (int32_t J = r + 1 + tid; J < R; J += blockDim.x) rowflags[(int64_t)r * R + J] = 0xffffffffu;
+    __syncthreads();
+    compact_trail(rowflags, R, r, list, cand, tiles, 1);
+    if (tid == 0) *counter = 0u;
 }
 
 __global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src, int n) {
     if ((int)threadIdx.x < n) dst[threadIdx.x] += src[threadIdx.x];
-}
-
-// Elimination form, after phase 2 of round r (r = -1: before round 0):
-//   list = the finite row tiles J > r of round r (phase 3 updates list x list);
-//   marks every pair of the list as a tile that may hold a finite entry from now on
-//   (2 where it was unmarked: only the marked tiles were initialised);
-//   cand = the marked tiles J > r + 1 of row r + 1 (phase 2 of the next round).
-__global__ void k_compact_trail(uint32_t* __restrict__ rowflags, int32_t R, int32_t r, uint32_t* __restrict__ list,
-                                uint32_t* __restrict__ cand, unsigned long long* __restrict__ tiles, int32_t do_list) {
-    if (r >= 0 && do_list) {
-        compact_row(rowflags + (int64_t)r * R, r + 1, R, list);
-        const uint32_t c = list[0];
-        for (uint32_t t = threadIdx.x; t < c * c; t += blockDim.x) {
-            const uint32_t x = t / c, y = t % c;
-            if (y > x) {
-                // 2: newly marked, its cells are not initialised yet (phase 3 starts it
-                // from infinity and then marks it 1)
-                uint32_t* f = rowflags + (int64_t)list[1 + x] * R + list[1 + y];
-                if (*f == 0u) *f = 2u;
-            }
-        }
-        if (threadIdx.x == 0) {
-            tiles[0] += (unsigned long long)c * (c + 1) / 2;  // phase-3 tiles of this round
-            tiles[1] += (unsigned long long)c;                // phase-2 tiles computed (finite)
-        }
-        __syncthreads();
-    }
-    if (r + 1 < R) compact_row(rowflags + (int64_t)(r + 1) * R, r + 2, R, cand);
 }
 
 // Upper-triangle task t (0 <= t < c(c+1)/2) -> pair (x, y), 0 <= x <= y < c, row-major.
@@ -507,6 +616,8 @@ cudaError_t set_smem_attrs() {
     cudaError_t e;
     e = cudaFuncSetAttribute(k_phase1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_ * T_ * (int)sizeof(T));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_phase1_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, T_ * T_ * (int)sizeof(float));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PanelSmem<T>));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_phase3_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -531,22 +642,25 @@ cudaError_t set_smem_attrs() {
 // the compaction (phase-3 list, marks, next candidates), phase 3 over the list.
 template <typename T>
 cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R, uint32_t* rowflags, uint32_t* cand,
-                       uint32_t* list, bool skip_inf, unsigned long long* tiles, int32_t shared_from, cudaEvent_t ev0,
-                       cudaEvent_t ev1, cudaStream_t st) {
+                       uint32_t* list, bool skip_inf, unsigned long long* tiles, uint32_t* counter,
+                       int32_t shared_from, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
     const size_t psm = sizeof(PanelSmem<T>);
     const int grid = sms() * 2;
-    k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
+    if constexpr (std::is_same<T, float>::value)
+        k_phase1_wide<<<1, 1024, T_ * T_ * sizeof(float), st>>>(M, N, r);
+    else
+        k_phase1<T><<<dim3(1, 1), NTH, T_ * T_ * sizeof(T), st>>>(M, dd, 1, r, nullptr);
     count_launches(1);
     const int32_t np2 = R - 1 - r;
     if (np2 > 0) {
-        k_phase2_cand<T><<<np2 < grid ? np2 : grid, NTH, psm, st>>>(M, N, r, R, cand, rowflags);
-        if (!skip_inf)  // mark every tile: the compaction then lists all J > r
-            cudaMemsetAsync(rowflags + (int64_t)r * R + r + 1, 0xff, (size_t)np2 * sizeof(uint32_t), st);
-        k_compact_trail<<<1, 1024, 0, st>>>(rowflags, R, r, list, cand, tiles, 1);
+        // phase 2, and the compaction in its last CTA (without skipping: every tile J > r
+        // marked, so the compaction lists them all)
+        k_phase2_cand<T><<<np2 < grid ? np2 : grid, NTH, psm, st>>>(M, N, r, R, cand, rowflags, list, tiles,
+                                                                     counter, skip_inf ? 0 : 1);
         if (ev0) cudaEventRecord(ev0, st);
         k_phase3_list<T><<<grid, NTH, psm, st>>>(M, N, r, list, rowflags, R, shared_from);
         if (ev1) cudaEventRecord(ev1, st);
-        count_launches(3);
+        count_launches(2);
     }
     return cudaGetLastError();
 }
@@ -651,7 +765,8 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
     one[0].shared_from = R;
     const std::vector<ElimTask>& runs = (rowflags && tasks && !tasks->empty()) ? *tasks : one;
     const size_t nrun = rowflags ? runs.size() : 0;
-    const int64_t rw = 2 * (int64_t)R + 8;  // per run: list[R + 2], cand[R + 2], tiles (2 x u64)
+    // per run: list[R + 2], cand[R + 2], tiles (2 x u64), the phase-2 CTA counter (+ pad)
+    const int64_t rw = 2 * (int64_t)R + 10;
     uint32_t* run_scratch = nullptr;
     std::vector<cudaStream_t> rs(nrun, nullptr);
     std::vector<cudaEvent_t> done(nrun, nullptr);
@@ -690,7 +805,8 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
                 if (state[i] == 1) {
                     if (next[i] < tk.hi) {
                         const int32_t r = next[i]++;
-                        e = elim_round<T>(M, dd, N, r, R, rowflags, rc, rl, skip_inf, rt, tk.shared_from,
+                        e = elim_round<T>(M, dd, N, r, R, rowflags, rc, rl, skip_inf, rt, rl + 2 * R + 8,
+                                          tk.shared_from,
                                           evs.empty() ? nullptr : evs[2 * r], evs.empty() ? nullptr : evs[2 * r + 1],
                                           rs[i]);
                     } else {
