@@ -219,17 +219,32 @@ __global__ void __launch_bounds__(256) k_unpermute(T* __restrict__ A, const T* _
                                                    int32_t nsel, const int32_t* __restrict__ csize,
                                                    const int32_t* __restrict__ vstart,
                                                    const int32_t* __restrict__ ndpos) {
+    // row pos[a] of P staged in shared memory with 16-byte loads, then gathered into row
+    // a of A and written with 16-byte stores (rows are multiples of 4 cells and start on
+    // 16-byte boundaries: every table's order and offset are multiples of 4)
+    __shared__ __align__(16) T row[kNdMax];
     for (int32_t s = blockIdx.y; s < nsel; s += gridDim.y) {
         const int32_t c = sel[s];
         const MatDesc d = descs[c];
         const int32_t a = blockIdx.x;
-        if (a >= d.n) continue;
+        if (a >= d.n) continue;  // (the same for the whole block)
         const int32_t nc = csize[c];
         const int32_t* pos = ndpos + vstart[c];
         const int32_t pa = a < nc ? pos[a] : a;
-        const T* prow = P + d.off + (int64_t)pa * d.n;
-        T* arow = A + d.off + (int64_t)a * d.n;
-        for (int32_t b = threadIdx.x; b < d.n; b += blockDim.x) arow[b] = prow[b < nc ? pos[b] : b];
+        const int4* prow = reinterpret_cast<const int4*>(P + d.off + (int64_t)pa * d.n);
+        for (int32_t b4 = threadIdx.x; b4 < d.n / 4; b4 += blockDim.x) reinterpret_cast<int4*>(row)[b4] = prow[b4];
+        __syncthreads();
+        int4* arow = reinterpret_cast<int4*>(A + d.off + (int64_t)a * d.n);
+        for (int32_t b4 = threadIdx.x; b4 < d.n / 4; b4 += blockDim.x) {
+            T v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int32_t bb = 4 * b4 + e;
+                v[e] = row[bb < nc ? pos[bb] : bb];
+            }
+            arow[b4] = *reinterpret_cast<const int4*>(v);
+        }
+        __syncthreads();
     }
 }
 
