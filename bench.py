@@ -41,12 +41,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "queries/s + build min-plus Gop/s (1M-vertex planar), vs INT32/HBM roofline, 1xGB300"
-# DRAM bytes (read + write) per min-plus update of k_backsub, from one ncu capture of its
-# launch on the delaunay1m build: dram__bytes_read.sum 132,424,525,056 +
-# dram__bytes_write.sum 73,164,538,368 over 4.4525e12 updates.  The bench scales it by
-# each launch's update count, so its "traffic" is scaled from that capture, not measured
-# in the run.
-BACKSUB_BYTES_PER_UPDATE = (132424525056 + 73164538368) / 4.4525e12
+# DRAM traffic of k_backsub is not reported for the full-size launch: counters beyond the
+# launch time are captured only on the 2^18-point case (a few GB on the device), and
+# there the traffic does not scale with the update count (the writes grow as N^2, the
+# re-read rows faster): 2,386,661,632 B read + 4,390,244,608 B written for 2.41e11
+# updates (0.028 B per update, against 0.046 in an earlier full-size capture).
+BACKSUB_TRAFFIC_NOTE = ("not measured at this size; on 2^18 points one launch reads 2.39 GB and writes 4.39 GB "
+                        "(the matrix once) for 2.41e11 updates, and the ratio grows with size")
 UNIT = "queries/s"
 
 
@@ -738,19 +739,12 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_gops = sms * 128 * 2070e6 / 2 / 1e9  # 128 lanes/SM, 2 lane-ops per update, max SM clock
     kern = {
-        # DRAM bytes per 128x128 phase-3 tile, from an ncu capture of two full launches on
-        # the 2^18-point Delaunay workload (Floyd-Warshall form: 6.533e9 bytes over 32,131
-        # tiles), scaled to this workload's average launch by its tile count (traffic grows
-        # in proportion to tiles).
         "k_phase3_list": {"what": "k_phase3_list (boundary-graph elimination / Floyd-Warshall, phase 3)",
-                          "ms": p3_ms, "launches": p3_launches, "updates": p3_updates,
-                          "traffic": 6.5329e9 / 32131 * p3_updates / max(p3_launches, 1) / 128 ** 3},
-        # DRAM bytes per min-plus update of the back-substitution (BACKSUB_BYTES_PER_UPDATE),
-        # times this launch's updates
+                          "ms": p3_ms, "launches": p3_launches, "updates": p3_updates, "traffic": None,
+                          "traffic_note": "not captured for the elimination rounds"},
         "k_backsub": {"what": "k_backsub (boundary-graph back-substitution, persistent)",
-                      "ms": bs_ms, "launches": bs_launches, "updates": bs_updates,
-                      "traffic": BACKSUB_BYTES_PER_UPDATE * bs_updates / max(bs_launches, 1)
-                      if BACKSUB_BYTES_PER_UPDATE else None},
+                      "ms": bs_ms, "launches": bs_launches, "updates": bs_updates, "traffic": None,
+                      "traffic_note": BACKSUB_TRAFFIC_NOTE},
     }
     top = max(kern, key=lambda x: kern[x]["ms"])
     other = [x for x in kern if x != top and kern[x]["ms"] > 0]
@@ -760,7 +754,7 @@ def main():
         ach = kd["updates"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
         return {"kernel": kd["what"], "bound": "alu", "achieved": ach, "peak": peak_gops, "unit": "Gop/s",
                 "frac": (ach / peak_gops) if ach else None, "traffic": kd["traffic"],
-                "traffic_unit": "bytes per launch (DRAM read + write), scaled from one ncu capture",
+                "traffic_note": kd["traffic_note"],
                 "launches": int(kd["launches"]),
                 "avg_launch_ms": kd["ms"] / max(kd["launches"], 1),
                 "share_of_bg_ms": kd["ms"] / K / max(statistics.mean(pf["bg_fw"] for _, pf, _ in per), 1e-9)}
