@@ -798,7 +798,8 @@ def main():
         "dtype": ("int32 results, exact float32 arithmetic (checked)" if st0["arith"] == spq.SPQ_ARITH_F32
                   else "int32"),
         "data": "synthetic",
-        "config": dict(desc, l2="inputs larger than L2 (the 71 GB boundary-graph matrix is rebuilt every step)",
+        "config": dict(desc, l2=f"inputs larger than L2 (the {4 * st0['n_bg'] ** 2 / 1e9:.1f} GB boundary-graph "
+                                f"matrix is rebuilt every step)",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "build_ms": statistics.mean(build_ms),
         "build_gops": total_updates / (statistics.mean(build_ms) * 1e-3) / 1e9,
