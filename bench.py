@@ -221,6 +221,13 @@ def tuning_summary(spq) -> dict:
             "config0_classes": sorted(c for (_, c), v in t.items() if v == 0)}
 
 
+def build_tuning_summary(spq) -> dict:
+    """The build autotuner's state: per size class of the boundary graph, the chosen depth
+    of concurrent elimination runs and the stage times measured at depths 3, 4, 5."""
+    return {str(c): {"depth": v["depth"], "bg_stage_ms": [round(x, 2) for x in v["ms"]]}
+            for (_, c), v in spq.spq_build_tuning().items()}
+
+
 def cpu_oracle_sample(w, budget_s: float, seed: int = 99):
     """Time the oracle (Dijkstra per pair, all host cores) on a bounded sample of the
     workload's pairs: chunks of uniformly drawn pairs until budget_s has elapsed.
@@ -818,7 +825,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,
-        "query_autotune": tuning_summary(spq),
+        "query_autotune": tuning_summary(spq), "build_autotune": build_tuning_summary(spq),
     }
 
     last_out = d_out.cpu().numpy()  # answers of the last timed step (outside the timed region)

@@ -51,6 +51,15 @@ int spq_boundary_order_host(int k, const long long* adj_ptr, const int* adj, con
  * Writes at most cap entries; returns how many there are. */
 int32_t spq_query_tuning(int32_t* keys, int32_t* choices, int32_t cap);
 
+/* The build's autotuner: how many bisection levels of the boundary graph's dissection
+ * (elimination form) run as concurrent chains of rounds, per (device, size class):
+ * keys[i] = device * 256 + class (class = bit length of |BG|), depths[i] = the chosen
+ * depth (3, 4 or 5; -1 while the candidates are still being tried, one per build), and
+ * ms[3 * i + j] = the boundary-graph stage time measured with candidate j (depth 3 + j;
+ * -1 if not tried yet).  Graphs with fewer than 4,096 boundary vertices are not tuned.
+ * Writes at most cap entries; returns how many there are. */
+int32_t spq_build_tuning(int32_t* keys, int32_t* depths, double* ms, int32_t cap);
+
 /* Test hook of the back-substitution's bounded dependency waits (a CTA waits on a flag that
  * another CTA of the same launch sets when it finishes a tile the first one reads; each
  * wait gives up after a bound, the launch stops and the build returns SPQ_ETIMEOUT).

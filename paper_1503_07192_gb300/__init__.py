@@ -536,6 +536,19 @@ def spq_query_tuning() -> dict:
     return {(keys[i] // 256, keys[i] % 256): int(ch[i]) for i in range(n)}
 
 
+def spq_build_tuning() -> dict:
+    """The build's autotuner so far: {(device, size class): {"depth": chosen depth of
+    concurrent elimination runs (-1 while trying), "ms": [stage ms at depth 3, 4, 5]}}."""
+    lib = _lib.load()
+    n = int(lib.spq_build_tuning(None, None, None, 0))
+    keys = (ctypes.c_int32 * max(n, 1))()
+    dep = (ctypes.c_int32 * max(n, 1))()
+    ms = (ctypes.c_double * (3 * max(n, 1)))()
+    n = min(n, int(lib.spq_build_tuning(keys, dep, ms, n)))
+    return {(keys[i] // 256, keys[i] % 256): {"depth": int(dep[i]), "ms": [ms[3 * i + j] for j in range(3)]}
+            for i in range(n)}
+
+
 def spq_query_profile(h) -> dict | None:
     """The last grouped query launch on h (built with opts.profile_kernels = 1): the
     block-copy kernel's device ms, its min-plus updates and algorithmic bytes; None if

@@ -46,6 +46,7 @@ SIGNATURES = {
     "spq_query_paths": (ctypes.c_int, [P, P, i64, P, ctypes.c_int32, P, P, P]),
     "spq_query_matrix": (ctypes.c_int, [P, P, i64, P, i64, P, P]),
     "spq_query_tuning": (i32, [P, P, i32]),
+    "spq_build_tuning": (i32, [P, P, P, i32]),
     "spq_query_plan_create": (ctypes.c_int, [i32, P, P, P, P, P, ctypes.POINTER(P)]),
     "spq_query_plan_run": (ctypes.c_int, [P, P]),
     "spq_query_plan_free": (None, [P]),

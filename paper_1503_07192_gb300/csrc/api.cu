@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -199,6 +200,45 @@ int bits_for(uint64_t x) {
 }
 
 // CUDA events bracketing the build stages (see spq_build_profile).
+// ---- the build's autotuned knob ----
+// How many bisection levels of the boundary graph's dissection become concurrent runs of
+// elimination rounds (up to 2^depth leaf runs, each on its own stream).  Deeper levels
+// give more and shorter runs, but more alignment padding, another frontier structure for
+// the back-substitution, and more streams than the context may have hardware queues for;
+// the best depth depends on the graph and the device.  Per device and size class of the
+// boundary graph (bit length of |BG|), the first builds try the candidate depths in turn,
+// each timed by the build's own stage events (the boundary graph's all-pairs stage), and
+// later builds take the fastest.  Every depth gives the same distances (only the matrix
+// order changes, and everything reaches the matrix through bgpos).
+constexpr int kDepthCand[3] = {3, 4, 5};
+struct DepthClass {
+    double ms[3] = {-1.0, -1.0, -1.0};
+    int next = 0;     // the next candidate to try
+    int chosen = -1;  // the fastest, once all are measured
+};
+std::mutex g_depth_mu;
+std::map<std::pair<int, int>, DepthClass> g_depth;
+
+int depth_pick(int dev, int cls) {
+    std::lock_guard<std::mutex> lk(g_depth_mu);
+    const DepthClass& c = g_depth[{dev, cls}];
+    return c.chosen >= 0 ? c.chosen : c.next;
+}
+
+void depth_report(int dev, int cls, int idx, double ms) {
+    std::lock_guard<std::mutex> lk(g_depth_mu);
+    DepthClass& c = g_depth[{dev, cls}];
+    if (c.chosen >= 0 || idx != c.next || !(ms > 0.0)) return;  // (a concurrent build measured it)
+    c.ms[idx] = ms;
+    c.next = idx + 1;
+    if (c.next == 3) {
+        int b = 0;
+        for (int i = 1; i < 3; ++i)
+            if (c.ms[i] < c.ms[b]) b = i;
+        c.chosen = b;
+    }
+}
+
 struct StageEvents {
     cudaEvent_t ev[8] = {};
     bool ok = true;
@@ -459,9 +499,11 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     }
     h->nbg = bo;
     h->max_nb = k > 0 ? *std::max_element(h->h_nb.begin(), h->h_nb.end()) : 0;
-    // matrix order: the slots, plus (elimination form) up to 15 alignment gaps of < 128
+    // matrix order: the slots, plus (elimination form) one alignment gap of < 128 per
+    // aligned piece start
     const bool may_elim = opts.bg_method != SPQ_BG_FW && bo > 0;
-    const int64_t n_max = round_up(bo + (may_elim ? 15 * (kTile - 1) : 0), 4);
+    const int64_t max_runs = ((int64_t)2 << kMaxRunDepth) - 1;
+    const int64_t n_max = round_up(bo + (may_elim ? max_runs * (kTile - 1) : 0), 4);
     if (n_max > 0 && n_max * n_max > (int64_t)1 << 40) return SPQ_ENOMEM;
 
     // ---- memory check (with the largest matrix order), then allocation ----
@@ -471,10 +513,10 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     const int64_t fw_words_max = n_max > 0 ? fw_single_scratch_words(n_max) : 1;
     size_t apanel_budget = std::min<size_t>(panel_cap, 4 * (size_t)n_max * (size_t)n_max + (1u << 20));
     // elimination scratch: per-round row flags, back-substitution bookkeeping, A panels,
-    // and per-run compaction lists (at most 15 runs)
-    const size_t elim_bytes =
-        may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(n_max) + apanel_budget + 15 * 4 * (size_t)fw_words_max
-                 : 0;
+    // and per-run compaction lists
+    const size_t elim_bytes = may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(n_max) + apanel_budget +
+                                             (size_t)max_runs * 4 * (size_t)fw_words_max
+                                       : 0;
     // (+ the component tables in dissection order, a second copy, for their elimination)
     const size_t comp_elim_bytes = opts.comp_method != SPQ_BG_FW ? 4 * (size_t)h->apsp_elems + 8 * (size_t)n : 0;
     size_t need = 4 * (size_t)h->apsp_elems + comp_elim_bytes + 4 * (size_t)n_max * (size_t)n_max + 8 * (size_t)n +
@@ -551,6 +593,10 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     std::vector<int32_t> bgpos;
     spq_status order_status = SPQ_OK;
     std::thread order_thread;
+    // the autotuned depth of concurrent runs (the root split needs two pieces of 16 tiles)
+    const int tune_cls = bits_for((uint64_t)h->nbg);
+    const int depth_idx = (may_elim && h->nbg >= 2 * 16 * kTile) ? depth_pick(h->device, tune_cls) : -1;
+    if (depth_idx >= 0) plan.layout.depth = kDepthCand[depth_idx];
     if (h->nbg > 0)
         order_thread = std::thread([&]() {
             order_status = boundary_order_from(k, h->h_nb, bpairs, (spq_order)opts.order, &bgpos, &h->order_method,
@@ -621,6 +667,8 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     evs.mark(7, st);
     CK(cudaStreamSynchronize(st));
     evs.collect(h->prof_ms);
+    if (depth_idx >= 0 && plan.elim && plan.layout.tasks.size() > 1)
+        depth_report(h->device, tune_cls, depth_idx, h->prof_ms[4]);
     return SPQ_OK;
 }
 
@@ -789,6 +837,21 @@ int32_t spq_build_profile(const spq_handle* h, double* ms, int32_t count) {
 }
 
 unsigned long long spq_kernel_launches(void) { return spq::g_kernel_launches.load(); }
+
+int32_t spq_build_tuning(int32_t* keys, int32_t* depths, double* ms, int32_t cap) {
+    std::lock_guard<std::mutex> lk(g_depth_mu);
+    int32_t n = 0;
+    for (const auto& kv : g_depth) {
+        if (n < cap) {
+            if (keys) keys[n] = kv.first.first * 256 + kv.first.second;
+            if (depths) depths[n] = kv.second.chosen >= 0 ? kDepthCand[kv.second.chosen] : -1;
+            if (ms)
+                for (int i = 0; i < 3; ++i) ms[3 * n + i] = kv.second.ms[i];
+        }
+        ++n;
+    }
+    return n;
+}
 
 spq_status spq_query_profile(const spq_handle* h, double* kernel_ms, double* updates, double* bytes) {
     if (!h || !h->qstats || !h->qprof_ran) return SPQ_EUNSUPPORTED;

@@ -686,9 +686,11 @@ spq_status boundary_order_host(int32_t k, const std::vector<int32_t>& nb, std::v
         }
         uptr[nslots] = wpos;
         std::vector<NdNode> nodes;
-        // pieces of at least 16 tiles, five levels deep: up to 32 runs side by side (as many
-        // as a context has hardware work queues when CUDA_DEVICE_MAX_CONNECTIONS is 32)
-        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order, layout ? 5 : 0, 16 * kTile,
+        // pieces of at least 16 tiles, layout->depth levels deep: up to 2^depth leaf runs
+        // side by side (32 at the most: as many as a context has hardware work queues when
+        // CUDA_DEVICE_MAX_CONNECTIONS is 32)
+        vertex_nd((int)best, k, ptr, adj, slot_off, uptr, snb, &slot_order,
+                  layout ? std::min(std::max(layout->depth, 0), kMaxRunDepth) : 0, 16 * kTile,
                   layout ? &nodes : nullptr);
         *method = (int32_t)best + 2;
         if ((int64_t)slot_order.size() != nslots) return SPQ_EINVAL;  // cannot happen: every slot is emitted once

@@ -29,7 +29,11 @@ struct ElimTask {
 // Layout of the boundary-graph matrix for the elimination form: the matrix order
 // (slots plus alignment padding) and the runs of elimination rounds.  With npad == 0 the
 // slots are packed (npad = number of slots) and there is a single run.
+// Most bisection levels whose pieces become concurrent runs (up to 2^depth leaf runs,
+// 2^(depth + 1) - 1 runs and as many aligned piece starts in all).
+constexpr int kMaxRunDepth = 5;
 struct BgLayout {
+    int32_t depth = kMaxRunDepth;  // in: bisection levels to align and run side by side
     int64_t npad = 0;
     std::vector<ElimTask> tasks;
 };
