@@ -515,7 +515,7 @@ spq_status build_impl(int32_t n, const int64_t* row_ptr, const int32_t* col, con
     // elimination scratch: per-round row flags, back-substitution bookkeeping, A panels,
     // and per-run compaction lists
     const size_t elim_bytes = may_elim ? 4 * (size_t)(nR * nR) + bg_backsub_scratch_bytes(n_max) + apanel_budget +
-                                             (size_t)max_runs * 4 * (size_t)fw_words_max
+                                             (size_t)max_runs * 4 * (size_t)(6 * nR + 10)
                                        : 0;
     // (+ the component tables in dissection order, a second copy, for their elimination)
     const size_t comp_elim_bytes = opts.comp_method != SPQ_BG_FW ? 4 * (size_t)h->apsp_elems + 8 * (size_t)n : 0;

@@ -219,7 +219,8 @@ template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__ base, const MatDesc* __restrict__ descs,
                                                    int32_t nmat, int32_t r, uint32_t* __restrict__ row_finite,
                                                    int32_t flag_stride, const int32_t* __restrict__ sel,
-                                                   int32_t trail = 0) {
+                                                   int32_t trail = 0, uint32_t* __restrict__ kmask = nullptr,
+                                                   int32_t kstride = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -243,7 +244,18 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2(T* __restrict__
 #pragma unroll
             for (int j = 0; j < 8; ++j) fin |= acc[i][j] < inf;
         if (!__syncthreads_or(fin)) continue;
-        minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        if (kmask) {  // (as in k_phase2_cand: chunk skipping, then the row mask for phase 3)
+            __shared__ uint32_t rm[4];
+            tile_row_mask<T>(acc, rm, tid, tx, ty);
+            uint32_t cm = 0u;
+#pragma unroll
+            for (int c = 0; c < NCHUNK; ++c) cm |= rm[c] ? (1u << c) : 0u;
+            minplus_panels_masked<T>(acc, M, n, o, o, cj, sm, tid, tx, ty, cm);
+            tile_row_mask<T>(acc, rm, tid, tx, ty);
+            if (tid < 4) kmask[(int64_t)mi * kstride + (int64_t)J * 4 + tid] = rm[tid];
+        } else {
+            minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        }
         store_c<T>(acc, M, n, o, cj, tx, ty);
         store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
         if (row_finite && tid == 0) row_finite[(int64_t)mi * flag_stride + J] = 1u;
@@ -326,7 +338,8 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restr
                                                                       uint32_t* __restrict__ list,
                                                                       unsigned long long* __restrict__ tiles,
                                                                       uint32_t* __restrict__ counter,
-                                                                      int32_t mark_all) {
+                                                                      int32_t mark_all,
+                                                                      uint32_t* __restrict__ kmask) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -347,7 +360,20 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase2_cand(T* __restr
             if (tid == 0) rowflags[(int64_t)r * R + J] = 0u;
             continue;
         }
-        minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        if (kmask) {
+            // the B panel is this tile's own rows: skip the chunks of rows that are all
+            // infinite; then record the updated tile's finite rows for phase 3
+            __shared__ uint32_t rm[4];
+            tile_row_mask<T>(acc, rm, tid, tx, ty);
+            uint32_t cm = 0u;
+#pragma unroll
+            for (int c = 0; c < NCHUNK; ++c) cm |= rm[c] ? (1u << c) : 0u;
+            minplus_panels_masked<T>(acc, M, n, o, o, cj, sm, tid, tx, ty, cm);
+            tile_row_mask<T>(acc, rm, tid, tx, ty);
+            if (tid < 4) kmask[(int64_t)J * 4 + tid] = rm[tid];
+        } else {
+            minplus_panels<T>(acc, M, n, o, o, cj, sm, tid, tx, ty);
+        }
         store_c<T>(acc, M, n, o, cj, tx, ty);
         store_c_transposed<T>(acc, M, n, o, cj, tx, ty);
     }
@@ -456,7 +482,8 @@ template <typename T>
 __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restrict__ M, int64_t n, int32_t r,
                                                         const uint32_t* __restrict__ list,
                                                         uint32_t* __restrict__ rowflags, int32_t R,
-                                                        int32_t shared_from) {
+                                                        int32_t shared_from,
+                                                        const uint32_t* __restrict__ kmask = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -467,27 +494,56 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_list(T* __restr
         tri_pair(t, c, x, y);
         const int64_t I = list[1 + x], J = list[1 + y];
         uint32_t* f = (rowflags && I < J) ? rowflags + I * R + J : nullptr;
-        if (f && *f == 2u) {
-            const int64_t ci = I * T_, cj = J * T_;
-            T acc[8][8];
+        if (!kmask) {
+            if (f && *f == 2u) {
+                const int64_t ci = I * T_, cj = J * T_;
+                T acc[8][8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = Inf<T>::value();
+                minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+                store_c<T>(acc, M, n, ci, cj, tx, ty);
+                store_c_transposed<T>(acc, M, n, ci, cj, tx, ty);
+                if (tid == 0) *f = 1u;  // (every thread read the flag before the panel barriers)
+            } else if (I >= shared_from) {
+                const int64_t ci = I * T_, cj = J * T_;
+                T acc[8][8];
+                load_c<T>(acc, M, n, ci, cj, tx, ty);
+                minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+                store_c_min<T>(acc, M, n, ci, cj, tx, ty);
+                if (I != J) store_c_transposed_min<T>(acc, M, n, ci, cj, tx, ty);
+            } else {
+                phase3_tile<T>(M, n, o, I, J, sm, tid, tx, ty);
+            }
+            continue;
+        }
+        // with the row masks of this round's row tiles (kmask: 4 words per tile, set by
+        // phase 2): only the chunks of pivot rows finite in both panels
+        uint32_t cm = 0u;
+#pragma unroll
+        for (int q = 0; q < NCHUNK; ++q) cm |= (kmask[I * 4 + q] & kmask[J * 4 + q]) ? (1u << q) : 0u;
+        const bool fresh = f && *f == 2u;
+        __syncthreads();  // (every thread has read the mark before thread 0 may change it)
+        const int64_t ci = I * T_, cj = J * T_;
+        T acc[8][8];
+        if (fresh) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = Inf<T>::value();
-            minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
-            store_c<T>(acc, M, n, ci, cj, tx, ty);
-            store_c_transposed<T>(acc, M, n, ci, cj, tx, ty);
-            if (tid == 0) *f = 1u;  // (every thread read the flag before the panel barriers)
-        } else if (I >= shared_from) {
-            const int64_t ci = I * T_, cj = J * T_;
-            T acc[8][8];
+        } else {
             load_c<T>(acc, M, n, ci, cj, tx, ty);
-            minplus_panels<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty);
+        }
+        minplus_panels_masked<T>(acc, M, n, o, ci, cj, sm, tid, tx, ty, cm);
+        if (!fresh && I >= shared_from) {
             store_c_min<T>(acc, M, n, ci, cj, tx, ty);
             if (I != J) store_c_transposed_min<T>(acc, M, n, ci, cj, tx, ty);
         } else {
-            phase3_tile<T>(M, n, o, I, J, sm, tid, tx, ty);
+            store_c<T>(acc, M, n, ci, cj, tx, ty);
+            if (I != J) store_c_transposed<T>(acc, M, n, ci, cj, tx, ty);
         }
+        if (fresh && tid == 0) *f = 1u;
     }
 }
 
@@ -578,7 +634,9 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_many(T* __restr
                                                                       const MatDesc* __restrict__ descs, int32_t nmat,
                                                                       int32_t r, const uint32_t* __restrict__ lists,
                                                                       int32_t lstride,
-                                                                      const uint32_t* __restrict__ offs) {
+                                                                      const uint32_t* __restrict__ offs,
+                                                                      const uint32_t* __restrict__ kmask = nullptr,
+                                                                      int32_t kstride = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PanelSmem<T>& sm = *reinterpret_cast<PanelSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -594,7 +652,23 @@ __global__ void __launch_bounds__(NTH, SPQ_FW_MIN_CTAS) k_phase3_many(T* __restr
         const uint32_t* list = lists + (int64_t)lo * lstride;
         int64_t x, y;
         tri_pair(t - (int64_t)offs[lo], (int64_t)list[0], x, y);
-        phase3_tile<T>(base + d.off, d.n, o, (int64_t)list[1 + x], (int64_t)list[1 + y], sm, tid, tx, ty);
+        const int64_t I = list[1 + x], J = list[1 + y];
+        if (!kmask) {
+            phase3_tile<T>(base + d.off, d.n, o, I, J, sm, tid, tx, ty);
+            continue;
+        }
+        // only the chunks of pivot rows finite in both row tiles (masks set by k_phase2)
+        const uint32_t* km = kmask + (int64_t)lo * kstride;
+        uint32_t cm = 0u;
+#pragma unroll
+        for (int q = 0; q < NCHUNK; ++q) cm |= (km[I * 4 + q] & km[J * 4 + q]) ? (1u << q) : 0u;
+        T* M = base + d.off;
+        const int64_t ci = I * T_, cj = J * T_;
+        T acc[8][8];
+        load_c<T>(acc, M, d.n, ci, cj, tx, ty);
+        minplus_panels_masked<T>(acc, M, d.n, o, ci, cj, sm, tid, tx, ty, cm);
+        store_c<T>(acc, M, d.n, ci, cj, tx, ty);
+        if (I != J) store_c_transposed<T>(acc, M, d.n, ci, cj, tx, ty);
     }
 }
 
@@ -643,7 +717,7 @@ cudaError_t set_smem_attrs() {
 template <typename T>
 cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R, uint32_t* rowflags, uint32_t* cand,
                        uint32_t* list, bool skip_inf, unsigned long long* tiles, uint32_t* counter,
-                       int32_t shared_from, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
+                       uint32_t* kmask, int32_t shared_from, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st) {
     const size_t psm = sizeof(PanelSmem<T>);
     const int grid = sms() * 2;
     if constexpr (std::is_same<T, float>::value)
@@ -655,10 +729,13 @@ cudaError_t elim_round(T* M, const MatDesc* dd, int64_t N, int32_t r, int32_t R,
     if (np2 > 0) {
         // phase 2, and the compaction in its last CTA (without skipping: every tile J > r
         // marked, so the compaction lists them all)
+        // (with skipping, phase 2 records the row masks of the row tiles it computed and
+        //  phase 3 skips the pivot-row chunks that are infinite in either panel)
+        uint32_t* km = skip_inf ? kmask : nullptr;
         k_phase2_cand<T><<<np2 < grid ? np2 : grid, NTH, psm, st>>>(M, N, r, R, cand, rowflags, list, tiles,
-                                                                     counter, skip_inf ? 0 : 1);
+                                                                     counter, skip_inf ? 0 : 1, km);
         if (ev0) cudaEventRecord(ev0, st);
-        k_phase3_list<T><<<grid, NTH, psm, st>>>(M, N, r, list, rowflags, R, shared_from);
+        k_phase3_list<T><<<grid, NTH, psm, st>>>(M, N, r, list, rowflags, R, shared_from, km);
         if (ev1) cudaEventRecord(ev1, st);
         count_launches(2);
     }
@@ -765,8 +842,9 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
     one[0].shared_from = R;
     const std::vector<ElimTask>& runs = (rowflags && tasks && !tasks->empty()) ? *tasks : one;
     const size_t nrun = rowflags ? runs.size() : 0;
-    // per run: list[R + 2], cand[R + 2], tiles (2 x u64), the phase-2 CTA counter (+ pad)
-    const int64_t rw = 2 * (int64_t)R + 10;
+    // per run: list[R + 2], cand[R + 2], tiles (2 x u64), the phase-2 CTA counter (+ pad),
+    // the row masks of the round's row tiles (4 words per tile)
+    const int64_t rw = 6 * (int64_t)R + 10;
     uint32_t* run_scratch = nullptr;
     std::vector<cudaStream_t> rs(nrun, nullptr);
     std::vector<cudaEvent_t> done(nrun, nullptr);
@@ -806,7 +884,7 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
                     if (next[i] < tk.hi) {
                         const int32_t r = next[i]++;
                         e = elim_round<T>(M, dd, N, r, R, rowflags, rc, rl, skip_inf, rt, rl + 2 * R + 8,
-                                          tk.shared_from,
+                                          rl + 2 * R + 10, tk.shared_from,
                                           evs.empty() ? nullptr : evs[2 * r], evs.empty() ? nullptr : evs[2 * r + 1],
                                           rs[i]);
                     } else {
@@ -876,7 +954,8 @@ cudaError_t fw_single(T* M, int64_t N, bool skip_inf, uint32_t* scratch, uint32_
 
 int64_t fw_many_scratch_words(int32_t nmat, int32_t max_n) {
     const int64_t R = (max_n + T_ - 1) / T_;
-    return (int64_t)nmat * R + (int64_t)nmat * (R + 1) + nmat + 1 + 1 + 4;
+    // flags, lists, offsets, (alignment), two u64 counters, row masks (4 words per tile)
+    return (int64_t)nmat * R + (int64_t)nmat * (R + 1) + nmat + 1 + 1 + 4 + (int64_t)nmat * R * 4;
 }
 
 template <typename T>
@@ -893,7 +972,9 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
     int64_t toff = (int64_t)nmat * R + (int64_t)nmat * (R + 1) + nmat + 1;
     toff += toff & 1;  // 8-byte alignment of the counters
     unsigned long long* tiles = reinterpret_cast<unsigned long long*>(scratch + toff);
-    e = cudaMemsetAsync(scratch, 0, fw_many_scratch_words(nmat, max_n) * sizeof(uint32_t), st);
+    uint32_t* kmask = scratch + toff + 4;  // per matrix R x 4 words
+    const int32_t kstride = 4 * R;
+    e = cudaMemsetAsync(scratch, 0, (size_t)(toff + 4) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const unsigned gy = (unsigned)(nmat < 65535 ? nmat : 65535);
     const size_t psm = sizeof(PanelSmem<T>);
@@ -904,13 +985,16 @@ cudaError_t fw_many_skip(T* base, const MatDesc* d_descs, int32_t nmat, int32_t 
         if (R > 1 && (!trail || r + 1 < R)) {
             // (elimination form: the flags of the tiles left of r stay clear, so the lists
             //  and phase 3 hold only tiles right of / below the pivot block)
+            // (row masks: phase 3 skips the pivot-row chunks infinite in either row tile)
             if (trail)
-                k_phase2<T><<<dim3(R - 1 - r, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr, 1);
+                k_phase2<T><<<dim3(R - 1 - r, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr, 1,
+                                                                    kmask, kstride);
             else
-                k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr);
+                k_phase2<T><<<dim3(R - 1, gy), NTH, psm, st>>>(base, d_descs, nmat, r, flags, R, nullptr, 0, kmask,
+                                                                kstride);
             k_compact_many<<<nmat, 1024, 0, st>>>(flags, R, d_descs, nmat, r, lists, R + 1, offs, tiles);
             launch_scan_excl(offs, nmat + 1, st);
-            k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs);
+            k_phase3_many<T><<<p3_grid, NTH, psm, st>>>(base, d_descs, nmat, r, lists, R + 1, offs, kmask, kstride);
             count_launches(4);
         }
         e = cudaGetLastError();

@@ -286,5 +286,61 @@ __device__ __forceinline__ void minplus_panels(T (&acc)[8][8], const T* __restri
     }
 }
 
+// minplus_panels restricted to the 32-row chunks of the pivot block whose bit is set in
+// cmask (bit c: rows [32c, 32c + 32)).  A chunk whose rows are all infinite in the A panel
+// or in the B panel (row by row) changes nothing: each of its terms is infinite.  cmask
+// must be the same for the whole CTA.
+template <typename T>
+__device__ __forceinline__ void minplus_panels_masked(T (&acc)[8][8], const T* __restrict__ M, int64_t n,
+                                                      int64_t prow0, int64_t acol0, int64_t bcol0, PanelSmem<T>& sm,
+                                                      int tid, int tx, int ty, uint32_t cmask) {
+    int chs[NCHUNK];
+    int nch = 0;
+#pragma unroll
+    for (int c = 0; c < NCHUNK; ++c)
+        if ((cmask >> c) & 1u) chs[nch++] = c;
+    if (nch == 0) return;
+    stage_chunk<T>(sm.a[0], M, n, prow0 + chs[0] * KC, acol0, tid);
+    stage_chunk<T>(sm.b[0], M, n, prow0 + chs[0] * KC, bcol0, tid);
+    cp_async_commit();
+#pragma unroll 1
+    for (int t = 0; t < nch; ++t) {
+        if (t + 1 < nch) {
+            const int s = (t + 1) & 1;
+            stage_chunk<T>(sm.a[s], M, n, prow0 + chs[t + 1] * KC, acol0, tid);
+            stage_chunk<T>(sm.b[s], M, n, prow0 + chs[t + 1] * KC, bcol0, tid);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        compute_chunk<T>(acc, sm, t & 1, tx, ty);
+        __syncthreads();
+    }
+}
+
+// Rows of the CTA's 128 x 128 tile (held in acc, 8 x 8 per thread) with a finite cell, as
+// a 128-bit mask in words[0 .. 4) (shared memory, cleared here).  Whole CTA; starts and
+// ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void tile_row_mask(const T (&acc)[8][8], uint32_t* words, int tid, int tx, int ty) {
+    __syncthreads();  // (earlier readers of words are done)
+    if (tid < 4) words[tid] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        bool f = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f |= acc[i][j] < Inf<T>::value();
+        if (f) {
+            const int row = own(ty, i);
+            atomicOr(&words[row >> 5], 1u << (row & 31));
+        }
+    }
+    (void)tx;
+    __syncthreads();
+}
+
 }  // namespace
 }  // namespace spq
