@@ -221,6 +221,20 @@ def tuning_summary(spq) -> dict:
             "config0_classes": sorted(c for (_, c), v in t.items() if v == 0)}
 
 
+def workload_config(desc: dict, world: int) -> dict:
+    """The `config` of a line (both arms): the workload, what it means for L2, and the
+    parallelism."""
+    sizes = {"delaunay1m": "71 GB", "grid1024diag": "61 GB", "delaunay262k": "4.2 GB", "delaunay131k": "1.1 GB"}
+    name = desc.get("workload", "")
+    if name == "grid64":
+        l2 = "inputs fit in L2 (a 2 MB boundary-graph matrix; a parity workload, not a benchmark configuration)"
+    elif name in sizes:
+        l2 = f"inputs larger than L2 (the {sizes[name]} boundary-graph matrix is rebuilt every step)"
+    else:
+        l2 = "inputs larger than L2 (the boundary-graph matrix is rebuilt every step)"
+    return dict(desc, l2=l2, parallelism="replicas" if world > 1 else "single GPU")
+
+
 def build_tuning_summary(spq) -> dict:
     """The build autotuner's state: per size class of the boundary graph, the chosen depth
     of concurrent elimination runs and the stage times measured at depths 3, 4, 5."""
@@ -284,7 +298,7 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "impl": "reference", "config": desc,
+            "impl": "reference", "config": workload_config(desc, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{step_q} uniformly drawn pairs of the workload per step, "
                                        f"binary-heap Dijkstra with early exit, OpenMP over pairs"},
@@ -805,9 +819,7 @@ def main():
         "dtype": ("int32 results, exact float32 arithmetic (checked)" if st0["arith"] == spq.SPQ_ARITH_F32
                   else "int32"),
         "data": "synthetic",
-        "config": dict(desc, l2=f"inputs larger than L2 (the {4 * st0['n_bg'] ** 2 / 1e9:.1f} GB boundary-graph "
-                                f"matrix is rebuilt every step)",
-                       parallelism="replicas" if world > 1 else "single GPU"),
+        "config": workload_config(desc, world),
         "build_ms": statistics.mean(build_ms),
         "build_gops": total_updates / (statistics.mean(build_ms) * 1e-3) / 1e9,
         "build_updates": total_updates,
