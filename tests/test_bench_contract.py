@@ -57,3 +57,16 @@ def test_clock_sampler_counts_the_timed_region_only():
     c2.proc = P()
     r2 = c2.stop()
     assert r2["samples"] == 1 and r2["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_both_arms_describe_the_workload_alike():
+    """The device arm and the reference arm build `config` with the same function, so
+    the lines of one workload carry the same object, including the L2 note."""
+    import bench
+
+    _, desc = bench.make_workload("grid64", None)
+    a, b = bench.workload_config(desc, 1), bench.workload_config(dict(desc), 1)
+    assert a == b and a["workload"] == "grid64" and a["parallelism"] == "single GPU"
+    assert "fit in L2" in a["l2"]
+    big = bench.workload_config({"workload": "delaunay1m"}, 4)
+    assert "larger than L2" in big["l2"] and big["parallelism"] == "replicas"
