@@ -43,6 +43,19 @@ int spq_component_order_host(int k, const long long* adj_ptr, const int* adj, co
 int spq_boundary_order_host(int k, const long long* adj_ptr, const int* adj, const long long* slot_off,
                             const long long* snb_ptr, const int* snb, int rule, int* slot_order_out);
 
+/* Host-only: the same order laid out for the elimination form with `depth` levels of
+ * concurrent runs (0..5), as a build does: bgpos_out[slot] = the slot's row of the
+ * boundary-graph matrix, *npad_out = the matrix order before rounding (slots plus the
+ * alignment padding that starts every piece and separator on a 128-row boundary), and per
+ * run of rounds 5 ints in tasks_out: first and last-plus-one block row, the block row from
+ * which its tiles may be shared with concurrent runs, and the indices of the (up to two)
+ * runs it waits for (-1: none).  Returns the number of runs (0: no split, one run over
+ * every block row; at most cap_tasks are written), or a negative value on bad input.
+ * Needs no GPU. */
+int spq_boundary_layout_host(int k, const long long* adj_ptr, const int* adj, const long long* slot_off,
+                             const long long* snb_ptr, const int* snb, int rule, int depth, int* bgpos_out,
+                             long long* npad_out, int* tasks_out, int cap_tasks);
+
 /* The grouped query's autotuner: its choices so far, per (device, size class), as
  * keys[i] = device * 256 + class and choices[i] = configuration (0: 4 pairs per warp,
  * two CTAs per SM; 1: 2 pairs per warp, three CTAs per SM; -1: measured, not read yet).  The class is

@@ -79,6 +79,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_ulonglong)]),
     "spq_component_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, ctypes.c_int, P, P]),
     "spq_boundary_order_host": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.c_int, P]),
+    "spq_boundary_layout_host": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, P,
+                                                ctypes.c_int]),
     "spq_get_meta": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "spq_get_apsp": (ctypes.c_int, [P, i32, P, P]),
     "spq_get_bg": (ctypes.c_int, [P, P, P]),

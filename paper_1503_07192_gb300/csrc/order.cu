@@ -837,6 +837,46 @@ extern "C" int spq_boundary_order_host(int k, const long long* adj_ptr, const in
     return 0;
 }
 
+extern "C" int spq_boundary_layout_host(int k, const long long* adj_ptr, const int* adj, const long long* slot_off,
+                                        const long long* snb_ptr, const int* snb, int rule, int depth, int* bgpos_out,
+                                        long long* npad_out, int* tasks_out, int cap_tasks) {
+    using namespace spq;
+    if (k <= 0 || !adj_ptr || !slot_off || !snb_ptr || !bgpos_out || !npad_out || rule < 1 || rule > 2 || depth < 0 ||
+        depth > kMaxRunDepth)
+        return -1;
+    std::vector<int64_t> ptr(adj_ptr, adj_ptr + k + 1);
+    std::vector<int32_t> ad(adj, adj + ptr[k]);
+    std::vector<int64_t> so(slot_off, slot_off + k + 1);
+    const int64_t ns = so[k];
+    std::vector<int64_t> sp(snb_ptr, snb_ptr + ns + 1);
+    std::vector<int32_t> sn(snb, snb + sp[ns]);
+    std::vector<int32_t> out;
+    std::vector<NdNode> nodes;
+    vertex_nd(rule, k, ptr, ad, so, sp, sn, &out, depth, 16 * kTile, &nodes);
+    if ((int64_t)out.size() != ns) return -2;
+    std::vector<int32_t> bgpos(ns);
+    BgLayout layout;
+    if (nodes.size() > 1) {
+        aligned_layout(out, nodes, &bgpos, &layout);
+    } else {  // (no split: the slots packed, one run over every block row)
+        for (int64_t i = 0; i < ns; ++i) bgpos[out[i]] = (int32_t)i;
+        layout.npad = ns;
+    }
+    for (int64_t i = 0; i < ns; ++i) bgpos_out[i] = bgpos[i];
+    *npad_out = layout.npad;
+    const int nt = (int)layout.tasks.size();
+    for (int t = 0; t < nt && t < cap_tasks && tasks_out; ++t) {
+        const ElimTask& tk = layout.tasks[t];
+        int* o = tasks_out + 5 * t;
+        o[0] = tk.lo;
+        o[1] = tk.hi;
+        o[2] = tk.shared_from;
+        o[3] = tk.deps.size() > 0 ? tk.deps[0] : -1;
+        o[4] = tk.deps.size() > 1 ? tk.deps[1] : -1;
+    }
+    return nt;
+}
+
 namespace spq {
 
 cudaError_t copy_table_out(bool to_i32, const void* src, int64_t rows, int64_t cols, int64_t ld, const int32_t* pos,

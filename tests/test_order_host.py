@@ -189,3 +189,45 @@ def test_vertex_order_is_a_permutation_and_cheaper(lib, rule):
     c_comp = vertex_cost(w, slots, slot_off, comp_order)
     c_vert = vertex_cost(w, slots, slot_off, out.tolist())
     assert c_vert < c_comp < c_id, (c_vert, c_comp, c_id)
+
+
+@pytest.mark.parametrize("depth", [0, 3, 4, 5])
+def test_layout_runs_cover_every_block_row_once(lib, depth):
+    """The elimination form's layout (the runs of rounds a build issues side by side):
+    every slot gets its own matrix row; the runs' block-row ranges partition the matrix
+    (every round done once); a run waits for the two runs of its halves, listed before it;
+    the padding stays within one partial tile per aligned start (the build's memory bound);
+    and there are at most 2^(depth + 1) - 1 runs."""
+    w = gen.configs.delaunay_rcb(1 << 17, 7, 10, seed=5)
+    slots, slot_off, ptr, flat, snb_ptr, snb, _ = bg_structure(w)
+    ns = len(slots)
+    assert ns >= 2 * 16 * 128 * 4  # room for at least two levels of pieces of 16 tiles
+    bgpos = np.empty(ns, np.int32)
+    npad = ctypes.c_longlong()
+    cap = 2 ** 6
+    tasks = np.full((cap, 5), -7, np.int32)
+    nt = lib.spq_boundary_layout_host(w.k, ptr.ctypes.data, flat.ctypes.data, slot_off.ctypes.data,
+                                      snb_ptr.ctypes.data, snb.ctypes.data, 1, depth, bgpos.ctypes.data,
+                                      ctypes.byref(npad), tasks.ctypes.data, cap)
+    assert nt >= 0
+    npad = npad.value
+    assert len(set(bgpos.tolist())) == ns and bgpos.min() >= 0 and bgpos.max() < npad
+    if depth == 0:
+        assert nt == 0 and npad == ns
+        return
+    assert 1 < nt <= 2 ** (depth + 1) - 1
+    assert npad - ns <= (nt - 1) * 127
+    R = (npad + 127) // 128
+    cover = np.zeros(R, np.int32)
+    for t in range(nt):
+        lo, hi, shared_from, d0, d1 = tasks[t].tolist()
+        assert 0 <= lo <= hi <= R and shared_from == hi
+        cover[lo:hi] += 1
+        assert (d0 == -1) == (d1 == -1), t
+        if d0 >= 0:
+            assert d0 < t and d1 < t and d0 != d1
+            # the halves' rows come before the separator's
+            assert tasks[d0][1] <= lo and tasks[d1][1] <= lo
+    assert (cover == 1).all(), np.nonzero(cover != 1)[0][:10]
+    leaves = sum(1 for t in range(nt) if tasks[t][3] < 0)
+    assert leaves <= 2 ** depth and nt == 2 * leaves - 1
