@@ -188,10 +188,13 @@ spq_status spq_build(int32_t n, const int64_t* row_ptr, const int32_t* col, cons
  * marks the handle: with host buffers the call then returns SPQ_EINVAL; with device
  * buffers, spq_query_status reports it.
  *
- * Kernel choice: the first grouped launch of a size class (see spq_query_tuning) in the
- * process runs both kernel configurations on its inputs, timed with CUDA events (the
- * answers are the same), so that call costs about twice the device time; the host does
- * not wait for the timing, which a later launch of the class reads once it is complete.
+ * Kernel choice: with the default query_kernel (0), batches of at least 4,096 pairs are
+ * answered by the staged kernel (blocks of up to 512 boundary vertices; wider ones by the
+ * gathering kernel).  For the gathering kernel (query_kernel = 1, and those wider
+ * blocks), the first launch of a size class (see spq_query_tuning) in the process runs
+ * both of its configurations on its inputs, timed with CUDA events (the answers are the
+ * same), so that call costs about twice that kernel's device time; the host does not wait
+ * for the timing, which a later launch of the class reads once it is complete.
  */
 spq_status spq_query(spq_handle* h, const int32_t* pairs, int64_t q, void* dist_out, void* stream);
 
